@@ -1,0 +1,324 @@
+"""Benchmark: vertex right-hand-side evaluations per second of the one-loop SIAM
+fRG flow at N_f = 128 on one GB300 (and N independent replicas for --gpus N).
+
+One benchmark step = one Dormand-Prince step attempt of the real flow through
+the C ABI (six rhs evaluations -- bubble weights, channel contractions,
+self-energy -- plus the FP64 stage sums, the error norm and the step
+controller), i.e. every row of the hot path.  value = rhs evaluations actually
+performed in the timed steps / device time (CUDA events, max over ranks),
+summed over ranks.
+
+Arms:
+  default            the CUDA library (precision --precision)
+  --impl reference   the FP64 CPU oracle as it stands, timed on the host cores on
+                     a bounded sample of the same workload (rows of the vertex)
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertex-rhs evals/s at N_f=128: split-TF32 vs FP64 on one GB300 @≤1e-6 rel"
+UNIT = "rhs evals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (CUDA cores)
+DTYPES = {"fp64": "f64", "3xtf32": "tf32x3", "bf16x3": "bf16x3"}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        p["_source"] = "measured"
+        return p
+    except Exception:
+        p = dict(FALLBACK_PEAKS)
+        p["_source"] = "fallback"
+        return p
+
+
+def contraction_macs(N):
+    """Useful complex multiply-adds of the three channel contractions per rhs:
+    4 N sum_m D_m^2 with D_m = N - |m| (pp: D x D x N, dph: D x 2D x N,
+    xph: D x D x N per transfer)."""
+    return 4 * N * sum((N - abs(m)) ** 2 for m in range(-(N - 1), N))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(N_rows, seconds=12.0):
+    """The FP64 oracle as it stands on the host cores, on whole rows i1 of the
+    N=128 vertex (a bounded sample), scaled to rhs evaluations per second."""
+    import numpy as np
+    import oracle
+    from paper_1510_07799_gb300 import inputs
+    w = inputs.SIAM_N128
+    m = oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+    V = inputs.random_vertex(w.N, w.U, seed=11)
+    sig = inputs.random_sigma(w.N, seed=12, amp=0.05)
+    rows, t0 = 0, time.perf_counter()
+    i = 0
+    while True:
+        a = (i * N_rows) % w.N
+        oracle.rhs_rows(m, 0.02, V, sig, a, a + N_rows)
+        rows += N_rows
+        i += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": (rows / w.N) / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d, repeated for %.1f s; "
+                      "scaled by rows/N" % (rows, w.N, w.N, el)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401
+    from oracle import build as oracle_build
+    oracle_build.build()
+    import numpy as np
+    import oracle as orc
+    from paper_1510_07799_gb300 import inputs
+    w = inputs.SIAM_N128
+    m = orc.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+    V = inputs.random_vertex(w.N, w.U, seed=11)
+    sig = inputs.random_sigma(w.N, seed=12, amp=0.05)
+    rows = 4  # one step = 4 of the 128 vertex rows of one rhs evaluation
+    for i in range(args.warmup):
+        orc.rhs_rows(m, 0.02, V, sig, 0, rows)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        a = (i * rows) % w.N
+        orc.rhs_rows(m, 0.02, V, sig, a, a + rows)
+    el = time.perf_counter() - t0
+    value = args.steps * rows / w.N / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "N_f": w.N, "step": "oracle rhs on %d of %d vertex rows" % (rows, w.N)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
+                             "sample": "%d rows of %d per step, %d steps" % (rows, w.N, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_init()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1510_07799_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1510_07799_gb300 import frg, inputs
+    w = inputs.SIAM_N128
+    N = w.N
+    prec = args.precision
+    try:
+        ctx = frg.Context([w], precision=prec)
+    except frg.FrgError as e:
+        if args.precision_explicit or e.code != frg.EINVAL:
+            raise
+        prec = "fp64"
+        ctx = frg.Context([w], precision=prec)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- flow steps (the headline value)
+    ctx.advance(args.warmup)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()[0]
+    if st0.done:
+        raise RuntimeError("flow finished during warm-up; lower --warmup")
+    barrier()
+    torch.cuda.synchronize()
+    l0 = frg.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        ctx.advance(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = frg.kernel_launches() - l0
+    st1 = ctx.stats()[0]
+    ms = e0.elapsed_time(e1)
+    evals = st1.rhs_evals - st0.rhs_evals
+    attempts = (st1.accepted + st1.rejected) - (st0.accepted + st0.rejected)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    ev = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(ev.item()) / (ms_max / 1e3)
+
+    # ---- per-phase timing of single rhs evaluations on the same stream
+    g, s, lam, _ = ctx.get_state(0)
+    dg = torch.empty_like(g)
+    ds = torch.empty_like(s)
+    for _ in range(2):
+        ctx.rhs_timed(0, lam, g, s, dg, ds)
+    phases = np.array([ctx.rhs_timed(0, lam, g, s, dg, ds) for _ in range(args.rhs_reps)])
+    ph = phases.mean(axis=0)
+    pk = peaks()
+    macs = contraction_macs(N)
+    if prec == "fp64":
+        flops = 8.0 * macs
+        achieved = flops / (ph[2] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_contract_fp64 (pp, dph, xph launches of one rhs)",
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                "algorithmic": "8 flops x %d useful complex MACs per rhs" % macs}
+    else:
+        flops = 8.0 * macs
+        tf_peak = pk["bf16_tflops"] * 0.5  # TF32 dense = half the bf16 rate
+        achieved = flops / (ph[2] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf_peak, "traffic": None,
+                "kernel": "tcgen05 channel contractions of one rhs",
+                "peak_source": "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)" % pk["_source"],
+                "algorithmic": "8 flops x %d useful complex MACs per rhs (useful, not executed)" % macs}
+    roof["phases_ms"] = {"bubble": ph[0], "gather": ph[1], "contraction": ph[2], "sigma": ph[3]}
+
+    # ---- end to end through the host-buffer entry point
+    hg = g.cpu().numpy()
+    hs = s.cpu().numpy()
+    og = np.empty_like(hg)
+    os_ = np.empty_like(hs)
+    ctx.rhs_host(0, lam, hg, hs, og, os_)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_reps):
+        ctx.rhs_host(0, lam, hg, hs, og, os_)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_reps
+    nb = (hg.nbytes + hs.nbytes)
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+           "what": "frg_rhs_host with pageable host buffers, copies inside the timed region"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
+            "config": {"workload": w.name, "N_f": N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
+                       "precision": prec, "rhs_evals_timed": evals, "step_attempts_timed": attempts,
+                       "step": "one Dormand-Prince step attempt of the flow (6 rhs + FP64 stage sums + "
+                               "error norm + controller)",
+                       "l2": "working set > L2 (state, 7 stage derivatives, stage input: %.0f MB)"
+                             % ((2 * 16 + 7 * (8 if prec != 'fp64' else 16) + 16) * N ** 3 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(8, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, choices=list(DTYPES))
+    ap.add_argument("--rhs-reps", type=int, default=5)
+    ap.add_argument("--e2e-reps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.precision_explicit = args.precision is not None
+    if args.precision is None:
+        args.precision = "3xtf32"
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * frg.h -- C ABI of the GB300 (sm_103a) one-loop fRG library.
+ *
+ * The problem (the paper, Sec. 2, Eq. 1): an ODE dV/dg = F[V; g] for one flat
+ * array V of discretised correlation functions, integrated with an explicit
+ * stepper so that every component of F can be computed independently at fixed
+ * V; the right-hand side is a numerical treatment of three one-loop diagrams
+ * (Sec. 4); the flow of the self-energy is the extension named in Sec. 2.
+ *
+ * The instance implemented here is the single-impurity Anderson model in
+ * Matsubara frequencies with the Omega-scheme cutoff:
+ *   G0^{-1}(iw) = iw - (eps_d + U/2) + i Delta sgn(w)     (Hartree U/2 absorbed)
+ *   G_L = 1/(Theta^{-1} G0^{-1} - Sigma),   Theta_L(w) = w^2/(w^2 + L^2)
+ *   S_L = -G^2 (2L/w^2) G0^{-1},            Lb(a,b) = S(a)G(b) + G(a)S(b)
+ * State per parameter point: the up-down vertex V(k1,k2,k3) on an N x N x N box
+ * of fermionic Matsubara indices and the self-energy Sigma on N frequencies.
+ * Flow variable l = ln L, from L0 down to L_f:
+ *   dV/dl = L (Tpp + Tdph + Txph)                 (three one-loop channels)
+ *   Tpp  = -T sum_p V(k1,k2,p) Lb(p,s-p) V(p,s-p,k3),                s = k1+k2
+ *   Tdph = +T sum_p Lb(p,p-t) [2V(k1,p,k3)V(p-t,k2,p) - V(k1,p,p-t)V(p-t,k2,p)
+ *                              - V(k1,p,k3)V(p-t,k2,k4)],           t = k3-k1
+ *   Txph = -T sum_p V(k1,p+Q,p) Lb(p,p+Q) V(p,k2,k3),                Q = k2-k3
+ *   dSigma(w)/dl = L T sum_p S(p) [2V(w,p,w) - V(w,p,p)]
+ * V takes the stored value when all four frequencies lie in the box and the
+ * bare U otherwise; loop sums run over internal frequencies inside the box.
+ *
+ * Memory conventions (all calls):
+ *  - Vertex buffers: N^3 complex128, interleaved (re, im), index
+ *    ((i1*N)+i2)*N+i3 with i = n + N/2 for Matsubara index n in [-N/2, N/2).
+ *    Self-energy buffers: N complex128.
+ *  - "d_" pointers are device pointers on the context's device, "h_" pointers
+ *    host pointers (pageable or pinned).  Buffers passed in stay owned by the
+ *    caller; the context owns its state and workspace.
+ *  - Work is issued on the stream given at frg_init (0 = legacy default
+ *    stream); calls that return results to host memory synchronise it.
+ *  - Every call returns FRG_OK (0) or a negative FRG_E* code; no exception or
+ *    abort crosses the ABI.  frg_last_error() describes the last failure.
+ *  - One context per host thread at a time.
+ */
+#ifndef FRG_H
+#define FRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FRG_OK 0
+#define FRG_EINVAL (-1)      /* bad argument or parameter */
+#define FRG_ENOMEM (-2)      /* device or host allocation failed */
+#define FRG_ECUDA (-3)       /* a CUDA call failed */
+#define FRG_ENONFINITE (-4)  /* NaN/Inf in the state or the error norm */
+#define FRG_ENOTCONV (-5)    /* step size underflow or step limit reached */
+#define FRG_ETIMEOUT (-6)    /* a bounded device-side wait ran out */
+
+/* Arithmetic of the channel contractions. */
+#define FRG_FP64 0    /* everything in FP64 (CUDA cores) */
+#define FRG_3XTF32 1  /* split-TF32 (hi*hi + hi*lo + lo*hi) on tcgen05, FP32 accumulate */
+#define FRG_BF16X3 2  /* three BF16 slices, six products, on tcgen05, FP32 accumulate */
+
+/* channel_mask bits */
+#define FRG_CH_PP 0x1
+#define FRG_CH_DPH 0x2
+#define FRG_CH_XPH 0x4
+#define FRG_CH_SIGMA 0x8
+#define FRG_CH_ALL 0xF
+
+typedef struct {
+    double U;         /* interaction */
+    double T;         /* temperature (> 0) */
+    double eps_d;     /* level energy; particle-hole symmetry at eps_d = -U/2 */
+    double Delta;     /* wide-band hybridisation (> 0) */
+    int N_f;          /* fermionic frequencies per axis: even, 2 <= N_f <= 256 */
+    double Lambda0;   /* initial scale (> Lambda_f > 0) */
+    double Lambda_f;  /* final scale */
+    double rtol;      /* relative tolerance of the step controller (> 0) */
+    double atol;      /* absolute tolerance (>= 0) */
+    double h0;        /* first step in l = ln Lambda (< 0); 0 selects -0.01 */
+    long max_steps;   /* step attempts before FRG_ENOTCONV; 0 selects 100000 */
+    int precision;    /* FRG_FP64, FRG_3XTF32 or FRG_BF16X3 */
+    int channel_mask; /* FRG_CH_* bits; 0 selects FRG_CH_ALL */
+} frg_params;
+
+typedef struct frg_ctx frg_ctx;
+
+typedef struct {
+    double Lambda;   /* scale reached */
+    double h;        /* next step proposal in l */
+    long accepted;   /* accepted steps */
+    long rejected;   /* rejected steps */
+    long rhs_evals;  /* right-hand-side evaluations */
+    int status;      /* FRG_OK while running or done, else FRG_E* */
+    int done;        /* 1 once Lambda_f is reached or the point failed */
+} frg_flow_stats;
+
+typedef struct {
+    double sigma_lowest_re, sigma_lowest_im; /* Sigma(i pi T) */
+    double Z;                                /* 1 / (1 - Im Sigma(i pi T) / (pi T)) */
+    double U_eff_re, U_eff_im;               /* V at n1 = n2 = n3 = 0 */
+    double n;                                /* 1/2 + T sum_box Re G (informational) */
+} frg_obs;
+
+/*
+ * Create a context for n_points parameter points (params[0..n_points-1]); all
+ * points must share precision and channel_mask.  Allocates the device state
+ * (initialised to V = U, Sigma = 0 at Lambda0) and all workspace, on the
+ * current device.  cuda_stream is a cudaStream_t (may be NULL).
+ * Errors: FRG_EINVAL (N_f odd or out of range, T <= 0, Delta <= 0, rtol <= 0,
+ * Lambda_f >= Lambda0, mixed precision/mask, n_points < 1), FRG_ENOMEM,
+ * FRG_ECUDA.  On error *out is NULL.
+ */
+int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx **out);
+
+/* Release everything the context owns.  NULL is ignored. */
+void frg_destroy(frg_ctx *ctx);
+
+/* Text of the last error on this context (never NULL). */
+const char *frg_last_error(const frg_ctx *ctx);
+
+/*
+ * One evaluation of the right-hand side, d/dl of (V, Sigma), for point
+ * `point` at scale Lambda (> 0), in the context's precision and channel mask:
+ * reads d_gamma (N^3 complex128) and d_sigma (N complex128), writes d_dgamma
+ * and d_dsigma (same shapes).  Device pointers, caller-owned; asynchronous on
+ * the context stream.  d_sigma may be NULL (Sigma = 0).  Uses the context
+ * workspace, so calls on one context must not overlap.
+ */
+int frg_rhs(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
+            const void *d_sigma, void *d_dgamma, void *d_dsigma);
+
+/*
+ * Same as frg_rhs with host buffers: copies the inputs to the device, evaluates,
+ * copies the results back and synchronises the stream before returning.
+ */
+int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma,
+                 const double *h_sigma, double *h_dgamma, double *h_dsigma);
+
+/*
+ * Integrate every point from its current state to its Lambda_f with the
+ * Dormand-Prince 5(4) stepper (device-resident FP64 stage sums, error norm and
+ * step control).  stats (host, n_points entries, may be NULL) receives the
+ * per-point statistics.  Returns FRG_OK if every point reached Lambda_f, else
+ * the first failing point's code (FRG_ENONFINITE, FRG_ENOTCONV).
+ */
+int frg_flow(frg_ctx *ctx, frg_flow_stats *stats);
+
+/*
+ * Advance every unfinished point by at most max_attempts step attempts
+ * (accepted or rejected); finished points are left alone.  Same error rules
+ * as frg_flow.  Used for checkpointing and for timing a fixed amount of work.
+ */
+int frg_advance(frg_ctx *ctx, long max_attempts, frg_flow_stats *stats);
+
+/* Observables of point `point` at its current scale (synchronises). */
+int frg_observables(frg_ctx *ctx, int point, frg_obs *out);
+
+/*
+ * Copy the current state of point `point` out to caller device buffers
+ * (d_gamma N^3, d_sigma N complex128), and its scale and next step (host).
+ * Any of the output pointers may be NULL.  Synchronises.
+ */
+int frg_get_state(frg_ctx *ctx, int point, void *d_gamma, void *d_sigma,
+                  double *Lambda, double *h);
+
+/*
+ * Replace the state of point `point` (resume from a checkpoint or start from a
+ * custom state): device buffers d_gamma / d_sigma (NULL sigma = 0), scale
+ * Lambda (Lambda_f < Lambda <= Lambda0 is not required, but Lambda > Lambda_f
+ * for the point to flow) and next step h in l (< 0; 0 selects the h0 of
+ * frg_init).  Clears the point's statistics and done flag.
+ */
+int frg_set_state(frg_ctx *ctx, int point, const void *d_gamma, const void *d_sigma,
+                  double Lambda, double h);
+
+/* Per-point statistics without advancing (synchronises). */
+int frg_stats(frg_ctx *ctx, frg_flow_stats *stats);
+
+/*
+ * Diagnostics.  frg_rhs_timed evaluates exactly like frg_rhs and records CUDA
+ * events on the context stream around its phases; ms[0..3] (host) receive the
+ * durations of the bubble-weight, operand-gather, contraction and self-energy
+ * phases (0 for a phase the path does not have).  Synchronises.
+ * frg_kernel_launches returns the number of kernels this library has launched
+ * in the process so far.
+ */
+int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
+                  const void *d_sigma, void *d_dgamma, void *d_dsigma, float *ms);
+long frg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRG_H */

@@ -1,0 +1,601 @@
+// frg_api.cu -- the C ABI (include/frg.h): context, workspace, rhs pipeline,
+// and the host loop that issues device-resident Dormand-Prince steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/frg.h"
+#include "frg_common.cuh"
+#include "frg_integrator.cuh"
+#include "frg_misc.cuh"
+#include "frg_tc.cuh"
+
+using namespace frg;
+
+struct frg_ctx {
+  int dev = 0;
+  int n = 0;
+  int precision = FRG_FP64;
+  int mask = FRG_CH_ALL;
+  int split = 0;
+  int maxN = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<frg_params> params;
+  std::vector<PointDesc> hpts;
+  PointDesc *d_pts = nullptr;
+  Ctl *d_ctl = nullptr;
+  Ctl *h_ctl = nullptr;        // pinned mirror
+  RhsIO *d_io_stage = nullptr; // flow evaluations
+  RhsIO *d_io_user = nullptr;  // stand-alone evaluations
+  // contraction work lists: [ch] all points cost-sorted; per-point slices
+  WorkItem *d_work_all[3] = {nullptr, nullptr, nullptr};
+  int nwork_all[3] = {0, 0, 0};
+  WorkItem *d_work_pt[3] = {nullptr, nullptr, nullptr};
+  std::vector<int> work_off[3];  // per point offsets into d_work_pt
+  int *d_seg_point = nullptr, *d_seg_base = nullptr;
+  int nseg = 0;
+  std::vector<void *> allocs;
+  // host-buffer entry point staging (per point, lazily)
+  std::vector<double2 *> user_in, user_out;
+  TcPlan *tc = nullptr;  // split-precision contraction plan
+  struct UserScratch {
+    float4 *ys = nullptr;
+    double2 *s64 = nullptr;
+    float2 *kout = nullptr;
+  };
+  std::vector<UserScratch> user_split;
+  bool need_k1 = true;
+  std::string err;
+};
+
+namespace {
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int fail(frg_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(frg_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, FRG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+#define LK(call, what)                                                        \
+  do {                                                                        \
+    if ((call) != 0) {                                                        \
+      cudaError_t e_ = cudaGetLastError();                                    \
+      return cuda_fail(ctx, e_ == cudaSuccess ? cudaErrorUnknown : e_, what); \
+    }                                                                         \
+  } while (0)
+
+template <class T>
+T *dalloc(frg_ctx *ctx, size_t count) {
+  void *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+  ctx->allocs.push_back(p);
+  return static_cast<T *>(p);
+}
+
+int validate(const frg_params &p, std::string &why) {
+  char b[256];
+  if (p.N_f < 2 || p.N_f > FRG_MAX_N || (p.N_f & 1)) {
+    snprintf(b, sizeof b, "N_f=%d must be even and in [2, %d]", p.N_f, FRG_MAX_N);
+    why = b;
+    return FRG_EINVAL;
+  }
+  if (!(p.T > 0.0) || !std::isfinite(p.T)) { why = "T must be > 0"; return FRG_EINVAL; }
+  if (!(p.Delta > 0.0) || !std::isfinite(p.Delta)) { why = "Delta must be > 0"; return FRG_EINVAL; }
+  if (!(p.rtol > 0.0)) { why = "rtol must be > 0"; return FRG_EINVAL; }
+  if (!(p.atol >= 0.0)) { why = "atol must be >= 0"; return FRG_EINVAL; }
+  if (!(p.Lambda_f > 0.0) || !(p.Lambda0 > p.Lambda_f) || !std::isfinite(p.Lambda0)) {
+    why = "need Lambda0 > Lambda_f > 0";
+    return FRG_EINVAL;
+  }
+  if (!std::isfinite(p.U) || !std::isfinite(p.eps_d)) { why = "U and eps_d must be finite"; return FRG_EINVAL; }
+  if (p.h0 > 0.0) { why = "h0 must be <= 0 (the flow runs towards small Lambda)"; return FRG_EINVAL; }
+  if (p.precision < FRG_FP64 || p.precision > FRG_BF16X3) { why = "unknown precision"; return FRG_EINVAL; }
+  if (p.channel_mask < 0 || p.channel_mask > 0xF) { why = "channel_mask must be within 0xF"; return FRG_EINVAL; }
+  return FRG_OK;
+}
+
+constexpr int TILE = 32;  // row / column tile of the FP64 contraction
+
+void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &out) {
+  for (int m = 0; m < 2 * N - 1; ++m) {
+    Geom g = geom(ch, N, m);
+    for (int rt = 0; rt * TILE < g.D; ++rt)
+      for (int ct = 0; ct * TILE < N; ++ct) out.push_back({g.K, WorkItem{pi, m, rt, ct}});
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ rhs pipeline ----
+// ev (optional, 5 events): before bubble, after bubble, after the operand
+// gather, after the contraction, after the self-energy.
+static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr) {
+  cudaStream_t st = ctx->stream;
+  if (ev) CK(cudaEventRecord(ev[0], st), "event");
+  LK(launch_bubble(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, st), "bubble weights");
+  if (ev) CK(cudaEventRecord(ev[1], st), "event");
+  const int chmask = ctx->mask & 7;
+  if (!ctx->split) {
+    const WorkItem *w[3];
+    int nw[3];
+    for (int ch = 0; ch < 3; ++ch) {
+      if (point < 0) {
+        w[ch] = ctx->d_work_all[ch];
+        nw[ch] = ctx->nwork_all[ch];
+      } else {
+        w[ch] = ctx->d_work_pt[ch] + ctx->work_off[ch][point];
+        nw[ch] = ctx->work_off[ch][point + 1] - ctx->work_off[ch][point];
+      }
+    }
+    if (ev) CK(cudaEventRecord(ev[2], st), "event");
+    if (chmask) {
+      LK(launch_contract_fp64(ctx->d_pts, d_io, w, nw, chmask, st), "fp64 contraction");
+    } else {
+      LK(launch_zero_vertex(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "zero vertex");
+    }
+  } else {
+    LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr), "split contraction");
+  }
+  if (ev) CK(cudaEventRecord(ev[3], st), "event");
+  LK(launch_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st), "self-energy");
+  if (ev) CK(cudaEventRecord(ev[4], st), "event");
+  return FRG_OK;
+}
+
+static int sync_ctl(frg_ctx *ctx) {
+  CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(Ctl) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream),
+     "read controller state");
+  CK(cudaStreamSynchronize(ctx->stream), "flow");
+  return FRG_OK;
+}
+
+static void fill_stats(frg_ctx *ctx, frg_flow_stats *stats) {
+  if (!stats) return;
+  for (int i = 0; i < ctx->n; ++i) {
+    const Ctl &c = ctx->h_ctl[i];
+    stats[i].Lambda = std::exp(c.t);
+    stats[i].h = c.h;
+    stats[i].accepted = c.accepted;
+    stats[i].rejected = c.rejected;
+    stats[i].rhs_evals = c.rhs_evals;
+    stats[i].status = c.status;
+    stats[i].done = c.done;
+  }
+}
+
+static int flow_status(frg_ctx *ctx) {
+  for (int i = 0; i < ctx->n; ++i) {
+    const int s = ctx->h_ctl[i].status;
+    if (s != 0) {
+      char b[160];
+      snprintf(b, sizeof b, "point %d: %s at Lambda=%.6g after %ld steps", i,
+               s == FRG_ENONFINITE ? "non-finite state or error norm" : "step size underflow or step limit",
+               std::exp(ctx->h_ctl[i].t), ctx->h_ctl[i].steps);
+      return fail(ctx, s, b);
+    }
+  }
+  return FRG_OK;
+}
+
+static SegTable seg(frg_ctx *ctx) { return SegTable{ctx->d_seg_point, ctx->d_seg_base}; }
+
+static int issue_k1(frg_ctx *ctx) {
+  cudaStream_t st = ctx->stream;
+  if (ctx->split) LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, st), "stage 0");
+  LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
+  int rc = run_rhs(ctx, ctx->d_io_stage, -1);
+  if (rc) return rc;
+  LK(launch_finish_k1(ctx->d_ctl, ctx->d_io_stage, ctx->n, st), "finish k1");
+  return FRG_OK;
+}
+
+static int issue_step(frg_ctx *ctx) {
+  cudaStream_t st = ctx->stream;
+  LK(launch_prepare(ctx->d_pts, ctx->d_ctl, ctx->n, st), "prepare");
+  for (int s = 1; s < 7; ++s) {
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, st), "stage sum");
+    LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, s, ctx->split, ctx->n, st), "stage io");
+    int rc = run_rhs(ctx, ctx->d_io_stage, -1);
+    if (rc) return rc;
+  }
+  LK(launch_error(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, ctx->split, st), "error norm");
+  LK(launch_controller(ctx->d_pts, ctx->d_ctl, ctx->n, st), "controller");
+  return FRG_OK;
+}
+
+// ------------------------------------------------------------------ ABI ----
+extern "C" {
+
+int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx **out) {
+  if (!out) return FRG_EINVAL;
+  *out = nullptr;
+  if (!params || n_points < 1) return FRG_EINVAL;
+  frg_ctx *ctx = new (std::nothrow) frg_ctx();
+  if (!ctx) return FRG_ENOMEM;
+  auto bail = [&](int code) {
+    frg_destroy(ctx);
+    return code;
+  };
+  std::string why;
+  for (int i = 0; i < n_points; ++i) {
+    frg_params p = params[i];
+    if (p.channel_mask == 0) p.channel_mask = FRG_CH_ALL;
+    if (p.h0 == 0.0) p.h0 = -0.01;
+    if (p.max_steps <= 0) p.max_steps = 100000;
+    if (validate(p, why) != FRG_OK) return bail(FRG_EINVAL);
+    if (i > 0 && (p.precision != ctx->params[0].precision || p.channel_mask != ctx->params[0].channel_mask))
+      return bail(FRG_EINVAL);
+    ctx->params.push_back(p);
+  }
+  if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(FRG_ECUDA);
+  ctx->n = n_points;
+  ctx->precision = ctx->params[0].precision;
+  ctx->mask = ctx->params[0].channel_mask;
+  ctx->split = ctx->precision != FRG_FP64;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  for (auto &p : ctx->params) ctx->maxN = std::max(ctx->maxN, p.N_f);
+  if (upload_tableau() != 0) return bail(FRG_ECUDA);
+
+  // ---- per-point buffers
+  ctx->hpts.resize(n_points);
+  for (int i = 0; i < n_points; ++i) {
+    const frg_params &p = ctx->params[i];
+    PointDesc &P = ctx->hpts[i];
+    memset(&P, 0, sizeof P);
+    const int N = p.N_f;
+    const size_t n3 = (size_t)N * N * N, nc = n3 + N;
+    P.N = N;
+    P.n3 = (int)n3;
+    P.U = p.U;
+    P.T = p.T;
+    P.et = p.eps_d + 0.5 * p.U;
+    P.Delta = p.Delta;
+    P.l0 = std::log(p.Lambda0);
+    P.l_end = std::log(p.Lambda_f);
+    P.rtol = p.rtol;
+    P.atol = p.atol;
+    P.h0 = p.h0;
+    P.max_steps = p.max_steps;
+    for (int b = 0; b < 2; ++b)
+      if (!(P.ybuf[b] = dalloc<double2>(ctx, nc))) return bail(FRG_ENOMEM);
+    if (!ctx->split) {
+      if (!(P.Y64 = dalloc<double2>(ctx, nc))) return bail(FRG_ENOMEM);
+      for (int j = 0; j < 7; ++j)
+        if (!(P.kG[j] = dalloc<double2>(ctx, n3))) return bail(FRG_ENOMEM);
+    } else {
+      if (!(P.Y64 = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
+      if (!(P.Ysplit = dalloc<float4>(ctx, n3))) return bail(FRG_ENOMEM);
+      for (int j = 0; j < 7; ++j)
+        if (!(P.kG[j] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
+    }
+    for (int j = 0; j < 7; ++j)
+      if (!(P.kS[j] = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
+    if (!(P.G = dalloc<double2>(ctx, N)) || !(P.S = dalloc<double2>(ctx, N)) ||
+        !(P.Lpp = dalloc<double2>(ctx, (size_t)(2 * N - 1) * N)) ||
+        !(P.Lph = dalloc<double2>(ctx, (size_t)(2 * N - 1) * N)))
+      return bail(FRG_ENOMEM);
+  }
+  if (!(ctx->d_pts = dalloc<PointDesc>(ctx, n_points)) || !(ctx->d_ctl = dalloc<Ctl>(ctx, n_points)) ||
+      !(ctx->d_io_stage = dalloc<RhsIO>(ctx, n_points)) || !(ctx->d_io_user = dalloc<RhsIO>(ctx, n_points)))
+    return bail(FRG_ENOMEM);
+  if (cudaMallocHost(&ctx->h_ctl, sizeof(Ctl) * n_points) != cudaSuccess) return bail(FRG_ENOMEM);
+  if (cudaMemcpy(ctx->d_pts, ctx->hpts.data(), sizeof(PointDesc) * n_points, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(FRG_ECUDA);
+  if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
+      cudaMemset(ctx->d_io_stage, 0, sizeof(RhsIO) * n_points) != cudaSuccess)
+    return bail(FRG_ECUDA);
+
+  // ---- contraction work lists (FP64 path): per point, and all points sorted
+  // heavy-first so that long transfers start early and short ones fill in.
+  if (!ctx->split) {
+    for (int ch = 0; ch < 3; ++ch) {
+      std::vector<std::pair<int, WorkItem>> all, one;
+      std::vector<WorkItem> per;
+      ctx->work_off[ch].push_back(0);
+      for (int i = 0; i < n_points; ++i) {
+        one.clear();
+        build_work(ch, i, ctx->params[i].N_f, one);
+        std::stable_sort(one.begin(), one.end(), [](auto &a, auto &b) { return a.first > b.first; });
+        for (auto &x : one) per.push_back(x.second);
+        all.insert(all.end(), one.begin(), one.end());
+        ctx->work_off[ch].push_back((int)per.size());
+      }
+      std::stable_sort(all.begin(), all.end(), [](auto &a, auto &b) { return a.first > b.first; });
+      std::vector<WorkItem> allw;
+      for (auto &x : all) allw.push_back(x.second);
+      ctx->nwork_all[ch] = (int)allw.size();
+      if (!(ctx->d_work_all[ch] = dalloc<WorkItem>(ctx, allw.size())) ||
+          !(ctx->d_work_pt[ch] = dalloc<WorkItem>(ctx, per.size())))
+        return bail(FRG_ENOMEM);
+      cudaMemcpy(ctx->d_work_all[ch], allw.data(), sizeof(WorkItem) * allw.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(ctx->d_work_pt[ch], per.data(), sizeof(WorkItem) * per.size(), cudaMemcpyHostToDevice);
+    }
+  } else {
+    int rc = tc_plan_create(&ctx->tc, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, why);
+    if (rc) {
+      ctx->err = why;
+      return bail(rc);
+    }
+  }
+
+  // ---- segment table for the elementwise kernels
+  {
+    std::vector<int> sp, sb;
+    for (int i = 0; i < n_points; ++i) {
+      const int nc = ctx->hpts[i].n3 + ctx->hpts[i].N;
+      for (int b = 0; b < nc; b += SEG_ELEMS) {
+        sp.push_back(i);
+        sb.push_back(b);
+      }
+    }
+    ctx->nseg = (int)sp.size();
+    if (!(ctx->d_seg_point = dalloc<int>(ctx, sp.size())) || !(ctx->d_seg_base = dalloc<int>(ctx, sb.size())))
+      return bail(FRG_ENOMEM);
+    cudaMemcpy(ctx->d_seg_point, sp.data(), sizeof(int) * sp.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->d_seg_base, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice);
+  }
+  ctx->user_in.assign(n_points, nullptr);
+  ctx->user_out.assign(n_points, nullptr);
+  ctx->user_split.assign(n_points, frg_ctx::UserScratch());
+  if (launch_init(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, n_points, ctx->stream) != 0) return bail(FRG_ECUDA);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(FRG_ECUDA);
+  *out = ctx;
+  return FRG_OK;
+}
+
+void frg_destroy(frg_ctx *ctx) {
+  if (!ctx) return;
+  DevGuard g(ctx->dev);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  if (ctx->tc) tc_plan_destroy(ctx->tc);
+  for (void *p : ctx->allocs) cudaFree(p);
+  for (auto p : ctx->user_in) if (p) cudaFree(p);
+  for (auto p : ctx->user_out) if (p) cudaFree(p);
+  if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  delete ctx;
+}
+
+const char *frg_last_error(const frg_ctx *ctx) {
+  if (!ctx) return "null context (frg_init failed or was not called)";
+  return ctx->err.c_str();
+}
+
+static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma, const void *d_sigma,
+                    void *d_dgamma, void *d_dsigma, cudaEvent_t *ev) {
+  if (!ctx) return FRG_EINVAL;
+  if (point < 0 || point >= ctx->n) return fail(ctx, FRG_EINVAL, "point out of range");
+  if (!(Lambda > 0.0) || !std::isfinite(Lambda)) return fail(ctx, FRG_EINVAL, "Lambda must be > 0");
+  if (!d_gamma || !d_dgamma || !d_dsigma) return fail(ctx, FRG_EINVAL, "null buffer");
+  DevGuard g(ctx->dev);
+  RhsIO o;
+  o.gam = d_gamma;
+  o.sig = static_cast<const double2 *>(d_sigma);
+  o.dgam = d_dgamma;
+  o.dsig = static_cast<double2 *>(d_dsigma);
+  o.lam = nullptr;
+  o.active = 1;
+  o.out_f32 = 0;
+  if (!ctx->split) {
+    LK(launch_set_user_io(ctx->d_io_user, ctx->d_ctl, ctx->n, point, o, Lambda, ctx->stream), "user io");
+    return run_rhs(ctx, ctx->d_io_user, point, ev);
+  }
+  // split path: convert the input to float pairs, evaluate into float2, widen.
+  // Scratch of its own so that a stand-alone call leaves the flow state intact.
+  const PointDesc &P = ctx->hpts[point];
+  frg_ctx::UserScratch &u = ctx->user_split[point];
+  if (!u.ys) {
+    if (!(u.ys = dalloc<float4>(ctx, P.n3)) || !(u.s64 = dalloc<double2>(ctx, P.N)) ||
+        !(u.kout = dalloc<float2>(ctx, P.n3)))
+      return fail(ctx, FRG_ENOMEM, "stand-alone rhs scratch");
+  }
+  LK(launch_split_input(u.ys, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, ctx->stream),
+     "split input");
+  RhsIO s = o;
+  s.gam = u.ys;
+  s.sig = u.s64;
+  s.dgam = u.kout;
+  s.out_f32 = 1;
+  LK(launch_set_user_io(ctx->d_io_user, ctx->d_ctl, ctx->n, point, s, Lambda, ctx->stream), "user io");
+  int rc = run_rhs(ctx, ctx->d_io_user, point, ev);
+  if (rc) return rc;
+  LK(launch_widen(static_cast<double2 *>(d_dgamma), u.kout, P.n3, ctx->stream), "widen output");
+  return FRG_OK;
+}
+
+int frg_rhs(frg_ctx *ctx, int point, double Lambda, const void *d_gamma, const void *d_sigma, void *d_dgamma,
+            void *d_dsigma) {
+  return rhs_impl(ctx, point, Lambda, d_gamma, d_sigma, d_dgamma, d_dsigma, nullptr);
+}
+
+int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma, const void *d_sigma,
+                  void *d_dgamma, void *d_dsigma, float *ms) {
+  if (!ctx || !ms) return FRG_EINVAL;
+  DevGuard g(ctx->dev);
+  cudaEvent_t ev[5] = {};
+  for (int i = 0; i < 5; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+      return fail(ctx, FRG_ECUDA, "event create");
+    }
+  int rc = rhs_impl(ctx, point, Lambda, d_gamma, d_sigma, d_dgamma, d_dsigma, ev);
+  if (rc == FRG_OK) {
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "rhs");
+    for (int i = 0; i < 4 && rc == FRG_OK; ++i) {
+      ms[i] = 0.f;
+      cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+    }
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
+long frg_kernel_launches(void) { return frg::g_kernel_launches; }
+
+int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma, const double *h_sigma,
+                 double *h_dgamma, double *h_dsigma) {
+  if (!ctx) return FRG_EINVAL;
+  if (point < 0 || point >= ctx->n) return fail(ctx, FRG_EINVAL, "point out of range");
+  if (!h_gamma || !h_dgamma || !h_dsigma) return fail(ctx, FRG_EINVAL, "null buffer");
+  DevGuard g(ctx->dev);
+  const PointDesc &P = ctx->hpts[point];
+  const size_t nc = (size_t)P.n3 + P.N;
+  if (!ctx->user_in[point]) {
+    CK(cudaMalloc(&ctx->user_in[point], nc * sizeof(double2)), "alloc host-call buffers");
+    CK(cudaMalloc(&ctx->user_out[point], nc * sizeof(double2)), "alloc host-call buffers");
+  }
+  double2 *din = ctx->user_in[point], *dout = ctx->user_out[point];
+  CK(cudaMemcpyAsync(din, h_gamma, (size_t)P.n3 * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream), "H2D");
+  if (h_sigma)
+    CK(cudaMemcpyAsync(din + P.n3, h_sigma, (size_t)P.N * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream),
+       "H2D");
+  int rc = frg_rhs(ctx, point, Lambda, din, h_sigma ? din + P.n3 : nullptr, dout, dout + P.n3);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h_dgamma, dout, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  CK(cudaMemcpyAsync(h_dsigma, dout + P.n3, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream),
+     "D2H");
+  CK(cudaStreamSynchronize(ctx->stream), "rhs");
+  return FRG_OK;
+}
+
+int frg_advance(frg_ctx *ctx, long max_attempts, frg_flow_stats *stats) {
+  if (!ctx) return FRG_EINVAL;
+  if (max_attempts < 0) return fail(ctx, FRG_EINVAL, "max_attempts must be >= 0");
+  DevGuard g(ctx->dev);
+  int rc;
+  if (ctx->need_k1) {
+    if ((rc = issue_k1(ctx))) return rc;
+    ctx->need_k1 = false;
+  }
+  const long period = ctx->split ? 8 : 2;
+  long a = 0;
+  while (a < max_attempts) {
+    const long burst = std::min(period, max_attempts - a);
+    for (long i = 0; i < burst; ++i)
+      if ((rc = issue_step(ctx))) return rc;
+    a += burst;
+    if ((rc = sync_ctl(ctx))) return rc;
+    bool all = true;
+    for (int i = 0; i < ctx->n; ++i) all = all && ctx->h_ctl[i].done;
+    if (all) break;
+  }
+  if (max_attempts == 0 && (rc = sync_ctl(ctx))) return rc;
+  fill_stats(ctx, stats);
+  return flow_status(ctx);
+}
+
+int frg_flow(frg_ctx *ctx, frg_flow_stats *stats) {
+  if (!ctx) return FRG_EINVAL;
+  long budget = 0;
+  for (auto &p : ctx->params) budget = std::max(budget, p.max_steps);
+  return frg_advance(ctx, budget + 1, stats);
+}
+
+int frg_stats(frg_ctx *ctx, frg_flow_stats *stats) {
+  if (!ctx || !stats) return FRG_EINVAL;
+  DevGuard g(ctx->dev);
+  int rc = sync_ctl(ctx);
+  if (rc) return rc;
+  fill_stats(ctx, stats);
+  return FRG_OK;
+}
+
+int frg_get_state(frg_ctx *ctx, int point, void *d_gamma, void *d_sigma, double *Lambda, double *h) {
+  if (!ctx) return FRG_EINVAL;
+  if (point < 0 || point >= ctx->n) return fail(ctx, FRG_EINVAL, "point out of range");
+  DevGuard g(ctx->dev);
+  int rc = sync_ctl(ctx);
+  if (rc) return rc;
+  const Ctl &c = ctx->h_ctl[point];
+  const PointDesc &P = ctx->hpts[point];
+  const double2 *y = P.ybuf[c.yslot];
+  if (d_gamma) CK(cudaMemcpyAsync(d_gamma, y, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "copy state");
+  if (d_sigma) CK(cudaMemcpyAsync(d_sigma, y + P.n3, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "copy state");
+  if (Lambda) *Lambda = std::exp(c.t);
+  if (h) *h = c.h;
+  CK(cudaStreamSynchronize(ctx->stream), "copy state");
+  return FRG_OK;
+}
+
+int frg_set_state(frg_ctx *ctx, int point, const void *d_gamma, const void *d_sigma, double Lambda, double h) {
+  if (!ctx) return FRG_EINVAL;
+  if (point < 0 || point >= ctx->n) return fail(ctx, FRG_EINVAL, "point out of range");
+  if (!d_gamma) return fail(ctx, FRG_EINVAL, "null vertex buffer");
+  if (!(Lambda > 0.0) || !std::isfinite(Lambda)) return fail(ctx, FRG_EINVAL, "Lambda must be > 0");
+  if (h > 0.0) return fail(ctx, FRG_EINVAL, "h must be <= 0");
+  DevGuard g(ctx->dev);
+  const PointDesc &P = ctx->hpts[point];
+  CK(cudaMemcpyAsync(P.ybuf[0], d_gamma, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "set state");
+  if (d_sigma)
+    CK(cudaMemcpyAsync(P.ybuf[0] + P.n3, d_sigma, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "set state");
+  else
+    CK(cudaMemsetAsync(P.ybuf[0] + P.n3, 0, (size_t)P.N * sizeof(double2), ctx->stream), "set state");
+  LK(launch_set_ctl(ctx->d_pts, ctx->d_ctl, point, std::log(Lambda), h, ctx->stream), "set state");
+  ctx->need_k1 = true;
+  CK(cudaStreamSynchronize(ctx->stream), "set state");
+  return FRG_OK;
+}
+
+int frg_observables(frg_ctx *ctx, int point, frg_obs *out) {
+  if (!ctx || !out) return FRG_EINVAL;
+  if (point < 0 || point >= ctx->n) return fail(ctx, FRG_EINVAL, "point out of range");
+  DevGuard g(ctx->dev);
+  int rc = sync_ctl(ctx);
+  if (rc) return rc;
+  const Ctl &c = ctx->h_ctl[point];
+  const PointDesc &P = ctx->hpts[point];
+  const int N = P.N, hN = N / 2;
+  std::vector<double2> sig(N);
+  double2 ueff;
+  const double2 *y = P.ybuf[c.yslot];
+  CK(cudaMemcpyAsync(sig.data(), y + P.n3, N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream), "observables");
+  CK(cudaMemcpyAsync(&ueff, y + ((size_t)hN * N + hN) * N + hN, sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream),
+     "observables");
+  CK(cudaStreamSynchronize(ctx->stream), "observables");
+  const double L = std::exp(c.t), T = P.T, w0 = M_PI * T;
+  out->sigma_lowest_re = sig[hN].x;
+  out->sigma_lowest_im = sig[hN].y;
+  out->Z = 1.0 / (1.0 - sig[hN].y / w0);
+  out->U_eff_re = ueff.x;
+  out->U_eff_im = ueff.y;
+  double n = 0.5;
+  for (int i = 0; i < N; ++i) {
+    const double w = (2.0 * (i - hN) + 1.0) * M_PI * T;
+    const double thinv = 1.0 + L * L / (w * w);
+    const double dr = -thinv * P.et - sig[i].x;
+    const double di = thinv * (w + (w > 0 ? P.Delta : -P.Delta)) - sig[i].y;
+    n += T * dr / (dr * dr + di * di);  // Re of 1/(dr + i di)
+  }
+  out->n = n;
+  return FRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// frg_common.cuh -- device data structures and helpers shared by the kernels of
+// the GB300 fRG library (internal; the public interface is include/frg.h).
+//
+// Frequency convention: index i in [0, N) <-> Matsubara n = i - N/2,
+// w_i = (2(i - N/2) + 1) pi T.  Vertex index ((i1*N)+i2)*N+i3, fourth index
+// i4 = i1 + i2 - i3.  Box rule: V = stored value if i1..i4 in [0,N), else U.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FRG_MAX_N 256
+
+namespace frg {
+
+// Process-wide count of kernel launches issued by this library (diagnostics).
+extern long g_kernel_launches;
+#define FRG_COUNT(n) (::frg::g_kernel_launches += (n))
+
+enum Channel { CH_PP = 0, CH_DPH = 1, CH_XPH = 2 };
+
+// Per-point constants and buffers (device-resident array, one entry per point).
+struct PointDesc {
+  int N;
+  int n3;                 // N^3
+  double U, T, et, Delta; // et = eps_d + U/2
+  double l0, l_end;       // ln Lambda0, ln Lambda_f
+  double rtol, atol, h0;
+  long max_steps;
+  double2 *ybuf[2];  // state (Gamma | Sigma), N^3 + N complex each; ctl.yslot picks y
+  double2 *Y64;      // FP64 stage input: (Gamma | Sigma) on the FP64 path, Sigma only (N) on split paths
+  float4 *Ysplit;    // split stage input (re_hi, re_lo, im_hi, im_lo) per vertex entry (split paths)
+  void *kG[7];       // vertex part of the stage derivatives: double2 (FP64) or float2 (split)
+  double2 *kS[7];    // self-energy part of the stage derivatives
+  double2 *G, *S;    // propagators on the box (N)
+  double2 *Lpp;      // Lpp[s*N + p] = Lb(p, s-p) (0 outside the box), s in [0, 2N-1)
+  double2 *Lph;      // Lph[(Q+N-1)*N + p] = Lb(p, p+Q) (0 outside the box)
+};
+
+// Device-side step controller state, one per point.
+struct Ctl {
+  double t, h;               // l = ln Lambda and the current step in l
+  double lam_stage[7];       // Lambda at the 7 stage abscissae of the current step
+  unsigned long long errbits;// max-norm of the scaled error (bits of a non-negative double)
+  int nonfinite;
+  long steps, accepted, rejected, rhs_evals;
+  int status, done, last, have_k1;
+  int yslot;                 // ybuf[yslot] holds y, ybuf[yslot^1] the candidate
+  int kslot[7];              // kG/kS[kslot[j]] holds k_{j+1}
+  double lam_user;           // scale of a stand-alone rhs call
+};
+
+// Inputs/outputs of one rhs evaluation for one point.
+struct RhsIO {
+  const void *gam;     // vertex input: double2* (FP64) or float4* split
+  const double2 *sig;  // self-energy input (FP64), may be null
+  void *dgam;          // vertex output: double2* or float2*
+  double2 *dsig;       // self-energy output
+  const double *lam;   // scale (device)
+  int active;          // 0: skip this point
+  int out_f32;         // vertex output as float2
+};
+
+// One CTA of a channel contraction.
+struct WorkItem {
+  int point;
+  int m;       // transfer index in [0, 2N-1): s for pp, t+N-1 for dph, Q+N-1 for xph
+  int rt, ct;  // row / column tile
+};
+
+// ------------------------------------------------------------ complex ----
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc += a*b
+__device__ __forceinline__ void cfma(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// --------------------------------------------------- channel geometry ----
+// Rows, contraction length and columns of the product for transfer m.
+//  pp : rows a (=k1) with a, s-a in box; K = p (same set); cols k3 in [0,N)
+//  dph: rows k1 with k1, k1+t in box;    K = 2 x p with p, p-t in box; cols k2 in [0,N)
+//  xph: rows k3 with k3, k3+Q in box;    K = p with p, p+Q in box;     cols k1 in [0,N)
+struct Geom {
+  int D;       // valid rows (= valid p)
+  int row_lo;  // first valid row index
+  int p_lo;    // first valid p
+  int K;       // contraction length (D or 2D)
+  int x;       // s, t or Q
+};
+
+__host__ __device__ __forceinline__ Geom geom(int ch, int N, int m) {
+  Geom g;
+  if (ch == CH_PP) {
+    int s = m;
+    g.x = s;
+    g.row_lo = s - (N - 1) > 0 ? s - (N - 1) : 0;
+    g.D = N - (s - (N - 1) >= 0 ? s - (N - 1) : (N - 1) - s);
+    g.p_lo = g.row_lo;
+    g.K = g.D;
+  } else if (ch == CH_DPH) {
+    int t = m - (N - 1);
+    g.x = t;
+    g.row_lo = t < 0 ? -t : 0;
+    g.D = N - (t >= 0 ? t : -t);
+    g.p_lo = t > 0 ? t : 0;
+    g.K = 2 * g.D;
+  } else {
+    int Q = m - (N - 1);
+    g.x = Q;
+    g.row_lo = Q < 0 ? -Q : 0;
+    g.D = N - (Q >= 0 ? Q : -Q);
+    g.p_lo = g.row_lo;
+    g.K = g.D;
+  }
+  return g;
+}
+
+__device__ __forceinline__ bool inbox(int N, int i) { return (unsigned)i < (unsigned)N; }
+
+// Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).
+struct StageArgs {
+  int stage;  // 0..6
+};
+
+}  // namespace frg
+
+// ------------------------------------------------- host-side launchers ----
+namespace frg {
+struct Workspace;
+int launch_bubble(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, cudaStream_t st);
+int launch_contract_fp64(const PointDesc *d_pts, const RhsIO *d_io, const WorkItem *const d_work[3],
+                         const int nwork[3], int mask, cudaStream_t st);
+int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
+                 cudaStream_t st);
+}  // namespace frg

@@ -1,0 +1,276 @@
+// frg_fp64.cu -- bubble weights, self-energy rhs and the plain-FP64 channel
+// contractions (CUDA cores) of the one-loop SIAM flow.
+//
+// Propagators (Omega scheme):  G = 1/(Theta^{-1} G0^{-1} - Sigma),
+//   Theta^{-1} = 1 + L^2/w^2,  S = -G^2 (2L/w^2) G0^{-1},
+//   G0^{-1} = iw - et + i Delta sgn w.
+// Bubble weights Lb(a,b) = S(a)G(b) + G(a)S(b), tabulated per transfer.
+// Channel sums (the three one-loop diagrams of the paper, Sec. 4) are
+// evaluated as one complex product Left . Right per transfer frequency, with
+// diag(Lb) folded into Left (see Geom in frg_common.cuh for the index sets).
+#include "frg_common.cuh"
+#include "frg_split.cuh"
+
+namespace frg {
+
+// ---------------------------------------------------------- propagators ----
+__global__ void k_bubble_gs(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
+  const int pi = blockIdx.x;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  const int i = threadIdx.x;
+  if (i >= P.N) return;
+  const double L = *o.lam;
+  const double w = (2.0 * (double)(i - P.N / 2) + 1.0) * M_PI * P.T;
+  const double thinv = 1.0 + (L * L) / (w * w);
+  const double2 gi = make_double2(-P.et, w + (w > 0.0 ? P.Delta : -P.Delta));
+  double2 sg = o.sig ? o.sig[i] : make_double2(0.0, 0.0);
+  // G = 1 / (thinv * gi - sigma)
+  const double2 den = make_double2(thinv * gi.x - sg.x, thinv * gi.y - sg.y);
+  const double nrm = den.x * den.x + den.y * den.y;
+  const double2 g = make_double2(den.x / nrm, -den.y / nrm);
+  const double2 g2 = cmul(g, g);
+  const double2 s = cscale(cmul(g2, gi), -2.0 * L / (w * w));
+  P.G[i] = g;
+  P.S[i] = s;
+}
+
+// Lpp[s][p] = Lb(p, s-p), Lph[Q+N-1][p] = Lb(p, p+Q); grid (2N-1, 2, points).
+__global__ void k_bubble_tables(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
+  const int pi = blockIdx.z;
+  if (!io[pi].active) return;
+  const PointDesc &P = pts[pi];
+  const int N = P.N;
+  const int row = blockIdx.x;
+  if (row >= 2 * N - 1) return;
+  const int which = blockIdx.y;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    int q = which == 0 ? row - p : p + (row - (N - 1));
+    double2 v = make_double2(0.0, 0.0);
+    if (inbox(N, q)) {
+      double2 gp = P.G[p], sp = P.S[p], gq = P.G[q], sq = P.S[q];
+      v = cadd(cmul(sp, gq), cmul(gp, sq));
+    }
+    (which == 0 ? P.Lpp : P.Lph)[(size_t)row * N + p] = v;
+  }
+}
+
+int launch_bubble(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split,
+                  cudaStream_t st) {
+  (void)split;
+  k_bubble_gs<<<n_points, maxN, 0, st>>>(d_pts, d_io);
+  FRG_COUNT(1);
+  dim3 g(2 * maxN - 1, 2, n_points);
+  k_bubble_tables<<<g, 128, 0, st>>>(d_pts, d_io);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// -------------------------------------------------------- vertex access ----
+template <bool SPLIT>
+__device__ __forceinline__ double2 vload(const void *gam, int N, double U, int i1, int i2, int i3) {
+  const int i4 = i1 + i2 - i3;
+  if (inbox(N, i1) && inbox(N, i2) && inbox(N, i3) && inbox(N, i4)) {
+    const size_t at = ((size_t)i1 * N + i2) * N + i3;
+    if (SPLIT) {
+      float4 v = static_cast<const float4 *>(gam)[at];
+      return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+    return static_cast<const double2 *>(gam)[at];
+  }
+  return make_double2(U, 0.0);
+}
+
+// ------------------------------------------------------------ self-energy ----
+// dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]; one warp per w.
+template <bool SPLIT>
+__global__ void k_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int enabled) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  const int N = P.N;
+  const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= N) return;
+  double2 acc = make_double2(0.0, 0.0);
+  if (enabled) {
+    for (int p = lane; p < N; p += 32) {
+      double2 a = vload<SPLIT>(o.gam, N, P.U, w, p, w);
+      double2 b = vload<SPLIT>(o.gam, N, P.U, w, p, p);
+      double2 t = make_double2(2.0 * a.x - b.x, 2.0 * a.y - b.y);
+      cfma(acc, P.S[p], t);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+  }
+  if (lane == 0) {
+    const double f = (*o.lam) * P.T;
+    o.dsig[w] = make_double2(acc.x * f, acc.y * f);
+  }
+}
+
+int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
+                 cudaStream_t st) {
+  dim3 g((maxN + 3) / 4, n_points);
+  if (split)
+    k_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, (mask & 8) != 0);
+  else
+    k_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, (mask & 8) != 0);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ------------------------------------------------- FP64 contraction ----
+constexpr int F64_TM = 32, F64_TN = 32, F64_TK = 16, F64_THREADS = 256;
+
+// Left[r][k] (r local row, k in [0,K)) of channel CH for transfer geometry g.
+template <int CH>
+__device__ __forceinline__ double2 left_elem(const PointDesc &P, const void *gam, const Geom &g, int r, int k) {
+  const int N = P.N;
+  if (CH == CH_PP) {
+    const int a = g.row_lo + r, p = g.p_lo + k, s = g.x;
+    return cmul(vload<false>(gam, N, P.U, a, s - a, p), P.Lpp[(size_t)s * N + p]);
+  } else if (CH == CH_DPH) {
+    const int t = g.x, k1 = g.row_lo + r;
+    const int half = k >= g.D;
+    const int p = g.p_lo + (half ? k - g.D : k);
+    const double2 L = P.Lph[(size_t)(-t + N - 1) * N + p];
+    const double2 A = vload<false>(gam, N, P.U, k1, p, k1 + t);
+    if (!half) {
+      const double2 C = vload<false>(gam, N, P.U, k1, p, p - t);
+      return cmul(make_double2(2.0 * A.x - C.x, 2.0 * A.y - C.y), L);
+    }
+    return cmul(make_double2(-A.x, -A.y), L);
+  } else {
+    const int Q = g.x, k3 = g.row_lo + r, p = g.p_lo + k;
+    return cmul(vload<false>(gam, N, P.U, p, k3 + Q, k3), P.Lph[(size_t)(Q + N - 1) * N + p]);
+  }
+}
+
+template <int CH>
+__device__ __forceinline__ double2 right_elem(const PointDesc &P, const void *gam, const Geom &g, int k, int c) {
+  const int N = P.N;
+  if (CH == CH_PP) {
+    const int p = g.p_lo + k, s = g.x;
+    return vload<false>(gam, N, P.U, p, s - p, c);
+  } else if (CH == CH_DPH) {
+    const int t = g.x;
+    const int half = k >= g.D;
+    const int p = g.p_lo + (half ? k - g.D : k);
+    return half ? vload<false>(gam, N, P.U, p - t, c, c - t) : vload<false>(gam, N, P.U, p - t, c, p);
+  } else {
+    const int Q = g.x, p = g.p_lo + k;
+    return vload<false>(gam, N, P.U, c, p + Q, p);
+  }
+}
+
+// Output element (local row r, column c) -> flat vertex index.
+template <int CH>
+__device__ __forceinline__ size_t out_index(int N, const Geom &g, int r, int c) {
+  if (CH == CH_PP) {
+    const int a = g.row_lo + r;
+    return ((size_t)a * N + (g.x - a)) * N + c;
+  } else if (CH == CH_DPH) {
+    const int k1 = g.row_lo + r;
+    return ((size_t)k1 * N + c) * N + (k1 + g.x);
+  } else {
+    const int k3 = g.row_lo + r;
+    return ((size_t)c * N + (k3 + g.x)) * N + k3;
+  }
+}
+
+template <int CH, bool ACCUM>
+__global__ void __launch_bounds__(F64_THREADS)
+    k_contract_fp64(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                    const WorkItem *__restrict__ work) {
+  __shared__ double2 Ls[F64_TM][F64_TK + 1];
+  __shared__ double2 Rs[F64_TK][F64_TN + 1];
+  const WorkItem w = work[blockIdx.x];
+  const RhsIO &o = io[w.point];
+  if (!o.active) return;
+  const PointDesc &P = pts[w.point];
+  const int N = P.N;
+  const Geom g = geom(CH, N, w.m);
+  const int r0 = w.rt * F64_TM, c0 = w.ct * F64_TN;
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (int k0 = 0; k0 < g.K; k0 += F64_TK) {
+#pragma unroll
+    for (int j = 0; j < (F64_TM * F64_TK) / F64_THREADS; ++j) {
+      const int e = tid + j * F64_THREADS;
+      const int r = e / F64_TK, kk = e % F64_TK;
+      const int rr = r0 + r, k = k0 + kk;
+      Ls[r][kk] = (rr < g.D && k < g.K) ? left_elem<CH>(P, o.gam, g, rr, k) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int j = 0; j < (F64_TK * F64_TN) / F64_THREADS; ++j) {
+      const int e = tid + j * F64_THREADS;
+      const int kk = e / F64_TN, c = e % F64_TN;
+      const int k = k0 + kk, cc = c0 + c;
+      Rs[kk][c] = (k < g.K && cc < N) ? right_elem<CH>(P, o.gam, g, k, cc) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < F64_TK; ++kk) {
+      const double2 a0 = Ls[ty * 2][kk], a1 = Ls[ty * 2 + 1][kk];
+      const double2 b0 = Rs[kk][tx * 2], b1 = Rs[kk][tx * 2 + 1];
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  const double sc = (CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam);
+  double2 *out = static_cast<double2 *>(o.dgam);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = r0 + ty * 2 + i, c = c0 + tx * 2 + j;
+      if (r < g.D && c < N) {
+        const size_t at = out_index<CH>(N, g, r, c);
+        double2 v = make_double2(acc[i][j].x * sc, acc[i][j].y * sc);
+        if (ACCUM) v = cadd(out[at], v);
+        out[at] = v;
+      }
+    }
+}
+
+// pp stores, dph and xph accumulate: the three channels run in this order so
+// that every vertex entry receives its three contributions in a fixed order.
+int launch_contract_fp64(const PointDesc *d_pts, const RhsIO *d_io, const WorkItem *const d_work[3],
+                         const int nwork[3], int mask, cudaStream_t st) {
+  bool first = true;
+  auto go = [&](int ch) {
+    if (!nwork[ch]) return;
+    const bool acc = !first;
+    first = false;
+    FRG_COUNT(1);
+    if (ch == CH_PP)
+      acc ? k_contract_fp64<CH_PP, true><<<nwork[ch], F64_THREADS, 0, st>>>(d_pts, d_io, d_work[ch])
+          : k_contract_fp64<CH_PP, false><<<nwork[ch], F64_THREADS, 0, st>>>(d_pts, d_io, d_work[ch]);
+    else if (ch == CH_DPH)
+      acc ? k_contract_fp64<CH_DPH, true><<<nwork[ch], F64_THREADS, 0, st>>>(d_pts, d_io, d_work[ch])
+          : k_contract_fp64<CH_DPH, false><<<nwork[ch], F64_THREADS, 0, st>>>(d_pts, d_io, d_work[ch]);
+    else
+      acc ? k_contract_fp64<CH_XPH, true><<<nwork[ch], F64_THREADS, 0, st>>>(d_pts, d_io, d_work[ch])
+          : k_contract_fp64<CH_XPH, false><<<nwork[ch], F64_THREADS, 0, st>>>(d_pts, d_io, d_work[ch]);
+  };
+  if (mask & 1) go(CH_PP);
+  if (mask & 2) go(CH_DPH);
+  if (mask & 4) go(CH_XPH);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace frg

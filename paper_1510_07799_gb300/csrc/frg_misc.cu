@@ -1,0 +1,82 @@
+// frg_misc.cu -- small stream-ordered helper kernels of the C ABI.
+#include "frg_common.cuh"
+#include "frg_misc.cuh"
+#include "frg_split.cuh"
+
+namespace frg {
+
+long g_kernel_launches = 0;
+
+// io[point] = o with its scale stored on the device; every other point inactive.
+__global__ void k_set_user_io(RhsIO *io, Ctl *ctl, int n, int point, RhsIO o, double lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i == point) {
+    ctl[i].lam_user = lam;
+    o.lam = &ctl[i].lam_user;
+    io[i] = o;
+  } else {
+    RhsIO z = {};
+    io[i] = z;
+  }
+}
+
+int launch_set_user_io(RhsIO *d_io, Ctl *d_ctl, int n, int point, RhsIO o, double lam, cudaStream_t st) {
+  k_set_user_io<<<(n + 127) / 128, 128, 0, st>>>(d_io, d_ctl, n, point, o, lam);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Vertex output = 0 for active points (no vertex channel enabled).
+__global__ void k_zero_vertex(const PointDesc *pts, const RhsIO *io) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const int n3 = pts[pi].n3;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    if (o.out_f32)
+      static_cast<float2 *>(o.dgam)[i] = make_float2(0.f, 0.f);
+    else
+      static_cast<double2 *>(o.dgam)[i] = make_double2(0.0, 0.0);
+  }
+}
+
+int launch_zero_vertex(const PointDesc *d_pts, const RhsIO *d_io, int n, int maxN, cudaStream_t st) {
+  (void)maxN;
+  k_zero_vertex<<<dim3(256, n), 256, 0, st>>>(d_pts, d_io);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+__global__ void k_split_input(float4 *ys, double2 *s64, const double2 *g, const double2 *sig, int n3, int N) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3 + N; i += gridDim.x * blockDim.x) {
+    if (i < n3)
+      ys[i] = split_c128(g[i]);
+    else
+      s64[i - n3] = sig ? sig[i - n3] : make_double2(0.0, 0.0);
+  }
+}
+
+int launch_split_input(float4 *ysplit, double2 *s64, const double2 *gam, const double2 *sig, int n3, int N,
+                       cudaStream_t st) {
+  const int blocks = (n3 + N + 255) / 256 < 4096 ? (n3 + N + 255) / 256 : 4096;
+  k_split_input<<<blocks, 256, 0, st>>>(ysplit, s64, gam, sig, n3, N);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+__global__ void k_widen(double2 *out, const float2 *in, int n3) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    const float2 v = in[i];
+    out[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+int launch_widen(double2 *out, const float2 *in, int n3, cudaStream_t st) {
+  const int blocks = (n3 + 255) / 256 < 4096 ? (n3 + 255) / 256 : 4096;
+  k_widen<<<blocks, 256, 0, st>>>(out, in, n3);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace frg

@@ -1,0 +1,82 @@
+"""Write oracle reference values for full flows into tests/golden/.
+
+Runs only the FP64 CPU oracle (oracle/) on a named workload from the input
+module, flowing from Lambda0 to Lambda_f, and stores a seeded sample of the final
+vertex, the whole self-energy, the observables, the norms needed for normwise
+relative errors, and the integrator statistics.  Nothing here touches the CUDA
+path.
+
+usage: python tests/golden/make_oracle_reference.py <workload-name> [samples]
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_1510_07799_gb300 import inputs  # noqa: E402
+
+SAMPLE_SEED = 20151025
+
+
+def sample_indices(N, count, seed=SAMPLE_SEED):
+    """Seeded sample of vertex entries, always including the lowest-frequency
+    entry (the effective interaction) and its crossing/reversal partners."""
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, N, (count, 3))
+    h = N // 2
+    extra = np.array([[h, h, h], [h - 1, h - 1, h - 1], [0, 0, 0], [N - 1, N - 1, N - 1],
+                      [h, h - 1, h], [h - 1, h, h - 1]])
+    return np.concatenate([extra, idx]).astype(np.int64)
+
+
+def main():
+    name = sys.argv[1]
+    count = int(sys.argv[2]) if len(sys.argv) > 2 else 2048
+    w = inputs.WORKLOADS[name]
+    m = oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+    t0 = time.time()
+    g, s, st = oracle.flow(m, Lambda0=w.Lambda0, Lambda_f=w.Lambda_f, rtol=w.rtol,
+                           atol=w.atol)
+    wall = time.time() - t0
+    if st.status != 0:
+        raise SystemExit("oracle flow failed: %s" % st)
+    idx = sample_indices(w.N, count)
+    vals = g[idx[:, 0], idx[:, 1], idx[:, 2]]
+    obs = oracle.observables(m, w.Lambda_f, g, s)
+    out = {
+        "workload": name,
+        "what": "oracle FP64 flow from Lambda0 to Lambda_f; sampled final vertex",
+        "params": {"N": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d, "Delta": w.Delta,
+                   "Lambda0": w.Lambda0, "Lambda_f": w.Lambda_f, "rtol": w.rtol,
+                   "atol": w.atol},
+        "stats": {"accepted": st.accepted, "rejected": st.rejected,
+                  "rhs_evals": st.rhs_evals, "first_step_evals": st.first_step_evals,
+                  "wall_s": wall, "threads": oracle.max_threads()},
+        "gamma_norm_inf": float(np.max(np.abs(g))),
+        "sigma_norm_inf": float(np.max(np.abs(s))),
+        "gamma_mean": [float(g.real.mean()), float(g.imag.mean())],
+        "sample_idx": idx.tolist(),
+        "sample_re": [float(x) for x in vals.real],
+        "sample_im": [float(x) for x in vals.imag],
+        "sigma_re": [float(x) for x in s.real],
+        "sigma_im": [float(x) for x in s.imag],
+        "observables": {"sigma_lowest": [obs["sigma_lowest"].real, obs["sigma_lowest"].imag],
+                        "Z": obs["Z"], "U_eff": [obs["U_eff"].real, obs["U_eff"].imag],
+                        "n": obs["n"]},
+    }
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "oracle_flow_%s.json" % name)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=0, separators=(",", ":"))
+        f.write("\n")
+    print(path, st, "%.1fs" % wall)
+
+
+if __name__ == "__main__":
+    main()
