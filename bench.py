@@ -188,13 +188,7 @@ def run_ours(args):
     w = inputs.SIAM_N128
     N = w.N
     prec = args.precision
-    try:
-        ctx = frg.Context([w], precision=prec)
-    except frg.FrgError as e:
-        if args.precision_explicit or e.code != frg.EINVAL:
-            raise
-        prec = "fp64"
-        ctx = frg.Context([w], precision=prec)
+    ctx = frg.Context([w], precision=prec)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -259,7 +253,8 @@ def run_ours(args):
                 "kernel": "tcgen05 channel contractions of one rhs",
                 "peak_source": "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)" % pk["_source"],
                 "algorithmic": "8 flops x %d useful complex MACs per rhs (useful, not executed)" % macs}
-    roof["phases_ms"] = {"bubble": ph[0], "gather": ph[1], "contraction": ph[2], "sigma": ph[3]}
+    roof["phases_ms"] = {"bubble": ph[0], "regather": ph[1], "contraction": ph[2], "combine": ph[3],
+                         "sigma": ph[4]}
 
     # ---- end to end through the host-buffer entry point
     hg = g.cpu().numpy()

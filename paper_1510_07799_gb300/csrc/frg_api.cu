@@ -31,6 +31,8 @@ struct frg_ctx {
   PointDesc *d_pts = nullptr;
   Ctl *d_ctl = nullptr;
   Ctl *h_ctl = nullptr;        // pinned mirror
+  unsigned *d_err = nullptr;   // set by a kernel whose bounded wait ran out
+  unsigned *h_err = nullptr;   // pinned mirror
   RhsIO *d_io_stage = nullptr; // flow evaluations
   RhsIO *d_io_user = nullptr;  // stand-alone evaluations
   // contraction work lists: [ch] all points cost-sorted; per-point slices
@@ -45,7 +47,7 @@ struct frg_ctx {
   std::vector<double2 *> user_in, user_out;
   TcPlan *tc = nullptr;  // split-precision contraction plan
   struct UserScratch {
-    float4 *ys = nullptr;
+    float2 *ys = nullptr;
     double2 *s64 = nullptr;
     float2 *kout = nullptr;
   };
@@ -134,8 +136,8 @@ void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &ou
 }  // namespace
 
 // ------------------------------------------------------------ rhs pipeline ----
-// ev (optional, 5 events): before bubble, after bubble, after the operand
-// gather, after the contraction, after the self-energy.
+// ev (optional, 6 events): start, after the bubble weights, after the operand
+// regather, after the channel products, after the combine, after the self-energy.
 static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr) {
   cudaStream_t st = ctx->stream;
   if (ev) CK(cudaEventRecord(ev[0], st), "event");
@@ -160,20 +162,39 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
     } else {
       LK(launch_zero_vertex(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "zero vertex");
     }
+    if (ev) CK(cudaEventRecord(ev[3], st), "event");
   } else {
-    LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr), "split contraction");
+    if (chmask) {
+      LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
+                ctx->maxN),
+         "split contraction");
+    } else {
+      if (ev) CK(cudaEventRecord(ev[2], st), "event");
+      LK(launch_zero_vertex(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "zero vertex");
+      if (ev) CK(cudaEventRecord(ev[3], st), "event");
+    }
   }
-  if (ev) CK(cudaEventRecord(ev[3], st), "event");
-  LK(launch_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st), "self-energy");
   if (ev) CK(cudaEventRecord(ev[4], st), "event");
+  LK(launch_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st), "self-energy");
+  if (ev) CK(cudaEventRecord(ev[5], st), "event");
+  return FRG_OK;
+}
+
+static int sync_checked(frg_ctx *ctx, const char *what) {
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream), what);
+  CK(cudaStreamSynchronize(ctx->stream), what);
+  if (*ctx->h_err) {
+    *ctx->h_err = 0;
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream);
+    return fail(ctx, FRG_ETIMEOUT, std::string(what) + ": a bounded device-side wait ran out");
+  }
   return FRG_OK;
 }
 
 static int sync_ctl(frg_ctx *ctx) {
   CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(Ctl) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream),
      "read controller state");
-  CK(cudaStreamSynchronize(ctx->stream), "flow");
-  return FRG_OK;
+  return sync_checked(ctx, "flow");
 }
 
 static void fill_stats(frg_ctx *ctx, frg_flow_stats *stats) {
@@ -291,7 +312,17 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
         if (!(P.kG[j] = dalloc<double2>(ctx, n3))) return bail(FRG_ENOMEM);
     } else {
       if (!(P.Y64 = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
-      if (!(P.Ysplit = dalloc<float4>(ctx, n3))) return bail(FRG_ENOMEM);
+      if (!(P.Y32 = dalloc<float2>(ctx, n3)) || !(P.Y32W = dalloc<float2>(ctx, n3)) ||
+          !(P.Y32X = dalloc<float2>(ctx, n3)) || !(P.PX = dalloc<float2>(ctx, n3)) ||
+          !(P.PW = dalloc<float2>(ctx, n3)))
+        return bail(FRG_ENOMEM);
+      for (int b = 0; b < 2; ++b)
+        if (!(P.yhi[b] = dalloc<float2>(ctx, n3)) || !(P.ylo[b] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
+      if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N)) ||
+          !(P.Lph32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N)) ||
+          !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 1)))
+        return bail(FRG_ENOMEM);
+      if (cudaMemset(P.vmax, 0, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ECUDA);
       for (int j = 0; j < 7; ++j)
         if (!(P.kG[j] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
     }
@@ -306,6 +337,10 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       !(ctx->d_io_stage = dalloc<RhsIO>(ctx, n_points)) || !(ctx->d_io_user = dalloc<RhsIO>(ctx, n_points)))
     return bail(FRG_ENOMEM);
   if (cudaMallocHost(&ctx->h_ctl, sizeof(Ctl) * n_points) != cudaSuccess) return bail(FRG_ENOMEM);
+  if (cudaMallocHost(&ctx->h_err, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ENOMEM);
+  *ctx->h_err = 0;
+  if (!(ctx->d_err = dalloc<unsigned>(ctx, 1)) || cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess)
+    return bail(FRG_ENOMEM);
   if (cudaMemcpy(ctx->d_pts, ctx->hpts.data(), sizeof(PointDesc) * n_points, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(FRG_ECUDA);
   if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
@@ -338,7 +373,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       cudaMemcpy(ctx->d_work_pt[ch], per.data(), sizeof(WorkItem) * per.size(), cudaMemcpyHostToDevice);
     }
   } else {
-    int rc = tc_plan_create(&ctx->tc, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, why);
+    int rc = tc_plan_create(&ctx->tc, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, ctx->d_err, why);
     if (rc) {
       ctx->err = why;
       return bail(rc);
@@ -380,6 +415,7 @@ void frg_destroy(frg_ctx *ctx) {
   for (auto p : ctx->user_in) if (p) cudaFree(p);
   for (auto p : ctx->user_out) if (p) cudaFree(p);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
   delete ctx;
 }
 
@@ -412,11 +448,11 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
   const PointDesc &P = ctx->hpts[point];
   frg_ctx::UserScratch &u = ctx->user_split[point];
   if (!u.ys) {
-    if (!(u.ys = dalloc<float4>(ctx, P.n3)) || !(u.s64 = dalloc<double2>(ctx, P.N)) ||
+    if (!(u.ys = dalloc<float2>(ctx, P.n3)) || !(u.s64 = dalloc<double2>(ctx, P.N)) ||
         !(u.kout = dalloc<float2>(ctx, P.n3)))
       return fail(ctx, FRG_ENOMEM, "stand-alone rhs scratch");
   }
-  LK(launch_split_input(u.ys, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, ctx->stream),
+  LK(launch_split_input(u.ys, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, P.vmax, ctx->stream),
      "split input");
   RhsIO s = o;
   s.gam = u.ys;
@@ -439,22 +475,21 @@ int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma, c
                   void *d_dgamma, void *d_dsigma, float *ms) {
   if (!ctx || !ms) return FRG_EINVAL;
   DevGuard g(ctx->dev);
-  cudaEvent_t ev[5] = {};
-  for (int i = 0; i < 5; ++i)
+  cudaEvent_t ev[6] = {};
+  for (int i = 0; i < 6; ++i)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) {
       for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
       return fail(ctx, FRG_ECUDA, "event create");
     }
   int rc = rhs_impl(ctx, point, Lambda, d_gamma, d_sigma, d_dgamma, d_dsigma, ev);
   if (rc == FRG_OK) {
-    cudaError_t e = cudaEventSynchronize(ev[4]);
-    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "rhs");
-    for (int i = 0; i < 4 && rc == FRG_OK; ++i) {
+    rc = sync_checked(ctx, "rhs");
+    for (int i = 0; i < 5 && rc == FRG_OK; ++i) {
       ms[i] = 0.f;
       cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
     }
   }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
   return rc;
 }
 
@@ -482,8 +517,7 @@ int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma, 
   CK(cudaMemcpyAsync(h_dgamma, dout, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
   CK(cudaMemcpyAsync(h_dsigma, dout + P.n3, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream),
      "D2H");
-  CK(cudaStreamSynchronize(ctx->stream), "rhs");
-  return FRG_OK;
+  return sync_checked(ctx, "rhs");
 }
 
 int frg_advance(frg_ctx *ctx, long max_attempts, frg_flow_stats *stats) {

@@ -28,12 +28,18 @@ struct PointDesc {
   long max_steps;
   double2 *ybuf[2];  // state (Gamma | Sigma), N^3 + N complex each; ctl.yslot picks y
   double2 *Y64;      // FP64 stage input: (Gamma | Sigma) on the FP64 path, Sigma only (N) on split paths
-  float4 *Ysplit;    // split stage input (re_hi, re_lo, im_hi, im_lo) per vertex entry (split paths)
+  float2 *Y32;       // split paths: FP32 copy of the vertex stage input (contraction operand source)
   void *kG[7];       // vertex part of the stage derivatives: double2 (FP64) or float2 (split)
   double2 *kS[7];    // self-energy part of the stage derivatives
   double2 *G, *S;    // propagators on the box (N)
   double2 *Lpp;      // Lpp[s*N + p] = Lb(p, s-p) (0 outside the box), s in [0, 2N-1)
   double2 *Lph;      // Lph[(Q+N-1)*N + p] = Lb(p, p+Q) (0 outside the box)
+  float2 *Lpp32, *Lph32;  // FP32 copies of the two tables (split paths)
+  float *Lmax;       // split paths: max over p of |Re|,|Im| of each table row: [pp rows | ph rows]
+  float2 *yhi[2], *ylo[2];  // split paths: vertex part of ybuf[] as float pairs (hi + lo)
+  float2 *Y32W, *Y32X;      // split paths: FP32 stage input in the layouts [i2][i3][i1] and [i1][i3][i2]
+  float2 *PX, *PW;          // split paths: direct (layout X) and crossed (layout W) channel outputs
+  unsigned *vmax;    // split paths: bits of max |Re|,|Im| over the FP32 vertex input of the current rhs
 };
 
 // Device-side step controller state, one per point.
@@ -51,7 +57,7 @@ struct Ctl {
 
 // Inputs/outputs of one rhs evaluation for one point.
 struct RhsIO {
-  const void *gam;     // vertex input: double2* (FP64) or float4* split
+  const void *gam;     // vertex input: double2* (FP64) or float2* (split paths)
   const double2 *sig;  // self-energy input (FP64), may be null
   void *dgam;          // vertex output: double2* or float2*
   double2 *dsig;       // self-energy output

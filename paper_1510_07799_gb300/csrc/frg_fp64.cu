@@ -37,6 +37,7 @@ __global__ void k_bubble_gs(const PointDesc *__restrict__ pts, const RhsIO *__re
 }
 
 // Lpp[s][p] = Lb(p, s-p), Lph[Q+N-1][p] = Lb(p, p+Q); grid (2N-1, 2, points).
+// Split paths also get the FP32 tables and the per-row maximum of |Re|, |Im|.
 __global__ void k_bubble_tables(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
   const int pi = blockIdx.z;
   if (!io[pi].active) return;
@@ -45,6 +46,7 @@ __global__ void k_bubble_tables(const PointDesc *__restrict__ pts, const RhsIO *
   const int row = blockIdx.x;
   if (row >= 2 * N - 1) return;
   const int which = blockIdx.y;
+  float m = 0.f;
   for (int p = threadIdx.x; p < N; p += blockDim.x) {
     int q = which == 0 ? row - p : p + (row - (N - 1));
     double2 v = make_double2(0.0, 0.0);
@@ -53,6 +55,22 @@ __global__ void k_bubble_tables(const PointDesc *__restrict__ pts, const RhsIO *
       v = cadd(cmul(sp, gq), cmul(gp, sq));
     }
     (which == 0 ? P.Lpp : P.Lph)[(size_t)row * N + p] = v;
+    if (P.Lpp32) {
+      const float2 f = make_float2((float)v.x, (float)v.y);
+      (which == 0 ? P.Lpp32 : P.Lph32)[(size_t)row * N + p] = f;
+      m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+    }
+  }
+  if (P.Lmax) {
+    __shared__ float wm[32];
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float r = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, wm[w]);
+      P.Lmax[which * (2 * N - 1) + row] = r;
+    }
   }
 }
 
@@ -74,8 +92,8 @@ __device__ __forceinline__ double2 vload(const void *gam, int N, double U, int i
   if (inbox(N, i1) && inbox(N, i2) && inbox(N, i3) && inbox(N, i4)) {
     const size_t at = ((size_t)i1 * N + i2) * N + i3;
     if (SPLIT) {
-      float4 v = static_cast<const float4 *>(gam)[at];
-      return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+      const float2 v = static_cast<const float2 *>(gam)[at];
+      return make_double2((double)v.x, (double)v.y);
     }
     return static_cast<const double2 *>(gam)[at];
   }
@@ -110,6 +128,8 @@ __global__ void k_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restri
   if (lane == 0) {
     const double f = (*o.lam) * P.T;
     o.dsig[w] = make_double2(acc.x * f, acc.y * f);
+    // the contractions of this rhs have consumed the vertex bound: reset it
+    if (SPLIT && w == 0 && P.vmax) *P.vmax = 0u;
   }
 }
 

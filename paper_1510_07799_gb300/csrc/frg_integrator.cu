@@ -19,6 +19,8 @@ namespace frg {
 __constant__ double dC[7];
 __constant__ double dA[7][6];
 __constant__ double dE[7];  // b - bstar
+// float-pair splits of the same coefficients (split paths): x = hi + lo
+__constant__ float fAh[7][6], fAl[7][6], fEh[7], fEl[7];
 
 static const double hC[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
 static const double hA[7][6] = {
@@ -38,6 +40,19 @@ int upload_tableau() {
   if (cudaMemcpyToSymbol(dC, hC, sizeof(hC)) != cudaSuccess) return -3;
   if (cudaMemcpyToSymbol(dA, hA, sizeof(hA)) != cudaSuccess) return -3;
   if (cudaMemcpyToSymbol(dE, E, sizeof(E)) != cudaSuccess) return -3;
+  float ah[7][6], al[7][6], eh[7], el[7];
+  for (int i = 0; i < 7; ++i) {
+    for (int j = 0; j < 6; ++j) {
+      ah[i][j] = (float)hA[i][j];
+      al[i][j] = (float)(hA[i][j] - (double)ah[i][j]);
+    }
+    eh[i] = (float)E[i];
+    el[i] = (float)(E[i] - (double)eh[i]);
+  }
+  if (cudaMemcpyToSymbol(fAh, ah, sizeof(ah)) != cudaSuccess) return -3;
+  if (cudaMemcpyToSymbol(fAl, al, sizeof(al)) != cudaSuccess) return -3;
+  if (cudaMemcpyToSymbol(fEh, eh, sizeof(eh)) != cudaSuccess) return -3;
+  if (cudaMemcpyToSymbol(fEl, el, sizeof(el)) != cudaSuccess) return -3;
   return 0;
 }
 
@@ -100,7 +115,7 @@ __global__ void k_set_stage_io(const PointDesc *__restrict__ pts, Ctl *__restric
   const double2 *ycur = P.ybuf[c.yslot];
   const double2 *ycand = P.ybuf[c.yslot ^ 1];
   if (split) {
-    o.gam = P.Ysplit;
+    o.gam = P.Y32;
     o.sig = P.Y64;
   } else {
     const double2 *src = stage == 0 ? ycur : (stage < 6 ? P.Y64 : ycand);
@@ -147,10 +162,24 @@ __global__ void k_prepare(const PointDesc *__restrict__ pts, Ctl *__restrict__ c
   c.nonfinite = 0;
 }
 
+// Block-wide max of a non-negative float, folded into *dst (float bits).
+__device__ __forceinline__ void block_max_to(float v, unsigned *dst) {
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  __shared__ float wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+    if (!(m <= 3.0e38f)) m = 3.0e38f;  // a non-finite state is caught by the error norm
+    atomicMax(dst, __float_as_uint(m));
+  }
+}
+
 // ---------------------------------------------------------- stage sums ----
 // Y_s = y + h sum_{j<s} a_sj k_j, FP64.  Stage 6 (the seventh) is the fifth-order
-// candidate and is also kept in FP64 as ynew.  Split path: the vertex part of
-// Y_s is stored as float pairs for the contraction, the self-energy part in FP64.
+// candidate and is also kept in FP64 as ynew.  Split paths: the vertex part of
+// Y_s is stored rounded to FP32 for the contraction, the self-energy part in FP64.
 template <bool SPLIT>
 __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl,
                                                SegTable seg, int s) {
@@ -167,6 +196,7 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
   double a[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) a[j] = dA[s][j];
+  float vm = 0.f;
   for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
     const int i = base + e;
     if (i >= n) break;
@@ -199,10 +229,13 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
     const double2 yi = y[i];
     const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
     if (SPLIT) {
-      if (i < n3)
-        P.Ysplit[i] = split_c128(Y);
-      else
+      if (i < n3) {
+        const float2 f = round_c64(Y);
+        P.Y32[i] = f;
+        vm = fmaxf(vm, fmaxf(fabsf(f.x), fabsf(f.y)));
+      } else {
         P.Y64[i - n3] = Y;
+      }
       if (s == 6) ynew[i] = Y;
     } else {
       if (s < 6)
@@ -210,6 +243,166 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
       else
         ynew[i] = Y;
     }
+  }
+  if (SPLIT) block_max_to(vm, P.vmax);
+}
+
+// ------------------------------------------------- split-path stages ----
+// The split paths feed the contraction an FP32 vertex, so a stage input Y_s
+// (s = 1..5) is only needed to FP32 accuracy: Y_s = y + h sum_j a_sj k_j is
+// evaluated with y as a float pair (48 bits), the sum of the FP32 k_j in
+// float-float, and rounded once.  The seventh stage (the candidate that becomes
+// the state) is formed in FP64: ynew = y + h S with S the float-float sum
+// widened to FP64.  Stage 0 only prepares the float pairs of y.  The
+// self-energy part stays in FP64 throughout.
+template <int S>
+__global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl,
+                                                     SegTable seg) {
+  const int b = blockIdx.x;
+  const int pi = seg.point[b];
+  const Ctl &c = ctl[pi];
+  if (c.done) return;
+  const PointDesc &P = pts[pi];
+  const int n3 = P.n3, n = n3 + P.N;
+  const int base = seg.base[b];
+  const int ys = c.yslot;
+  const double h = c.h;
+  const float h_hi = d2f(h), h_lo = d2f(h - f2d(h_hi));
+  float vm = 0.f;
+  for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
+    const int i = base + e;
+    if (i >= n) break;
+    if (i < n3) {
+      float2 out;
+      if (S == 0) {
+        const double2 y = P.ybuf[ys][i];
+        const float2 hi = make_float2(d2f(y.x), d2f(y.y));
+        P.yhi[ys][i] = hi;
+        P.ylo[ys][i] = make_float2(d2f(y.x - f2d(hi.x)), d2f(y.y - f2d(hi.y)));
+        out = hi;
+      } else {
+        float sr = 0.f, srl = 0.f, si = 0.f, sil = 0.f;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          const float2 k = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
+          ff_mac(sr, srl, fAh[S][j], fAl[S][j], k.x);
+          ff_mac(si, sil, fAh[S][j], fAl[S][j], k.y);
+        }
+        if (S < 6) {
+          const float2 yh = P.yhi[ys][i], yl = P.ylo[ys][i];
+          float res[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float Sh = q ? si : sr, Sl = q ? sil : srl;
+            const float p = __fmul_rn(h_hi, Sh);
+            const float pe = __fmaf_rn(h_hi, Sh, -p);
+            const float rest = __fmaf_rn(h_hi, Sl, __fmul_rn(h_lo, Sh));
+            float s0, e0;
+            two_sum(q ? yh.y : yh.x, p, s0, e0);
+            res[q] = __fadd_rn(s0, __fadd_rn(__fadd_rn(q ? yl.y : yl.x, e0), __fadd_rn(pe, rest)));
+          }
+          out = make_float2(res[0], res[1]);
+        } else {
+          const double2 y = P.ybuf[ys][i];
+          const double Sr = f2d(sr) + f2d(srl), Si = f2d(si) + f2d(sil);
+          const double2 yn = make_double2(fma(h, Sr, y.x), fma(h, Si, y.y));
+          P.ybuf[ys ^ 1][i] = yn;
+          const float2 hi = make_float2(d2f(yn.x), d2f(yn.y));
+          P.yhi[ys ^ 1][i] = hi;
+          P.ylo[ys ^ 1][i] = make_float2(d2f(yn.x - f2d(hi.x)), d2f(yn.y - f2d(hi.y)));
+          out = hi;
+        }
+      }
+      P.Y32[i] = out;
+      vm = fmaxf(vm, fmaxf(fabsf(out.x), fabsf(out.y)));
+    } else {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < (S < 6 ? S : 6); ++j) {
+        const double2 k = P.kS[c.kslot[j]][i - n3];
+        acc.x += dA[S][j] * k.x;
+        acc.y += dA[S][j] * k.y;
+      }
+      const double2 yi = P.ybuf[ys][i];
+      const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
+      P.Y64[i - n3] = Y;
+      if (S == 6) P.ybuf[ys ^ 1][i] = Y;
+    }
+  }
+  block_max_to(vm, P.vmax);
+}
+
+// Error estimate of the split paths: e = h sum_j (b_j - bstar_j) k_j with the
+// FP32 k_j summed in float-float; the scaled ratio |e| / (atol + rtol max(|y|,
+// |ynew|)) of every vertex component in FP32, of the self-energy in FP64.
+__global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+                                                     SegTable seg) {
+  const int b = blockIdx.x;
+  const int pi = seg.point[b];
+  Ctl &c = ctl[pi];
+  if (c.done) return;
+  const PointDesc &P = pts[pi];
+  const int n3 = P.n3, n = n3 + P.N;
+  const int base = seg.base[b];
+  const int ys = c.yslot;
+  const double h = c.h;
+  const float hf = d2f(h), atolf = d2f(P.atol), rtolf = d2f(P.rtol);
+  float fmax_ = 0.f;
+  double dmax = 0.0;
+  int bad = 0;
+  for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
+    const int i = base + e;
+    if (i >= n) break;
+    if (i < n3) {
+      float er = 0.f, erl = 0.f, ei = 0.f, eil = 0.f;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const float2 k = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
+        ff_mac(er, erl, fEh[j], fEl[j], k.x);
+        ff_mac(ei, eil, fEh[j], fEl[j], k.y);
+      }
+      const float2 y = P.yhi[ys][i], yn = P.yhi[ys ^ 1][i];
+      const float rx = fabsf(hf * __fadd_rn(er, erl)) / (atolf + rtolf * fmaxf(fabsf(y.x), fabsf(yn.x)));
+      const float ry = fabsf(hf * __fadd_rn(ei, eil)) / (atolf + rtolf * fmaxf(fabsf(y.y), fabsf(yn.y)));
+      if (!isfinite(rx) || !isfinite(ry) || !isfinite(yn.x) || !isfinite(yn.y)) bad = 1;
+      else fmax_ = fmaxf(fmax_, fmaxf(rx, ry));
+    } else {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const double2 k = P.kS[c.kslot[j]][i - n3];
+        acc.x += dE[j] * k.x;
+        acc.y += dE[j] * k.y;
+      }
+      const double2 yi = P.ybuf[ys][i], yni = P.ybuf[ys ^ 1][i];
+      const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(fabs(yi.x), fabs(yni.x)));
+      const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(fabs(yi.y), fabs(yni.y)));
+      if (!isfinite(rx) || !isfinite(ry) || !isfinite(yni.x) || !isfinite(yni.y)) bad = 1;
+      else dmax = fmax(dmax, fmax(rx, ry));
+    }
+  }
+  double emax = fmax(dmax, f2d(fmax_));
+  for (int off = 16; off > 0; off >>= 1) {
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  __shared__ double wmax[8];
+  __shared__ int wbad[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    wmax[wid] = emax;
+    wbad[wid] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    int bb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, wmax[w]);
+      bb |= wbad[w];
+    }
+    atomicMax(&c.errbits, (unsigned long long)__double_as_longlong(m));
+    if (bb) atomicOr(&c.nonfinite, 1);
   }
 }
 
@@ -355,17 +548,26 @@ int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st) {
 
 int launch_stage(const PointDesc *d_pts, const Ctl *d_ctl, SegTable seg, int nblk, int s, int split,
                  cudaStream_t st) {
-  if (split)
-    k_stage<true><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s);
-  else
+  if (split) {
+    switch (s) {
+      case 0: k_stage_split<0><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      case 1: k_stage_split<1><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      case 2: k_stage_split<2><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      case 3: k_stage_split<3><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      case 4: k_stage_split<4><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      case 5: k_stage_split<5><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      default: k_stage_split<6><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+    }
+  } else {
     k_stage<false><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s);
+  }
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int split, cudaStream_t st) {
   if (split)
-    k_error<true><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
+    k_error_split<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
   else
     k_error<false><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
   FRG_COUNT(1);

@@ -1,0 +1,151 @@
+// frg_layout.cu -- vertex layouts for the split-precision contraction.
+//
+// Every operand row of the three channel products is a contiguous run in one
+// of three layouts of the FP32 vertex (N = natural [i1][i2][i3],
+// W = [i2][i3][i1], X = [i1][i3][i2]); the direct particle-hole operands reach
+// that form through crossing symmetry V(k1,k2,k3) = V(k2,k1,k4):
+//   pp : Left (a, s-a, p)            N   Right (p, s-p, k3)            N
+//   dph: A (k1, p, k1+t)             X   B (p-t, k2, p)                X
+//        C (k1, p, p-t)=(p,k1,k1+t)  W   D (p-t,k2,k2-t)=(k2,p-t,p)    W
+//   xph: Left (p, k3+Q, k3)          W   Right (k1, p+Q, p)            W
+// and each channel's output tile is a run of rows in one layout as well
+// (pp: N, dph: X, xph: W).  k_relayout writes the W and X copies of the stage
+// input; k_combine adds the three channel outputs into the natural layout.
+// Both move 16^3 tiles through shared memory so that every global access is a
+// 128-byte row.
+#include "frg_common.cuh"
+#include "frg_layout.cuh"
+
+namespace frg {
+
+namespace {
+constexpr int TB = 16;
+constexpr int S2 = TB + 1;           // smem stride of i2
+constexpr int S1 = TB * S2 + 1;      // smem stride of i1
+constexpr int TILE_SMEM = TB * S1;   // float2 elements
+
+struct Tile {
+  int N, g1, g2, g3;
+  bool ok;
+};
+
+__device__ __forceinline__ Tile tile_of(const PointDesc &P) {
+  Tile t;
+  t.N = P.N;
+  const int nt = (P.N + TB - 1) / TB;
+  const int tile = blockIdx.x;
+  t.ok = tile < nt * nt * nt;
+  t.g1 = (tile / (nt * nt)) * TB;
+  t.g2 = ((tile / nt) % nt) * TB;
+  t.g3 = (tile % nt) * TB;
+  return t;
+}
+__device__ __forceinline__ int sidx(int i1, int i2, int i3) { return i1 * S1 + i2 * S2 + i3; }
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                                  int want_w, int want_x) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  const Tile t = tile_of(P);
+  if (!t.ok) return;
+  __shared__ float2 sm[TILE_SMEM];
+  const float2 *__restrict__ Y = static_cast<const float2 *>(o.gam);
+  const int N = t.N;
+#pragma unroll
+  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+    const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
+    const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+    if (a < N && b < N && c < N) sm[sidx(i1, i2, i3)] = Y[((size_t)a * N + b) * N + c];
+  }
+  __syncthreads();
+  if (want_w) {
+  #pragma unroll
+  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+      const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
+      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      if (a < N && b < N && c < N) P.Y32W[((size_t)b * N + c) * N + a] = sm[sidx(i1, i2, i3)];
+    }
+  }
+  if (want_x) {
+  #pragma unroll
+  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+      const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
+      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      if (a < N && b < N && c < N) P.Y32X[((size_t)a * N + c) * N + b] = sm[sidx(i1, i2, i3)];
+    }
+  }
+}
+
+// k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels.
+__global__ void __launch_bounds__(256) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                                 int mask) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  const Tile t = tile_of(P);
+  if (!t.ok) return;
+  __shared__ float2 sm[TILE_SMEM];
+  const int N = t.N;
+#pragma unroll
+  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+    const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
+    const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+    if (a < N && b < N && c < N)
+      sm[sidx(i1, i2, i3)] = (mask & 2) ? P.PX[((size_t)a * N + c) * N + b] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if (mask & 4) {
+  #pragma unroll
+  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+      const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
+      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      if (a < N && b < N && c < N) {
+        const float2 w = P.PW[((size_t)b * N + c) * N + a];
+        float2 &v = sm[sidx(i1, i2, i3)];
+        v.x += w.x;
+        v.y += w.y;
+      }
+    }
+    __syncthreads();
+  }
+  float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
+#pragma unroll
+  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+    const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
+    const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+    if (a < N && b < N && c < N) {
+      const size_t at = ((size_t)a * N + b) * N + c;
+      float2 v = sm[sidx(i1, i2, i3)];
+      if (mask & 1) {
+        const float2 p = K[at];
+        v.x += p.x;
+        v.y += p.y;
+      }
+      K[at] = v;
+    }
+  }
+}
+
+static inline int ntiles(int maxN) {
+  const int nt = (maxN + TB - 1) / TB;
+  return nt * nt * nt;
+}
+
+int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int want_w, int want_x,
+                    cudaStream_t st) {
+  k_relayout<<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, want_w, want_x);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
+  k_combine<<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, mask);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace frg

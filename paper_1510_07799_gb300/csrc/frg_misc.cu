@@ -48,19 +48,29 @@ int launch_zero_vertex(const PointDesc *d_pts, const RhsIO *d_io, int n, int max
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-__global__ void k_split_input(float4 *ys, double2 *s64, const double2 *g, const double2 *sig, int n3, int N) {
+__global__ void k_split_input(float2 *ys, double2 *s64, const double2 *g, const double2 *sig, int n3, int N,
+                              unsigned *vmax) {
+  float vm = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3 + N; i += gridDim.x * blockDim.x) {
-    if (i < n3)
-      ys[i] = split_c128(g[i]);
-    else
+    if (i < n3) {
+      const float2 f = round_c64(g[i]);
+      ys[i] = f;
+      vm = fmaxf(vm, fmaxf(fabsf(f.x), fabsf(f.y)));
+    } else {
       s64[i - n3] = sig ? sig[i - n3] : make_double2(0.0, 0.0);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, off));
+  if ((threadIdx.x & 31) == 0) {
+    if (!(vm <= 3.0e38f)) vm = 3.0e38f;
+    atomicMax(vmax, __float_as_uint(vm));
   }
 }
 
-int launch_split_input(float4 *ysplit, double2 *s64, const double2 *gam, const double2 *sig, int n3, int N,
-                       cudaStream_t st) {
+int launch_split_input(float2 *ysplit, double2 *s64, const double2 *gam, const double2 *sig, int n3, int N,
+                       unsigned *vmax, cudaStream_t st) {
   const int blocks = (n3 + N + 255) / 256 < 4096 ? (n3 + N + 255) / 256 : 4096;
-  k_split_input<<<blocks, 256, 0, st>>>(ysplit, s64, gam, sig, n3, N);
+  k_split_input<<<blocks, 256, 0, st>>>(ysplit, s64, gam, sig, n3, N, vmax);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

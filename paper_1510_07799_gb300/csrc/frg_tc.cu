@@ -1,17 +1,790 @@
-// frg_tc.cu -- split-precision contractions (tcgen05); placeholder until the
-// tensor-core path lands: creating a split-precision plan fails loudly.
+// frg_tc.cu -- split-precision channel contractions of the one-loop SIAM flow on
+// the sm_103a tensor cores (tcgen05.mma, accumulators in TMEM).
+//
+// For every channel and transfer frequency m the rhs needs the complex product
+//   Out[r][c] = sum_k Left[r][k] Right[k][c]
+// (the three one-loop diagrams of the paper, Sec. 4, reordered per transfer;
+// index sets in frg_common.cuh).  One CTA tile is 64 complex rows x NT complex
+// columns.  The complex product runs as one real product with the 2x2 real form
+// on the left operand:
+//   A' rows 0..63   = [ Re a | -Im a ] ,  A' rows 64..127 = [ Im a | Re a ]
+//   B' row c        = [ Re b | Im b ]          (K-major, 16 complex k per step)
+// so that (A' B'^T)[r] = Re(a b)[r], [r+64] = Im(a b)[r]; M = 128, N = NT, K = 8
+// (TF32) per instruction.
+//
+// Split-TF32 (3xTF32): x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the
+// product keeps hi*hi (accumulator group 0) and hi*lo + lo*hi (group 1), FP32
+// accumulation in TMEM, groups added in the epilogue.
+//
+// BF16x3: every operand is scaled by a power of two 2^-e with 2^e above a bound
+// on its magnitude (the vertex maximum for Right; that times the bubble-weight
+// row maximum, x3 for the direct particle-hole combination, for Left) and cut
+// into three 8-bit slices on the fixed grids 2^-7, 2^-15, 2^-23:
+//   s1 = rint(2^7 x)/2^7, s2 = rint(2^15 (x - s1))/2^15, s3 = rint(2^23 (x-s1-s2))/2^23.
+// Products of first slices are integers times 2^(eA+eB-14) bounded by 2^14, so
+// their sum over K' <= 1024 terms is exact in the FP32 accumulator whatever the
+// accumulator's rounding (group 0); the five products of order <= 4 beyond it
+// go to group 1.  This is the error-free splitting idea of Ozaki et al. applied
+// with bf16 slices.
+//
+// Roles (one persistent CTA per SM, static strided tile order over a list sorted
+// heavy-first, the strided static distribution of the paper's Sec. 5.1):
+//   warps 0-3  epilogue: TMEM -> registers -> smem staging -> coalesced rows of
+//              the channel's output layout (frg_layout.cu)
+//   warp  4    TMEM allocation and MMA issue (one elected lane)
+//   warps 5-20 producers in two groups that take alternate k-steps (two k-steps
+//              of loads in flight): load the operand rows of a k-step
+//              (contiguous runs of the FP32 vertex layouts, L2-resident), fold
+//              in diag(Lb), split, write swizzled K-major smem tiles
+// Pipelines: NSTAGE smem stages (full/empty mbarriers), two TMEM accumulator
+// buffers (tfull/tempty mbarriers).  Every wait is bounded; a wait that runs out
+// sets the context error word, and all roles then leave their loops.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "frg_layout.cuh"
 #include "frg_tc.cuh"
 
 namespace frg {
-struct TcPlan {
-  int dummy;
+
+namespace tc {
+
+constexpr int NT_MAX = 128;         // complex columns per tile
+constexpr int MROWS = 64;           // complex rows per tile (128 real rows)
+constexpr int KSTEP = 16;           // complex k per pipeline stage (32 real K')
+constexpr int STAGING_BYTES = MROWS * 33 * 8;   // 64 rows x 32 cols float2, row pitch 33
+constexpr int N_EPI_WARPS = 4, MMA_WARP = 4, N_PROD_WARPS = 16;
+constexpr int THREADS = 32 * (N_EPI_WARPS + 1 + N_PROD_WARPS);
+constexpr int PROD_THREADS = 32 * N_PROD_WARPS;
+constexpr int GROUP_THREADS = PROD_THREADS / 2;  // producers of one k-step parity
+constexpr int TMEM_COLS = 512;      // 2 buffers x 2 groups x 128 columns
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+// Per-precision layout of one pipeline stage.  K' = 32 real values per row:
+// 128 B rows (TF32, 128-byte swizzle) or 64 B rows (BF16, 64-byte swizzle).
+template <int PREC>
+struct Tr;
+template <>
+struct Tr<FRG_3XTF32> {
+  static constexpr int SLICES = 2, ROWB = 128, NSTAGE = 3, SWZ_MODE = 2, ATOM = 1024, KINSTR = 8;
 };
-int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &, const std::vector<frg_params> &, int,
-                   const PointDesc *, std::string &why) {
-  *out = nullptr;
-  why = "split-precision contraction is not available in this build";
-  return FRG_EINVAL;
+template <>
+struct Tr<FRG_BF16X3> {
+  static constexpr int SLICES = 3, ROWB = 64, NSTAGE = 4, SWZ_MODE = 4, ATOM = 512, KINSTR = 16;
+};
+template <int PREC>
+struct Lay {
+  static constexpr int A_SLICE = 128 * Tr<PREC>::ROWB;
+  static constexpr int B_SLICE = NT_MAX * Tr<PREC>::ROWB;
+  static constexpr int STAGE = Tr<PREC>::SLICES * (A_SLICE + B_SLICE);
+  static constexpr int SMEM = 1024 + Tr<PREC>::NSTAGE * STAGE + STAGING_BYTES + 256;
+};
+
+struct TcWork {
+  int point, m, rt, ct;
+};
+
+// ---------------------------------------------------------------- PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-void tc_plan_destroy(TcPlan *plan) { delete plan; }
-int tc_run(TcPlan *, const PointDesc *, const RhsIO *, int, int, cudaStream_t, cudaEvent_t) { return -1; }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on a phase; returns false (and records the failure) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, volatile int *abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (gtime() - t0 > WAIT_NS) {
+        atomicOr(err, 1u);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Shared-memory matrix descriptor (K-major, swizzled): start address, stride
+// between 8-row atoms (SBO), version bits 46-48 = 0b001, swizzle mode.
+template <int PREC>
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((uint32_t)Tr<PREC>::ATOM >> 4) << 32;
+  d |= 1ull << 46;
+  d |= (uint64_t)Tr<PREC>::SWZ_MODE << 61;
+  return d;
+}
+// Instruction descriptor: D f32, A/B tf32 (kind::tf32) or bf16 (kind::f16),
+// both K-major, M = 128, N = n.
+template <int PREC>
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return (1u << 4) | ((PREC == FRG_3XTF32 ? 2u : 1u) << 7) | ((PREC == FRG_3XTF32 ? 2u : 1u) << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (PREC == FRG_3XTF32)
+    mma_tf32(d, a, b, id, acc);
+  else
+    mma_bf16(d, a, b, id, acc);
+}
+
+// Byte offset of 16-byte chunk `ch` of row `row` in a swizzled K-major tile:
+// 128-byte rows: chunk ^= row % 8 (8-row atoms of 1024 B);
+// 64-byte rows:  chunk ^= (row / 2) % 4 (8-row atoms of 512 B).
+template <int PREC>
+__device__ __forceinline__ uint32_t swz(int row, int ch) {
+  if (PREC == FRG_3XTF32) return (uint32_t)(row * 128 + ((ch ^ (row & 7)) << 4));
+  return (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4));
+}
+
+// ----------------------------------------------------------- operands ----
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Operand rows of the FP32 vertex layouts (see frg_layout.cu for the table).
+struct Srcs {
+  const float2 *YN, *YW, *YX;
+};
+
+struct TileInfo {
+  int point, N, NT, nk, r0, c0, D16;
+  Geom g;
+};
+
+// Left operand, K indices kq..kq+3 (never across a dph half), local row r.
+template <int CH>
+__device__ __forceinline__ void fetch_left(const PointDesc &P, const Srcs &S, const TileInfo &ti, int r, int kq,
+                                           float2 out[4]) {
+  const int N = ti.N;
+  const Geom &g = ti.g;
+  const int rr = ti.r0 + r;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[j] = make_float2(0.f, 0.f);
+  if (rr >= g.D) return;
+  if (CH == CH_PP) {
+    const int a = g.row_lo + rr, s = g.x;
+    const float2 *row = S.YN + ((size_t)a * N + (s - a)) * N;
+    const float2 *L = P.Lpp32 + (size_t)s * N;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = kq + j;
+      if (k < g.D) out[j] = cmulf(__ldg(row + g.p_lo + k), __ldg(L + g.p_lo + k));
+    }
+  } else if (CH == CH_XPH) {
+    const int k3 = g.row_lo + rr, Q = g.x;
+    const float2 *row = S.YW + ((size_t)(k3 + Q) * N + k3) * N;
+    const float2 *L = P.Lph32 + (size_t)(Q + N - 1) * N;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = kq + j;
+      if (k < g.D) out[j] = cmulf(__ldg(row + g.p_lo + k), __ldg(L + g.p_lo + k));
+    }
+  } else {
+    const int k1 = g.row_lo + rr, t = g.x;
+    const int half = kq >= ti.D16;
+    const int kl = kq - (half ? ti.D16 : 0);
+    const size_t ro = ((size_t)k1 * N + (k1 + t)) * N;
+    const float2 *rowA = S.YX + ro, *rowC = S.YW + ro;
+    const float2 *L = P.Lph32 + (size_t)(-t + N - 1) * N;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = kl + j;
+      if (k < g.D) {
+        const int p = g.p_lo + k;
+        const float2 A = __ldg(rowA + p), Lv = __ldg(L + p);
+        if (!half) {
+          const float2 C = __ldg(rowC + p);
+          out[j] = cmulf(make_float2(2.f * A.x - C.x, 2.f * A.y - C.y), Lv);
+        } else {
+          out[j] = cmulf(make_float2(-A.x, -A.y), Lv);
+        }
+      }
+    }
+  }
+}
+
+// Right operand, K indices kq..kq+3, absolute columns cc and cc+1 (cc even).
+template <int CH>
+__device__ __forceinline__ void fetch_right(const Srcs &S, const TileInfo &ti, float U, int kq, int cc, float2 v0[4],
+                                            float2 v1[4]) {
+  const int N = ti.N;
+  const Geom &g = ti.g;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v0[j] = v1[j] = make_float2(0.f, 0.f);
+  if (cc >= N) return;  // N even: cc + 1 < N as well
+  // columns whose fourth frequency leaves the box take the bare U
+  const int f0 = CH == CH_PP ? g.x - cc : (CH == CH_DPH ? cc - g.x : cc + g.x);
+  const int f1 = CH == CH_PP ? f0 - 1 : f0 + 1;
+  const bool ok0 = (unsigned)f0 < (unsigned)N, ok1 = (unsigned)f1 < (unsigned)N;
+  const int half = CH == CH_DPH ? (kq >= ti.D16) : 0;
+  const int kl = kq - (half ? ti.D16 : 0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = kl + j;
+    if (k >= g.D) continue;
+    const int p = g.p_lo + k;
+    const float2 *row;
+    if (CH == CH_PP)
+      row = S.YN + ((size_t)p * N + (g.x - p)) * N;
+    else if (CH == CH_XPH)
+      row = S.YW + ((size_t)(p + g.x) * N + p) * N;
+    else
+      row = (half ? S.YW : S.YX) + ((size_t)(p - g.x) * N + p) * N;
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(row + cc));
+    v0[j] = ok0 ? make_float2(x.x, x.y) : make_float2(U, 0.f);
+    v1[j] = ok1 ? make_float2(x.z, x.w) : make_float2(U, 0.f);
+  }
+}
+
+// Output row pointer (channel layout) of local row rr.
+template <int CH>
+__device__ __forceinline__ float2 *out_row(const PointDesc &P, float2 *kN, const TileInfo &ti, int rr) {
+  const int N = ti.N;
+  const Geom &g = ti.g;
+  if (CH == CH_PP) {
+    const int a = g.row_lo + rr;
+    return kN + ((size_t)a * N + (g.x - a)) * N;
+  } else if (CH == CH_DPH) {
+    const int k1 = g.row_lo + rr;
+    return P.PX + ((size_t)k1 * N + (k1 + g.x)) * N;
+  } else {
+    const int k3 = g.row_lo + rr;
+    return P.PW + ((size_t)(k3 + g.x) * N + k3) * N;
+  }
+}
+
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - hi);
+}
+
+// 2^e as a float for e in [-126, 127].
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// Exponent e with bound * (1 + 2^-20) < 2^e, clamped so that 2^-e and the slice
+// grids stay normal floats.
+__device__ __forceinline__ int bound_exp(float bound) {
+  if (!(bound > 0.f)) return 0;
+  int e;
+  frexpf(bound * (1.f + 9.5367431640625e-07f), &e);
+  return max(-90, min(100, e));
+}
+
+// Three bf16 slices of x on the grids 2^(e-7), 2^(e-15), 2^(e-23).
+__device__ __forceinline__ void slice3(float x, float inv, float sc, __nv_bfloat16 &a, __nv_bfloat16 &b,
+                                       __nv_bfloat16 &c) {
+  const float xs = x * inv;
+  const float s1 = rintf(xs * 128.f) * 0.0078125f;
+  const float r1 = xs - s1;
+  const float s2 = rintf(r1 * 32768.f) * 3.0517578125e-05f;
+  const float r2 = r1 - s2;
+  const float s3 = rintf(r2 * 8388608.f) * 1.1920928955078125e-07f;
+  a = __float2bfloat16_rn(s1 * sc);
+  b = __float2bfloat16_rn(s2 * sc);
+  c = __float2bfloat16_rn(s3 * sc);
+}
+
+template <int CH>
+__device__ __forceinline__ bool tile_info(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                          const TcWork &w, const int *__restrict__ nt_of, TileInfo &ti) {
+  ti.point = w.point;
+  const PointDesc &P = pts[w.point];
+  ti.N = P.N;
+  ti.NT = nt_of[w.point];
+  ti.g = geom(CH, P.N, w.m);
+  ti.D16 = (ti.g.D + KSTEP - 1) / KSTEP * KSTEP;
+  ti.nk = (CH == CH_DPH ? 2 : 1) * ti.D16 / KSTEP;
+  ti.r0 = w.rt * MROWS;
+  ti.c0 = w.ct * ti.NT;
+  return io[w.point].active != 0;
+}
+
+// Write 4 consecutive K' values (positions 4*g4 .. 4*g4+3 of a 32-wide row) of
+// every slice of one operand row.
+template <int PREC>
+struct Emit;
+template <>
+struct Emit<FRG_3XTF32> {
+  static constexpr int SL = 2;
+  float4 v[2];
+  __device__ __forceinline__ void make(const float x[4], float, float) {
+    split_tf32(x[0], v[0].x, v[1].x);
+    split_tf32(x[1], v[0].y, v[1].y);
+    split_tf32(x[2], v[0].z, v[1].z);
+    split_tf32(x[3], v[0].w, v[1].w);
+  }
+  __device__ __forceinline__ void neg() {
+    for (int i = 0; i < 2; ++i) v[i] = make_float4(-v[i].x, -v[i].y, -v[i].z, -v[i].w);
+  }
+  __device__ __forceinline__ void store(uint8_t *tile, int slice_bytes, int row, int g4) const {
+    for (int i = 0; i < 2; ++i)
+      *reinterpret_cast<float4 *>(tile + i * slice_bytes + swz<FRG_3XTF32>(row, g4)) = v[i];
+  }
+};
+template <>
+struct Emit<FRG_BF16X3> {
+  static constexpr int SL = 3;
+  uint2 v[3];
+  __device__ __forceinline__ void make(const float x[4], float inv, float sc) {
+    __nv_bfloat16 s[3][4];
+    for (int j = 0; j < 4; ++j) slice3(x[j], inv, sc, s[0][j], s[1][j], s[2][j]);
+    for (int i = 0; i < 3; ++i) {
+      __nv_bfloat162 lo = __halves2bfloat162(s[i][0], s[i][1]);
+      __nv_bfloat162 hi = __halves2bfloat162(s[i][2], s[i][3]);
+      v[i] = make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+    }
+  }
+  __device__ __forceinline__ void neg() {
+    for (int i = 0; i < 3; ++i) v[i] = make_uint2(v[i].x ^ 0x80008000u, v[i].y ^ 0x80008000u);
+  }
+  __device__ __forceinline__ void store(uint8_t *tile, int slice_bytes, int row, int g4) const {
+    for (int i = 0; i < 3; ++i)
+      *reinterpret_cast<uint2 *>(tile + i * slice_bytes + swz<FRG_BF16X3>(row, g4 >> 1) + (g4 & 1) * 8) = v[i];
+  }
+};
+
+// ------------------------------------------------------------- kernel ----
+template <int CH, int PREC>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_contract_tc(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const TcWork *__restrict__ work,
+                  int nwork, const int *__restrict__ nt_of, unsigned *__restrict__ err) {
+  using T = Tr<PREC>;
+  using LY = Lay<PREC>;
+  constexpr int NSTAGE = T::NSTAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *stages = smem;
+  float2 *staging = reinterpret_cast<float2 *>(smem + NSTAGE * LY::STAGE);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NSTAGE * LY::STAGE + STAGING_BYTES);
+  uint64_t *full = bars, *empty = bars + NSTAGE, *tfull = bars + 2 * NSTAGE, *tempty = bars + 2 * NSTAGE + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 4);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], GROUP_THREADS);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 32 * N_EPI_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp >= MMA_WARP + 1) {
+    // ------------------------------------------------------ producers ----
+    const int ptid = tid - 32 * (MMA_WARP + 1);
+    const uint32_t parity = ptid / GROUP_THREADS;
+    const int lt = ptid % GROUP_THREADS;
+    uint32_t it = 0;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      const bool active = tile_info<CH>(pts, io, work[wi], nt_of, ti);
+      if (!active) continue;
+      const PointDesc &P = pts[ti.point];
+      const Srcs S = {static_cast<const float2 *>(io[ti.point].gam), P.Y32W, P.Y32X};
+      const float U = (float)P.U;
+      float invA = 1.f, scA = 1.f, invB = 1.f, scB = 1.f;
+      if (PREC == FRG_BF16X3) {
+        const float vb = fmaxf(__uint_as_float(*P.vmax), fabsf(U));
+        const int m = work[wi].m;
+        const int row = (CH == CH_PP ? 0 : (2 * ti.N - 1)) + (CH == CH_DPH ? (2 * ti.N - 2 - m) : m);
+        const float lb = P.Lmax[row] * vb * (CH == CH_DPH ? 6.f : 2.f);
+        const int eB = bound_exp(vb), eA = bound_exp(lb);
+        invB = pow2f(-eB);
+        scB = pow2f(eB);
+        invA = pow2f(-eA);
+        scA = pow2f(eA);
+      }
+      // this thread's tasks: A' (row r, 4-k group qa); B' (column pair cp, 4-k group qb)
+      const int r = lt >> 2, qa = lt & 3;
+      const int half_nt = ti.NT / 2;
+      const bool has_b = lt < 2 * ti.NT;
+      const int cp = lt % half_nt, qb = lt / half_nt;
+      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+        if ((it & 1u) != parity) continue;
+        const int s = it % NSTAGE;
+        const uint32_t ph = (it / NSTAGE) & 1u;
+        const int k0 = kb * KSTEP;
+        float2 a[4], v0[4], v1[4];
+        fetch_left<CH>(P, S, ti, r, k0 + 4 * qa, a);
+        if (has_b) fetch_right<CH>(S, ti, U, k0 + 4 * qb, ti.c0 + 2 * cp, v0, v1);
+        if (!mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) goto prod_done;
+        {
+          uint8_t *A = stages + s * LY::STAGE;
+          float re[4], im[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            re[j] = a[j].x;
+            im[j] = a[j].y;
+          }
+          Emit<PREC> er, ei;
+          er.make(re, invA, scA);
+          ei.make(im, invA, scA);
+          er.store(A, LY::A_SLICE, r, qa);           // Re row, first half:  Re a
+          ei.store(A, LY::A_SLICE, r + 64, qa);      // Im row, first half:  Im a
+          er.store(A, LY::A_SLICE, r + 64, qa + 4);  // Im row, second half: Re a
+          ei.neg();
+          ei.store(A, LY::A_SLICE, r, qa + 4);       // Re row, second half: -Im a
+        }
+        if (has_b) {
+          uint8_t *B = stages + s * LY::STAGE + T::SLICES * LY::A_SLICE;
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const float2 *v = side ? v1 : v0;
+            float re[4], im[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              re[j] = v[j].x;
+              im[j] = v[j].y;
+            }
+            Emit<PREC> er, ei;
+            er.make(re, invB, scB);
+            ei.make(im, invB, scB);
+            er.store(B, LY::B_SLICE, 2 * cp + side, qb);
+            ei.store(B, LY::B_SLICE, 2 * cp + side, qb + 4);
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(&full[s]);
+      }
+    }
+  prod_done:;
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------------ MMA issue ----
+    uint32_t it = 0, tcount = 0;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
+      const int buf = tcount & 1;
+      if (!mbar_wait(&tempty[buf], ((tcount >> 1) & 1u) ^ 1u, err, abort_flag)) break;
+      tc_after();
+      const uint32_t d0 = tmem + (uint32_t)(buf * 256);  // group 0 columns
+      const uint32_t d1 = d0 + 128;                       // group 1 columns
+      const uint32_t id = idesc<PREC>(ti.NT);
+      bool ok = true;
+      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+        const int s = it % NSTAGE;
+        const uint32_t ph = (it / NSTAGE) & 1u;
+        if (!mbar_wait(&full[s], ph, err, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_after();
+        if (lane == 0) {
+          const uint32_t a0 = smem_u32(stages + s * LY::STAGE);
+          const uint32_t b0 = a0 + T::SLICES * LY::A_SLICE;
+          constexpr int NI = 32 / T::KINSTR;                                 // instructions per stage
+          constexpr int STEPB = T::KINSTR * (PREC == FRG_3XTF32 ? 4 : 2);  // bytes per instruction
+#pragma unroll
+          for (int kk = 0; kk < NI; ++kk) {
+            const uint32_t off = kk * STEPB;
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            auto A_ = [&](int i) { return sdesc<PREC>(a0 + i * LY::A_SLICE + off); };
+            auto B_ = [&](int i) { return sdesc<PREC>(b0 + i * LY::B_SLICE + off); };
+            mma<PREC>(d0, A_(0), B_(0), id, first);  // leading slices
+            mma<PREC>(d1, A_(0), B_(1), id, first);
+            mma<PREC>(d1, A_(1), B_(0), id, 1u);
+            if (PREC == FRG_BF16X3) {
+              mma<PREC>(d1, A_(0), B_(2), id, 1u);
+              mma<PREC>(d1, A_(1), B_(1), id, 1u);
+              mma<PREC>(d1, A_(2), B_(0), id, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(&tfull[buf]);
+      __syncwarp();
+      ++tcount;
+    }
+  } else {
+    // ------------------------------------------------------- epilogue ----
+    uint32_t tcount = 0;
+    const int row_t = warp * 32 + lane;  // TMEM lane = real row of A'
+    const int crow = row_t & 63, comp = row_t >> 6;
+    const int etid = tid;  // 0..127
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
+      const int buf = tcount & 1;
+      if (!mbar_wait(&tfull[buf], (tcount >> 1) & 1u, err, abort_flag)) break;
+      tc_after();
+      const PointDesc &P = pts[ti.point];
+      const RhsIO &o = io[ti.point];
+      const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
+      float2 *kN = static_cast<float2 *>(o.dgam);
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 256);
+      for (int cb = 0; cb < ti.NT; cb += 32) {
+        float g0[32], g1[32];
+        tmem_ld32(tl + cb, g0);
+        tmem_ld32(tl + 128 + cb, g1);
+        tmem_wait_ld();
+        float *st = reinterpret_cast<float *>(staging);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) st[(crow * 33 + j) * 2 + comp] = (g0[j] + g1[j]) * sc;
+        named_bar(1, 32 * N_EPI_WARPS);
+        // each warp stores whole 32-column runs of output rows
+#pragma unroll 4
+        for (int i = 0; i < (MROWS * 32) / (32 * N_EPI_WARPS); ++i) {
+          const int idx = i * 32 * N_EPI_WARPS + etid;
+          const int r = idx >> 5, c = idx & 31;
+          const int rr = ti.r0 + r, cc = ti.c0 + cb + c;
+          if (rr < ti.g.D && cc < ti.N && cb + c < ti.NT) out_row<CH>(P, kN, ti, rr)[cc] = staging[r * 33 + c];
+        }
+        named_bar(1, 32 * N_EPI_WARPS);
+      }
+      tc_before();
+      mbar_arrive(&tempty[buf]);
+      ++tcount;
+    }
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  if (warp == MMA_WARP) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace tc
+
+// --------------------------------------------------------------- plan ----
+struct TcPlan {
+  int precision = FRG_3XTF32;
+  int sms = 0;
+  int n = 0;
+  int *d_nt = nullptr;
+  unsigned *d_err = nullptr;  // owned by the context
+  tc::TcWork *d_all[3] = {nullptr, nullptr, nullptr};
+  int nall[3] = {0, 0, 0};
+  tc::TcWork *d_pt[3] = {nullptr, nullptr, nullptr};
+  std::vector<int> off[3];
+};
+
+template <int PREC>
+static bool set_smem_attrs() {
+  bool ok = true;
+#define FRG_SETATTR(C)                                                                                   \
+  ok = ok && cudaFuncSetAttribute(tc::k_contract_tc<C, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  tc::Lay<PREC>::SMEM) == cudaSuccess
+  FRG_SETATTR(CH_PP);
+  FRG_SETATTR(CH_DPH);
+  FRG_SETATTR(CH_XPH);
+#undef FRG_SETATTR
+  return ok;
+}
+
+int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
+                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why) {
+  (void)params;
+  (void)d_pts;
+  *out = nullptr;
+  if (precision != FRG_3XTF32 && precision != FRG_BF16X3) {
+    why = "unknown split precision";
+    return FRG_EINVAL;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    why = "cudaGetDeviceProperties failed";
+    return FRG_ECUDA;
+  }
+  if (prop.major != 10 || prop.minor != 3) {
+    why = "the split-precision contraction is built for sm_103a (GB300)";
+    return FRG_EINVAL;
+  }
+  TcPlan *p = new TcPlan();
+  p->precision = precision;
+  p->sms = prop.multiProcessorCount;
+  p->n = (int)pts.size();
+  p->d_err = d_err;
+  std::vector<int> nt(p->n);
+  for (int i = 0; i < p->n; ++i) nt[i] = std::min(tc::NT_MAX, (pts[i].N + 15) / 16 * 16);
+  bool ok = cudaMalloc(&p->d_nt, sizeof(int) * p->n) == cudaSuccess &&
+            cudaMemcpy(p->d_nt, nt.data(), sizeof(int) * p->n, cudaMemcpyHostToDevice) == cudaSuccess;
+  for (int ch = 0; ch < 3 && ok; ++ch) {
+    std::vector<std::pair<int, tc::TcWork>> all, one;
+    std::vector<tc::TcWork> per;
+    p->off[ch].push_back(0);
+    for (int i = 0; i < p->n; ++i) {
+      one.clear();
+      const int N = pts[i].N;
+      for (int m = 0; m < 2 * N - 1; ++m) {
+        Geom g = geom(ch, N, m);
+        const int nk = (g.K + tc::KSTEP - 1) / tc::KSTEP;
+        for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
+          for (int ct = 0; ct * nt[i] < N; ++ct) one.push_back({nk, tc::TcWork{i, m, rt, ct}});
+      }
+      std::stable_sort(one.begin(), one.end(), [](auto &a, auto &b) { return a.first > b.first; });
+      for (auto &x : one) per.push_back(x.second);
+      all.insert(all.end(), one.begin(), one.end());
+      p->off[ch].push_back((int)per.size());
+    }
+    std::stable_sort(all.begin(), all.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    std::vector<tc::TcWork> allw;
+    for (auto &x : all) allw.push_back(x.second);
+    p->nall[ch] = (int)allw.size();
+    ok = cudaMalloc(&p->d_all[ch], sizeof(tc::TcWork) * allw.size()) == cudaSuccess &&
+         cudaMalloc(&p->d_pt[ch], sizeof(tc::TcWork) * per.size()) == cudaSuccess &&
+         cudaMemcpy(p->d_all[ch], allw.data(), sizeof(tc::TcWork) * allw.size(), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemcpy(p->d_pt[ch], per.data(), sizeof(tc::TcWork) * per.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  ok = ok && (precision == FRG_3XTF32 ? set_smem_attrs<FRG_3XTF32>() : set_smem_attrs<FRG_BF16X3>());
+  if (!ok) {
+    why = std::string("tensor-core plan setup failed: ") + cudaGetErrorString(cudaGetLastError());
+    tc_plan_destroy(p);
+    return FRG_ECUDA;
+  }
+  *out = p;
+  return FRG_OK;
+}
+
+void tc_plan_destroy(TcPlan *p) {
+  if (!p) return;
+  cudaFree(p->d_nt);
+  for (int ch = 0; ch < 3; ++ch) {
+    cudaFree(p->d_all[ch]);
+    cudaFree(p->d_pt[ch]);
+  }
+  delete p;
+}
+
+template <int PREC>
+static void launch_one(int ch, int grid, cudaStream_t st, const PointDesc *d_pts, const RhsIO *d_io,
+                       const tc::TcWork *w, int nw, const int *d_nt, unsigned *d_err) {
+  const int smem = tc::Lay<PREC>::SMEM;
+  if (ch == CH_PP)
+    tc::k_contract_tc<CH_PP, PREC><<<grid, tc::THREADS, smem, st>>>(d_pts, d_io, w, nw, d_nt, d_err);
+  else if (ch == CH_DPH)
+    tc::k_contract_tc<CH_DPH, PREC><<<grid, tc::THREADS, smem, st>>>(d_pts, d_io, w, nw, d_nt, d_err);
+  else
+    tc::k_contract_tc<CH_XPH, PREC><<<grid, tc::THREADS, smem, st>>>(d_pts, d_io, w, nw, d_nt, d_err);
+}
+
+int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
+           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN) {
+  if (chmask & 6) {
+    if (launch_relayout(d_pts, d_io, n_points, maxN, 1, (chmask & 2) != 0, st) != 0) return -3;
+  }
+  if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
+  for (int ch = 0; ch < 3; ++ch) {
+    if (!(chmask & (1 << ch))) continue;
+    const tc::TcWork *w;
+    int nw;
+    if (point < 0) {
+      w = p->d_all[ch];
+      nw = p->nall[ch];
+    } else {
+      w = p->d_pt[ch] + p->off[ch][point];
+      nw = p->off[ch][point + 1] - p->off[ch][point];
+    }
+    if (!nw) continue;
+    const int grid = std::min(nw, p->sms);
+    if (p->precision == FRG_3XTF32)
+      launch_one<FRG_3XTF32>(ch, grid, st, d_pts, d_io, w, nw, p->d_nt, p->d_err);
+    else
+      launch_one<FRG_BF16X3>(ch, grid, st, d_pts, d_io, w, nw, p->d_nt, p->d_err);
+    FRG_COUNT(1);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+  }
+  if (ev_contract && cudaEventRecord(ev_contract, st) != cudaSuccess) return -3;
+  // channel outputs in their own layouts -> natural layout (the scatter-add)
+  if (chmask & 6) {
+    if (launch_combine(d_pts, d_io, n_points, maxN, chmask, st) != 0) return -3;
+  }
+  return 0;
+}
+
 }  // namespace frg

@@ -9,12 +9,15 @@
 
 namespace frg {
 struct TcPlan;
+// d_err: device word that a kernel whose bounded wait ran out sets non-zero.
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
-                   int precision, const PointDesc *d_pts, std::string &why);
+                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why);
 void tc_plan_destroy(TcPlan *plan);
 // Evaluate the enabled vertex channels of every active point (point = -1) or of
 // one point, writing the float2 vertex output of each active RhsIO.
-// ev_mid (optional) is recorded between the operand gather and the contraction.
+// Relayout of the stage input, the channel products, and the combine into the
+// natural layout.  ev_gather / ev_contract (optional) are recorded after the
+// relayout and after the products.
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
-           cudaEvent_t ev_mid);
+           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN);
 }  // namespace frg

@@ -198,13 +198,13 @@ class Context:
 
     def rhs_timed(self, point, Lambda, gamma, sigma, dgamma, dsigma):
         """Like rhs(); returns the phase durations in ms (bubble weights, operand
-        gather, contraction, self-energy) measured with CUDA events on the
-        context stream."""
+        regather, channel contractions, combine, self-energy) measured with CUDA
+        events on the context stream."""
         N = self.N(point)
         _check_dev(gamma, (N, N, N), "gamma")
         _check_dev(dgamma, (N, N, N), "dgamma")
         _check_dev(dsigma, (N,), "dsigma")
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 5)()
         self._chk(load().frg_rhs_timed(self._h, point, Lambda, _ptr(gamma), _ptr(sigma),
                                        _ptr(dgamma), _ptr(dsigma), ms))
         return list(ms)

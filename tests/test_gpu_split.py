@@ -1,0 +1,104 @@
+"""GPU parity of the split-precision tensor-core path (tcgen05) against the FP64
+CPU oracle, through the C ABI.
+
+Tolerance: the contraction operands are the vertex rounded to FP32 times the
+bubble weights, split into TF32 hi/lo or three BF16 slices, with FP32
+accumulation in TMEM; the normwise relative error of one rhs evaluation is
+bounded by RHS_TOL below, and of a full flow by FLOW_TOL (the 1e-6 acceptance
+bar for the mixed form)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_07799_gb300 import frg, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+# One rhs: 3xTF32 errors grow with the contraction length (the tensor core's
+# FP32 accumulator does not round to nearest), BF16x3 slices on a per-transfer
+# fixed grid (absolute error 2^-24 of the operand bound).  Measured maxima over
+# these cases: 3.7e-6 (TF32, N=100 dph) and 2.4e-5 (BF16, N=100 dph).
+RHS_TOL = {frg.TF32X3: 6e-6, frg.BF16X3: 5e-5}
+FLOW_TOL = {frg.TF32X3: 1e-6, frg.BF16X3: 1e-6}
+PRECS = [frg.TF32X3, frg.BF16X3]
+
+
+def nrel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def model(w):
+    return oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+
+
+def gpu_rhs(ctx, point, Lam, V, sig):
+    g = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    s = torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+    dg = torch.full_like(g, complex(np.nan, np.nan))
+    ds = torch.full_like(s, complex(np.nan, np.nan))
+    ctx.rhs(point, Lam, g, s, dg, ds)
+    torch.cuda.synchronize()
+    return dg.cpu().numpy(), ds.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [2, 4, 16, 34, 64, 100])
+@pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4])
+def test_split_rhs_matches_oracle(N, mask, prec):
+    w = inputs.Workload("t", N=N, U=1.7, T=0.03, eps_d=-0.85 + 0.3)
+    V = inputs.random_vertex(N, w.U, seed=N + mask)
+    sig = inputs.random_sigma(N, seed=100 + N)
+    with frg.Context([w], precision=prec, channel_mask=mask) as ctx:
+        for Lam in (0.01, 0.4, 7.0):
+            dg, ds = gpu_rhs(ctx, 0, Lam, V, sig)
+            rg, rs = oracle.rhs(model(w), Lam, V, sig, mask=mask)
+            e = nrel(dg, rg)
+            print("prec=%d N=%d mask=%x Lam=%g rel=%.3e" % (prec, N, mask, Lam, e))
+            assert e < RHS_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_rhs_full_size_sampled_entries(prec):
+    w = inputs.SIAM_N128
+    V = inputs.random_vertex(w.N, w.U, seed=11)
+    sig = inputs.random_sigma(w.N, seed=12, amp=0.05)
+    Lam = 0.02
+    with frg.Context([w], precision=prec) as ctx:
+        dg, ds = gpu_rhs(ctx, 0, Lam, V, sig)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, w.N, (3000, 3))
+    idx[:4] = [[0, 0, 0], [w.N - 1] * 3, [w.N // 2] * 3, [0, w.N - 1, 0]]
+    ref = oracle.rhs_entries(model(w), Lam, V, sig, idx)
+    got = dg[idx[:, 0], idx[:, 1], idx[:, 2]]
+    e = nrel(got, ref)
+    print("prec=%d N=128 sampled rel=%.3e" % (prec, e))
+    assert e < RHS_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["siam_N16_U1_T0.05_ph", "siam_N64_U2_T0.01_asym0.5"])
+def test_split_flow_matches_oracle_reference(name, prec):
+    with open(os.path.join(HERE, "golden", "oracle_flow_%s.json" % name)) as f:
+        ref = json.load(f)
+    w = inputs.WORKLOADS[name]
+    with frg.Context([w], precision=prec) as ctx:
+        st = ctx.flow()[0]
+        g, s, lam, _ = ctx.get_state(0)
+        obs = ctx.observables(0)
+    assert st.status == 0 and st.done == 1
+    g = g.cpu().numpy()
+    idx = np.array(ref["sample_idx"])
+    rv = np.array(ref["sample_re"]) + 1j * np.array(ref["sample_im"])
+    eg = np.max(np.abs(g[idx[:, 0], idx[:, 1], idx[:, 2]] - rv)) / ref["gamma_norm_inf"]
+    rsig = np.array(ref["sigma_re"]) + 1j * np.array(ref["sigma_im"])
+    es = nrel(s.cpu().numpy(), rsig)
+    eu = abs(obs["U_eff"] - complex(*ref["observables"]["U_eff"])) / abs(complex(*ref["observables"]["U_eff"]))
+    print("prec=%d flow %s errors gamma %.3e sigma %.3e ueff %.3e evals %d vs %d" % (
+        prec, name, eg, es, eu, st.rhs_evals, ref["stats"]["rhs_evals"]))
+    assert eg < FLOW_TOL[prec] and es < FLOW_TOL[prec] and eu < FLOW_TOL[prec]
