@@ -47,7 +47,6 @@ struct frg_ctx {
   std::vector<double2 *> user_in, user_out;
   TcPlan *tc = nullptr;  // split-precision contraction plan
   struct UserScratch {
-    float2 *ys = nullptr;
     double2 *s64 = nullptr;
     float2 *kout = nullptr;
   };
@@ -124,6 +123,7 @@ int validate(const frg_params &p, std::string &why) {
 }
 
 constexpr int TILE = 32;  // row / column tile of the FP64 contraction
+constexpr size_t OPERAND_SLACK = 32;  // float2 elements
 
 void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &out) {
   for (int m = 0; m < 2 * N - 1; ++m) {
@@ -312,14 +312,16 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
         if (!(P.kG[j] = dalloc<double2>(ctx, n3))) return bail(FRG_ENOMEM);
     } else {
       if (!(P.Y64 = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
-      if (!(P.Y32 = dalloc<float2>(ctx, n3)) || !(P.Y32W = dalloc<float2>(ctx, n3)) ||
-          !(P.Y32X = dalloc<float2>(ctx, n3)) || !(P.PX = dalloc<float2>(ctx, n3)) ||
+      // the W and X layouts are read through tensor maps whose rows along the
+      // (N+1)-strided lines reach up to 2 N^2 rows: allocate 2 N^3 elements
+      if (!(P.Y32 = dalloc<float2>(ctx, n3 + OPERAND_SLACK)) || !(P.Y32W = dalloc<float2>(ctx, 2 * n3 + OPERAND_SLACK)) ||
+          !(P.Y32X = dalloc<float2>(ctx, 2 * n3 + OPERAND_SLACK)) || !(P.PX = dalloc<float2>(ctx, n3)) ||
           !(P.PW = dalloc<float2>(ctx, n3)))
         return bail(FRG_ENOMEM);
       for (int b = 0; b < 2; ++b)
         if (!(P.yhi[b] = dalloc<float2>(ctx, n3)) || !(P.ylo[b] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
-      if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N)) ||
-          !(P.Lph32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N)) ||
+      if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
+          !(P.Lph32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
           !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 1)))
         return bail(FRG_ENOMEM);
       if (cudaMemset(P.vmax, 0, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ECUDA);
@@ -446,16 +448,17 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
   // split path: convert the input to float pairs, evaluate into float2, widen.
   // Scratch of its own so that a stand-alone call leaves the flow state intact.
   const PointDesc &P = ctx->hpts[point];
+  // the stage input buffers (FP32 vertex and its layouts) are scratch between
+  // stages, and the contraction's tensor maps point at them
   frg_ctx::UserScratch &u = ctx->user_split[point];
-  if (!u.ys) {
-    if (!(u.ys = dalloc<float2>(ctx, P.n3)) || !(u.s64 = dalloc<double2>(ctx, P.N)) ||
-        !(u.kout = dalloc<float2>(ctx, P.n3)))
+  if (!u.kout) {
+    if (!(u.s64 = dalloc<double2>(ctx, P.N)) || !(u.kout = dalloc<float2>(ctx, P.n3)))
       return fail(ctx, FRG_ENOMEM, "stand-alone rhs scratch");
   }
-  LK(launch_split_input(u.ys, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, P.vmax, ctx->stream),
+  LK(launch_split_input(P.Y32, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, P.vmax, ctx->stream),
      "split input");
   RhsIO s = o;
-  s.gam = u.ys;
+  s.gam = P.Y32;
   s.sig = u.s64;
   s.dgam = u.kout;
   s.out_f32 = 1;

@@ -39,6 +39,8 @@
 // Pipelines: NSTAGE smem stages (full/empty mbarriers), two TMEM accumulator
 // buffers (tfull/tempty mbarriers).  Every wait is bounded; a wait that runs out
 // sets the context error word, and all roles then leave their loops.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -433,7 +435,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   using LY = Lay<PREC>;
   constexpr int NSTAGE = T::NSTAGE;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // offset the shared array itself (keeps the shared state space for ld/st.shared)
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *stages = smem;
   float2 *staging = reinterpret_cast<float2 *>(smem + NSTAGE * LY::STAGE);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NSTAGE * LY::STAGE + STAGING_BYTES);
@@ -636,10 +639,414 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == MMA_WARP) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ===================================================================
+// 3xTF32 with bulk-copy staging.
+//
+// The complex product uses the real form on the output side:
+//   A'' rows 0..63 = Re a, rows 64..127 = Im a          (K = 16 per k-step)
+//   B'  rows 2c    = Re b(.,c), rows 2c+1 = Im b(.,c)   (N' = 2 NT rows)
+//   D[r][2c] - D[r+64][2c+1] = Re(a b)[r][c],  D[r][2c+1] + D[r+64][2c] = Im
+// one MMA shape M = 128, N = 2 NT (<= 256), K = 8 per instruction, three
+// products (hi*hi, hi*lo, lo*hi) into one TMEM accumulator.
+// Roles: warps 0-3 epilogue, warp 4 MMA, warp 5 loader (cp.async.bulk of the
+// contiguous operand rows, NRAW k-steps ahead), warps 6-17 transform (raw ->
+// bubble-weighted, split, swizzled K-major operand tiles).
+namespace st {
+constexpr int KS = 16;                                  // complex k per step
+constexpr int ROWB = 64;                                // bytes per operand row: 16 tf32
+constexpr int A_SLICE = 128 * ROWB;                     // 8 KB
+constexpr int B_SLICE = 2 * NT_MAX * ROWB;              // 16 KB
+constexpr int OP_STAGE = 2 * (A_SLICE + B_SLICE);       // 48 KB
+constexpr int NOP = 2;
+constexpr int RA = 18;                                  // complex per raw left row (aligned window)
+constexpr int RAW_A = MROWS * RA * 8;                   // 9216 B
+constexpr int RAW_B = KS * NT_MAX * 8;                  // 16 KB
+constexpr int RAW_L = 256;
+constexpr int RAW_STAGE = 2 * RAW_A + RAW_B + RAW_L;    // A, C (direct channel), B, bubble weights
+constexpr int NRAW = 3;
+constexpr int STG = MROWS * 17 * 8;                     // 64 rows x 16 complex (+1 pad)
+constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 2 * STG + 512;
+constexpr int EPI_W = 4, MMA_W = 4, LOAD_W = 5, XF_W0 = 6, N_XF = 12;
+constexpr int THREADS = 32 * (XF_W0 + N_XF);
+constexpr int XF_THREADS = 32 * N_XF;
+static_assert(SMEM <= 232448, "shared memory budget");
+
+__device__ __forceinline__ uint32_t swz64(int row, int ch) {
+  return (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4));
+}
+__device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= 1ull << 46;
+  d |= 4ull << 61;
+  return d;
+}
+__device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tma3(void *dst, const CUtensorMap *m, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(m), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma2(void *dst, const CUtensorMap *m, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(m), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Tensor maps per point (all FP32 elements, x = float index within a row):
+//   the rows of one operand family for one transfer lie on a line through a
+//   vertex layout, row index R = y*(N-1) + z (pp, layout N), y*(N+1) + z
+//   ("D1") or y*(N+1) + z*N ("D2") (layouts W and X), y counted along the line.
+enum MapId {
+  M_PA = 0, M_PB,            // natural layout, left / right boxes
+  M_W1A, M_W1B, M_W2A, M_W2B,  // layout W, forms D1 / D2
+  M_X1A, M_X1B, M_X2A, M_X2B,  // layout X
+  M_LPP, M_LPH,              // bubble-weight tables, one row
+  M_COUNT
+};
+
+// Geometry of one k-step of a tile.
+struct Step {
+  int half, kl, p0, a0, nA, nK, ncols;
+};
+template <int CH>
+__device__ __forceinline__ Step step_of(const TileInfo &ti, int kb) {
+  Step q;
+  const int k0 = kb * KS;
+  q.half = (CH == CH_DPH && k0 >= ti.D16) ? 1 : 0;
+  q.kl = k0 - (q.half ? ti.D16 : 0);
+  q.p0 = ti.g.p_lo + q.kl;
+  q.a0 = q.p0 & ~1;
+  q.nA = min(MROWS, ti.g.D - ti.r0);
+  q.nK = min(KS, ti.g.D - q.kl);
+  q.ncols = min(ti.NT, ti.N - ti.c0);
+  return q;
+}
+template <int CH>
+__device__ __forceinline__ const float2 *left_row(const Srcs &S, const TileInfo &ti, int rr, bool c_row) {
+  const int N = ti.N;
+  const Geom &g = ti.g;
+  if (CH == CH_PP) {
+    const int a = g.row_lo + rr;
+    return S.YN + ((size_t)a * N + (g.x - a)) * N;
+  } else if (CH == CH_XPH) {
+    const int k3 = g.row_lo + rr;
+    return S.YW + ((size_t)(k3 + g.x) * N + k3) * N;
+  } else {
+    const int k1 = g.row_lo + rr;
+    return (c_row ? S.YW : S.YX) + ((size_t)k1 * N + (k1 + g.x)) * N;
+  }
+}
+template <int CH>
+__device__ __forceinline__ const float2 *right_row(const Srcs &S, const TileInfo &ti, int kk, int half) {
+  const int N = ti.N;
+  const Geom &g = ti.g;
+  const int p = g.p_lo + kk;
+  if (CH == CH_PP) return S.YN + ((size_t)p * N + (g.x - p)) * N;
+  if (CH == CH_XPH) return S.YW + ((size_t)(p + g.x) * N + p) * N;
+  return (half ? S.YW : S.YX) + ((size_t)(p - g.x) * N + p) * N;
+}
+template <int CH>
+__device__ __forceinline__ const float2 *l_row(const PointDesc &P, const TileInfo &ti) {
+  const int N = ti.N;
+  if (CH == CH_PP) return P.Lpp32 + (size_t)ti.g.x * N;
+  if (CH == CH_XPH) return P.Lph32 + (size_t)(ti.g.x + N - 1) * N;
+  return P.Lph32 + (size_t)(-ti.g.x + N - 1) * N;
+}
+
+template <int CH>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const TcWork *__restrict__ work,
+                    int nwork, const int *__restrict__ nt_of, unsigned *__restrict__ err,
+                    const CUtensorMap *__restrict__ maps) {
+  extern __shared__ uint8_t smem_raw[];
+  // offset the shared array itself (keeps the shared state space for ld/st.shared)
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t *ops = smem;
+  uint8_t *raws = ops + NOP * OP_STAGE;
+  float2 *stgT = reinterpret_cast<float2 *>(raws + NRAW * RAW_STAGE);
+  float2 *stgB = stgT + MROWS * 17;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(raws + NRAW * RAW_STAGE + 2 * STG);
+  uint64_t *raw_full = bars, *raw_empty = bars + NRAW, *op_full = bars + 2 * NRAW, *op_empty = op_full + NOP;
+  uint64_t *tfull = op_empty + NOP, *tempty = tfull + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int j = 0; j < NRAW; ++j) {
+      mbar_init(&raw_full[j], 1);
+      mbar_init(&raw_empty[j], XF_THREADS);
+    }
+    for (int s = 0; s < NOP; ++s) {
+      mbar_init(&op_full[s], XF_THREADS);
+      mbar_init(&op_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 32 * EPI_W);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_W) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == LOAD_W) {
+    // ---------------------------------------------------------- loader ----
+    uint32_t it = 0;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
+      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+        const int j = it % NRAW;
+        if (!mbar_wait(&raw_empty[j], ((it / NRAW) & 1u) ^ 1u, err, abort_flag)) goto load_done;
+        const Step q = step_of<CH>(ti, kb);
+        const bool two = CH == CH_DPH && !q.half;
+        uint8_t *raw = raws + j * RAW_STAGE;
+        const uint32_t bytes = (uint32_t)(RAW_A * (two ? 2 : 1) + KS * ti.NT * 8 + RA * 8);
+        if (lane == 0) {
+          const CUtensorMap *mp = maps + (size_t)ti.point * M_COUNT;
+          arrive_expect_tx(&raw_full[j], bytes);
+          const int xa = 2 * q.a0, xb = 2 * ti.c0, x = ti.g.x;
+          if (CH == CH_PP) {
+            tma3(raw, mp + M_PA, xa, ti.g.row_lo + ti.r0, x, &raw_full[j]);
+            tma3(raw + 2 * RAW_A, mp + M_PB, xb, ti.g.p_lo + q.kl, x, &raw_full[j]);
+            tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPP, xa, x, &raw_full[j]);
+          } else if (CH == CH_XPH) {
+            const bool d2 = x >= 0;
+            const int z = x >= 0 ? x : -x;
+            tma3(raw, mp + (d2 ? M_W2A : M_W1A), xa, ti.r0, z, &raw_full[j]);
+            tma3(raw + 2 * RAW_A, mp + (d2 ? M_W2B : M_W1B), xb, q.kl, z, &raw_full[j]);
+            tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, x + ti.N - 1, &raw_full[j]);
+          } else {
+            const bool d1 = x >= 0;
+            const int z = x >= 0 ? x : -x;
+            tma3(raw, mp + (d1 ? M_X1A : M_X2A), xa, ti.r0, z, &raw_full[j]);
+            if (two) tma3(raw + RAW_A, mp + (d1 ? M_W1A : M_W2A), xa, ti.r0, z, &raw_full[j]);
+            const CUtensorMap *mb = q.half ? mp + (d1 ? M_W1B : M_W2B) : mp + (d1 ? M_X1B : M_X2B);
+            tma3(raw + 2 * RAW_A, mb, xb, q.kl, z, &raw_full[j]);
+            tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, -x + ti.N - 1, &raw_full[j]);
+          }
+        }
+        __syncwarp();
+      }
+    }
+  load_done:
+    // copies still in flight must land before the CTA leaves
+    for (uint32_t k = it > (uint32_t)NRAW ? it - NRAW : 0u; k < it; ++k)
+      mbar_wait(&raw_full[k % NRAW], (k / NRAW) & 1u, err, abort_flag);
+  } else if (warp >= XF_W0) {
+    // ------------------------------------------------------- transform ----
+    const int xt = tid - 32 * XF_W0;
+    uint32_t it = 0;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
+      const PointDesc &P = pts[ti.point];
+      const float U = (float)P.U;
+      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+        const int j = it % NRAW, s = it % NOP;
+        if (!mbar_wait(&raw_full[j], (it / NRAW) & 1u, err, abort_flag)) goto xf_done;
+        if (!mbar_wait(&op_empty[s], ((it / NOP) & 1u) ^ 1u, err, abort_flag)) goto xf_done;
+        const Step q = step_of<CH>(ti, kb);
+        const int off = q.p0 - q.a0;
+        const uint8_t *raw = raws + j * RAW_STAGE;
+        const float2 *rA = reinterpret_cast<const float2 *>(raw);
+        const float2 *rC = reinterpret_cast<const float2 *>(raw + RAW_A);
+        const float2 *rB = reinterpret_cast<const float2 *>(raw + 2 * RAW_A);
+        const float2 *rL = reinterpret_cast<const float2 *>(raw + 2 * RAW_A + RAW_B);
+        uint8_t *A = ops + s * OP_STAGE;
+        uint8_t *B = A + 2 * A_SLICE;
+        for (int t = xt; t < 256 + 4 * ti.NT; t += XF_THREADS) {
+          if (t < 256) {
+            const int r = t >> 2, g4 = t & 3;
+            const bool rv = r < q.nA;
+            float4 rh, rl, ih, il;
+            float re[4], im[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const int kk = 4 * g4 + x;
+              float2 a = make_float2(0.f, 0.f);
+              if (rv && kk < q.nK) {
+                const float2 v = rA[r * RA + off + kk], L = rL[off + kk];
+                if (CH == CH_DPH) {
+                  if (!q.half) {
+                    const float2 c = rC[r * RA + off + kk];
+                    a = cmulf(make_float2(2.f * v.x - c.x, 2.f * v.y - c.y), L);
+                  } else {
+                    a = cmulf(make_float2(-v.x, -v.y), L);
+                  }
+                } else {
+                  a = cmulf(v, L);
+                }
+              }
+              re[x] = a.x;
+              im[x] = a.y;
+            }
+            split_tf32(re[0], rh.x, rl.x);
+            split_tf32(re[1], rh.y, rl.y);
+            split_tf32(re[2], rh.z, rl.z);
+            split_tf32(re[3], rh.w, rl.w);
+            split_tf32(im[0], ih.x, il.x);
+            split_tf32(im[1], ih.y, il.y);
+            split_tf32(im[2], ih.z, il.z);
+            split_tf32(im[3], ih.w, il.w);
+            *reinterpret_cast<float4 *>(A + swz64(r, g4)) = rh;
+            *reinterpret_cast<float4 *>(A + swz64(r + 64, g4)) = ih;
+            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(r, g4)) = rl;
+            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(r + 64, g4)) = il;
+          } else {
+            const int bt = t - 256;
+            const int c = bt % ti.NT, g4 = bt / ti.NT;
+            const int cc = ti.c0 + c;
+            const int f = CH == CH_PP ? ti.g.x - cc : (CH == CH_DPH ? cc - ti.g.x : cc + ti.g.x);
+            const bool cv = c < q.ncols, ok = (unsigned)f < (unsigned)ti.N;
+            float re[4], im[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const int kk = 4 * g4 + x;
+              float2 b = make_float2(0.f, 0.f);
+              if (cv && kk < q.nK) b = ok ? rB[kk * ti.NT + c] : make_float2(U, 0.f);
+              re[x] = b.x;
+              im[x] = b.y;
+            }
+            float4 rh, rl, ih, il;
+            split_tf32(re[0], rh.x, rl.x);
+            split_tf32(re[1], rh.y, rl.y);
+            split_tf32(re[2], rh.z, rl.z);
+            split_tf32(re[3], rh.w, rl.w);
+            split_tf32(im[0], ih.x, il.x);
+            split_tf32(im[1], ih.y, il.y);
+            split_tf32(im[2], ih.z, il.z);
+            split_tf32(im[3], ih.w, il.w);
+            *reinterpret_cast<float4 *>(B + swz64(2 * c, g4)) = rh;
+            *reinterpret_cast<float4 *>(B + swz64(2 * c + 1, g4)) = ih;
+            *reinterpret_cast<float4 *>(B + B_SLICE + swz64(2 * c, g4)) = rl;
+            *reinterpret_cast<float4 *>(B + B_SLICE + swz64(2 * c + 1, g4)) = il;
+          }
+        }
+        mbar_arrive(&raw_empty[j]);
+        fence_async_smem();
+        mbar_arrive(&op_full[s]);
+      }
+    }
+  xf_done:;
+  } else if (warp == MMA_W) {
+    // ------------------------------------------------------ MMA issue ----
+    uint32_t it = 0, tcount = 0;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
+      const int buf = tcount & 1;
+      if (!mbar_wait(&tempty[buf], ((tcount >> 1) & 1u) ^ 1u, err, abort_flag)) break;
+      tc_after();
+      const uint32_t d = tmem + (uint32_t)(buf * 256);
+      const uint32_t id = idesc<FRG_3XTF32>(2 * ti.NT);
+      bool ok = true;
+      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+        const int s = it % NOP;
+        if (!mbar_wait(&op_full[s], (it / NOP) & 1u, err, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_after();
+        if (lane == 0) {
+          const uint32_t a0 = smem_u32(ops + s * OP_STAGE), b0 = a0 + 2 * A_SLICE;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t o = kk * 32;
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + o), id, first);                    // hi*hi
+            mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + B_SLICE + o), id, 1u);             // hi*lo
+            mma_tf32(d, sdesc64(a0 + A_SLICE + o), sdesc64(b0 + o), id, 1u);             // lo*hi
+          }
+          mma_commit(&op_empty[s]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(&tfull[buf]);
+      __syncwarp();
+      ++tcount;
+    }
+  } else {
+    // ------------------------------------------------------- epilogue ----
+    uint32_t tcount = 0;
+    const int L = warp * 32 + lane;
+    const bool top = L < 64;
+    const int r = L & 63;
+    const int etid = tid;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
+      const int buf = tcount & 1;
+      if (!mbar_wait(&tfull[buf], (tcount >> 1) & 1u, err, abort_flag)) break;
+      tc_after();
+      const PointDesc &P = pts[ti.point];
+      const RhsIO &o = io[ti.point];
+      const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
+      float2 *kN = static_cast<float2 *>(o.dgam);
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 256);
+      for (int cb = 0; cb < 2 * ti.NT; cb += 32) {
+        float v[32];
+        tmem_ld32(tl + cb, v);
+        tmem_wait_ld();
+        if (top) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) stgT[r * 17 + i] = make_float2(v[2 * i], v[2 * i + 1]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) stgB[r * 17 + i] = make_float2(-v[2 * i + 1], v[2 * i]);
+        }
+        named_bar(1, 32 * EPI_W);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+          const int idx = n * 128 + etid;
+          const int rr0 = idx >> 4, c = idx & 15;
+          const int rr = ti.r0 + rr0, cc = ti.c0 + cb / 2 + c;
+          if (rr < ti.g.D && cc < ti.N && cb / 2 + c < ti.NT) {
+            const float2 x = stgT[rr0 * 17 + c], y = stgB[rr0 * 17 + c];
+            out_row<CH>(P, kN, ti, rr)[cc] = make_float2((x.x + y.x) * sc, (x.y + y.y) * sc);
+          }
+        }
+        named_bar(1, 32 * EPI_W);
+      }
+      tc_before();
+      mbar_arrive(&tempty[buf]);
+      ++tcount;
+    }
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  if (warp == MMA_W) tmem_dealloc(tmem, TMEM_COLS);
+}
+}  // namespace st
+
 }  // namespace tc
 
 // --------------------------------------------------------------- plan ----
 struct TcPlan {
+  CUtensorMap *d_maps = nullptr;  // M_COUNT per point
   int precision = FRG_3XTF32;
   int sms = 0;
   int n = 0;
@@ -650,6 +1057,72 @@ struct TcPlan {
   tc::TcWork *d_pt[3] = {nullptr, nullptr, nullptr};
   std::vector<int> off[3];
 };
+
+// Tensor maps of the operand tiles (see MapId): box {2*RA floats, 64 rows} for
+// left operands, {2*NT floats, 16 rows} for right operands, {2*RA, 1} for the
+// bubble-weight rows.  Rows beyond a tensor's dims are filled with zeros.
+static bool encode_maps(TcPlan *p, const std::vector<PointDesc> &pts, std::string &why) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+      qr != cudaDriverEntryPointSuccess || !fn) {
+    why = "cuTensorMapEncodeTiled is not available";
+    return false;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  std::vector<CUtensorMap> maps(pts.size() * tc::st::M_COUNT);
+  for (size_t i = 0; i < pts.size(); ++i) {
+    const PointDesc &P = pts[i];
+    const cuuint64_t N = (cuuint64_t)P.N;
+    const cuuint32_t NT = (cuuint32_t)std::min(tc::NT_MAX, (P.N + 15) / 16 * 16);
+    const cuuint64_t row = N * 8;  // bytes per vertex row (N complex)
+    CUtensorMap *m = &maps[i * tc::st::M_COUNT];
+    const cuuint32_t estr[3] = {1, 1, 1};
+    auto enc3 = [&](CUtensorMap *dst, void *base, cuuint64_t ny, cuuint64_t nz, cuuint64_t sy, cuuint64_t sz,
+                    cuuint32_t bx, cuuint32_t by) {
+      const cuuint64_t dims[3] = {2 * N, ny, nz};
+      const cuuint64_t strides[2] = {sy, sz};
+      const cuuint32_t box[3] = {bx, by, 1};
+      return encode(dst, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    auto enc2 = [&](CUtensorMap *dst, void *base, cuuint64_t ny) {
+      const cuuint64_t dims[2] = {2 * N, ny};
+      const cuuint64_t strides[1] = {row};
+      const cuuint32_t box[2] = {(cuuint32_t)(2 * tc::st::RA), 1};
+      return encode(dst, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    const cuuint32_t BA = 2 * tc::st::RA, BB = 2 * NT;
+    bool ok = true;
+    // natural layout: R = y (N-1) + z, y in [0,N), z = s in [0, 2N-1)
+    ok = ok && enc3(&m[tc::st::M_PA], P.Y32, N, 2 * N - 1, (N - 1) * row, row, BA, tc::MROWS);
+    ok = ok && enc3(&m[tc::st::M_PB], P.Y32, N, 2 * N - 1, (N - 1) * row, row, BB, tc::st::KS);
+    // layouts W, X: D1 R = y (N+1) + z, D2 R = y (N+1) + z N; y, z in [0, N)
+    for (int l = 0; l < 2; ++l) {
+      void *base = l == 0 ? (void *)P.Y32W : (void *)P.Y32X;
+      const int o = l == 0 ? tc::st::M_W1A : tc::st::M_X1A;
+      ok = ok && enc3(&m[o + 0], base, N, N, (N + 1) * row, row, BA, tc::MROWS);
+      ok = ok && enc3(&m[o + 1], base, N, N, (N + 1) * row, row, BB, tc::st::KS);
+      ok = ok && enc3(&m[o + 2], base, N, N, (N + 1) * row, N * row, BA, tc::MROWS);
+      ok = ok && enc3(&m[o + 3], base, N, N, (N + 1) * row, N * row, BB, tc::st::KS);
+    }
+    ok = ok && enc2(&m[tc::st::M_LPP], P.Lpp32, 2 * N - 1);
+    ok = ok && enc2(&m[tc::st::M_LPH], P.Lph32, 2 * N - 1);
+    if (!ok) {
+      why = "cuTensorMapEncodeTiled rejected an operand map";
+      return false;
+    }
+  }
+  if (cudaMalloc(&p->d_maps, sizeof(CUtensorMap) * maps.size()) != cudaSuccess ||
+      cudaMemcpy(p->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    why = "tensor map upload failed";
+    return false;
+  }
+  return true;
+}
 
 template <int PREC>
 static bool set_smem_attrs() {
@@ -721,7 +1194,26 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
              cudaSuccess &&
          cudaMemcpy(p->d_pt[ch], per.data(), sizeof(tc::TcWork) * per.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   }
-  ok = ok && (precision == FRG_3XTF32 ? set_smem_attrs<FRG_3XTF32>() : set_smem_attrs<FRG_BF16X3>());
+  if (precision == FRG_3XTF32 && ok) {
+    std::string mw;
+    ok = encode_maps(p, pts, mw);
+    if (!ok) {
+      why = mw;
+      tc_plan_destroy(p);
+      return FRG_ECUDA;
+    }
+  }
+  if (precision == FRG_3XTF32) {
+    ok = ok &&
+         cudaFuncSetAttribute(tc::st::k_contract_tf32<CH_PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc::st::SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(tc::st::k_contract_tf32<CH_DPH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc::st::SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(tc::st::k_contract_tf32<CH_XPH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc::st::SMEM) == cudaSuccess;
+  } else {
+    ok = ok && set_smem_attrs<FRG_BF16X3>();
+  }
   if (!ok) {
     why = std::string("tensor-core plan setup failed: ") + cudaGetErrorString(cudaGetLastError());
     tc_plan_destroy(p);
@@ -733,6 +1225,7 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
 
 void tc_plan_destroy(TcPlan *p) {
   if (!p) return;
+  cudaFree(p->d_maps);
   cudaFree(p->d_nt);
   for (int ch = 0; ch < 3; ++ch) {
     cudaFree(p->d_all[ch]);
@@ -772,9 +1265,18 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
     }
     if (!nw) continue;
     const int grid = std::min(nw, p->sms);
-    if (p->precision == FRG_3XTF32)
-      launch_one<FRG_3XTF32>(ch, grid, st, d_pts, d_io, w, nw, p->d_nt, p->d_err);
-    else
+    if (p->precision == FRG_3XTF32) {
+      const int sm = tc::st::SMEM;
+      if (ch == CH_PP)
+        tc::st::k_contract_tf32<CH_PP><<<grid, tc::st::THREADS, sm, st>>>(d_pts, d_io, w, nw, p->d_nt, p->d_err,
+                                                                         p->d_maps);
+      else if (ch == CH_DPH)
+        tc::st::k_contract_tf32<CH_DPH><<<grid, tc::st::THREADS, sm, st>>>(d_pts, d_io, w, nw, p->d_nt, p->d_err,
+                                                                          p->d_maps);
+      else
+        tc::st::k_contract_tf32<CH_XPH><<<grid, tc::st::THREADS, sm, st>>>(d_pts, d_io, w, nw, p->d_nt, p->d_err,
+                                                                          p->d_maps);
+    } else
       launch_one<FRG_BF16X3>(ch, grid, st, d_pts, d_io, w, nw, p->d_nt, p->d_err);
     FRG_COUNT(1);
     if (cudaGetLastError() != cudaSuccess) return -3;
