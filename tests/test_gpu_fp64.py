@@ -95,7 +95,8 @@ def load_golden(name):
         return json.load(f)
 
 
-@pytest.mark.parametrize("name", ["siam_N16_U1_T0.05_ph", "siam_N64_U2_T0.01_asym0.5"])
+@pytest.mark.parametrize("name", ["siam_N16_U1_T0.05_ph", "siam_N64_U2_T0.01_asym0.5",
+                                  "siam_N128_U3_T0.005_ph"])
 def test_full_flow_matches_oracle_reference(name):
     ref = load_golden(name)
     w = inputs.WORKLOADS[name]

@@ -82,7 +82,8 @@ def test_split_rhs_full_size_sampled_entries(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("name", ["siam_N16_U1_T0.05_ph", "siam_N64_U2_T0.01_asym0.5"])
+@pytest.mark.parametrize("name", ["siam_N16_U1_T0.05_ph", "siam_N64_U2_T0.01_asym0.5",
+                                  "siam_N128_U3_T0.005_ph"])
 def test_split_flow_matches_oracle_reference(name, prec):
     with open(os.path.join(HERE, "golden", "oracle_flow_%s.json" % name)) as f:
         ref = json.load(f)
