@@ -45,6 +45,25 @@ def peaks():
         return p
 
 
+def profiled_traffic(kind):
+    """DRAM bytes per rhs of the contraction launches from the committed ncu
+    summary, or None if the kernel source changed since it was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "contraction_%s_N128.md" % kind)
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(("|", "#", " ", "`")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        src = os.path.join(ROOT, kv["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != kv["source_sha256"]:
+            return None
+        return float(kv["dram_bytes_per_rhs"])
+    except Exception:
+        return None
+
+
 def contraction_macs(N):
     """Useful complex multiply-adds of the three channel contractions per rhs:
     4 N sum_m D_m^2 with D_m = N - |m| (pp: D x D x N, dph: D x 2D x N,
@@ -249,7 +268,9 @@ def run_ours(args):
         tf_peak = pk["bf16_tflops"] * 0.5  # TF32 dense = half the bf16 rate
         achieved = flops / (ph[2] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf_peak, "traffic": None,
+                "frac": achieved / tf_peak,
+                "traffic": profiled_traffic("tf32") if prec == "3xtf32" else None,
+                "traffic_unit": "DRAM bytes per rhs (three contraction launches, ncu, cold cache)",
                 "kernel": "tcgen05 channel contractions of one rhs",
                 "peak_source": "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)" % pk["_source"],
                 "algorithmic": "8 flops x %d useful complex MACs per rhs (useful, not executed)" % macs}

@@ -1,0 +1,35 @@
+"""One right-hand-side evaluation per call of the library, for ncu captures.
+
+usage: python -m paper_1510_07799_gb300.profile_rhs [precision] [N] [repeats]
+Runs `repeats` rhs evaluations (default 2) of a seeded vertex at N (default
+128, the U=3, T=0.005 workload parameters) and prints the phase timings of the
+last one.
+"""
+import sys
+
+import torch
+
+from . import build, frg, inputs
+
+
+def main():
+    prec = sys.argv[1] if len(sys.argv) > 1 else "3xtf32"
+    N = int(sys.argv[2]) if len(sys.argv) > 2 else 128
+    reps = int(sys.argv[3]) if len(sys.argv) > 3 else 2
+    build.build()
+    w = inputs.Workload("profile", N=N, U=3.0, T=0.005, eps_d=-1.5)
+    ctx = frg.Context([w], precision=prec)
+    V = torch.from_numpy(inputs.random_vertex(N, w.U, 1)).cuda()
+    s = torch.from_numpy(inputs.random_sigma(N, 2)).cuda()
+    dg = torch.empty_like(V)
+    ds = torch.empty_like(s)
+    ph = None
+    for _ in range(reps):
+        ph = ctx.rhs_timed(0, 0.02, V, s, dg, ds)
+    torch.cuda.synchronize()
+    print("phases ms (bubble, regather, contraction, combine, sigma):", [round(x, 4) for x in ph])
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
