@@ -322,7 +322,8 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
         if (!(P.yhi[b] = dalloc<float2>(ctx, n3)) || !(P.ylo[b] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
       if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
           !(P.Lph32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
-          !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 1)))
+          !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 1)) ||
+          !(P.kord = dalloc<unsigned char>(ctx, (size_t)2 * (2 * N - 1) * 16)))
         return bail(FRG_ENOMEM);
       if (cudaMemset(P.vmax, 0, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ECUDA);
       for (int j = 0; j < 7; ++j)

@@ -61,6 +61,42 @@ __global__ void k_bubble_tables(const PointDesc *__restrict__ pts, const RhsIO *
       m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
     }
   }
+  if (P.kord) {
+    // order of the row's 16-wide k-chunks (starting at the first valid p) by
+    // increasing max |Lb|: the tensor-core accumulator loses up to an ulp of
+    // its running sum per addition, so small terms go first
+    __shared__ float am[FRG_MAX_N];
+    __shared__ float cmax[16];
+    const int Q = which == 0 ? 0 : row - (N - 1);
+    const int p_lo = which == 0 ? (row - (N - 1) > 0 ? row - (N - 1) : 0) : (Q < 0 ? -Q : 0);
+    const int D = which == 0 ? N - (row >= N - 1 ? row - (N - 1) : (N - 1) - row) : N - (Q >= 0 ? Q : -Q);
+    const int nch = (D + 15) / 16;
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+      const float2 f = (which == 0 ? P.Lpp32 : P.Lph32)[(size_t)row * N + p];
+      am[p] = fmaxf(fabsf(f.x), fabsf(f.y));
+    }
+    __syncthreads();
+    if (threadIdx.x < nch) {
+      float mx = 0.f;
+      for (int j = 0; j < 16; ++j) {
+        const int p = p_lo + 16 * threadIdx.x + j;
+        if (p < p_lo + D) mx = fmaxf(mx, am[p]);
+      }
+      cmax[threadIdx.x] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+      unsigned char *ord = P.kord + ((size_t)which * (2 * N - 1) + row) * 16;
+      if (threadIdx.x < nch) {
+        // rank of chunk c: chunks smaller than it, ties by index
+        const int c = threadIdx.x;
+        int rank = 0;
+        for (int j = 0; j < nch; ++j)
+          if (cmax[j] < cmax[c] || (cmax[j] == cmax[c] && j < c)) ++rank;
+        ord[rank] = (unsigned char)c;
+      }
+    }
+  }
   if (P.Lmax) {
     __shared__ float wm[32];
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));

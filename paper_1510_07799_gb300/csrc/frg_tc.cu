@@ -643,11 +643,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 // 3xTF32 with bulk-copy staging.
 //
 // The complex product uses the real form on the output side:
-//   A'' rows 0..63 = Re a, rows 64..127 = Im a          (K = 16 per k-step)
-//   B'  rows 2c    = Re b(.,c), rows 2c+1 = Im b(.,c)   (N' = 2 NT rows)
-//   D[r][2c] - D[r+64][2c+1] = Re(a b)[r][c],  D[r][2c+1] + D[r+64][2c] = Im
+//   A'' rows 2r = Re a(r,.), rows 2r+1 = Im a(r,.)     (K = 16 per k-step)
+//   B'  rows 2c = Re b(.,c), rows 2c+1 = Im b(.,c)     (N' = 2 NT rows)
+//   D[2r][2c] - D[2r+1][2c+1] = Re(a b)[r][c],  D[2r][2c+1] + D[2r+1][2c] = Im
 // one MMA shape M = 128, N = 2 NT (<= 256), K = 8 per instruction, three
-// products (hi*hi, hi*lo, lo*hi) into one TMEM accumulator.
+// products: hi*hi into one TMEM accumulator, hi*lo + lo*hi into a second one
+// (the FP32 accumulator does not round to nearest, so the large sum should see
+// as few additions as possible).
 // Roles: warps 0-3 epilogue, warp 4 MMA, warp 5 loader (cp.async.bulk of the
 // contiguous operand rows, NRAW k-steps ahead), warps 6-17 transform (raw ->
 // bubble-weighted, split, swizzled K-major operand tiles).
@@ -769,6 +771,17 @@ __device__ __forceinline__ const float2 *l_row(const PointDesc &P, const TileInf
   return P.Lph32 + (size_t)(-ti.g.x + N - 1) * N;
 }
 
+// k-step processed i-th in a tile: chunks in increasing max |Lb| (table
+// written by the bubble kernel), both halves of the direct channel interleaved.
+template <int CH>
+__device__ __forceinline__ int kstep_at(const PointDesc &P, const TileInfo &ti, int m, int i) {
+  const int N = ti.N;
+  const int row = CH == CH_PP ? m : (2 * N - 1) + (CH == CH_XPH ? m : 2 * N - 2 - m);
+  const unsigned char *ord = P.kord + (size_t)row * 16;
+  if (CH == CH_DPH) return (i & 1) * (ti.D16 / KS) + ord[i >> 1];
+  return ord[i];
+}
+
 template <int CH>
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const TcWork *__restrict__ work,
@@ -816,9 +829,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
       TileInfo ti;
       if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+      const PointDesc &PL = pts[ti.point];
+      for (int ki = 0; ki < ti.nk; ++ki, ++it) {
         const int j = it % NRAW;
         if (!mbar_wait(&raw_empty[j], ((it / NRAW) & 1u) ^ 1u, err, abort_flag)) goto load_done;
+        const int kb = kstep_at<CH>(PL, ti, work[wi].m, ki);
         const Step q = step_of<CH>(ti, kb);
         const bool two = CH == CH_DPH && !q.half;
         uint8_t *raw = raws + j * RAW_STAGE;
@@ -863,11 +878,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
       const PointDesc &P = pts[ti.point];
       const float U = (float)P.U;
-      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+      for (int ki = 0; ki < ti.nk; ++ki, ++it) {
         const int j = it % NRAW, s = it % NOP;
         if (!mbar_wait(&raw_full[j], (it / NRAW) & 1u, err, abort_flag)) goto xf_done;
         if (!mbar_wait(&op_empty[s], ((it / NOP) & 1u) ^ 1u, err, abort_flag)) goto xf_done;
-        const Step q = step_of<CH>(ti, kb);
+        const Step q = step_of<CH>(ti, kstep_at<CH>(P, ti, work[wi].m, ki));
         const int off = q.p0 - q.a0;
         const uint8_t *raw = raws + j * RAW_STAGE;
         const float2 *rA = reinterpret_cast<const float2 *>(raw);
@@ -910,10 +925,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             split_tf32(im[1], ih.y, il.y);
             split_tf32(im[2], ih.z, il.z);
             split_tf32(im[3], ih.w, il.w);
-            *reinterpret_cast<float4 *>(A + swz64(r, g4)) = rh;
-            *reinterpret_cast<float4 *>(A + swz64(r + 64, g4)) = ih;
-            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(r, g4)) = rl;
-            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(r + 64, g4)) = il;
+            *reinterpret_cast<float4 *>(A + swz64(2 * r, g4)) = rh;
+            *reinterpret_cast<float4 *>(A + swz64(2 * r + 1, g4)) = ih;
+            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(2 * r, g4)) = rl;
+            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(2 * r + 1, g4)) = il;
           } else {
             const int bt = t - 256;
             const int c = bt % ti.NT, g4 = bt / ti.NT;
@@ -956,10 +971,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
       TileInfo ti;
       if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      const int buf = tcount & 1;
-      if (!mbar_wait(&tempty[buf], ((tcount >> 1) & 1u) ^ 1u, err, abort_flag)) break;
+      // one TMEM buffer: columns [0,256) hold hi*hi, [256,512) hi*lo + lo*hi, so
+      // that the large sum takes a third of the accumulation steps
+      if (!mbar_wait(&tempty[0], (tcount & 1u) ^ 1u, err, abort_flag)) break;
       tc_after();
-      const uint32_t d = tmem + (uint32_t)(buf * 256);
+      const uint32_t d = tmem, dx = tmem + 256;
       const uint32_t id = idesc<FRG_3XTF32>(2 * ti.NT);
       bool ok = true;
       for (int kb = 0; kb < ti.nk; ++kb, ++it) {
@@ -976,62 +992,69 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t o = kk * 32;
             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
             mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + o), id, first);                    // hi*hi
-            mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + B_SLICE + o), id, 1u);             // hi*lo
-            mma_tf32(d, sdesc64(a0 + A_SLICE + o), sdesc64(b0 + o), id, 1u);             // lo*hi
+            mma_tf32(dx, sdesc64(a0 + o), sdesc64(b0 + B_SLICE + o), id, first);         // hi*lo
+            mma_tf32(dx, sdesc64(a0 + A_SLICE + o), sdesc64(b0 + o), id, 1u);            // lo*hi
           }
           mma_commit(&op_empty[s]);
         }
         __syncwarp();
       }
       if (!ok) break;
-      if (lane == 0) mma_commit(&tfull[buf]);
+      if (lane == 0) mma_commit(&tfull[0]);
       __syncwarp();
       ++tcount;
     }
   } else {
     // ------------------------------------------------------- epilogue ----
+    // TMEM lane 2r holds (Re a . Re b, Re a . Im b), lane 2r+1 (Im a . Re b,
+    // Im a . Im b) of complex row r: the lane pair combines them by shuffles and
+    // each lane stores 8 of the pair's 16 complex columns (64 contiguous bytes).
     uint32_t tcount = 0;
     const int L = warp * 32 + lane;
-    const bool top = L < 64;
-    const int r = L & 63;
-    const int etid = tid;
+    const int r = L >> 1, odd = L & 1;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
       TileInfo ti;
       if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      const int buf = tcount & 1;
-      if (!mbar_wait(&tfull[buf], (tcount >> 1) & 1u, err, abort_flag)) break;
+      if (!mbar_wait(&tfull[0], tcount & 1u, err, abort_flag)) break;
       tc_after();
       const PointDesc &P = pts[ti.point];
       const RhsIO &o = io[ti.point];
       const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
       float2 *kN = static_cast<float2 *>(o.dgam);
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 256);
+      const int rr = ti.r0 + r;
+      float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
       for (int cb = 0; cb < 2 * ti.NT; cb += 32) {
-        float v[32];
+        float v[32], vx[32];
         tmem_ld32(tl + cb, v);
+        tmem_ld32(tl + 256 + cb, vx);
         tmem_wait_ld();
-        if (top) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) stgT[r * 17 + i] = make_float2(v[2 * i], v[2 * i + 1]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) stgB[r * 17 + i] = make_float2(-v[2 * i + 1], v[2 * i]);
+        if (cb + 32 >= 2 * ti.NT) {
+          // all TMEM reads of this tile are done: let the next tile's MMAs start
+          tc_before();
+          mbar_arrive(&tempty[0]);
         }
-        named_bar(1, 32 * EPI_W);
 #pragma unroll
-        for (int n = 0; n < 8; ++n) {
-          const int idx = n * 128 + etid;
-          const int rr0 = idx >> 4, c = idx & 15;
-          const int rr = ti.r0 + rr0, cc = ti.c0 + cb / 2 + c;
-          if (rr < ti.g.D && cc < ti.N && cb / 2 + c < ti.NT) {
-            const float2 x = stgT[rr0 * 17 + c], y = stgB[rr0 * 17 + c];
-            out_row<CH>(P, kN, ti, rr)[cc] = make_float2((x.x + y.x) * sc, (x.y + y.y) * sc);
-          }
+        for (int i = 0; i < 32; ++i) v[i] += vx[i];
+        // even lane keeps columns 0..7 of the chunk, odd lane 8..15
+        float2 out[8];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float pr = __shfl_xor_sync(0xffffffffu, v[2 * c], 1);      // partner's x.Re b
+          const float pi = __shfl_xor_sync(0xffffffffu, v[2 * c + 1], 1);  // partner's x.Im b
+          // even lane: own (ArBr, ArBi), partner (AiBr, AiBi)
+          // odd lane:  own (AiBr, AiBi), partner (ArBr, ArBi)
+          const float re = odd ? pr - v[2 * c + 1] : v[2 * c] - pi;
+          const float im = odd ? pi + v[2 * c] : v[2 * c + 1] + pr;
+          if ((c >> 3) == odd) out[c & 7] = make_float2(re * sc, im * sc);
         }
-        named_bar(1, 32 * EPI_W);
+        const int c0 = ti.c0 + cb / 2 + 8 * odd;
+        if (orow) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c0 + c < ti.N && cb / 2 + 8 * odd + c < ti.NT) orow[c0 + c] = out[c];
+        }
       }
-      tc_before();
-      mbar_arrive(&tempty[buf]);
       ++tcount;
     }
   }
