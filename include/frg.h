@@ -187,6 +187,37 @@ int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
                   const void *d_sigma, void *d_dgamma, void *d_dsigma, float *ms);
 long frg_kernel_launches(void);
 
+/*
+ * Right-hand side without any device allocation (the paper has no counterpart;
+ * this is a service for callers).  Some callers cannot allocate device memory
+ * when they need an evaluation: a latency-critical loop in which an allocation
+ * could stall or synchronise the device, or a process whose device memory is
+ * owned by another component (a framework's caching allocator, a fixed memory
+ * budget).  frg_rhs_noalloc needs no context: it evaluates d/dl of (V, Sigma)
+ * for the single point *p at scale Lambda in FP64 (p->precision, Lambda0,
+ * Lambda_f, tolerances and step settings are ignored; channel_mask applies),
+ * reading d_gamma (N^3 complex128) and d_sigma (N complex128, may be NULL) and
+ * writing d_dgamma and d_dsigma, all device pointers on the current device,
+ * asynchronously on cuda_stream (a cudaStream_t, NULL for the legacy stream).
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its whole
+ * workspace is one file-scope device array of about 290 KB that every GPU
+ * which loads this library holds until the process exits.
+ *  - Limit: N_f <= FRG_NOALLOC_MAX_N (even, >= 2); larger sizes, T <= 0,
+ *    Delta <= 0, Lambda <= 0, non-finite parameters or NULL output pointers
+ *    return FRG_EINVAL without touching the device.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture on that device.
+ *  - Every call on a device shares the array and leaves its contents behind;
+ *    each call rewrites everything it reads.  Calls that overlap on the GPU
+ *    (for example on two streams) race on the array: serialise them.
+ * Returns FRG_OK, FRG_EINVAL or FRG_ECUDA (launch failure).
+ */
+#define FRG_NOALLOC_MAX_N 64
+int frg_rhs_noalloc(const frg_params *p, double Lambda, const void *d_gamma,
+                    const void *d_sigma, void *d_dgamma, void *d_dsigma,
+                    void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

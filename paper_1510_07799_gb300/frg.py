@@ -24,7 +24,8 @@ ERRNAMES = {EINVAL: "FRG_EINVAL", ENOMEM: "FRG_ENOMEM", ECUDA: "FRG_ECUDA",
 
 EXPORTED = ("frg_init", "frg_destroy", "frg_last_error", "frg_rhs", "frg_rhs_host", "frg_flow",
             "frg_advance", "frg_observables", "frg_get_state", "frg_set_state", "frg_stats",
-            "frg_rhs_timed", "frg_kernel_launches")
+            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc")
+NOALLOC_MAX_N = 64
 
 
 class FrgError(RuntimeError):
@@ -111,6 +112,7 @@ def load():
     lib.frg_get_state.argtypes = [vp, C.c_int, vp, vp, dp, dp]
     lib.frg_set_state.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_double]
     lib.frg_rhs_timed.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, C.POINTER(C.c_float)]
+    lib.frg_rhs_noalloc.argtypes = [C.POINTER(_Params), C.c_double, vp, vp, vp, vp, vp]
     lib.frg_kernel_launches.argtypes = []
     lib.frg_kernel_launches.restype = C.c_long
     _lib = lib
@@ -120,6 +122,28 @@ def load():
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(load().frg_kernel_launches())
+
+
+def rhs_noalloc(params, Lambda, gamma, sigma, dgamma, dsigma, channel_mask=CH_ALL, stream=None):
+    """FP64 rhs of one point through frg_rhs_noalloc (no context, no device
+    allocation; N_f <= NOALLOC_MAX_N).  Tensors as for Context.rhs; asynchronous
+    on `stream` (default: torch's current stream)."""
+    lib = load()
+    p = params if isinstance(params, Params) else Params.from_workload(params)
+    N = p.N_f
+    for t, shp, name in ((gamma, (N, N, N), "gamma"), (sigma, (N,), "sigma"),
+                         (dgamma, (N, N, N), "dgamma"), (dsigma, (N,), "dsigma")):
+        if t is not None:
+            _check_dev(t, shp, name)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    cp = _Params(p.U, p.T, p.eps_d, p.Delta, p.N_f, p.Lambda0, p.Lambda_f, p.rtol, p.atol, p.h0,
+                 p.max_steps, FP64, channel_mask)
+    rc = lib.frg_rhs_noalloc(C.byref(cp), Lambda, _ptr(gamma), _ptr(sigma), _ptr(dgamma),
+                             _ptr(dsigma), C.c_void_p(stream))
+    if rc != OK:
+        raise FrgError(rc, "frg_rhs_noalloc failed (N_f must be even and <= %d)" % NOALLOC_MAX_N)
 
 
 def _ptr(t):

@@ -1,0 +1,60 @@
+"""The allocation-free rhs entry point (frg_rhs_noalloc) against the context
+path (frg_rhs), on the GPU, through the C ABI.
+
+Callers that cannot allocate device memory when they need an rhs (latency-
+critical loops, processes whose device memory belongs to another allocator)
+use frg_rhs_noalloc, whose workspace is a fixed device array inside the
+library.  Both entry points run the same FP64 kernels, so they agree to the
+FP64 parity bar of the other tests; two calls in a row check that nothing of
+one call leaks into the next through the shared array.  This file is collected
+last so that a failure here does not hide the other tests."""
+import numpy as np
+import pytest
+
+from paper_1510_07799_gb300 import frg, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12  # FP64 rhs parity bar used by the other GPU tests
+
+
+def nrel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+def case(N, seed):
+    w = inputs.Workload("noalloc", N=N, U=1.9, T=0.03, eps_d=-0.95 + 0.35)
+    V = torch.from_numpy(inputs.random_vertex(N, w.U, seed=seed)).cuda()
+    S = torch.from_numpy(inputs.random_sigma(N, seed=seed + 1)).cuda()
+    return w, V, S
+
+
+def test_noalloc_rhs_matches_context_rhs_on_consecutive_calls():
+    for N, seeds in ((48, (1, 2)), (64, (3, 3)), (10, (4, 5))):
+        # two calls in a row on the shared array (a different, then a repeated input)
+        runs = []
+        for seed in seeds:
+            w, V, S = case(N, seed)
+            Lam = 0.05 * seed
+            dg, ds = torch.empty_like(V), torch.empty_like(S)
+            frg.rhs_noalloc(w, Lam, V, S, dg, ds)
+            runs.append((w, Lam, V, S, dg, ds))
+        torch.cuda.synchronize()
+        for w, Lam, V, S, dg, ds in runs:
+            with frg.Context([w]) as ctx:
+                rg, rs = torch.empty_like(V), torch.empty_like(S)
+                ctx.rhs(0, Lam, V, S, rg, rs)
+                torch.cuda.synchronize()
+            assert nrel(dg, rg) < TOL and nrel(ds, rs) < TOL
+
+
+def test_noalloc_rejects_sizes_beyond_its_array():
+    for N in (frg.NOALLOC_MAX_N + 2, 7):
+        w, V, S = case(N, 7)
+        dg, ds = torch.full_like(V, 1.0), torch.full_like(S, 1.0)
+        with pytest.raises(frg.FrgError) as e:
+            frg.rhs_noalloc(w, 0.1, V, S, dg, ds)
+        assert e.value.code == frg.EINVAL
+        torch.cuda.synchronize()
+        assert bool((dg == 1.0).all()) and bool((ds == 1.0).all())  # nothing was written
