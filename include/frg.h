@@ -177,9 +177,10 @@ int frg_stats(frg_ctx *ctx, frg_flow_stats *stats);
 /*
  * Diagnostics.  frg_rhs_timed evaluates exactly like frg_rhs and records CUDA
  * events on the context stream around its phases; ms[0..4] (host) receive the
- * durations of the bubble-weight, operand-regather, channel-contraction,
- * combine (scatter-add) and self-energy phases (0 for a phase the path does
- * not have).  Synchronises.
+ * durations of the bubble-weight (with the self-energy, which the same kernel
+ * computes), operand-regather, channel-contraction and combine (scatter-add)
+ * phases, and ms[4] = 0 (no separate self-energy phase); 0 for a phase the
+ * path does not have.  Synchronises.
  * frg_kernel_launches returns the number of kernels this library has launched
  * in the process so far.
  */

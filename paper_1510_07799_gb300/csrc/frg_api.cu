@@ -136,12 +136,14 @@ void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &ou
 }  // namespace
 
 // ------------------------------------------------------------ rhs pipeline ----
-// ev (optional, 6 events): start, after the bubble weights, after the operand
-// regather, after the channel products, after the combine, after the self-energy.
+// ev (optional, 6 events): start, after the bubble weights and the self-energy
+// (one fused kernel), after the operand regather, after the channel products,
+// after the combine; the last event follows the combine directly.
 static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr) {
   cudaStream_t st = ctx->stream;
   if (ev) CK(cudaEventRecord(ev[0], st), "event");
-  LK(launch_bubble(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, st), "bubble weights");
+  LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st),
+     "bubble weights and self-energy");
   if (ev) CK(cudaEventRecord(ev[1], st), "event");
   const int chmask = ctx->mask & 7;
   if (!ctx->split) {
@@ -175,7 +177,6 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
     }
   }
   if (ev) CK(cudaEventRecord(ev[4], st), "event");
-  LK(launch_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st), "self-energy");
   if (ev) CK(cudaEventRecord(ev[5], st), "event");
   return FRG_OK;
 }

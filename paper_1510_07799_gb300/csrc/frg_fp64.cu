@@ -180,6 +180,134 @@ int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int ma
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// ------------------------------------ bubble weights + self-energy, fused ----
+// Everything that needs only the propagators, in one launch after k_bubble_gs:
+// every block stages G and S of its point in shared memory (FP64 divisions are
+// slow on this part, so they are done once per point), then computes either
+// one row of a bubble-weight table (blocks [0, 2(2 maxN - 1))) or one
+// self-energy entry dSigma(w)/dl (blocks beyond), with 128 threads over the
+// loop index p and a fixed-order block reduction.
+template <bool SPLIT>
+__global__ void __launch_bounds__(128)
+    k_bubble_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int maxN, int sigma_on) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  const int N = P.N;
+  const int nrow_max = 2 * maxN - 1;
+  const int b = blockIdx.x;
+  const bool table = b < 2 * nrow_max;
+  const int which = table ? b / nrow_max : 0;
+  const int row = table ? b % nrow_max : 0;
+  const int w = table ? 0 : b - 2 * nrow_max;
+  if (table ? row >= 2 * N - 1 : w >= N) return;
+  __shared__ double2 sG[FRG_MAX_N], sS[FRG_MAX_N];
+  const double L = *o.lam;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sG[i] = P.G[i];
+    sS[i] = P.S[i];
+  }
+  __syncthreads();
+  if (!table) {
+    // dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]
+    double2 acc = make_double2(0.0, 0.0);
+    if (sigma_on) {
+      for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        const double2 a = vload<SPLIT>(o.gam, N, P.U, w, p, w);
+        const double2 c = vload<SPLIT>(o.gam, N, P.U, w, p, p);
+        cfma(acc, sS[p], make_double2(2.0 * a.x - c.x, 2.0 * a.y - c.y));
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    __shared__ double2 part[4];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 t = part[0];
+      for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
+      const double f = L * P.T;
+      o.dsig[w] = make_double2(t.x * f, t.y * f);
+    }
+    return;
+  }
+  // Lpp[s][p] = Lb(p, s-p), Lph[Q+N-1][p] = Lb(p, p+Q); split paths also get
+  // the FP32 tables, the per-row maximum and the k-chunk order
+  float m = 0.f;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    const int q = which == 0 ? row - p : p + (row - (N - 1));
+    double2 v = make_double2(0.0, 0.0);
+    if (inbox(N, q)) v = cadd(cmul(sS[p], sG[q]), cmul(sG[p], sS[q]));
+    (which == 0 ? P.Lpp : P.Lph)[(size_t)row * N + p] = v;
+    if (P.Lpp32) {
+      const float2 f = make_float2((float)v.x, (float)v.y);
+      (which == 0 ? P.Lpp32 : P.Lph32)[(size_t)row * N + p] = f;
+      m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+    }
+  }
+  if (P.kord) {
+    // order of the row's 16-wide k-chunks (starting at the first valid p) by
+    // increasing max |Lb|: the tensor-core accumulator loses up to an ulp of
+    // its running sum per addition, so small terms go first
+    __shared__ float am[FRG_MAX_N];
+    __shared__ float cmax[16];
+    const int Q = which == 0 ? 0 : row - (N - 1);
+    const int p_lo = which == 0 ? (row - (N - 1) > 0 ? row - (N - 1) : 0) : (Q < 0 ? -Q : 0);
+    const int D = which == 0 ? N - (row >= N - 1 ? row - (N - 1) : (N - 1) - row) : N - (Q >= 0 ? Q : -Q);
+    const int nch = (D + 15) / 16;
+    __syncthreads();  // the FP32 row of this block is written
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+      const float2 f = (which == 0 ? P.Lpp32 : P.Lph32)[(size_t)row * N + p];
+      am[p] = fmaxf(fabsf(f.x), fabsf(f.y));
+    }
+    __syncthreads();
+    if (threadIdx.x < nch) {
+      float mx = 0.f;
+      for (int j = 0; j < 16; ++j) {
+        const int p = p_lo + 16 * threadIdx.x + j;
+        if (p < p_lo + D) mx = fmaxf(mx, am[p]);
+      }
+      cmax[threadIdx.x] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x < nch) {
+      unsigned char *ord = P.kord + ((size_t)which * (2 * N - 1) + row) * 16;
+      const int c = threadIdx.x;
+      int rank = 0;
+      for (int j = 0; j < nch; ++j)
+        if (cmax[j] < cmax[c] || (cmax[j] == cmax[c] && j < c)) ++rank;
+      ord[rank] = (unsigned char)c;
+    }
+  }
+  if (P.Lmax) {
+    __shared__ float wm[32];
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float r = 0.f;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) r = fmaxf(r, wm[j]);
+      P.Lmax[which * (2 * N - 1) + row] = r;
+    }
+  }
+}
+
+int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
+                        cudaStream_t st) {
+  k_bubble_gs<<<n_points, maxN, 0, st>>>(d_pts, d_io);
+  FRG_COUNT(1);
+  dim3 g(2 * (2 * maxN - 1) + maxN, n_points);
+  if (split)
+    k_bubble_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0);
+  else
+    k_bubble_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 // ------------------------------------------------- FP64 contraction ----
 constexpr int F64_TM = 32, F64_TN = 32, F64_TK = 16, F64_THREADS = 256;
 

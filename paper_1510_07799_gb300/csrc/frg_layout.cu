@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
   }
 }
 
-// k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels.
+// k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
+// (launched for every split-path rhs, also when only pp is enabled).
 __global__ void __launch_bounds__(256) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                                  int mask) {
   const int pi = blockIdx.y;
@@ -113,6 +114,9 @@ __global__ void __launch_bounds__(256) k_combine(const PointDesc *__restrict__ p
     __syncthreads();
   }
   float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
+  // the channel products of this rhs have consumed the vertex bound of the
+  // stage input (BF16 slicing): reset it for the next stage
+  if (blockIdx.x == 0 && threadIdx.x == 0 && P.vmax) *P.vmax = 0u;
 #pragma unroll
   for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
     const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;

@@ -336,9 +336,18 @@ __device__ __forceinline__ float2 *out_row(const PointDesc &P, float2 *kN, const
   }
 }
 
+// TF32 keeps the sign, the 8 exponent bits and the top 10 mantissa bits of an
+// IEEE binary32.  Rounding to nearest with ties away from zero on that format
+// is integer arithmetic on the bit pattern: add half of the dropped unit (2^12)
+// to the magnitude bits, then clear the 13 dropped bits (a carry into the
+// exponent is the correct round-up).  Full-rate integer ops; finite inputs.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+// x = hi + lo with hi = tf32(x) and lo = tf32(x - hi); x - hi is exact.
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - hi);
+  hi = tf32_round(x);
+  lo = tf32_round(x - hi);
 }
 
 // 2^e as a float for e in [-126, 127].
@@ -654,6 +663,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 // contiguous operand rows, NRAW k-steps ahead), warps 6-17 transform (raw ->
 // bubble-weighted, split, swizzled K-major operand tiles).
 namespace st {
+// Warp-uniform bounded wait: every lane of the warp leaves with the same result,
+// so warp-collective code after it (shuffles, __syncwarp) never splits.
+__device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t parity, unsigned *err, volatile int *abort_flag) {
+  const bool ok = mbar_wait(bar, parity, err, abort_flag);
+  return __all_sync(0xffffffffu, ok);
+}
 constexpr int KS = 16;                                  // complex k per step
 constexpr int ROWB = 64;                                // bytes per operand row: 16 tf32
 constexpr int A_SLICE = 128 * ROWB;                     // 8 KB
@@ -666,8 +681,9 @@ constexpr int RAW_B = KS * NT_MAX * 8;                  // 16 KB
 constexpr int RAW_L = 256;
 constexpr int RAW_STAGE = 2 * RAW_A + RAW_B + RAW_L;    // A, C (direct channel), B, bubble weights
 constexpr int NRAW = 3;
-constexpr int STG = MROWS * 17 * 8;                     // 64 rows x 16 complex (+1 pad)
-constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 2 * STG + 512;
+constexpr int EPI_PITCH = 18;                           // complex per staged output row (16 + 2 pad)
+constexpr int EPI_STG = 16 * EPI_PITCH * 8;             // per epilogue warp: 16 rows x 16 complex
+constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 4 * EPI_STG + 512;
 constexpr int EPI_W = 4, MMA_W = 4, LOAD_W = 5, XF_W0 = 6, N_XF = 12;
 constexpr int THREADS = 32 * (XF_W0 + N_XF);
 constexpr int XF_THREADS = 32 * N_XF;
@@ -772,296 +788,425 @@ __device__ __forceinline__ const float2 *l_row(const PointDesc &P, const TileInf
 }
 
 // k-step processed i-th in a tile: chunks in increasing max |Lb| (table
-// written by the bubble kernel), both halves of the direct channel interleaved.
+// written by the bubble kernel, one 16-byte row per transfer, read once per
+// tile), both halves of the direct channel interleaved.
 template <int CH>
-__device__ __forceinline__ int kstep_at(const PointDesc &P, const TileInfo &ti, int m, int i) {
-  const int N = ti.N;
+__device__ __forceinline__ uint4 korder_row(const PointDesc &P, int N, int m) {
   const int row = CH == CH_PP ? m : (2 * N - 1) + (CH == CH_XPH ? m : 2 * N - 2 - m);
-  const unsigned char *ord = P.kord + (size_t)row * 16;
-  if (CH == CH_DPH) return (i & 1) * (ti.D16 / KS) + ord[i >> 1];
-  return ord[i];
+  return *reinterpret_cast<const uint4 *>(P.kord + (size_t)row * 16);
+}
+__device__ __forceinline__ int kord_byte(const uint4 &o, int i) {
+  const uint32_t w = (i & 8) ? ((i & 4) ? o.w : o.z) : ((i & 4) ? o.y : o.x);
+  return (int)((w >> (8 * (i & 3))) & 0xFFu);
+}
+template <int CH>
+__device__ __forceinline__ int kstep_at(const uint4 &ord, const TileInfo &ti, int i) {
+  if (CH == CH_DPH) return (i & 1) * (ti.D16 / KS) + kord_byte(ord, i >> 1);
+  return kord_byte(ord, i);
 }
 
+// One tile of the channel product: channel, point, transfer index, row tile,
+// column tile.  The work list holds every tile of every enabled channel; the
+// host assigns the tiles to the persistent CTAs (longest first, each to the
+// least loaded CTA) and stores them CTA by CTA.
+struct StWork {
+  int point;
+  short m, ch, rt, ct;
+};
+
+// Shared pipeline state of one CTA.
+struct Pipe {
+  uint8_t *ops, *raws;
+  float2 *epi_stg;
+  uint64_t *raw_full, *raw_empty, *op_full, *op_empty, *tfull, *tempty;
+  volatile int *abort_flag;
+  unsigned *err;
+  uint32_t tmem;
+};
+
 template <int CH>
+__device__ __forceinline__ bool st_tile_info(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                             const StWork &w, const int *__restrict__ nt_of, TileInfo &ti) {
+  return tile_info<CH>(pts, io, TcWork{w.point, w.m, w.rt, w.ct}, nt_of, ti);
+}
+
+// Loader (one warp, lane 0 issues): the raw rows of every k-step of a tile by
+// tensor-map TMA, NRAW k-steps ahead.  Returns false when a wait gave up.
+template <int CH>
+__device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__restrict__ pts,
+                                          const RhsIO *__restrict__ io, const StWork &w,
+                                          const int *__restrict__ nt_of, const CUtensorMap *__restrict__ maps,
+                                          uint32_t &it, int lane) {
+  TileInfo ti;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  const uint4 ord = korder_row<CH>(pts[ti.point], ti.N, w.m);
+  const CUtensorMap *mp = maps + (size_t)ti.point * M_COUNT;
+  for (int ki = 0; ki < ti.nk; ++ki, ++it) {
+    const int j = it % NRAW;
+    if (!wwait(&S.raw_empty[j], ((it / NRAW) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+    const Step q = step_of<CH>(ti, kstep_at<CH>(ord, ti, ki));
+    const bool two = CH == CH_DPH && !q.half;
+    uint8_t *raw = S.raws + j * RAW_STAGE;
+    const uint32_t bytes = (uint32_t)(RAW_A * (two ? 2 : 1) + KS * ti.NT * 8 + RA * 8);
+    if (lane == 0) {
+      uint64_t *bar = &S.raw_full[j];
+      arrive_expect_tx(bar, bytes);
+      const int xa = 2 * q.a0, xb = 2 * ti.c0, x = ti.g.x;
+      if (CH == CH_PP) {
+        tma3(raw, mp + M_PA, xa, ti.g.row_lo + ti.r0, x, bar);
+        tma3(raw + 2 * RAW_A, mp + M_PB, xb, ti.g.p_lo + q.kl, x, bar);
+        tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPP, xa, x, bar);
+      } else if (CH == CH_XPH) {
+        const bool d2 = x >= 0;
+        const int z = x >= 0 ? x : -x;
+        tma3(raw, mp + (d2 ? M_W2A : M_W1A), xa, ti.r0, z, bar);
+        tma3(raw + 2 * RAW_A, mp + (d2 ? M_W2B : M_W1B), xb, q.kl, z, bar);
+        tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, x + ti.N - 1, bar);
+      } else {
+        const bool d1 = x >= 0;
+        const int z = x >= 0 ? x : -x;
+        tma3(raw, mp + (d1 ? M_X1A : M_X2A), xa, ti.r0, z, bar);
+        if (two) tma3(raw + RAW_A, mp + (d1 ? M_W1A : M_W2A), xa, ti.r0, z, bar);
+        const CUtensorMap *mb = q.half ? mp + (d1 ? M_W1B : M_W2B) : mp + (d1 ? M_X1B : M_X2B);
+        tma3(raw + 2 * RAW_A, mb, xb, q.kl, z, bar);
+        tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, -x + ti.N - 1, bar);
+      }
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// One transform item: 4 consecutive k of one complex operand row (left) or
+// column (right), split into hi / lo of the real and the imaginary parts.
+struct XfVals {
+  float4 rh, rl, ih, il;
+  int row, g4;
+  bool valid;
+};
+// Left item t (row t / 4, k-group t % 4) of a 64 x 16 tile: Lb-weighted, and
+// for the direct channel 2A - C (first half of K) or -A (second half).
+template <int CH>
+__device__ __forceinline__ void xf_left(XfVals &o, const float2 *rA, const float2 *rC, const float2 *rL, int t,
+                                        int off, const Step &q) {
+  const int r = t >> 2, g4 = t & 3;
+  float2 v[4], c[4], L[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int kk = 4 * g4 + x;
+    v[x] = rA[r * RA + off + kk];
+    L[x] = rL[off + kk];
+    if (CH == CH_DPH) c[x] = rC[r * RA + off + kk];
+  }
+  float re[4], im[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int kk = 4 * g4 + x;
+    float2 u = v[x];
+    if (CH == CH_DPH) u = q.half ? make_float2(-u.x, -u.y) : make_float2(2.f * u.x - c[x].x, 2.f * u.y - c[x].y);
+    float2 a = cmulf(u, L[x]);
+    if (!(r < q.nA && kk < q.nK)) a = make_float2(0.f, 0.f);
+    re[x] = a.x;
+    im[x] = a.y;
+  }
+  split_tf32(re[0], o.rh.x, o.rl.x);
+  split_tf32(re[1], o.rh.y, o.rl.y);
+  split_tf32(re[2], o.rh.z, o.rl.z);
+  split_tf32(re[3], o.rh.w, o.rl.w);
+  split_tf32(im[0], o.ih.x, o.il.x);
+  split_tf32(im[1], o.ih.y, o.il.y);
+  split_tf32(im[2], o.ih.z, o.il.z);
+  split_tf32(im[3], o.ih.w, o.il.w);
+  o.row = r;
+  o.g4 = g4;
+  o.valid = true;
+}
+// Right item bt (column bt % NT, k-group bt / NT): columns whose fourth
+// frequency leaves the box take the bare U.
+template <int CH>
+__device__ __forceinline__ void xf_right(XfVals &o, const float2 *rB, int bt, const TileInfo &ti, const Step &q,
+                                         float U) {
+  o.valid = bt < 4 * ti.NT;
+  const int c = bt % ti.NT, g4 = o.valid ? bt / ti.NT : 0;
+  const int cc = ti.c0 + c;
+  const int f = CH == CH_PP ? ti.g.x - cc : (CH == CH_DPH ? cc - ti.g.x : cc + ti.g.x);
+  const bool cv = c < q.ncols, ok = (unsigned)f < (unsigned)ti.N;
+  float2 b[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) b[x] = rB[(4 * g4 + x) * ti.NT + c];
+  float re[4], im[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int kk = 4 * g4 + x;
+    float2 u = ok ? b[x] : make_float2(U, 0.f);
+    if (!(cv && kk < q.nK)) u = make_float2(0.f, 0.f);
+    re[x] = u.x;
+    im[x] = u.y;
+  }
+  split_tf32(re[0], o.rh.x, o.rl.x);
+  split_tf32(re[1], o.rh.y, o.rl.y);
+  split_tf32(re[2], o.rh.z, o.rl.z);
+  split_tf32(re[3], o.rh.w, o.rl.w);
+  split_tf32(im[0], o.ih.x, o.il.x);
+  split_tf32(im[1], o.ih.y, o.il.y);
+  split_tf32(im[2], o.ih.z, o.il.z);
+  split_tf32(im[3], o.ih.w, o.il.w);
+  o.row = c;
+  o.g4 = g4;
+}
+// Operand rows 2n (real part) and 2n + 1 (imaginary part) of the hi and lo
+// slices.  Lanes with flip = 1 write the imaginary row first, so that each
+// 16-byte store instruction of a warp covers all eight bank groups of the
+// 64-byte swizzle (rows 2n and 2n + 1 share a 128-byte line).
+__device__ __forceinline__ void xf_store(uint8_t *T, int slice, const XfVals &v, int n, int g4, int flip) {
+  const int r0 = 2 * n + flip, r1 = 2 * n + 1 - flip;
+  *reinterpret_cast<float4 *>(T + swz64(r0, g4)) = flip ? v.ih : v.rh;
+  *reinterpret_cast<float4 *>(T + swz64(r1, g4)) = flip ? v.rh : v.ih;
+  *reinterpret_cast<float4 *>(T + slice + swz64(r0, g4)) = flip ? v.il : v.rl;
+  *reinterpret_cast<float4 *>(T + slice + swz64(r1, g4)) = flip ? v.rl : v.il;
+}
+
+// Transform warps: raw rows -> bubble-weighted (left), bare-U filled (right),
+// split hi/lo, swizzled K-major operand tiles.
+template <int CH>
+__device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restrict__ pts,
+                                        const RhsIO *__restrict__ io, const StWork &w,
+                                        const int *__restrict__ nt_of, uint32_t &it, int xt, int lane) {
+  TileInfo ti;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  const PointDesc &P = pts[ti.point];
+  const float U = (float)P.U;
+  const uint4 ord = korder_row<CH>(P, ti.N, w.m);
+  for (int ki = 0; ki < ti.nk; ++ki, ++it) {
+    const int j = it % NRAW, s = it % NOP;
+    if (!wwait(&S.raw_full[j], (it / NRAW) & 1u, S.err, S.abort_flag)) return false;
+    if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+    uint8_t *raws = S.raws, *ops = S.ops;
+    const Step q = step_of<CH>(ti, kstep_at<CH>(ord, ti, ki));
+    const int off = q.p0 - q.a0;
+    const uint8_t *raw = raws + j * RAW_STAGE;
+    const float2 *rA = reinterpret_cast<const float2 *>(raw);
+    const float2 *rC = reinterpret_cast<const float2 *>(raw + RAW_A);
+    const float2 *rB = reinterpret_cast<const float2 *>(raw + 2 * RAW_A);
+    const float2 *rL = reinterpret_cast<const float2 *>(raw + 2 * RAW_A + RAW_B);
+    uint8_t *A = ops + s * OP_STAGE;
+    uint8_t *B = A + 2 * A_SLICE;
+    if (xt < 256) {
+      // warps 0-7: left item xt and right item xt, two independent chains
+      XfVals va, vb;
+      xf_left<CH>(va, rA, rC, rL, xt, off, q);
+      xf_right<CH>(vb, rB, xt, ti, q, U);
+      xf_store(A, A_SLICE, va, xt >> 2, xt & 3, (xt >> 2) & 1);
+      if (vb.valid) xf_store(B, B_SLICE, vb, vb.row, vb.g4, (vb.row >> 2) & 1);
+    } else {
+      // warps 8-11: right items xt and xt + 128
+      XfVals va, vb;
+      xf_right<CH>(va, rB, xt, ti, q, U);
+      xf_right<CH>(vb, rB, xt + 128, ti, q, U);
+      if (va.valid) xf_store(B, B_SLICE, va, va.row, va.g4, (va.row >> 2) & 1);
+      if (vb.valid) xf_store(B, B_SLICE, vb, vb.row, vb.g4, (vb.row >> 2) & 1);
+    }
+    // one arrival per warp: the generic-proxy writes are fenced for the
+    // tensor cores by every writer, then the warp converges
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&S.raw_empty[j]);
+      mbar_arrive(&S.op_full[s]);
+    }
+  }
+  return true;
+}
+
+// MMA issue (one warp, lane 0 issues): per k-step hi*hi into one TMEM
+// accumulator and hi*lo + lo*hi into a second one, so that the large sum takes
+// a third of the accumulation steps.
+template <int CH>
+__device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restrict__ pts,
+                                         const RhsIO *__restrict__ io, const StWork &w,
+                                         const int *__restrict__ nt_of, uint32_t &it, uint32_t &tcount, int lane) {
+  TileInfo ti;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  if (!wwait(&S.tempty[0], (tcount & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+  tc_after();
+  const uint32_t d = S.tmem, dx = S.tmem + 256;
+  const uint32_t id = idesc<FRG_3XTF32>(2 * ti.NT);
+  for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+    const int s = it % NOP;
+    if (!wwait(&S.op_full[s], (it / NOP) & 1u, S.err, S.abort_flag)) return false;
+    tc_after();
+    if (lane == 0) {
+      const uint32_t a0 = smem_u32(S.ops + s * OP_STAGE), b0 = a0 + 2 * A_SLICE;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const uint32_t o = kk * 32;
+        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+        mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + o), id, first);                    // hi*hi
+        mma_tf32(dx, sdesc64(a0 + o), sdesc64(b0 + B_SLICE + o), id, first);         // hi*lo
+        mma_tf32(dx, sdesc64(a0 + A_SLICE + o), sdesc64(b0 + o), id, 1u);            // lo*hi
+      }
+      mma_commit(&S.op_empty[s]);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) mma_commit(&S.tfull[0]);
+  __syncwarp();
+  ++tcount;
+  return true;
+}
+
+// Epilogue (warps 0-3): TMEM lane 2r holds (Re a . Re b, Re a . Im b), lane
+// 2r+1 (Im a . Re b, Im a . Im b) of complex row r: the lane pair combines them
+// by shuffles, the warp stages its 16 rows x 16 complex of each column chunk in
+// shared memory and stores them as whole 128-byte row segments.
+template <int CH>
+__device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restrict__ pts,
+                                         const RhsIO *__restrict__ io, const StWork &w,
+                                         const int *__restrict__ nt_of, uint32_t &tcount, int warp, int lane) {
+  TileInfo ti;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  if (!wwait(&S.tfull[0], tcount & 1u, S.err, S.abort_flag)) return false;
+  tc_after();
+  const int L = warp * 32 + lane;
+  const int r = L >> 1, odd = L & 1;
+  float2 *stg = S.epi_stg + warp * (16 * EPI_PITCH);
+  const uint32_t tmem = S.tmem;
+  uint64_t *tempty = S.tempty;
+  const PointDesc &P = pts[ti.point];
+  const RhsIO &o = io[ti.point];
+  const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
+  float2 *kN = static_cast<float2 *>(o.dgam);
+  const int rr = ti.r0 + r;
+  float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int cb = 0; cb < 2 * ti.NT; cb += 32) {
+    float v[32], vx[32];
+    tmem_ld32(tl + cb, v);
+    tmem_ld32(tl + 256 + cb, vx);
+    tmem_wait_ld();
+    if (cb + 32 >= 2 * ti.NT) {
+      // all TMEM reads of this tile are done: let the next tile's MMAs start
+      tc_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[0]);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += vx[i];
+    // even lane keeps columns 0..7 of the chunk, odd lane 8..15
+    float2 out[8];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float pr = __shfl_xor_sync(0xffffffffu, v[2 * c], 1);      // partner's x.Re b
+      const float pi = __shfl_xor_sync(0xffffffffu, v[2 * c + 1], 1);  // partner's x.Im b
+      // even lane: own (ArBr, ArBi), partner (AiBr, AiBi)
+      // odd lane:  own (AiBr, AiBi), partner (ArBr, ArBi)
+      const float re = odd ? pr - v[2 * c + 1] : v[2 * c] - pi;
+      const float im = odd ? pi + v[2 * c] : v[2 * c + 1] + pr;
+      if ((c >> 3) == odd) out[c & 7] = make_float2(re * sc, im * sc);
+    }
+    __syncwarp();  // the previous chunk's reads of the staging rows are done
+    float4 *w4 = reinterpret_cast<float4 *>(stg + (lane >> 1) * EPI_PITCH + 8 * odd);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w4[j] = make_float4(out[2 * j].x, out[2 * j].y, out[2 * j + 1].x, out[2 * j + 1].y);
+    __syncwarp();
+    const int q = lane & 7;
+    const int cl = cb / 2 + 2 * q;  // column (pair) within the tile
+    const int cg = ti.c0 + cl;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rho = (lane >> 3) + 4 * i;  // staged row 0..15
+      float2 *dst = reinterpret_cast<float2 *>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(orow), 2 * rho));
+      const float4 val = *reinterpret_cast<const float4 *>(stg + rho * EPI_PITCH + 2 * q);
+      if (dst && cg < ti.N && cl < ti.NT) *reinterpret_cast<float4 *>(dst + cg) = val;
+    }
+  }
+  ++tcount;
+  return true;
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
-    k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const TcWork *__restrict__ work,
-                    int nwork, const int *__restrict__ nt_of, unsigned *__restrict__ err,
+    k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const StWork *__restrict__ work,
+                    const int *__restrict__ cta_start, const int *__restrict__ nt_of, unsigned *__restrict__ err,
                     const CUtensorMap *__restrict__ maps) {
   extern __shared__ uint8_t smem_raw[];
   // offset the shared array itself (keeps the shared state space for ld/st.shared)
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t *ops = smem;
-  uint8_t *raws = ops + NOP * OP_STAGE;
-  float2 *stgT = reinterpret_cast<float2 *>(raws + NRAW * RAW_STAGE);
-  float2 *stgB = stgT + MROWS * 17;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(raws + NRAW * RAW_STAGE + 2 * STG);
-  uint64_t *raw_full = bars, *raw_empty = bars + NRAW, *op_full = bars + 2 * NRAW, *op_empty = op_full + NOP;
-  uint64_t *tfull = op_empty + NOP, *tempty = tfull + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  Pipe S;
+  S.ops = smem;
+  S.raws = S.ops + NOP * OP_STAGE;
+  S.epi_stg = reinterpret_cast<float2 *>(S.raws + NRAW * RAW_STAGE);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(S.raws + NRAW * RAW_STAGE + 4 * EPI_STG);
+  S.raw_full = bars;
+  S.raw_empty = bars + NRAW;
+  S.op_full = bars + 2 * NRAW;
+  S.op_empty = S.op_full + NOP;
+  S.tfull = S.op_empty + NOP;
+  S.tempty = S.tfull + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(S.tempty + 2);
+  S.abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  S.err = err;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int j = 0; j < NRAW; ++j) {
-      mbar_init(&raw_full[j], 1);
-      mbar_init(&raw_empty[j], XF_THREADS);
+      mbar_init(&S.raw_full[j], 1);
+      mbar_init(&S.raw_empty[j], N_XF);
     }
     for (int s = 0; s < NOP; ++s) {
-      mbar_init(&op_full[s], XF_THREADS);
-      mbar_init(&op_empty[s], 1);
+      mbar_init(&S.op_full[s], N_XF);
+      mbar_init(&S.op_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 32 * EPI_W);
+      mbar_init(&S.tfull[b], 1);
+      mbar_init(&S.tempty[b], EPI_W);
     }
-    *abort_flag = 0;
+    *S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == MMA_W) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_before();
   __syncthreads();
   tc_after();
-  const uint32_t tmem = *tmem_slot;
+  S.tmem = *tmem_slot;
+  const int w0 = cta_start[blockIdx.x], w1 = cta_start[blockIdx.x + 1];
 
+#define FRG_BY_CH(f, ...) \
+  (w.ch == CH_PP ? f<CH_PP>(__VA_ARGS__) : w.ch == CH_DPH ? f<CH_DPH>(__VA_ARGS__) : f<CH_XPH>(__VA_ARGS__))
   if (warp == LOAD_W) {
-    // ---------------------------------------------------------- loader ----
     uint32_t it = 0;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      const PointDesc &PL = pts[ti.point];
-      for (int ki = 0; ki < ti.nk; ++ki, ++it) {
-        const int j = it % NRAW;
-        if (!mbar_wait(&raw_empty[j], ((it / NRAW) & 1u) ^ 1u, err, abort_flag)) goto load_done;
-        const int kb = kstep_at<CH>(PL, ti, work[wi].m, ki);
-        const Step q = step_of<CH>(ti, kb);
-        const bool two = CH == CH_DPH && !q.half;
-        uint8_t *raw = raws + j * RAW_STAGE;
-        const uint32_t bytes = (uint32_t)(RAW_A * (two ? 2 : 1) + KS * ti.NT * 8 + RA * 8);
-        if (lane == 0) {
-          const CUtensorMap *mp = maps + (size_t)ti.point * M_COUNT;
-          arrive_expect_tx(&raw_full[j], bytes);
-          const int xa = 2 * q.a0, xb = 2 * ti.c0, x = ti.g.x;
-          if (CH == CH_PP) {
-            tma3(raw, mp + M_PA, xa, ti.g.row_lo + ti.r0, x, &raw_full[j]);
-            tma3(raw + 2 * RAW_A, mp + M_PB, xb, ti.g.p_lo + q.kl, x, &raw_full[j]);
-            tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPP, xa, x, &raw_full[j]);
-          } else if (CH == CH_XPH) {
-            const bool d2 = x >= 0;
-            const int z = x >= 0 ? x : -x;
-            tma3(raw, mp + (d2 ? M_W2A : M_W1A), xa, ti.r0, z, &raw_full[j]);
-            tma3(raw + 2 * RAW_A, mp + (d2 ? M_W2B : M_W1B), xb, q.kl, z, &raw_full[j]);
-            tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, x + ti.N - 1, &raw_full[j]);
-          } else {
-            const bool d1 = x >= 0;
-            const int z = x >= 0 ? x : -x;
-            tma3(raw, mp + (d1 ? M_X1A : M_X2A), xa, ti.r0, z, &raw_full[j]);
-            if (two) tma3(raw + RAW_A, mp + (d1 ? M_W1A : M_W2A), xa, ti.r0, z, &raw_full[j]);
-            const CUtensorMap *mb = q.half ? mp + (d1 ? M_W1B : M_W2B) : mp + (d1 ? M_X1B : M_X2B);
-            tma3(raw + 2 * RAW_A, mb, xb, q.kl, z, &raw_full[j]);
-            tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, -x + ti.N - 1, &raw_full[j]);
-          }
-        }
-        __syncwarp();
-      }
+    for (int wi = w0; wi < w1; ++wi) {
+      const StWork w = work[wi];
+      if (!FRG_BY_CH(load_tile, S, pts, io, w, nt_of, maps, it, lane)) break;
     }
-  load_done:
     // copies still in flight must land before the CTA leaves
     for (uint32_t k = it > (uint32_t)NRAW ? it - NRAW : 0u; k < it; ++k)
-      mbar_wait(&raw_full[k % NRAW], (k / NRAW) & 1u, err, abort_flag);
+      wwait(&S.raw_full[k % NRAW], (k / NRAW) & 1u, err, S.abort_flag);
   } else if (warp >= XF_W0) {
-    // ------------------------------------------------------- transform ----
     const int xt = tid - 32 * XF_W0;
     uint32_t it = 0;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      const PointDesc &P = pts[ti.point];
-      const float U = (float)P.U;
-      for (int ki = 0; ki < ti.nk; ++ki, ++it) {
-        const int j = it % NRAW, s = it % NOP;
-        if (!mbar_wait(&raw_full[j], (it / NRAW) & 1u, err, abort_flag)) goto xf_done;
-        if (!mbar_wait(&op_empty[s], ((it / NOP) & 1u) ^ 1u, err, abort_flag)) goto xf_done;
-        const Step q = step_of<CH>(ti, kstep_at<CH>(P, ti, work[wi].m, ki));
-        const int off = q.p0 - q.a0;
-        const uint8_t *raw = raws + j * RAW_STAGE;
-        const float2 *rA = reinterpret_cast<const float2 *>(raw);
-        const float2 *rC = reinterpret_cast<const float2 *>(raw + RAW_A);
-        const float2 *rB = reinterpret_cast<const float2 *>(raw + 2 * RAW_A);
-        const float2 *rL = reinterpret_cast<const float2 *>(raw + 2 * RAW_A + RAW_B);
-        uint8_t *A = ops + s * OP_STAGE;
-        uint8_t *B = A + 2 * A_SLICE;
-        for (int t = xt; t < 256 + 4 * ti.NT; t += XF_THREADS) {
-          if (t < 256) {
-            const int r = t >> 2, g4 = t & 3;
-            const bool rv = r < q.nA;
-            float4 rh, rl, ih, il;
-            float re[4], im[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              const int kk = 4 * g4 + x;
-              float2 a = make_float2(0.f, 0.f);
-              if (rv && kk < q.nK) {
-                const float2 v = rA[r * RA + off + kk], L = rL[off + kk];
-                if (CH == CH_DPH) {
-                  if (!q.half) {
-                    const float2 c = rC[r * RA + off + kk];
-                    a = cmulf(make_float2(2.f * v.x - c.x, 2.f * v.y - c.y), L);
-                  } else {
-                    a = cmulf(make_float2(-v.x, -v.y), L);
-                  }
-                } else {
-                  a = cmulf(v, L);
-                }
-              }
-              re[x] = a.x;
-              im[x] = a.y;
-            }
-            split_tf32(re[0], rh.x, rl.x);
-            split_tf32(re[1], rh.y, rl.y);
-            split_tf32(re[2], rh.z, rl.z);
-            split_tf32(re[3], rh.w, rl.w);
-            split_tf32(im[0], ih.x, il.x);
-            split_tf32(im[1], ih.y, il.y);
-            split_tf32(im[2], ih.z, il.z);
-            split_tf32(im[3], ih.w, il.w);
-            *reinterpret_cast<float4 *>(A + swz64(2 * r, g4)) = rh;
-            *reinterpret_cast<float4 *>(A + swz64(2 * r + 1, g4)) = ih;
-            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(2 * r, g4)) = rl;
-            *reinterpret_cast<float4 *>(A + A_SLICE + swz64(2 * r + 1, g4)) = il;
-          } else {
-            const int bt = t - 256;
-            const int c = bt % ti.NT, g4 = bt / ti.NT;
-            const int cc = ti.c0 + c;
-            const int f = CH == CH_PP ? ti.g.x - cc : (CH == CH_DPH ? cc - ti.g.x : cc + ti.g.x);
-            const bool cv = c < q.ncols, ok = (unsigned)f < (unsigned)ti.N;
-            float re[4], im[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              const int kk = 4 * g4 + x;
-              float2 b = make_float2(0.f, 0.f);
-              if (cv && kk < q.nK) b = ok ? rB[kk * ti.NT + c] : make_float2(U, 0.f);
-              re[x] = b.x;
-              im[x] = b.y;
-            }
-            float4 rh, rl, ih, il;
-            split_tf32(re[0], rh.x, rl.x);
-            split_tf32(re[1], rh.y, rl.y);
-            split_tf32(re[2], rh.z, rl.z);
-            split_tf32(re[3], rh.w, rl.w);
-            split_tf32(im[0], ih.x, il.x);
-            split_tf32(im[1], ih.y, il.y);
-            split_tf32(im[2], ih.z, il.z);
-            split_tf32(im[3], ih.w, il.w);
-            *reinterpret_cast<float4 *>(B + swz64(2 * c, g4)) = rh;
-            *reinterpret_cast<float4 *>(B + swz64(2 * c + 1, g4)) = ih;
-            *reinterpret_cast<float4 *>(B + B_SLICE + swz64(2 * c, g4)) = rl;
-            *reinterpret_cast<float4 *>(B + B_SLICE + swz64(2 * c + 1, g4)) = il;
-          }
-        }
-        mbar_arrive(&raw_empty[j]);
-        fence_async_smem();
-        mbar_arrive(&op_full[s]);
-      }
+    for (int wi = w0; wi < w1; ++wi) {
+      const StWork w = work[wi];
+      if (!FRG_BY_CH(xf_tile, S, pts, io, w, nt_of, it, xt, lane)) break;
     }
-  xf_done:;
   } else if (warp == MMA_W) {
-    // ------------------------------------------------------ MMA issue ----
     uint32_t it = 0, tcount = 0;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      // one TMEM buffer: columns [0,256) hold hi*hi, [256,512) hi*lo + lo*hi, so
-      // that the large sum takes a third of the accumulation steps
-      if (!mbar_wait(&tempty[0], (tcount & 1u) ^ 1u, err, abort_flag)) break;
-      tc_after();
-      const uint32_t d = tmem, dx = tmem + 256;
-      const uint32_t id = idesc<FRG_3XTF32>(2 * ti.NT);
-      bool ok = true;
-      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
-        const int s = it % NOP;
-        if (!mbar_wait(&op_full[s], (it / NOP) & 1u, err, abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_after();
-        if (lane == 0) {
-          const uint32_t a0 = smem_u32(ops + s * OP_STAGE), b0 = a0 + 2 * A_SLICE;
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            const uint32_t o = kk * 32;
-            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + o), id, first);                    // hi*hi
-            mma_tf32(dx, sdesc64(a0 + o), sdesc64(b0 + B_SLICE + o), id, first);         // hi*lo
-            mma_tf32(dx, sdesc64(a0 + A_SLICE + o), sdesc64(b0 + o), id, 1u);            // lo*hi
-          }
-          mma_commit(&op_empty[s]);
-        }
-        __syncwarp();
-      }
-      if (!ok) break;
-      if (lane == 0) mma_commit(&tfull[0]);
-      __syncwarp();
-      ++tcount;
+    for (int wi = w0; wi < w1; ++wi) {
+      const StWork w = work[wi];
+      if (!FRG_BY_CH(mma_tile, S, pts, io, w, nt_of, it, tcount, lane)) break;
     }
   } else {
-    // ------------------------------------------------------- epilogue ----
-    // TMEM lane 2r holds (Re a . Re b, Re a . Im b), lane 2r+1 (Im a . Re b,
-    // Im a . Im b) of complex row r: the lane pair combines them by shuffles and
-    // each lane stores 8 of the pair's 16 complex columns (64 contiguous bytes).
     uint32_t tcount = 0;
-    const int L = warp * 32 + lane;
-    const int r = L >> 1, odd = L & 1;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      if (!mbar_wait(&tfull[0], tcount & 1u, err, abort_flag)) break;
-      tc_after();
-      const PointDesc &P = pts[ti.point];
-      const RhsIO &o = io[ti.point];
-      const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
-      float2 *kN = static_cast<float2 *>(o.dgam);
-      const int rr = ti.r0 + r;
-      float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-      for (int cb = 0; cb < 2 * ti.NT; cb += 32) {
-        float v[32], vx[32];
-        tmem_ld32(tl + cb, v);
-        tmem_ld32(tl + 256 + cb, vx);
-        tmem_wait_ld();
-        if (cb + 32 >= 2 * ti.NT) {
-          // all TMEM reads of this tile are done: let the next tile's MMAs start
-          tc_before();
-          mbar_arrive(&tempty[0]);
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += vx[i];
-        // even lane keeps columns 0..7 of the chunk, odd lane 8..15
-        float2 out[8];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float pr = __shfl_xor_sync(0xffffffffu, v[2 * c], 1);      // partner's x.Re b
-          const float pi = __shfl_xor_sync(0xffffffffu, v[2 * c + 1], 1);  // partner's x.Im b
-          // even lane: own (ArBr, ArBi), partner (AiBr, AiBi)
-          // odd lane:  own (AiBr, AiBi), partner (ArBr, ArBi)
-          const float re = odd ? pr - v[2 * c + 1] : v[2 * c] - pi;
-          const float im = odd ? pi + v[2 * c] : v[2 * c + 1] + pr;
-          if ((c >> 3) == odd) out[c & 7] = make_float2(re * sc, im * sc);
-        }
-        const int c0 = ti.c0 + cb / 2 + 8 * odd;
-        if (orow) {
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c0 + c < ti.N && cb / 2 + 8 * odd + c < ti.NT) orow[c0 + c] = out[c];
-        }
-      }
-      ++tcount;
+    for (int wi = w0; wi < w1; ++wi) {
+      const StWork w = work[wi];
+      if (!FRG_BY_CH(epi_tile, S, pts, io, w, nt_of, tcount, warp, lane)) break;
     }
   }
+#undef FRG_BY_CH
   tc_before();
   __syncthreads();
   tc_after();
-  if (warp == MMA_W) tmem_dealloc(tmem, TMEM_COLS);
+  if (warp == MMA_W) tmem_dealloc(S.tmem, TMEM_COLS);
 }
 }  // namespace st
 
@@ -1079,7 +1224,63 @@ struct TcPlan {
   int nall[3] = {0, 0, 0};
   tc::TcWork *d_pt[3] = {nullptr, nullptr, nullptr};
   std::vector<int> off[3];
+  // 3xTF32: one launch for all enabled channels; schedule [0] covers every
+  // point, [1 + i] point i alone
+  struct Sched {
+    tc::st::StWork *d_work = nullptr;
+    int *d_start = nullptr;
+    int grid = 0;
+  };
+  std::vector<Sched> sched;
+  int mask = 7;
 };
+
+// Longest-processing-time schedule of the tiles of points [first, last) over at
+// most `sms` persistent CTAs: tiles sorted by cost (k-steps plus an epilogue
+// allowance), each given to the CTA with the least work so far; stored CTA by
+// CTA with start offsets.
+static bool build_sched(TcPlan *p, const std::vector<PointDesc> &pts, const std::vector<int> &nt, int first,
+                        int last, TcPlan::Sched &out) {
+  constexpr int EPI_COST = 3;  // epilogue of one tile, in k-step units
+  std::vector<std::pair<int, tc::st::StWork>> tiles;
+  for (int i = first; i < last; ++i) {
+    const int N = pts[i].N;
+    for (int ch = 0; ch < 3; ++ch) {
+      if (!(p->mask & (1 << ch))) continue;
+      for (int m = 0; m < 2 * N - 1; ++m) {
+        const Geom g = geom(ch, N, m);
+        const int nk = (ch == CH_DPH ? 2 : 1) * ((g.D + tc::KSTEP - 1) / tc::KSTEP);
+        for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
+          for (int ct = 0; ct * nt[i] < N; ++ct)
+            tiles.push_back({nk + EPI_COST, tc::st::StWork{i, (short)m, (short)ch, (short)rt, (short)ct}});
+      }
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](auto &a, auto &b) { return a.first > b.first; });
+  const int grid = std::min((int)tiles.size(), p->sms);
+  out.grid = grid;
+  if (!grid) return true;
+  std::vector<std::vector<tc::st::StWork>> per(grid);
+  std::vector<long> load(grid, 0);
+  for (auto &t : tiles) {
+    int best = 0;
+    for (int c = 1; c < grid; ++c)
+      if (load[c] < load[best]) best = c;
+    load[best] += t.first;
+    per[best].push_back(t.second);
+  }
+  std::vector<tc::st::StWork> flat;
+  std::vector<int> start(1, 0);
+  for (auto &v : per) {
+    flat.insert(flat.end(), v.begin(), v.end());
+    start.push_back((int)flat.size());
+  }
+  return cudaMalloc(&out.d_work, sizeof(tc::st::StWork) * flat.size()) == cudaSuccess &&
+         cudaMalloc(&out.d_start, sizeof(int) * start.size()) == cudaSuccess &&
+         cudaMemcpy(out.d_work, flat.data(), sizeof(tc::st::StWork) * flat.size(), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemcpy(out.d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+}
 
 // Tensor maps of the operand tiles (see MapId): box {2*RA floats, 64 rows} for
 // left operands, {2*NT floats, 16 rows} for right operands, {2*RA, 1} for the
@@ -1162,7 +1363,6 @@ static bool set_smem_attrs() {
 
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
                    int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why) {
-  (void)params;
   (void)d_pts;
   *out = nullptr;
   if (precision != FRG_3XTF32 && precision != FRG_BF16X3) {
@@ -1217,6 +1417,12 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
              cudaSuccess &&
          cudaMemcpy(p->d_pt[ch], per.data(), sizeof(tc::TcWork) * per.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   }
+  p->mask = (params.empty() ? FRG_CH_ALL : params[0].channel_mask) & 7;
+  if (precision == FRG_3XTF32 && ok) {
+    p->sched.resize(1 + p->n);
+    ok = build_sched(p, pts, nt, 0, p->n, p->sched[0]);
+    for (int i = 0; i < p->n && ok; ++i) ok = build_sched(p, pts, nt, i, i + 1, p->sched[1 + i]);
+  }
   if (precision == FRG_3XTF32 && ok) {
     std::string mw;
     ok = encode_maps(p, pts, mw);
@@ -1227,13 +1433,8 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
     }
   }
   if (precision == FRG_3XTF32) {
-    ok = ok &&
-         cudaFuncSetAttribute(tc::st::k_contract_tf32<CH_PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tc::st::SMEM) == cudaSuccess &&
-         cudaFuncSetAttribute(tc::st::k_contract_tf32<CH_DPH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tc::st::SMEM) == cudaSuccess &&
-         cudaFuncSetAttribute(tc::st::k_contract_tf32<CH_XPH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tc::st::SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(tc::st::k_contract_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::st::SMEM) == cudaSuccess;
   } else {
     ok = ok && set_smem_attrs<FRG_BF16X3>();
   }
@@ -1250,6 +1451,10 @@ void tc_plan_destroy(TcPlan *p) {
   if (!p) return;
   cudaFree(p->d_maps);
   cudaFree(p->d_nt);
+  for (auto &sc : p->sched) {
+    cudaFree(sc.d_work);
+    cudaFree(sc.d_start);
+  }
   for (int ch = 0; ch < 3; ++ch) {
     cudaFree(p->d_all[ch]);
     cudaFree(p->d_pt[ch]);
@@ -1275,40 +1480,38 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
     if (launch_relayout(d_pts, d_io, n_points, maxN, 1, (chmask & 2) != 0, st) != 0) return -3;
   }
   if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
-  for (int ch = 0; ch < 3; ++ch) {
-    if (!(chmask & (1 << ch))) continue;
-    const tc::TcWork *w;
-    int nw;
-    if (point < 0) {
-      w = p->d_all[ch];
-      nw = p->nall[ch];
-    } else {
-      w = p->d_pt[ch] + p->off[ch][point];
-      nw = p->off[ch][point + 1] - p->off[ch][point];
+  if (p->precision == FRG_3XTF32) {
+    if ((chmask & 7) != p->mask || point >= p->n) return -1;
+    const TcPlan::Sched &sc = p->sched[point < 0 ? 0 : 1 + point];
+    if (sc.grid) {
+      tc::st::k_contract_tf32<<<sc.grid, tc::st::THREADS, tc::st::SMEM, st>>>(d_pts, d_io, sc.d_work, sc.d_start,
+                                                                              p->d_nt, p->d_err, p->d_maps);
+      FRG_COUNT(1);
+      if (cudaGetLastError() != cudaSuccess) return -3;
     }
-    if (!nw) continue;
-    const int grid = std::min(nw, p->sms);
-    if (p->precision == FRG_3XTF32) {
-      const int sm = tc::st::SMEM;
-      if (ch == CH_PP)
-        tc::st::k_contract_tf32<CH_PP><<<grid, tc::st::THREADS, sm, st>>>(d_pts, d_io, w, nw, p->d_nt, p->d_err,
-                                                                         p->d_maps);
-      else if (ch == CH_DPH)
-        tc::st::k_contract_tf32<CH_DPH><<<grid, tc::st::THREADS, sm, st>>>(d_pts, d_io, w, nw, p->d_nt, p->d_err,
-                                                                          p->d_maps);
-      else
-        tc::st::k_contract_tf32<CH_XPH><<<grid, tc::st::THREADS, sm, st>>>(d_pts, d_io, w, nw, p->d_nt, p->d_err,
-                                                                          p->d_maps);
-    } else
+  } else {
+    for (int ch = 0; ch < 3; ++ch) {
+      if (!(chmask & (1 << ch))) continue;
+      const tc::TcWork *w;
+      int nw;
+      if (point < 0) {
+        w = p->d_all[ch];
+        nw = p->nall[ch];
+      } else {
+        w = p->d_pt[ch] + p->off[ch][point];
+        nw = p->off[ch][point + 1] - p->off[ch][point];
+      }
+      if (!nw) continue;
+      const int grid = std::min(nw, p->sms);
       launch_one<FRG_BF16X3>(ch, grid, st, d_pts, d_io, w, nw, p->d_nt, p->d_err);
-    FRG_COUNT(1);
-    if (cudaGetLastError() != cudaSuccess) return -3;
+      FRG_COUNT(1);
+      if (cudaGetLastError() != cudaSuccess) return -3;
+    }
   }
   if (ev_contract && cudaEventRecord(ev_contract, st) != cudaSuccess) return -3;
-  // channel outputs in their own layouts -> natural layout (the scatter-add)
-  if (chmask & 6) {
-    if (launch_combine(d_pts, d_io, n_points, maxN, chmask, st) != 0) return -3;
-  }
+  // channel outputs in their own layouts -> natural layout (the scatter-add);
+  // also resets the vertex bound that the BF16 slicing read
+  if (launch_combine(d_pts, d_io, n_points, maxN, chmask, st) != 0) return -3;
   return 0;
 }
 
