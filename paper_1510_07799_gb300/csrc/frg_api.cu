@@ -52,6 +52,13 @@ struct frg_ctx {
   };
   std::vector<UserScratch> user_split;
   bool need_k1 = true;
+  // flow driver: one DP5 step attempt of every point is captured once as a
+  // CUDA graph and replayed on an internal stream, ordered after and before
+  // the caller's stream by events
+  cudaStream_t fstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  long step_launches = 0;  // kernels in one replay of the step graph
   std::string err;
 };
 
@@ -252,6 +259,53 @@ static int issue_step(frg_ctx *ctx) {
   return FRG_OK;
 }
 
+// The issue functions use ctx->stream; during a flow it is the internal
+// stream, which first waits for the work already on the caller's stream, and
+// the caller's stream waits for the flow's work afterwards.
+struct FlowStream {
+  frg_ctx *ctx;
+  cudaStream_t user;
+  bool ok = false;
+  explicit FlowStream(frg_ctx *c) : ctx(c), user(c->stream) {
+    ok = cudaEventRecord(ctx->ev_in, user) == cudaSuccess &&
+         cudaStreamWaitEvent(ctx->fstream, ctx->ev_in, 0) == cudaSuccess;
+    ctx->stream = ctx->fstream;
+  }
+  ~FlowStream() {
+    ctx->stream = user;
+    if (cudaEventRecord(ctx->ev_out, ctx->fstream) == cudaSuccess) cudaStreamWaitEvent(user, ctx->ev_out, 0);
+  }
+};
+
+// Capture issue_step into the step graph (once per context).
+static int build_step_graph(frg_ctx *ctx) {
+  cudaGraph_t gr = nullptr;
+  const long l0 = g_kernel_launches;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin step capture");
+  const int rc = issue_step(ctx);
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+  ctx->step_launches = g_kernel_launches - l0;
+  g_kernel_launches = l0;  // counted when the graph runs
+  if (rc || e != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return rc ? rc : fail(ctx, FRG_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&ctx->step_exec, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e2 != cudaSuccess) {
+    ctx->step_exec = nullptr;
+    return fail(ctx, FRG_ECUDA, std::string("step graph instantiation: ") + cudaGetErrorString(e2));
+  }
+  return FRG_OK;
+}
+
+static int launch_step(frg_ctx *ctx) {
+  CK(cudaGraphLaunch(ctx->step_exec, ctx->stream), "step graph launch");
+  FRG_COUNT(ctx->step_launches);
+  return FRG_OK;
+}
+
 // ------------------------------------------------------------------ ABI ----
 extern "C" {
 
@@ -282,6 +336,10 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
   ctx->mask = ctx->params[0].channel_mask;
   ctx->split = ctx->precision != FRG_FP64;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaStreamCreateWithFlags(&ctx->fstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return bail(FRG_ECUDA);
   for (auto &p : ctx->params) ctx->maxN = std::max(ctx->maxN, p.N_f);
   if (upload_tableau() != 0) return bail(FRG_ECUDA);
 
@@ -414,6 +472,11 @@ void frg_destroy(frg_ctx *ctx) {
   DevGuard g(ctx->dev);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  if (ctx->fstream) cudaStreamSynchronize(ctx->fstream);
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->fstream) cudaStreamDestroy(ctx->fstream);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->tc) tc_plan_destroy(ctx->tc);
   for (void *p : ctx->allocs) cudaFree(p);
   for (auto p : ctx->user_in) if (p) cudaFree(p);
@@ -529,17 +592,20 @@ int frg_advance(frg_ctx *ctx, long max_attempts, frg_flow_stats *stats) {
   if (!ctx) return FRG_EINVAL;
   if (max_attempts < 0) return fail(ctx, FRG_EINVAL, "max_attempts must be >= 0");
   DevGuard g(ctx->dev);
+  FlowStream fs(ctx);
+  if (!fs.ok) return fail(ctx, FRG_ECUDA, "flow stream ordering");
   int rc;
   if (ctx->need_k1) {
     if ((rc = issue_k1(ctx))) return rc;
     ctx->need_k1 = false;
   }
+  if (max_attempts > 0 && !ctx->step_exec && (rc = build_step_graph(ctx))) return rc;
   const long period = ctx->split ? 8 : 2;
   long a = 0;
   while (a < max_attempts) {
     const long burst = std::min(period, max_attempts - a);
     for (long i = 0; i < burst; ++i)
-      if ((rc = issue_step(ctx))) return rc;
+      if ((rc = launch_step(ctx))) return rc;
     a += burst;
     if ((rc = sync_ctl(ctx))) return rc;
     bool all = true;

@@ -103,3 +103,61 @@ def test_split_flow_matches_oracle_reference(name, prec):
     print("prec=%d flow %s errors gamma %.3e sigma %.3e ueff %.3e evals %d vs %d" % (
         prec, name, eg, es, eu, st.rhs_evals, ref["stats"]["rhs_evals"]))
     assert eg < FLOW_TOL[prec] and es < FLOW_TOL[prec] and eu < FLOW_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_batched_points_equal_single_point_runs(prec):
+    """Uneven grid sizes in one context: every tile's sum runs in a fixed order
+    whichever CTA the schedule gives it to, so each point's flow is bitwise the
+    flow of a context that holds only that point."""
+    pts = [inputs.Workload("a", N=16, U=1.0, T=0.05, eps_d=-0.5),
+           inputs.Workload("b", N=34, U=2.5, T=0.02, eps_d=-1.0),
+           inputs.Workload("c", N=48, U=0.7, T=0.08, eps_d=0.1)]
+    with frg.Context(pts, precision=prec) as ctx:
+        stb = ctx.flow()
+        batched = [ctx.get_state(i)[:2] for i in range(len(pts))]
+    for i, w in enumerate(pts):
+        with frg.Context([w], precision=prec) as ctx:
+            st = ctx.flow()[0]
+            g, s, _, _ = ctx.get_state(0)
+        assert torch.equal(g, batched[i][0]) and torch.equal(s, batched[i][1])
+        assert st.rhs_evals == stb[i].rhs_evals and st.accepted == stb[i].accepted
+
+
+def test_split_batched_rhs_matches_oracle():
+    """One rhs of each point of a mixed-size context against the oracle."""
+    pts = [inputs.Workload("a", N=32, U=1.3, T=0.03, eps_d=-0.2),
+           inputs.Workload("b", N=48, U=3.1, T=0.011, eps_d=-1.9),
+           inputs.Workload("c", N=96, U=0.6, T=0.07, eps_d=-0.5)]
+    with frg.Context(pts, precision=frg.TF32X3) as ctx:
+        for i, w in enumerate(pts):
+            V = inputs.random_vertex(w.N, w.U, seed=40 + i)
+            sig = inputs.random_sigma(w.N, seed=50 + i)
+            dg, ds = gpu_rhs(ctx, i, 0.05, V, sig)
+            rg, rs = oracle.rhs(model(w), 0.05, V, sig)
+            assert nrel(dg, rg) < RHS_TOL[frg.TF32X3] and nrel(ds, rs) < RHS_TOL[frg.TF32X3]
+
+
+def test_split_rhs_largest_grid_n256():
+    """N = 256 (the largest grid): both split precisions against the plain FP64
+    GPU path on the whole rhs, and against the oracle on sampled entries."""
+    w = inputs.SIAM_N256
+    V = inputs.random_vertex(w.N, w.U, seed=21)
+    sig = inputs.random_sigma(w.N, seed=22, amp=0.05)
+    Lam = 0.01
+    with frg.Context([w]) as ctx:
+        fg, fs = gpu_rhs(ctx, 0, Lam, V, sig)
+    rng = np.random.default_rng(6)
+    idx = rng.integers(0, w.N, (2000, 3))
+    idx[:4] = [[0, 0, 0], [w.N - 1] * 3, [w.N // 2] * 3, [0, w.N - 1, 0]]
+    ref = oracle.rhs_entries(model(w), Lam, V, sig, idx)
+    assert nrel(fg[idx[:, 0], idx[:, 1], idx[:, 2]], ref) < 1e-12
+    for prec in PRECS:
+        with frg.Context([w], precision=prec) as ctx:
+            dg, ds = gpu_rhs(ctx, 0, Lam, V, sig)
+        e_full = nrel(dg, fg)
+        e_samp = nrel(dg[idx[:, 0], idx[:, 1], idx[:, 2]], ref)
+        print("prec=%d N=256 vs fp64 gpu %.3e, vs oracle sampled %.3e, sigma %.3e" % (
+            prec, e_full, e_samp, nrel(ds, fs)))
+        # the split path's self-energy sums the FP32 stage input in FP64
+        assert e_full < RHS_TOL[prec] and e_samp < RHS_TOL[prec] and nrel(ds, fs) < RHS_TOL[prec]
