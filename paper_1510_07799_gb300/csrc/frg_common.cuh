@@ -54,6 +54,11 @@ struct Ctl {
   int yslot;                 // ybuf[yslot] holds y, ybuf[yslot^1] the candidate
   int kslot[7];              // kG/kS[kslot[j]] holds k_{j+1}
   double lam_user;           // scale of a stand-alone rhs call
+  // split paths: tolerance floors of the error norm (largest |Re|, |Im| of the
+  // vertex and of the self-energy seen by the previous error evaluation) and
+  // their accumulators for the current one (bits of non-negative doubles)
+  double yfloor, sfloor;
+  unsigned long long ymax_acc, smax_acc;
 };
 
 // Inputs/outputs of one rhs evaluation for one point.

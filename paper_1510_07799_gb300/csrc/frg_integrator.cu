@@ -160,6 +160,8 @@ __global__ void k_prepare(const PointDesc *__restrict__ pts, Ctl *__restrict__ c
   for (int s = 0; s < 7; ++s) c.lam_stage[s] = exp(c.t + dC[s] * c.h);
   c.errbits = 0ull;
   c.nonfinite = 0;
+  c.ymax_acc = 0ull;
+  c.smax_acc = 0ull;
 }
 
 // Block-wide max of a non-negative float, folded into *dst (float bits).
@@ -347,8 +349,12 @@ __global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict
   const int ys = c.yslot;
   const double h = c.h;
   const float hf = d2f(h), atolf = d2f(P.atol), rtolf = d2f(P.rtol);
-  float fmax_ = 0.f;
-  double dmax = 0.0;
+  // the split rhs carries a normwise relative error of order 1e-7 (3xTF32),
+  // so no component's tolerance is taken below rtol x the largest component
+  const float yfl = d2f(c.yfloor);
+  const double sfl = c.sfloor;
+  float fmax_ = 0.f, ym = 0.f;
+  double dmax = 0.0, sm = 0.0;
   int bad = 0;
   for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
     const int i = base + e;
@@ -362,8 +368,10 @@ __global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict
         ff_mac(ei, eil, fEh[j], fEl[j], k.y);
       }
       const float2 y = P.yhi[ys][i], yn = P.yhi[ys ^ 1][i];
-      const float rx = fabsf(hf * __fadd_rn(er, erl)) / (atolf + rtolf * fmaxf(fabsf(y.x), fabsf(yn.x)));
-      const float ry = fabsf(hf * __fadd_rn(ei, eil)) / (atolf + rtolf * fmaxf(fabsf(y.y), fabsf(yn.y)));
+      const float mx = fmaxf(fabsf(y.x), fabsf(yn.x)), my = fmaxf(fabsf(y.y), fabsf(yn.y));
+      ym = fmaxf(ym, fmaxf(mx, my));
+      const float rx = fabsf(hf * __fadd_rn(er, erl)) / (atolf + rtolf * fmaxf(mx, yfl));
+      const float ry = fabsf(hf * __fadd_rn(ei, eil)) / (atolf + rtolf * fmaxf(my, yfl));
       if (!isfinite(rx) || !isfinite(ry) || !isfinite(yn.x) || !isfinite(yn.y)) bad = 1;
       else fmax_ = fmaxf(fmax_, fmaxf(rx, ry));
     } else {
@@ -375,33 +383,44 @@ __global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict
         acc.y += dE[j] * k.y;
       }
       const double2 yi = P.ybuf[ys][i], yni = P.ybuf[ys ^ 1][i];
-      const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(fabs(yi.x), fabs(yni.x)));
-      const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(fabs(yi.y), fabs(yni.y)));
+      const double mx = fmax(fabs(yi.x), fabs(yni.x)), my = fmax(fabs(yi.y), fabs(yni.y));
+      sm = fmax(sm, fmax(mx, my));
+      const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(mx, sfl));
+      const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(my, sfl));
       if (!isfinite(rx) || !isfinite(ry) || !isfinite(yni.x) || !isfinite(yni.y)) bad = 1;
       else dmax = fmax(dmax, fmax(rx, ry));
     }
   }
   double emax = fmax(dmax, f2d(fmax_));
+  double ymd = f2d(ym);
   for (int off = 16; off > 0; off >>= 1) {
     emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    ymd = fmax(ymd, __shfl_xor_sync(0xffffffffu, ymd, off));
+    sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, off));
     bad |= __shfl_xor_sync(0xffffffffu, bad, off);
   }
-  __shared__ double wmax[8];
+  __shared__ double wmax[8], wy[8], ws[8];
   __shared__ int wbad[8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     wmax[wid] = emax;
+    wy[wid] = ymd;
+    ws[wid] = sm;
     wbad[wid] = bad;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
+    double m = 0.0, a = 0.0, b2 = 0.0;
     int bb = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       m = fmax(m, wmax[w]);
+      a = fmax(a, wy[w]);
+      b2 = fmax(b2, ws[w]);
       bb |= wbad[w];
     }
     atomicMax(&c.errbits, (unsigned long long)__double_as_longlong(m));
+    if (a > 0.0) atomicMax(&c.ymax_acc, (unsigned long long)__double_as_longlong(a));
+    if (b2 > 0.0) atomicMax(&c.smax_acc, (unsigned long long)__double_as_longlong(b2));
     if (bb) atomicOr(&c.nonfinite, 1);
   }
 }
@@ -490,6 +509,9 @@ __global__ void k_controller(const PointDesc *__restrict__ pts, Ctl *__restrict_
     return;
   }
   const double err = __longlong_as_double((long long)c.errbits);
+  // tolerance floors of the split paths' next error evaluation (0 in FP64)
+  c.yfloor = __longlong_as_double((long long)c.ymax_acc);
+  c.sfloor = __longlong_as_double((long long)c.smax_acc);
   if (err <= 1.0) {
     c.t = c.last ? P.l_end : c.t + c.h;
     c.yslot ^= 1;
