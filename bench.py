@@ -12,6 +12,15 @@ Arms:
   default            the CUDA library (precision --precision)
   --impl reference   the FP64 CPU oracle as it stands, timed on the host cores on
                      a bounded sample of the same workload (rows of the vertex)
+
+Secondary workloads (--workload; each prints its own JSON line, not the
+headline):
+  batch64    64 parameter points with N_f in {32, 48, 64, 96} integrated in one
+             context (one captured graph per step over all points): full flows
+             per second, next to 64 sequential plain-FP64 GPU flows
+  siam_N256  the largest single flow, N_f = 256: rhs evaluations per second,
+             phase times and the error of one rhs against the FP64 GPU path on
+             the same state
 """
 import argparse
 import json
@@ -208,6 +217,7 @@ def run_ours(args):
     N = w.N
     prec = args.precision
     ctx = frg.Context([w], precision=prec)
+    tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -277,10 +287,10 @@ def run_ours(args):
     roof["phases_ms"] = {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2], "combine": ph[3]}
 
     # ---- end to end through the host-buffer entry point
-    hg = g.cpu().numpy()
-    hs = s.cpu().numpy()
-    og = np.empty_like(hg)
-    os_ = np.empty_like(hs)
+    hg = g.cpu().pin_memory().numpy()
+    hs = s.cpu().pin_memory().numpy()
+    og = torch.empty(hg.shape, dtype=torch.complex128).pin_memory().numpy()
+    os_ = torch.empty(hs.shape, dtype=torch.complex128).pin_memory().numpy()
     ctx.rhs_host(0, lam, hg, hs, og, os_)
     t0 = time.perf_counter()
     for _ in range(args.e2e_reps):
@@ -288,7 +298,23 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / args.e2e_reps
     nb = (hg.nbytes + hs.nbytes)
     e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-           "what": "frg_rhs_host with pageable host buffers, copies inside the timed region"}
+           "what": "frg_rhs_host with pinned host buffers, copies inside the timed region"}
+
+    # the plain FP64 GPU path on the same state (the metric's comparison arm)
+    fp64_gpu = None
+    if prec != "fp64":
+        with frg.Context([w], precision="fp64") as c64:
+            for _ in range(2):
+                c64.rhs_timed(0, lam, g, s, dg, ds)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                c64.rhs(0, lam, g, s, dg, ds)
+            torch.cuda.synchronize()
+            r64 = reps / (time.perf_counter() - t0)
+        fp64_gpu = {"value": r64, "unit": UNIT, "what": "plain FP64 GPU rhs on the same state",
+                    "speedup_split_vs_fp64": (1e3 / sum(ph)) / r64}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
@@ -299,9 +325,9 @@ def run_ours(args):
                                "error norm + controller)",
                        "l2": "working set > L2 (state, 7 stage derivatives, stage input: %.0f MB)"
                              % ((2 * 16 + 7 * (8 if prec != 'fp64' else 16) + 16) * N ** 3 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single", "autotune": tune},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "fp64_gpu": fp64_gpu}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(8, seconds=args.cpu_seconds)
     if rank == 0:
@@ -310,6 +336,134 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def reset_flows(ctx, pts, torch):
+    """Every point back to the bare vertex, Sigma = 0 at Lambda0."""
+    for i, p in enumerate(pts):
+        g = torch.full((p.N,) * 3, p.U, dtype=torch.complex128, device="cuda")
+        ctx.set_state(i, g, None, p.Lambda0)
+
+
+def run_batch(args):
+    """64 points, uneven N_f, one context: full flows per second."""
+    import torch
+    from paper_1510_07799_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1510_07799_gb300 import frg, inputs
+    pts = inputs.batch_points()
+    prec = args.precision
+    ctx = frg.Context(pts, precision=prec)
+    tune = ctx.autotune() if prec != "fp64" else None
+    stream = torch.cuda.current_stream()
+    times, evals = [], []
+    for k in range(args.warmup + args.steps):
+        reset_flows(ctx, pts, torch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.flow()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1) / 1e3)
+            evals.append(sum(x.rhs_evals for x in st))
+    ctx.close()
+    tb = sum(times) / len(times)
+    # 64 sequential plain-FP64 GPU flows, one context each
+    t64, ev64 = 0.0, 0
+    if not args.no_fp64_baseline:
+        for p in pts:
+            with frg.Context([p], precision="fp64") as c:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = c.flow()[0]
+                torch.cuda.synchronize()
+                t64 += time.perf_counter() - t0
+                ev64 += st.rhs_evals
+    line = {"metric": "full flows/s, 64-point batch (N_f 32/48/64/96) in one context", "value": len(pts) / tb,
+            "unit": "flows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[prec], "data": "synthetic",
+            "config": {"workload": "batch64", "seed": inputs.BATCH_SEED, "points": len(pts),
+                       "N_f": {str(n): sum(1 for p in pts if p.N == n) for n in inputs.BATCH_SIZES},
+                       "precision": prec, "step": "one full flow of all 64 points (Lambda 1e3 -> 1e-3)",
+                       "rhs_evals_per_step": int(sum(evals) / len(evals)), "autotune": tune},
+            "fp64_sequential": None if args.no_fp64_baseline else {
+                "value": len(pts) / t64, "unit": "flows/s", "rhs_evals": ev64,
+                "what": "64 plain-FP64 GPU flows, one context each, one after the other"}}
+    if not args.no_fp64_baseline:
+        line["speedup_vs_fp64_sequential"] = line["value"] / line["fp64_sequential"]["value"]
+    print(json.dumps(line))
+    return 0
+
+
+def run_n256(args):
+    """The largest single flow: rhs evaluations per second at N_f = 256, and
+    the error of the split rhs against the FP64 GPU path on the same state."""
+    import numpy as np
+    import torch
+    from paper_1510_07799_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1510_07799_gb300 import frg, inputs
+    w = inputs.SIAM_N256
+    prec = args.precision
+    ctx = frg.Context([w], precision=prec)
+    tune = ctx.autotune() if prec != "fp64" else None
+    stream = torch.cuda.current_stream()
+    ctx.advance(args.warmup)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        ctx.advance(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    st1 = ctx.stats()[0]
+    ms = e0.elapsed_time(e1)
+    evals = st1.rhs_evals - st0.rhs_evals
+    g, s, lam, _ = ctx.get_state(0)
+    dg, ds = torch.empty_like(g), torch.empty_like(s)
+    for _ in range(2):
+        ctx.rhs_timed(0, lam, g, s, dg, ds)
+    ph = np.array([ctx.rhs_timed(0, lam, g, s, dg, ds) for _ in range(args.rhs_reps)]).mean(axis=0)
+    ctx.close()
+    with frg.Context([w], precision="fp64") as c64:
+        fg, fs = torch.empty_like(g), torch.empty_like(s)
+        c64.rhs(0, lam, g, s, fg, fs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c64.rhs(0, lam, g, s, fg, fs)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+
+    def nrel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+
+    pk = peaks()
+    macs = contraction_macs(w.N)
+    tf_peak = 0.5 * pk["bf16_tflops"]
+    achieved = 8.0 * macs / (ph[2] * 1e-3) / 1e12
+    line = {"metric": "vertex-rhs evals/s at N_f=256 (largest single flow)", "value": evals / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / max(1, (st1.accepted + st1.rejected) - (st0.accepted + st0.rejected)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
+            "data": "synthetic",
+            "config": {"workload": w.name, "N_f": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
+                       "precision": prec, "rhs_evals_timed": evals, "autotune": tune},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
+                         "frac": achieved / tf_peak, "kernel": "tcgen05 channel contractions of one rhs",
+                         "peak_source": "%s bf16 burst x 0.5" % pk["_source"],
+                         "phases_ms": {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2],
+                                       "combine": ph[3]}},
+            "error_vs_fp64_gpu": {"gamma": nrel(dg, fg), "sigma": nrel(ds, fs),
+                                  "state": "flow state at Lambda=%.4g after %d warm-up steps" % (lam, args.warmup)},
+            "fp64_gpu": {"value": 1.0 / t64, "unit": UNIT,
+                         "speedup_split_vs_fp64": (1e3 / sum(ph)) * t64},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
     return 0
 
 
@@ -324,6 +478,8 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="siam_N128", choices=["siam_N128", "batch64", "siam_N256"])
+    ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
     args.precision_explicit = args.precision is not None
     if args.precision is None:
@@ -332,6 +488,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "siam_N256":
+        return run_n256(args)
     return run_ours(args)
 
 

@@ -189,6 +189,29 @@ int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
 long frg_kernel_launches(void);
 
 /*
+ * Contraction autotuning (split precisions).  The paper distributes work over
+ * MPI ranks and has no tile shapes to tune; on this GPU the channel products
+ * run as tiles of 64 complex rows x NT complex columns on persistent CTAs, and
+ * the fastest NT and work assignment depend on the grid sizes of the batch.
+ * frg_autotune times one rhs evaluation of every point of the context (at the
+ * current flow state) for each candidate plan -- cap on NT of 128, 64 or 32
+ * (NT = min(cap, N rounded up to 16)) times an epilogue allowance of 0, 3 or 8
+ * k-steps per tile in the longest-first scheduler's cost model -- and keeps the
+ * fastest plan for all later evaluations of the context.  Plans differ only in
+ * how the same per-element sums are distributed, not in their arithmetic.
+ * *out (may be NULL) receives the choice; an FP64 context has nothing to tune
+ * (returns FRG_OK, out->candidates = 0).  Synchronises.
+ */
+typedef struct {
+  int nt_cap;       /* chosen cap on the complex columns of a tile */
+  int epi_cost;     /* chosen per-tile epilogue allowance (k-steps) */
+  int candidates;   /* plans timed */
+  float ms;         /* one rhs of all points with the chosen plan */
+  float ms_default; /* the same with the default plan (128, 3) */
+} frg_tune;
+int frg_autotune(frg_ctx *ctx, frg_tune *out);
+
+/*
  * Right-hand side without any device allocation (the paper has no counterpart;
  * this is a service for callers).  Some callers cannot allocate device memory
  * when they need an evaluation: a latency-critical loop in which an allocation

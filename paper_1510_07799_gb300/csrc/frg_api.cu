@@ -624,6 +624,84 @@ int frg_flow(frg_ctx *ctx, frg_flow_stats *stats) {
   return frg_advance(ctx, budget + 1, stats);
 }
 
+int frg_autotune(frg_ctx *ctx, frg_tune *out) {
+  if (!ctx) return FRG_EINVAL;
+  if (out) memset(out, 0, sizeof *out);
+  if (!ctx->split) return FRG_OK;
+  DevGuard g(ctx->dev);
+  int rc;
+  {
+    FlowStream fs(ctx);
+    if (!fs.ok) return fail(ctx, FRG_ECUDA, "flow stream ordering");
+    cudaStream_t st = ctx->stream;
+    // stage input of the current state of every point
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, st), "stage 0");
+    LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "events");
+    CK(cudaEventCreate(&e1), "events");
+    int n16 = 16;
+    for (const auto &p : ctx->params) n16 = std::max(n16, (p.N_f + 15) / 16 * 16);
+    const int caps[] = {128, 64, 32}, costs[] = {0, 3, 8};
+    TcPlan *keep = ctx->tc;
+    TcTune best{128, 3};
+    float best_ms = 1e30f, def_ms = 0.f;
+    int cand = 0;
+    rc = FRG_OK;
+    for (int ci = 0; ci < 3 && rc == FRG_OK; ++ci) {
+      if (ci > 0 && caps[ci] >= n16) continue;  // same tiles as the larger cap before it
+      for (int cj = 0; cj < 3 && rc == FRG_OK; ++cj) {
+        const TcTune t{caps[ci], costs[cj]};
+        TcPlan *p = nullptr;
+        std::string why;
+        if ((rc = tc_plan_create(&p, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, ctx->d_err, why, t))) {
+          fail(ctx, rc, why);
+          break;
+        }
+        ctx->tc = p;
+        float ms = 1e30f;
+        for (int r = 0; r < 4 && rc == FRG_OK; ++r) {
+          if (cudaEventRecord(e0, st) != cudaSuccess) rc = FRG_ECUDA;
+          if (rc == FRG_OK) rc = run_rhs(ctx, ctx->d_io_stage, -1);
+          if (rc == FRG_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = FRG_ECUDA;
+          if (rc == FRG_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FRG_ECUDA;
+          float x = 0.f;
+          if (rc == FRG_OK && r > 0 && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess) ms = std::min(ms, x);
+        }
+        ++cand;
+        if (t.nt_cap == 128 && t.epi_cost == 3) def_ms = ms;
+        if (rc == FRG_OK && ms < best_ms) {
+          best_ms = ms;
+          best = t;
+          if (keep != ctx->tc && keep) tc_plan_destroy(keep);
+          keep = p;
+        } else if (p != keep) {
+          tc_plan_destroy(p);
+        }
+        ctx->tc = keep;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == FRG_OK) rc = sync_checked(ctx, "autotune");
+    if (rc) return rc;
+    // the step graph holds the old plan's launch arguments
+    if (ctx->step_exec) {
+      cudaGraphExecDestroy(ctx->step_exec);
+      ctx->step_exec = nullptr;
+    }
+    ctx->need_k1 = true;
+    if (out) {
+      out->nt_cap = best.nt_cap;
+      out->epi_cost = best.epi_cost;
+      out->candidates = cand;
+      out->ms = best_ms;
+      out->ms_default = def_ms;
+    }
+  }
+  return FRG_OK;
+}
+
 int frg_stats(frg_ctx *ctx, frg_flow_stats *stats) {
   if (!ctx || !stats) return FRG_EINVAL;
   DevGuard g(ctx->dev);

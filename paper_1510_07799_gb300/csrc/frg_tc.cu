@@ -1233,6 +1233,7 @@ struct TcPlan {
   };
   std::vector<Sched> sched;
   int mask = 7;
+  TcTune tune;
 };
 
 // Longest-processing-time schedule of the tiles of points [first, last) over at
@@ -1241,7 +1242,7 @@ struct TcPlan {
 // CTA with start offsets.
 static bool build_sched(TcPlan *p, const std::vector<PointDesc> &pts, const std::vector<int> &nt, int first,
                         int last, TcPlan::Sched &out) {
-  constexpr int EPI_COST = 3;  // epilogue of one tile, in k-step units
+  const int EPI_COST = p->tune.epi_cost;  // epilogue of one tile, in k-step units
   std::vector<std::pair<int, tc::st::StWork>> tiles;
   for (int i = first; i < last; ++i) {
     const int N = pts[i].N;
@@ -1298,7 +1299,8 @@ static bool encode_maps(TcPlan *p, const std::vector<PointDesc> &pts, std::strin
   for (size_t i = 0; i < pts.size(); ++i) {
     const PointDesc &P = pts[i];
     const cuuint64_t N = (cuuint64_t)P.N;
-    const cuuint32_t NT = (cuuint32_t)std::min(tc::NT_MAX, (P.N + 15) / 16 * 16);
+    // must equal the tile width of the plan (the loader's expected byte count)
+    const cuuint32_t NT = (cuuint32_t)std::min(p->tune.nt_cap, (P.N + 15) / 16 * 16);
     const cuuint64_t row = N * 8;  // bytes per vertex row (N complex)
     CUtensorMap *m = &maps[i * tc::st::M_COUNT];
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -1362,7 +1364,7 @@ static bool set_smem_attrs() {
 }
 
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
-                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why) {
+                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why, TcTune tune) {
   (void)d_pts;
   *out = nullptr;
   if (precision != FRG_3XTF32 && precision != FRG_BF16X3) {
@@ -1385,8 +1387,14 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
   p->sms = prop.multiProcessorCount;
   p->n = (int)pts.size();
   p->d_err = d_err;
+  if (tune.nt_cap < 16 || tune.nt_cap > tc::NT_MAX || tune.nt_cap % 16 || tune.epi_cost < 0) {
+    why = "invalid contraction tuning";
+    delete p;
+    return FRG_EINVAL;
+  }
+  p->tune = tune;
   std::vector<int> nt(p->n);
-  for (int i = 0; i < p->n; ++i) nt[i] = std::min(tc::NT_MAX, (pts[i].N + 15) / 16 * 16);
+  for (int i = 0; i < p->n; ++i) nt[i] = std::min(tune.nt_cap, (pts[i].N + 15) / 16 * 16);
   bool ok = cudaMalloc(&p->d_nt, sizeof(int) * p->n) == cudaSuccess &&
             cudaMemcpy(p->d_nt, nt.data(), sizeof(int) * p->n, cudaMemcpyHostToDevice) == cudaSuccess;
   for (int ch = 0; ch < 3 && ok; ++ch) {

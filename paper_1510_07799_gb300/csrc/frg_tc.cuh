@@ -9,9 +9,18 @@
 
 namespace frg {
 struct TcPlan;
+// Tunable shape of a contraction plan: the cap on the complex columns of one
+// tile (a multiple of 16, at most 128; the tile width is min(cap, N rounded up
+// to 16)) and the per-tile epilogue allowance, in k-steps, of the scheduler's
+// cost model.
+struct TcTune {
+  int nt_cap = 128;
+  int epi_cost = 3;
+};
 // d_err: device word that a kernel whose bounded wait ran out sets non-zero.
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
-                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why);
+                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why,
+                   TcTune tune = TcTune());
 void tc_plan_destroy(TcPlan *plan);
 // Evaluate the enabled vertex channels of every active point (point = -1) or of
 // one point, writing the float2 vertex output of each active RhsIO.

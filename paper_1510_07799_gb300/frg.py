@@ -24,7 +24,7 @@ ERRNAMES = {EINVAL: "FRG_EINVAL", ENOMEM: "FRG_ENOMEM", ECUDA: "FRG_ECUDA",
 
 EXPORTED = ("frg_init", "frg_destroy", "frg_last_error", "frg_rhs", "frg_rhs_host", "frg_flow",
             "frg_advance", "frg_observables", "frg_get_state", "frg_set_state", "frg_stats",
-            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc")
+            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune")
 NOALLOC_MAX_N = 64
 
 
@@ -46,6 +46,11 @@ class _Stats(C.Structure):
     _fields_ = [("Lambda", C.c_double), ("h", C.c_double), ("accepted", C.c_long),
                 ("rejected", C.c_long), ("rhs_evals", C.c_long), ("status", C.c_int),
                 ("done", C.c_int)]
+
+
+class _Tune(C.Structure):
+    _fields_ = [("nt_cap", C.c_int), ("epi_cost", C.c_int), ("candidates", C.c_int),
+                ("ms", C.c_float), ("ms_default", C.c_float)]
 
 
 class _Obs(C.Structure):
@@ -113,6 +118,7 @@ def load():
     lib.frg_set_state.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_double]
     lib.frg_rhs_timed.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, C.POINTER(C.c_float)]
     lib.frg_rhs_noalloc.argtypes = [C.POINTER(_Params), C.c_double, vp, vp, vp, vp, vp]
+    lib.frg_autotune.argtypes = [vp, C.POINTER(_Tune)]
     lib.frg_kernel_launches.argtypes = []
     lib.frg_kernel_launches.restype = C.c_long
     _lib = lib
@@ -221,9 +227,9 @@ class Context:
                                  _ptr(dsigma)))
 
     def rhs_timed(self, point, Lambda, gamma, sigma, dgamma, dsigma):
-        """Like rhs(); returns the phase durations in ms (bubble weights, operand
-        regather, channel contractions, combine, self-energy) measured with CUDA
-        events on the context stream."""
+        """Like rhs(); returns the phase durations in ms (bubble weights with the
+        self-energy, operand regather, channel contractions, combine, and 0)
+        measured with CUDA events on the context stream."""
         N = self.N(point)
         _check_dev(gamma, (N, N, N), "gamma")
         _check_dev(dgamma, (N, N, N), "dgamma")
@@ -263,6 +269,14 @@ class Context:
         arr = (_Stats * self.n)()
         self._chk(load().frg_stats(self._h, arr))
         return self._stats(arr)
+
+    def autotune(self):
+        """Time the candidate contraction plans on the current state and keep
+        the fastest (split precisions); returns the choice."""
+        t = _Tune()
+        self._chk(load().frg_autotune(self._h, C.byref(t)))
+        return {"nt_cap": t.nt_cap, "epi_cost": t.epi_cost, "candidates": t.candidates,
+                "ms": t.ms, "ms_default": t.ms_default}
 
     def observables(self, point):
         o = _Obs()

@@ -79,4 +79,5 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.frg_flow(None, None) == frg.EINVAL
     assert lib.frg_advance(None, 1, None) == frg.EINVAL
     assert b"null context" in lib.frg_last_error(None)
+    assert lib.frg_autotune(None, None) == frg.EINVAL
     lib.frg_destroy(None)

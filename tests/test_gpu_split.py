@@ -161,3 +161,21 @@ def test_split_rhs_largest_grid_n256():
             prec, e_full, e_samp, nrel(ds, fs)))
         # the split path's self-energy sums the FP32 stage input in FP64
         assert e_full < RHS_TOL[prec] and e_samp < RHS_TOL[prec] and nrel(ds, fs) < RHS_TOL[prec]
+
+
+def test_autotuned_plan_keeps_the_results():
+    """The autotuner only redistributes the same per-element sums: a tuned
+    context's rhs and flow stay within the split bars of the oracle."""
+    pts = [inputs.Workload("a", N=32, U=1.3, T=0.03, eps_d=-0.2),
+           inputs.Workload("b", N=96, U=2.2, T=0.02, eps_d=-1.4)]
+    with frg.Context(pts, precision=frg.TF32X3) as ctx:
+        tune = ctx.autotune()
+        assert tune["candidates"] >= 3 and tune["nt_cap"] in (32, 64, 128) and tune["ms"] > 0
+        for i, w in enumerate(pts):
+            V = inputs.random_vertex(w.N, w.U, seed=60 + i)
+            sig = inputs.random_sigma(w.N, seed=70 + i)
+            dg, ds = gpu_rhs(ctx, i, 0.03, V, sig)
+            rg, rs = oracle.rhs(model(w), 0.03, V, sig)
+            assert nrel(dg, rg) < RHS_TOL[frg.TF32X3] and nrel(ds, rs) < RHS_TOL[frg.TF32X3]
+        st = ctx.flow()
+        assert all(s.status == 0 and s.done for s in st)
