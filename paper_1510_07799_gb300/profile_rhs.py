@@ -1,9 +1,11 @@
-"""One right-hand-side evaluation per call of the library, for ncu captures.
+"""Small, self-terminating workloads of the library for ncu captures.
 
-usage: python -m paper_1510_07799_gb300.profile_rhs [precision] [N] [repeats]
+usage: python -m paper_1510_07799_gb300.profile_rhs [precision] [N] [repeats] [steps]
 Runs `repeats` rhs evaluations (default 2) of a seeded vertex at N (default
 128, the U=3, T=0.005 workload parameters) and prints the phase timings of the
-last one.
+last one; with a fourth argument `steps` > 0 it then advances a flow of the
+same workload by that many Dormand-Prince step attempts (one captured graph
+per step), so that a launch list shows the kernels of the flow step.
 """
 import sys
 
@@ -16,6 +18,7 @@ def main():
     prec = sys.argv[1] if len(sys.argv) > 1 else "3xtf32"
     N = int(sys.argv[2]) if len(sys.argv) > 2 else 128
     reps = int(sys.argv[3]) if len(sys.argv) > 3 else 2
+    steps = int(sys.argv[4]) if len(sys.argv) > 4 else 0
     build.build()
     w = inputs.Workload("profile", N=N, U=3.0, T=0.005, eps_d=-1.5)
     ctx = frg.Context([w], precision=prec)
@@ -27,7 +30,11 @@ def main():
     for _ in range(reps):
         ph = ctx.rhs_timed(0, 0.02, V, s, dg, ds)
     torch.cuda.synchronize()
-    print("phases ms (bubble, regather, contraction, combine, sigma):", [round(x, 4) for x in ph])
+    print("phases ms (bubble+sigma, regather, contraction, combine):", [round(x, 4) for x in ph[:4]])
+    if steps > 0:
+        st = ctx.advance(steps)[0]
+        torch.cuda.synchronize()
+        print("flow: %d step attempts, %d rhs evaluations" % (st.accepted + st.rejected, st.rhs_evals))
     ctx.close()
 
 
