@@ -57,6 +57,10 @@ struct frg_ctx {
   // the caller's stream by events
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // split paths: the bubble weights and the self-energy run on a side stream
+  // while the stage input is relaid (fork / join by events)
+  cudaStream_t sstream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t step_exec = nullptr;
   long step_launches = 0;  // kernels in one replay of the step graph
   std::string err;
@@ -149,8 +153,18 @@ void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &ou
 static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr) {
   cudaStream_t st = ctx->stream;
   if (ev) CK(cudaEventRecord(ev[0], st), "event");
-  LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st),
-     "bubble weights and self-energy");
+  // untimed split evaluations overlap the bubble weights with the relayout
+  const bool fork = !ev && ctx->split && ctx->sstream;
+  if (fork) {
+    CK(cudaEventRecord(ctx->ev_fork, st), "fork");
+    CK(cudaStreamWaitEvent(ctx->sstream, ctx->ev_fork, 0), "fork");
+    LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, ctx->sstream),
+       "bubble weights and self-energy");
+    CK(cudaEventRecord(ctx->ev_join, ctx->sstream), "join");
+  } else {
+    LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st),
+       "bubble weights and self-energy");
+  }
   if (ev) CK(cudaEventRecord(ev[1], st), "event");
   const int chmask = ctx->mask & 7;
   if (!ctx->split) {
@@ -175,10 +189,11 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
   } else {
     if (chmask) {
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
-                ctx->maxN),
+                ctx->maxN, fork ? ctx->ev_join : nullptr),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
+      if (fork) CK(cudaStreamWaitEvent(st, ctx->ev_join, 0), "join");
       LK(launch_zero_vertex(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "zero vertex");
       if (ev) CK(cudaEventRecord(ev[3], st), "event");
     }
@@ -337,6 +352,9 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
   ctx->split = ctx->precision != FRG_FP64;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaStreamCreateWithFlags(&ctx->fstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return bail(FRG_ECUDA);
@@ -475,6 +493,12 @@ void frg_destroy(frg_ctx *ctx) {
   if (ctx->fstream) cudaStreamSynchronize(ctx->fstream);
   if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
   if (ctx->fstream) cudaStreamDestroy(ctx->fstream);
+  if (ctx->sstream) {
+    cudaStreamSynchronize(ctx->sstream);
+    cudaStreamDestroy(ctx->sstream);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->tc) tc_plan_destroy(ctx->tc);

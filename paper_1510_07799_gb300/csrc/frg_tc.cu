@@ -1483,11 +1483,12 @@ static void launch_one(int ch, int grid, cudaStream_t st, const PointDesc *d_pts
 }
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
-           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN) {
+           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before) {
   if (chmask & 6) {
     if (launch_relayout(d_pts, d_io, n_points, maxN, 1, (chmask & 2) != 0, st) != 0) return -3;
   }
   if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
+  if (wait_before && cudaStreamWaitEvent(st, wait_before, 0) != cudaSuccess) return -3;
   if (p->precision == FRG_3XTF32) {
     if ((chmask & 7) != p->mask || point >= p->n) return -1;
     const TcPlan::Sched &sc = p->sched[point < 0 ? 0 : 1 + point];

@@ -26,7 +26,9 @@ void tc_plan_destroy(TcPlan *plan);
 // one point, writing the float2 vertex output of each active RhsIO.
 // Relayout of the stage input, the channel products, and the combine into the
 // natural layout.  ev_gather / ev_contract (optional) are recorded after the
-// relayout and after the products.
+// relayout and after the products; the products wait for wait_before
+// (optional: the bubble weights computed on another stream).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
-           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN);
+           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
+           cudaEvent_t wait_before = nullptr);
 }  // namespace frg
