@@ -674,13 +674,13 @@ constexpr int ROWB = 64;                                // bytes per operand row
 constexpr int A_SLICE = 128 * ROWB;                     // 8 KB
 constexpr int B_SLICE = 2 * NT_MAX * ROWB;              // 16 KB
 constexpr int OP_STAGE = 2 * (A_SLICE + B_SLICE);       // 48 KB
-constexpr int NOP = 2;
+constexpr int NOP = 3;
 constexpr int RA = 18;                                  // complex per raw left row (aligned window)
 constexpr int RAW_A = MROWS * RA * 8;                   // 9216 B
 constexpr int RAW_B = KS * NT_MAX * 8;                  // 16 KB
 constexpr int RAW_L = 256;
 constexpr int RAW_STAGE = 2 * RAW_A + RAW_B + RAW_L;    // A, C (direct channel), B, bubble weights
-constexpr int NRAW = 3;
+constexpr int NRAW = 2;
 constexpr int EPI_PITCH = 18;                           // complex per staged output row (16 + 2 pad)
 constexpr int EPI_STG = 16 * EPI_PITCH * 8;             // per epilogue warp: 16 rows x 16 complex
 constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 4 * EPI_STG + 512;
@@ -1018,18 +1018,51 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
   return true;
 }
 
+// TMEM use of consecutive tiles.  A tile's two accumulators take 2 x 2NT
+// columns: tiles with NT <= 64 alternate between the halves [0, 256) and
+// [256, 512) (the next tile's products overlap the previous tile's epilogue), a
+// wider tile takes all 512 columns.  The MMA warp and the epilogue walk the
+// same tile list and keep identical counts of the uses of each barrier.
+struct TBuf {
+  uint32_t e0 = 0u, e1 = 0u;  // completed uses of tempty[0], tempty[1]
+  uint32_t f0 = 0u, f1 = 0u;  // completed uses of tfull[0], tfull[1]
+  int flip = 0;
+};
+struct TSlot {
+  bool wide;
+  int b;               // 0 / 1: half of TMEM; wide tiles: 0 (barriers) and both halves
+  uint32_t dcol, xcol; // columns of the hi*hi and the cross accumulator
+};
+__device__ __forceinline__ TSlot tslot_next(TBuf &t, int NT) {
+  TSlot s;
+  s.wide = 2 * NT > 128;
+  s.b = s.wide ? 0 : t.flip;
+  if (!s.wide) t.flip ^= 1;
+  s.dcol = s.wide ? 0u : 256u * s.b;
+  s.xcol = s.wide ? 256u : s.dcol + 128u;
+  return s;
+}
+
 // MMA issue (one warp, lane 0 issues): per k-step hi*hi into one TMEM
 // accumulator and hi*lo + lo*hi into a second one, so that the large sum takes
 // a third of the accumulation steps.
 template <int CH>
 __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
-                                         const int *__restrict__ nt_of, uint32_t &it, uint32_t &tcount, int lane) {
+                                         const int *__restrict__ nt_of, uint32_t &it, TBuf &tb, int lane) {
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  if (!wwait(&S.tempty[0], (tcount & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+  const TSlot ts = tslot_next(tb, ti.NT);
+  if (ts.wide || ts.b == 0) {
+    if (!wwait(&S.tempty[0], (tb.e0 & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+    ++tb.e0;
+  }
+  if (ts.wide || ts.b == 1) {
+    if (!wwait(&S.tempty[1], (tb.e1 & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+    ++tb.e1;
+  }
   tc_after();
-  const uint32_t d = S.tmem, dx = S.tmem + 256;
+  const uint32_t d = S.tmem + ts.dcol, dx = S.tmem + ts.xcol;
   const uint32_t id = idesc<FRG_3XTF32>(2 * ti.NT);
   for (int kb = 0; kb < ti.nk; ++kb, ++it) {
     const int s = it % NOP;
@@ -1049,9 +1082,10 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
     }
     __syncwarp();
   }
-  if (lane == 0) mma_commit(&S.tfull[0]);
+  if (lane == 0) mma_commit(&S.tfull[ts.b]);
   __syncwarp();
-  ++tcount;
+  if (ts.b) ++tb.f1;
+  else ++tb.f0;
   return true;
 }
 
@@ -1062,10 +1096,13 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
 template <int CH>
 __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
-                                         const int *__restrict__ nt_of, uint32_t &tcount, int warp, int lane) {
+                                         const int *__restrict__ nt_of, TBuf &tb, int warp, int lane) {
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  if (!wwait(&S.tfull[0], tcount & 1u, S.err, S.abort_flag)) return false;
+  const TSlot ts = tslot_next(tb, ti.NT);
+  if (!wwait(&S.tfull[ts.b], (ts.b ? tb.f1 : tb.f0) & 1u, S.err, S.abort_flag)) return false;
+  if (ts.b) ++tb.f1;
+  else ++tb.f0;
   tc_after();
   const int L = warp * 32 + lane;
   const int r = L >> 1, odd = L & 1;
@@ -1081,14 +1118,17 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
   for (int cb = 0; cb < 2 * ti.NT; cb += 32) {
     float v[32], vx[32];
-    tmem_ld32(tl + cb, v);
-    tmem_ld32(tl + 256 + cb, vx);
+    tmem_ld32(tl + ts.dcol + cb, v);
+    tmem_ld32(tl + ts.xcol + cb, vx);
     tmem_wait_ld();
     if (cb + 32 >= 2 * ti.NT) {
       // all TMEM reads of this tile are done: let the next tile's MMAs start
       tc_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[0]);
+      if (lane == 0) {
+        mbar_arrive(&tempty[ts.b]);
+        if (ts.wide) mbar_arrive(&tempty[1]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] += vx[i];
@@ -1121,7 +1161,8 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
       if (dst && cg < ti.N && cl < ti.NT) *reinterpret_cast<float4 *>(dst + cg) = val;
     }
   }
-  ++tcount;
+  if (ts.wide || ts.b == 0) ++tb.e0;
+  if (ts.wide || ts.b == 1) ++tb.e1;
   return true;
 }
 
@@ -1190,16 +1231,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!FRG_BY_CH(xf_tile, S, pts, io, w, nt_of, it, xt, lane)) break;
     }
   } else if (warp == MMA_W) {
-    uint32_t it = 0, tcount = 0;
+    uint32_t it = 0;
+    TBuf tb;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH(mma_tile, S, pts, io, w, nt_of, it, tcount, lane)) break;
+      if (!FRG_BY_CH(mma_tile, S, pts, io, w, nt_of, it, tb, lane)) break;
     }
   } else {
-    uint32_t tcount = 0;
+    TBuf tb;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH(epi_tile, S, pts, io, w, nt_of, tcount, warp, lane)) break;
+      if (!FRG_BY_CH(epi_tile, S, pts, io, w, nt_of, tb, warp, lane)) break;
     }
   }
 #undef FRG_BY_CH
