@@ -141,6 +141,23 @@ def dist_init():
     return world, rank, local
 
 
+def reduce_over_ranks(ms, evals, device=None):
+    """Whole-job figures of N independent replicas (one flow per rank, no
+    data-path collective): the slowest rank's time and the evaluations of all
+    ranks.  With one rank (or no process group) the inputs come back."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    ev = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+    except ImportError:
+        pass
+    return float(t.item()), float(ev.item())
+
+
 def cpu_baseline(N_rows, seconds=12.0):
     """The FP64 oracle as it stands on the host cores, on whole rows i1 of the
     N=128 vertex (a bounded sample), scaled to rhs evaluations per second."""
@@ -246,14 +263,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     evals = st1.rhs_evals - st0.rhs_evals
     attempts = (st1.accepted + st1.rejected) - (st0.accepted + st0.rejected)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    ev = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(ev.item()) / (ms_max / 1e3)
+    ms_max, ev_all = reduce_over_ranks(ms, evals, device=dev)
+    value = ev_all / (ms_max / 1e3)
 
     # ---- per-phase timing of single rhs evaluations on the same stream
     g, s, lam, _ = ctx.get_state(0)
