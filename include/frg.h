@@ -187,6 +187,17 @@ int frg_stats(frg_ctx *ctx, frg_flow_stats *stats);
 int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
                   const void *d_sigma, void *d_dgamma, void *d_dsigma, float *ms);
 long frg_kernel_launches(void);
+/*
+ * Failure-path self-test (no counterpart in the paper).  Every wait of the
+ * tensor-core pipeline is bounded: a wait that runs out records the failure in
+ * the context's device error word and the kernel returns, so the host sees
+ * FRG_ETIMEOUT instead of a hung device.  frg_selftest_wait runs one such wait,
+ * with a limit of limit_ms (clamped to [1, 2000] ms), on a barrier that nothing
+ * completes, on the context stream; it returns FRG_ETIMEOUT when the mechanism
+ * works (the error word is cleared again and the context stays usable), or
+ * FRG_EINVAL / FRG_ECUDA.  Synchronises.
+ */
+int frg_selftest_wait(frg_ctx *ctx, double limit_ms);
 
 /*
  * Contraction autotuning (split precisions).  The paper distributes work over

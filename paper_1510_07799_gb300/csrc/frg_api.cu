@@ -587,6 +587,14 @@ int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma, c
 
 long frg_kernel_launches(void) { return frg::g_kernel_launches; }
 
+int frg_selftest_wait(frg_ctx *ctx, double limit_ms) {
+  if (!ctx) return FRG_EINVAL;
+  if (!(limit_ms > 0.0) || !std::isfinite(limit_ms)) return fail(ctx, FRG_EINVAL, "limit_ms must be > 0");
+  DevGuard g(ctx->dev);
+  LK(tc_wait_selftest(ctx->d_err, limit_ms, ctx->stream), "wait self-test");
+  return sync_checked(ctx, "wait self-test");
+}
+
 int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma, const double *h_sigma,
                  double *h_dgamma, double *h_dsigma) {
   if (!ctx) return FRG_EINVAL;

@@ -116,14 +116,15 @@ __device__ __forceinline__ unsigned long long gtime() {
   return t;
 }
 // Bounded wait on a phase; returns false (and records the failure) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, volatile int *abort_flag,
+                                          unsigned long long limit_ns = WAIT_NS) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtime();
   for (unsigned it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*abort_flag) return false;
-      if (gtime() - t0 > WAIT_NS) {
+      if (gtime() - t0 > limit_ns) {
         atomicOr(err, 1u);
         *abort_flag = 1;
         return false;
@@ -1252,7 +1253,29 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 }  // namespace st
 
+// Self-test of the failure path of every pipeline wait: one thread waits, with
+// the same bounded wait, on an mbarrier that nothing arrives at; the wait gives
+// up after limit_ns, records the failure in *err and the kernel returns.
+__global__ void k_wait_selftest(unsigned *err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0u, err, &abort_flag, limit_ns);
+}
+
 }  // namespace tc
+
+int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st) {
+  const double ms = std::min(2000.0, std::max(1.0, limit_ms));
+  tc::k_wait_selftest<<<1, 32, 0, st>>>(d_err, (unsigned long long)(ms * 1e6));
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
 
 // --------------------------------------------------------------- plan ----
 struct TcPlan {

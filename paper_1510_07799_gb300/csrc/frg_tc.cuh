@@ -22,6 +22,9 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
                    int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why,
                    TcTune tune = TcTune());
 void tc_plan_destroy(TcPlan *plan);
+// One bounded pipeline wait on a barrier nothing completes (limit in ms,
+// clamped to [1, 2000]): the kernel sets *d_err and returns.
+int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // Evaluate the enabled vertex channels of every active point (point = -1) or of
 // one point, writing the float2 vertex output of each active RhsIO.
 // Relayout of the stage input, the channel products, and the combine into the

@@ -24,7 +24,7 @@ ERRNAMES = {EINVAL: "FRG_EINVAL", ENOMEM: "FRG_ENOMEM", ECUDA: "FRG_ECUDA",
 
 EXPORTED = ("frg_init", "frg_destroy", "frg_last_error", "frg_rhs", "frg_rhs_host", "frg_flow",
             "frg_advance", "frg_observables", "frg_get_state", "frg_set_state", "frg_stats",
-            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune")
+            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune", "frg_selftest_wait")
 NOALLOC_MAX_N = 64
 
 
@@ -119,6 +119,7 @@ def load():
     lib.frg_rhs_timed.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, C.POINTER(C.c_float)]
     lib.frg_rhs_noalloc.argtypes = [C.POINTER(_Params), C.c_double, vp, vp, vp, vp, vp]
     lib.frg_autotune.argtypes = [vp, C.POINTER(_Tune)]
+    lib.frg_selftest_wait.argtypes = [vp, C.c_double]
     lib.frg_kernel_launches.argtypes = []
     lib.frg_kernel_launches.restype = C.c_long
     _lib = lib
@@ -277,6 +278,11 @@ class Context:
         self._chk(load().frg_autotune(self._h, C.byref(t)))
         return {"nt_cap": t.nt_cap, "epi_cost": t.epi_cost, "candidates": t.candidates,
                 "ms": t.ms, "ms_default": t.ms_default}
+
+    def selftest_wait(self, limit_ms=50.0):
+        """Run one bounded pipeline wait that must run out; raises FrgError
+        with code ETIMEOUT when the failure path works."""
+        self._chk(load().frg_selftest_wait(self._h, float(limit_ms)))
 
     def observables(self, point):
         o = _Obs()

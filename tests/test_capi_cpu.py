@@ -80,4 +80,5 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.frg_advance(None, 1, None) == frg.EINVAL
     assert b"null context" in lib.frg_last_error(None)
     assert lib.frg_autotune(None, None) == frg.EINVAL
+    assert lib.frg_selftest_wait(None, 10.0) == frg.EINVAL
     lib.frg_destroy(None)
