@@ -252,8 +252,10 @@ static SegTable seg(frg_ctx *ctx) { return SegTable{ctx->d_seg_point, ctx->d_seg
 
 static int issue_k1(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
-  if (ctx->split) LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, st), "stage 0");
-  LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
+  if (ctx->split)
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st), "stage 0");
+  else
+    LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
   int rc = run_rhs(ctx, ctx->d_io_stage, -1);
   if (rc) return rc;
   LK(launch_finish_k1(ctx->d_ctl, ctx->d_io_stage, ctx->n, st), "finish k1");
@@ -264,8 +266,7 @@ static int issue_step(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   LK(launch_prepare(ctx->d_pts, ctx->d_ctl, ctx->n, st), "prepare");
   for (int s = 1; s < 7; ++s) {
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, st), "stage sum");
-    LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, s, ctx->split, ctx->n, st), "stage io");
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, ctx->d_io_stage, st), "stage sum");
     int rc = run_rhs(ctx, ctx->d_io_stage, -1);
     if (rc) return rc;
   }
@@ -667,8 +668,7 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out) {
     if (!fs.ok) return fail(ctx, FRG_ECUDA, "flow stream ordering");
     cudaStream_t st = ctx->stream;
     // stage input of the current state of every point
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, st), "stage 0");
-    LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st), "stage 0");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "events");
     CK(cudaEventCreate(&e1), "events");

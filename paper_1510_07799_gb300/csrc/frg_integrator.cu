@@ -102,12 +102,9 @@ __global__ void k_set_ctl(const PointDesc *__restrict__ pts, Ctl *__restrict__ c
 }
 
 // ------------------------------------------------------------ stage IO ----
-__global__ void k_set_stage_io(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl, RhsIO *__restrict__ io,
-                               int stage, int split, int n) {
-  const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pi >= n) return;
-  const PointDesc &P = pts[pi];
-  Ctl &c = ctl[pi];
+// The rhs IO record of one point for stage `stage` (written by k_set_stage_io,
+// or by the first block of the point's stage kernel).
+__device__ __forceinline__ void write_stage_io(const PointDesc &P, Ctl &c, RhsIO *io, int stage, int split) {
   RhsIO o;
   o.active = !c.done && (stage > 0 || !c.have_k1);
   if (stage == 0) c.lam_stage[0] = exp(c.t);
@@ -125,7 +122,14 @@ __global__ void k_set_stage_io(const PointDesc *__restrict__ pts, Ctl *__restric
   o.dgam = P.kG[c.kslot[stage]];
   o.dsig = P.kS[c.kslot[stage]];
   o.out_f32 = split;
-  io[pi] = o;
+  *io = o;
+}
+
+__global__ void k_set_stage_io(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl, RhsIO *__restrict__ io,
+                               int stage, int split, int n) {
+  const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pi >= n) return;
+  write_stage_io(pts[pi], ctl[pi], io + pi, stage, split);
 }
 
 // After the first-stage evaluation of a step that had no k1.
@@ -183,10 +187,12 @@ __device__ __forceinline__ void block_max_to(float v, unsigned *dst) {
 // candidate and is also kept in FP64 as ynew.  Split paths: the vertex part of
 // Y_s is stored rounded to FP32 for the contraction, the self-energy part in FP64.
 template <bool SPLIT>
-__global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl,
-                                               SegTable seg, int s) {
+__global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+                                               SegTable seg, int s, RhsIO *__restrict__ io) {
   const int b = blockIdx.x;
   const int pi = seg.point[b];
+  // the first block of the point also writes the stage's rhs IO record
+  if (io && seg.base[b] == 0 && threadIdx.x == 0) write_stage_io(pts[pi], ctl[pi], io + pi, s, SPLIT);
   const Ctl &c = ctl[pi];
   if (c.done) return;
   const PointDesc &P = pts[pi];
@@ -258,10 +264,12 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
 // widened to FP64.  Stage 0 only prepares the float pairs of y.  The
 // self-energy part stays in FP64 throughout.
 template <int S>
-__global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl,
-                                                     SegTable seg) {
+__global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+                                                     SegTable seg, RhsIO *__restrict__ io) {
   const int b = blockIdx.x;
   const int pi = seg.point[b];
+  // the first block of the point also writes the stage's rhs IO record
+  if (io && seg.base[b] == 0 && threadIdx.x == 0) write_stage_io(pts[pi], ctl[pi], io + pi, S, 1);
   const Ctl &c = ctl[pi];
   if (c.done) return;
   const PointDesc &P = pts[pi];
@@ -370,8 +378,10 @@ __global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict
       const float2 y = P.yhi[ys][i], yn = P.yhi[ys ^ 1][i];
       const float mx = fmaxf(fabsf(y.x), fabsf(yn.x)), my = fmaxf(fabsf(y.y), fabsf(yn.y));
       ym = fmaxf(ym, fmaxf(mx, my));
-      const float rx = fabsf(hf * __fadd_rn(er, erl)) / (atolf + rtolf * fmaxf(mx, yfl));
-      const float ry = fabsf(hf * __fadd_rn(ei, eil)) / (atolf + rtolf * fmaxf(my, yfl));
+      // the ratio only decides accept / reject and the step factor: a fast
+      // division (a few ulp) is enough
+      const float rx = __fdividef(fabsf(hf * __fadd_rn(er, erl)), atolf + rtolf * fmaxf(mx, yfl));
+      const float ry = __fdividef(fabsf(hf * __fadd_rn(ei, eil)), atolf + rtolf * fmaxf(my, yfl));
       if (!isfinite(rx) || !isfinite(ry) || !isfinite(yn.x) || !isfinite(yn.y)) bad = 1;
       else fmax_ = fmaxf(fmax_, fmaxf(rx, ry));
     } else {
@@ -568,20 +578,20 @@ int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int launch_stage(const PointDesc *d_pts, const Ctl *d_ctl, SegTable seg, int nblk, int s, int split,
+int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int s, int split, RhsIO *d_io,
                  cudaStream_t st) {
   if (split) {
     switch (s) {
-      case 0: k_stage_split<0><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
-      case 1: k_stage_split<1><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
-      case 2: k_stage_split<2><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
-      case 3: k_stage_split<3><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
-      case 4: k_stage_split<4><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
-      case 5: k_stage_split<5><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
-      default: k_stage_split<6><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg); break;
+      case 0: k_stage_split<0><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      case 1: k_stage_split<1><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      case 2: k_stage_split<2><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      case 3: k_stage_split<3><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      case 4: k_stage_split<4><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      case 5: k_stage_split<5><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      default: k_stage_split<6><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
     }
   } else {
-    k_stage<false><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s);
+    k_stage<false><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);
   }
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;

@@ -20,7 +20,9 @@ int launch_set_stage_io(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int sta
                         cudaStream_t st);
 int launch_finish_k1(Ctl *d_ctl, const RhsIO *d_io, int n, cudaStream_t st);
 int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st);
-int launch_stage(const PointDesc *d_pts, const Ctl *d_ctl, SegTable seg, int nblk, int s, int split,
+// Stage sum s of every point; with d_io non-null the first block of each point
+// also writes the stage's rhs IO record (as launch_set_stage_io).
+int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int s, int split, RhsIO *d_io,
                  cudaStream_t st);
 int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int split, cudaStream_t st);
 int launch_controller(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st);
