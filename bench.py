@@ -21,6 +21,9 @@ headline):
   siam_N256  the largest single flow, N_f = 256: rhs evaluations per second,
              phase times and the error of one rhs against the FP64 GPU path on
              the same state
+  siam_N64   full flows per second at N_f = 64 (off particle-hole symmetry):
+             the plain FP64 GPU path and the 3xTF32 path, next to the oracle's
+             flow on the host cores (one flow, --no-oracle skips it)
 """
 import argparse
 import json
@@ -478,6 +481,58 @@ def run_n256(args):
     return 0
 
 
+def run_n64(args):
+    """Full flows per second at N_f = 64: plain FP64 and 3xTF32 on the GPU,
+    and the FP64 oracle on the host cores; parity of the final vertex."""
+    import numpy as np
+    import torch
+    from paper_1510_07799_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1510_07799_gb300 import frg, inputs
+    w = inputs.SIAM_N64
+    res = {}
+    finals = {}
+    for prec in ("fp64", "3xtf32"):
+        times, evals = [], []
+        for k in range(args.warmup + args.steps):
+            with frg.Context([w], precision=prec) as ctx:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = ctx.flow()[0]
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if k >= args.warmup:
+                    times.append(dt)
+                    evals.append(st.rhs_evals)
+                g, s, _, _ = ctx.get_state(0)
+                finals[prec] = g.cpu().numpy()
+        t = sum(times) / len(times)
+        res[prec] = {"flows_per_s": 1.0 / t, "rhs_evals_per_s": evals[-1] / t, "rhs_evals": evals[-1]}
+    line = {"metric": "full flows/s at N_f=64 (off particle-hole symmetry)", "value": res["fp64"]["flows_per_s"],
+            "unit": "flows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / res["fp64"]["flows_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N_f": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
+                       "step": "one full flow (Lambda 1e3 -> 1e-3, rtol 1e-8)"},
+            "fp64_gpu": res["fp64"], "tf32x3_gpu": res["3xtf32"],
+            "tf32x3_vs_fp64_gamma": float(np.max(np.abs(finals["3xtf32"] - finals["fp64"]))
+                                          / np.max(np.abs(finals["fp64"])))}
+    if not args.no_oracle:
+        import oracle as orc
+        from oracle import build as oracle_build
+        oracle_build.build()
+        m = orc.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+        t0 = time.perf_counter()
+        g0, _, st0 = orc.flow(m)
+        dt = time.perf_counter() - t0
+        line["oracle_cpu"] = {"flows_per_s": 1.0 / dt, "rhs_evals_per_s": st0.rhs_evals / dt,
+                              "rhs_evals": int(st0.rhs_evals), "cores": orc.max_threads(), "kind": "oracle",
+                              "sample": "one full flow"}
+        line["fp64_vs_oracle_gamma"] = float(np.max(np.abs(finals["fp64"] - g0)) / np.max(np.abs(g0)))
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,7 +544,8 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="siam_N128", choices=["siam_N128", "batch64", "siam_N256"])
+    ap.add_argument("--workload", default="siam_N128", choices=["siam_N128", "batch64", "siam_N256", "siam_N64"])
+    ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
     args.precision_explicit = args.precision is not None
@@ -503,6 +559,8 @@ def main():
         return run_batch(args)
     if args.workload == "siam_N256":
         return run_n256(args)
+    if args.workload == "siam_N64":
+        return run_n64(args)
     return run_ours(args)
 
 
