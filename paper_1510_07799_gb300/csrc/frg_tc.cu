@@ -4,41 +4,36 @@
 // For every channel and transfer frequency m the rhs needs the complex product
 //   Out[r][c] = sum_k Left[r][k] Right[k][c]
 // (the three one-loop diagrams of the paper, Sec. 4, reordered per transfer;
-// index sets in frg_common.cuh).  One CTA tile is 64 complex rows x NT complex
-// columns.  The complex product runs as one real product with the 2x2 real form
-// on the left operand:
-//   A' rows 0..63   = [ Re a | -Im a ] ,  A' rows 64..127 = [ Im a | Re a ]
-//   B' row c        = [ Re b | Im b ]          (K-major, 16 complex k per step)
-// so that (A' B'^T)[r] = Re(a b)[r], [r+64] = Im(a b)[r]; M = 128, N = NT, K = 8
-// (TF32) per instruction.
+// index sets in frg_common.cuh).  A CTA tile is 64 complex rows x NT complex
+// columns; the complex product runs as real products on the tensor cores.
 //
-// Split-TF32 (3xTF32): x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the
-// product keeps hi*hi (accumulator group 0) and hi*lo + lo*hi (group 1), FP32
-// accumulation in TMEM, groups added in the epilogue.
-//
-// BF16x3: every operand is scaled by a power of two 2^-e with 2^e above a bound
-// on its magnitude (the vertex maximum for Right; that times the bubble-weight
-// row maximum, x3 for the direct particle-hole combination, for Left) and cut
-// into three 8-bit slices on the fixed grids 2^-7, 2^-15, 2^-23:
-//   s1 = rint(2^7 x)/2^7, s2 = rint(2^15 (x - s1))/2^15, s3 = rint(2^23 (x-s1-s2))/2^23.
-// Products of first slices are integers times 2^(eA+eB-14) bounded by 2^14, so
-// their sum over K' <= 1024 terms is exact in the FP32 accumulator whatever the
-// accumulator's rounding (group 0); the five products of order <= 4 beyond it
-// go to group 1.  This is the error-free splitting idea of Ozaki et al. applied
-// with bf16 slices.
-//
-// Roles (one persistent CTA per SM, static strided tile order over a list sorted
-// heavy-first, the strided static distribution of the paper's Sec. 5.1):
-//   warps 0-3  epilogue: TMEM -> registers -> smem staging -> coalesced rows of
-//              the channel's output layout (frg_layout.cu)
-//   warp  4    TMEM allocation and MMA issue (one elected lane)
-//   warps 5-20 producers in two groups that take alternate k-steps (two k-steps
-//              of loads in flight): load the operand rows of a k-step
-//              (contiguous runs of the FP32 vertex layouts, L2-resident), fold
-//              in diag(Lb), split, write swizzled K-major smem tiles
-// Pipelines: NSTAGE smem stages (full/empty mbarriers), two TMEM accumulator
-// buffers (tfull/tempty mbarriers).  Every wait is bounded; a wait that runs out
-// sets the context error word, and all roles then leave their loops.
+// Two kernels:
+//  * st::k_contract_tf32 (3xTF32, the headline precision): one persistent
+//    launch per rhs over the tiles of all channels and points, tensor-map TMA
+//    loader, transform warps, MMA warp, epilogue warps (see namespace st below).
+//    Split: x = hi + lo with hi = tf32(x), lo = tf32(x - hi); hi*hi in one TMEM
+//    accumulator, hi*lo + lo*hi in another, added in the epilogue.
+//  * k_contract_tc<CH, FRG_BF16X3>: one launch per channel.  Real form on the
+//    left operand, A' rows 0..63 = [Re a | -Im a], rows 64..127 = [Im a | Re a],
+//    B' row c = [Re b | Im b] (K-major), so that (A' B'^T)[r] = Re(a b)[r] and
+//    [r + 64] = Im(a b)[r].  Every operand is scaled by a power of two 2^-e
+//    with 2^e above a bound on its magnitude (the vertex maximum for Right;
+//    that times the bubble-weight row maximum, x3 for the direct particle-hole
+//    combination, for Left) and cut into three 8-bit slices on the fixed grids
+//    2^-7, 2^-15, 2^-23:
+//      s1 = rint(2^7 x)/2^7, s2 = rint(2^15 (x - s1))/2^15, s3 = rint(2^23 (x-s1-s2))/2^23.
+//    Products of first slices are integers times 2^(eA+eB-14) bounded by 2^14,
+//    so their sum over K' <= 1024 terms is exact in the FP32 accumulator
+//    whatever the accumulator's rounding (group 0); the five products of order
+//    <= 4 beyond it go to group 1 (the error-free splitting idea of Ozaki et
+//    al. with bf16 slices).  Roles: warps 0-3 epilogue, warp 4 TMEM allocation
+//    and MMA issue, warps 5-20 producers in two groups that take alternate
+//    k-steps (load the operand rows from the FP32 vertex layouts, fold in
+//    diag(Lb), slice, write swizzled K-major tiles); tiles in a static strided
+//    order over a list sorted heavy-first (the strided static distribution of
+//    the paper's Sec. 5.1).
+// Every wait is bounded; a wait that runs out sets the context error word, and
+// all roles then leave their loops.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -650,7 +645,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ===================================================================
-// 3xTF32 with bulk-copy staging.
+// 3xTF32: one persistent launch over the tiles of all channels and points.
 //
 // The complex product uses the real form on the output side:
 //   A'' rows 2r = Re a(r,.), rows 2r+1 = Im a(r,.)     (K = 16 per k-step)
@@ -659,10 +654,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 // one MMA shape M = 128, N = 2 NT (<= 256), K = 8 per instruction, three
 // products: hi*hi into one TMEM accumulator, hi*lo + lo*hi into a second one
 // (the FP32 accumulator does not round to nearest, so the large sum should see
-// as few additions as possible).
-// Roles: warps 0-3 epilogue, warp 4 MMA, warp 5 loader (cp.async.bulk of the
-// contiguous operand rows, NRAW k-steps ahead), warps 6-17 transform (raw ->
-// bubble-weighted, split, swizzled K-major operand tiles).
+// as few additions as possible); each transfer's k-chunks are fed in increasing
+// order of their largest bubble weight.
+// Roles: warps 0-3 epilogue (TMEM -> shuffles -> staged, coalesced stores),
+// warp 4 MMA issue, warp 5 loader (tensor-map TMA of the raw operand rows,
+// NRAW k-steps ahead), warps 6-17 transform (raw -> bubble-weighted, bare-U
+// filled, split, 64-byte-swizzled K-major operand tiles in NOP stages).  Every
+// wait is bounded: a wait that runs out sets the context error word and all
+// roles leave their loops.
 namespace st {
 // Warp-uniform bounded wait: every lane of the warp leaves with the same result,
 // so warp-collective code after it (shuffles, __syncwarp) never splits.
@@ -687,7 +686,6 @@ constexpr int EPI_STG = 16 * EPI_PITCH * 8;             // per epilogue warp: 16
 constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 4 * EPI_STG + 512;
 constexpr int EPI_W = 4, MMA_W = 4, LOAD_W = 5, XF_W0 = 6, N_XF = 12;
 constexpr int THREADS = 32 * (XF_W0 + N_XF);
-constexpr int XF_THREADS = 32 * N_XF;
 static_assert(SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ uint32_t swz64(int row, int ch) {
@@ -703,12 +701,6 @@ __device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
 }
 __device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
 
@@ -755,37 +747,6 @@ __device__ __forceinline__ Step step_of(const TileInfo &ti, int kb) {
   q.nK = min(KS, ti.g.D - q.kl);
   q.ncols = min(ti.NT, ti.N - ti.c0);
   return q;
-}
-template <int CH>
-__device__ __forceinline__ const float2 *left_row(const Srcs &S, const TileInfo &ti, int rr, bool c_row) {
-  const int N = ti.N;
-  const Geom &g = ti.g;
-  if (CH == CH_PP) {
-    const int a = g.row_lo + rr;
-    return S.YN + ((size_t)a * N + (g.x - a)) * N;
-  } else if (CH == CH_XPH) {
-    const int k3 = g.row_lo + rr;
-    return S.YW + ((size_t)(k3 + g.x) * N + k3) * N;
-  } else {
-    const int k1 = g.row_lo + rr;
-    return (c_row ? S.YW : S.YX) + ((size_t)k1 * N + (k1 + g.x)) * N;
-  }
-}
-template <int CH>
-__device__ __forceinline__ const float2 *right_row(const Srcs &S, const TileInfo &ti, int kk, int half) {
-  const int N = ti.N;
-  const Geom &g = ti.g;
-  const int p = g.p_lo + kk;
-  if (CH == CH_PP) return S.YN + ((size_t)p * N + (g.x - p)) * N;
-  if (CH == CH_XPH) return S.YW + ((size_t)(p + g.x) * N + p) * N;
-  return (half ? S.YW : S.YX) + ((size_t)(p - g.x) * N + p) * N;
-}
-template <int CH>
-__device__ __forceinline__ const float2 *l_row(const PointDesc &P, const TileInfo &ti) {
-  const int N = ti.N;
-  if (CH == CH_PP) return P.Lpp32 + (size_t)ti.g.x * N;
-  if (CH == CH_XPH) return P.Lph32 + (size_t)(ti.g.x + N - 1) * N;
-  return P.Lph32 + (size_t)(-ti.g.x + N - 1) * N;
 }
 
 // k-step processed i-th in a tile: chunks in increasing max |Lb| (table
