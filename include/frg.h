@@ -141,6 +141,22 @@ int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma,
  * per-point statistics.  Returns FRG_OK if every point reached Lambda_f, else
  * the first failing point's code (FRG_ENONFINITE, FRG_ENOTCONV).
  */
+/*
+ * Pipelined host-buffer evaluations.  frg_rhs_host_async enqueues the same
+ * evaluation as frg_rhs_host and returns at once: the host->device copy of the
+ * input runs on a copy-in stream, the evaluation on the context stream, the
+ * device->host copy of the result on a copy-out stream, through two device
+ * buffer slots, so that in a sequence of calls the input of one evaluation, the
+ * computation of the previous one and the output of the one before that overlap
+ * (both directions of the host link busy at once).  The host buffers of a call
+ * must stay valid, and the output buffers unread, until frg_sync returns; the
+ * output buffers of calls in flight must not overlap.  frg_sync waits for every
+ * enqueued evaluation and returns its first device-side failure
+ * (FRG_ETIMEOUT); argument errors are returned by frg_rhs_host_async itself.
+ */
+int frg_rhs_host_async(frg_ctx *ctx, int point, double Lambda, const double *h_gamma,
+                       const double *h_sigma, double *h_dgamma, double *h_dsigma);
+int frg_sync(frg_ctx *ctx);
 int frg_flow(frg_ctx *ctx, frg_flow_stats *stats);
 
 /*

@@ -61,6 +61,12 @@ struct frg_ctx {
   // while the stage input is relaid (fork / join by events)
   cudaStream_t sstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // pipelined host-buffer evaluations: copy-in and copy-out streams, two device
+  // slots per point, per-slot events (input copied, compute done, output read)
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t aev_in[2] = {}, aev_cdone[2] = {}, aev_odone[2] = {};
+  std::vector<double2 *> ain[2], aout[2];
+  int aslot = 0;
   cudaGraphExec_t step_exec = nullptr;
   long step_launches = 0;  // kernels in one replay of the step graph
   std::string err;
@@ -499,6 +505,19 @@ void frg_destroy(frg_ctx *ctx) {
     cudaStreamDestroy(ctx->sstream);
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->cin) {
+    cudaStreamSynchronize(ctx->cin);
+    cudaStreamDestroy(ctx->cin);
+  }
+  if (ctx->cout) {
+    cudaStreamSynchronize(ctx->cout);
+    cudaStreamDestroy(ctx->cout);
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->aev_in[b]) cudaEventDestroy(ctx->aev_in[b]);
+    if (ctx->aev_cdone[b]) cudaEventDestroy(ctx->aev_cdone[b]);
+    if (ctx->aev_odone[b]) cudaEventDestroy(ctx->aev_odone[b]);
+  }
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -587,6 +606,63 @@ int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma, c
 }
 
 long frg_kernel_launches(void) { return frg::g_kernel_launches; }
+
+int frg_rhs_host_async(frg_ctx *ctx, int point, double Lambda, const double *h_gamma, const double *h_sigma,
+                       double *h_dgamma, double *h_dsigma) {
+  if (!ctx) return FRG_EINVAL;
+  if (point < 0 || point >= ctx->n) return fail(ctx, FRG_EINVAL, "point out of range");
+  if (!h_gamma || !h_dgamma || !h_dsigma) return fail(ctx, FRG_EINVAL, "null buffer");
+  if (!(Lambda > 0.0) || !std::isfinite(Lambda)) return fail(ctx, FRG_EINVAL, "Lambda must be > 0");
+  DevGuard g(ctx->dev);
+  if (!ctx->cin) {
+    CK(cudaStreamCreateWithFlags(&ctx->cin, cudaStreamNonBlocking), "copy streams");
+    CK(cudaStreamCreateWithFlags(&ctx->cout, cudaStreamNonBlocking), "copy streams");
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaEventCreateWithFlags(&ctx->aev_in[b], cudaEventDisableTiming), "events");
+      CK(cudaEventCreateWithFlags(&ctx->aev_cdone[b], cudaEventDisableTiming), "events");
+      CK(cudaEventCreateWithFlags(&ctx->aev_odone[b], cudaEventDisableTiming), "events");
+      ctx->ain[b].assign(ctx->n, nullptr);
+      ctx->aout[b].assign(ctx->n, nullptr);
+    }
+  }
+  const PointDesc &P = ctx->hpts[point];
+  const size_t nc = (size_t)P.n3 + P.N;
+  const int b = ctx->aslot;
+  if (!ctx->ain[b][point]) {
+    if (!(ctx->ain[b][point] = dalloc<double2>(ctx, nc)) || !(ctx->aout[b][point] = dalloc<double2>(ctx, nc)))
+      return fail(ctx, FRG_ENOMEM, "pipelined host-call buffers");
+  }
+  ctx->aslot ^= 1;
+  double2 *din = ctx->ain[b][point], *dout = ctx->aout[b][point];
+  // input copy: after the evaluation that last read this slot
+  CK(cudaStreamWaitEvent(ctx->cin, ctx->aev_cdone[b], 0), "order");
+  CK(cudaMemcpyAsync(din, h_gamma, (size_t)P.n3 * sizeof(double2), cudaMemcpyHostToDevice, ctx->cin), "H2D");
+  if (h_sigma)
+    CK(cudaMemcpyAsync(din + P.n3, h_sigma, (size_t)P.N * sizeof(double2), cudaMemcpyHostToDevice, ctx->cin),
+       "H2D");
+  CK(cudaEventRecord(ctx->aev_in[b], ctx->cin), "order");
+  // evaluation: after its input landed and the output copy that last read the slot
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->aev_in[b], 0), "order");
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->aev_odone[b], 0), "order");
+  int rc = frg_rhs(ctx, point, Lambda, din, h_sigma ? din + P.n3 : nullptr, dout, dout + P.n3);
+  if (rc) return rc;
+  CK(cudaEventRecord(ctx->aev_cdone[b], ctx->stream), "order");
+  // output copy
+  CK(cudaStreamWaitEvent(ctx->cout, ctx->aev_cdone[b], 0), "order");
+  CK(cudaMemcpyAsync(h_dgamma, dout, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToHost, ctx->cout), "D2H");
+  CK(cudaMemcpyAsync(h_dsigma, dout + P.n3, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->cout),
+     "D2H");
+  CK(cudaEventRecord(ctx->aev_odone[b], ctx->cout), "order");
+  return FRG_OK;
+}
+
+int frg_sync(frg_ctx *ctx) {
+  if (!ctx) return FRG_EINVAL;
+  DevGuard g(ctx->dev);
+  if (ctx->cin) CK(cudaStreamSynchronize(ctx->cin), "sync");
+  if (ctx->cout) CK(cudaStreamSynchronize(ctx->cout), "sync");
+  return sync_checked(ctx, "sync");
+}
 
 int frg_selftest_wait(frg_ctx *ctx, double limit_ms) {
   if (!ctx) return FRG_EINVAL;

@@ -24,7 +24,7 @@ ERRNAMES = {EINVAL: "FRG_EINVAL", ENOMEM: "FRG_ENOMEM", ECUDA: "FRG_ECUDA",
 
 EXPORTED = ("frg_init", "frg_destroy", "frg_last_error", "frg_rhs", "frg_rhs_host", "frg_flow",
             "frg_advance", "frg_observables", "frg_get_state", "frg_set_state", "frg_stats",
-            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune", "frg_selftest_wait")
+            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune", "frg_selftest_wait", "frg_rhs_host_async", "frg_sync")
 NOALLOC_MAX_N = 64
 
 
@@ -120,6 +120,8 @@ def load():
     lib.frg_rhs_noalloc.argtypes = [C.POINTER(_Params), C.c_double, vp, vp, vp, vp, vp]
     lib.frg_autotune.argtypes = [vp, C.POINTER(_Tune)]
     lib.frg_selftest_wait.argtypes = [vp, C.c_double]
+    lib.frg_rhs_host_async.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp]
+    lib.frg_sync.argtypes = [vp]
     lib.frg_kernel_launches.argtypes = []
     lib.frg_kernel_launches.restype = C.c_long
     _lib = lib
@@ -251,6 +253,22 @@ class Context:
         sp = None if sigma is None else sigma.ctypes.data_as(dp)
         self._chk(load().frg_rhs_host(self._h, point, Lambda, gamma.ctypes.data_as(dp), sp,
                                       dgamma.ctypes.data_as(dp), dsigma.ctypes.data_as(dp)))
+
+    def rhs_host_async(self, point, Lambda, gamma, sigma, dgamma, dsigma):
+        """Pipelined host-buffer evaluation (returns at once; the buffers must
+        stay alive and the outputs unread until sync())."""
+        import numpy as np
+        N = self.N(point)
+        for a, shp in ((gamma, (N, N, N)), (dgamma, (N, N, N)), (dsigma, (N,))):
+            if a.dtype != np.complex128 or not a.flags.c_contiguous or a.shape != shp:
+                raise ValueError("host buffers must be contiguous complex128 arrays")
+        dp = C.POINTER(C.c_double)
+        sp = None if sigma is None else sigma.ctypes.data_as(dp)
+        self._chk(load().frg_rhs_host_async(self._h, point, Lambda, gamma.ctypes.data_as(dp), sp,
+                                            dgamma.ctypes.data_as(dp), dsigma.ctypes.data_as(dp)))
+
+    def sync(self):
+        self._chk(load().frg_sync(self._h))
 
     def _stats(self, arr):
         return [Stats(s.Lambda, s.h, s.accepted, s.rejected, s.rhs_evals, s.status, s.done)

@@ -181,3 +181,24 @@ def test_autotuned_plan_keeps_the_results():
             assert nrel(dg, rg) < RHS_TOL[frg.TF32X3] and nrel(ds, rs) < RHS_TOL[frg.TF32X3]
         st = ctx.flow()
         assert all(s.status == 0 and s.done for s in st)
+
+
+@pytest.mark.parametrize("prec", [frg.FP64, frg.TF32X3])
+def test_pipelined_host_calls_equal_synchronous_calls(prec):
+    """frg_rhs_host_async: several evaluations in flight (two device slots, two
+    copy streams) give bitwise the results of one-by-one frg_rhs_host calls."""
+    w = inputs.Workload("t", N=24, U=1.6, T=0.03, eps_d=-0.4)
+    ins = [(inputs.random_vertex(w.N, w.U, seed=90 + i), inputs.random_sigma(w.N, seed=95 + i), 0.02 + 0.1 * i)
+           for i in range(5)]
+    with frg.Context([w], precision=prec) as ctx:
+        ref = []
+        for V, sig, lam in ins:
+            og, os_ = np.empty_like(V), np.empty_like(sig)
+            ctx.rhs_host(0, lam, V, sig, og, os_)
+            ref.append((og, os_))
+        outs = [(np.full_like(V, np.nan), np.full_like(sig, np.nan)) for V, sig, _ in ins]
+        for (V, sig, lam), (og, os_) in zip(ins, outs):
+            ctx.rhs_host_async(0, lam, V, sig, og, os_)
+        ctx.sync()
+    for (og, os_), (rg, rs) in zip(outs, ref):
+        assert np.array_equal(og, rg) and np.array_equal(os_, rs)
