@@ -548,7 +548,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=list(DTYPES))
     ap.add_argument("--rhs-reps", type=int, default=5)
-    ap.add_argument("--e2e-reps", type=int, default=6)
+    ap.add_argument("--e2e-reps", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="siam_N128", choices=["siam_N128", "batch64", "siam_N256", "siam_N64"])

@@ -81,4 +81,6 @@ def test_null_context_calls_fail_cleanly(lib):
     assert b"null context" in lib.frg_last_error(None)
     assert lib.frg_autotune(None, None) == frg.EINVAL
     assert lib.frg_selftest_wait(None, 10.0) == frg.EINVAL
+    assert lib.frg_rhs_host_async(None, 0, 1.0, None, None, None, None) == frg.EINVAL
+    assert lib.frg_sync(None) == frg.EINVAL
     lib.frg_destroy(None)
