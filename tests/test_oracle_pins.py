@@ -115,6 +115,47 @@ def test_second_order_perturbation_theory(eps_shift):
         assert np.max(np.abs(sref)) < 1e-15
 
 
+# ----------------------------------------------------------- observables ----
+
+def test_observables_of_the_bare_state():
+    """Bare vertex, no self-energy: U_eff = U, Z = 1, Sigma(pi T) = 0."""
+    N, U = 8, 1.7
+    m = Model(U=U, T=0.04, eps_d=-U / 2 + 0.3, Delta=1.0, N=N)
+    o = oracle.observables(m, 1e-3, np.full((N, N, N), U, np.complex128), np.zeros(N, np.complex128))
+    assert o["U_eff"] == U and o["Z"] == 1.0 and o["sigma_lowest"] == 0.0
+
+
+def test_quasiparticle_weight_of_a_linear_self_energy():
+    """Fermi-liquid form Sigma(i w_n) = -i a_n w_n: Z = 1 / (1 + a) at the lowest
+    positive Matsubara frequency w = pi T (index N/2); a different a_n on every
+    frequency pins which one the observable reads."""
+    N, T = 10, 0.03
+    m = Model(U=1.0, T=T, eps_d=-0.5, Delta=1.0, N=N)
+    w = cf.freqs(N, T)
+    a = 0.1 + 0.05 * np.arange(N)
+    sig = -1j * a * w
+    o = oracle.observables(m, 1e-3, np.full((N, N, N), 1.0, np.complex128), sig)
+    i0 = N // 2
+    assert abs(w[i0] - np.pi * T) < 1e-15
+    assert abs(o["Z"] - 1.0 / (1.0 + a[i0])) < 1e-14
+    assert o["sigma_lowest"] == sig[i0]
+
+
+def test_effective_interaction_of_the_pp_ladder():
+    """U_eff is the vertex at n1 = n2 = n3 = 0 (all external frequencies pi T):
+    after a pp-only flow it equals the ladder value U / (1 + U dB_pp(s)) at
+    s = i1 + i2 = N, the bosonic transfer of two frequencies pi T."""
+    N, T, D, U = 10, 0.05, 1.0, 2.5
+    m = Model(U=U, T=T, eps_d=-U / 2, Delta=D, N=N)
+    g, s, st = oracle.flow(m, mask=0x1, rtol=1e-11, atol=1e-14)
+    o = oracle.observables(m, 1e-3, g, s)
+    _, dBpp, _ = cf.second_order_vertex(N, T, 0.0, D, 1.0, 1e3, 1e-3)
+    ref = U / (1 + U * dBpp)
+    i0 = N // 2
+    assert abs(o["U_eff"] - ref[i0, i0, i0]) / abs(ref[i0, i0, i0]) < 2e-8
+    assert abs(ref[i0, i0, i0] - U) / U > 0.05
+
+
 # ------------------------------------------------------- ladder solutions ----
 
 def _aib(N):
