@@ -14,12 +14,16 @@
 namespace frg {
 
 // ---------------------------------------------------------- propagators ----
+// grid (ceil(maxN / GS_PER_BLOCK), points): GS_PER_BLOCK frequencies per block,
+// so that the FP64 divisions of one point spread over many SMs (this part's
+// FP64 rate per SM is low).
+constexpr int GS_PER_BLOCK = 16;
 __global__ void k_bubble_gs(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
-  const int pi = blockIdx.x;
+  const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
   const PointDesc &P = pts[pi];
-  const int i = threadIdx.x;
+  const int i = blockIdx.x * GS_PER_BLOCK + threadIdx.x;
   if (i >= P.N) return;
   const double L = *o.lam;
   const double w = (2.0 * (double)(i - P.N / 2) + 1.0) * M_PI * P.T;
@@ -113,7 +117,7 @@ __global__ void k_bubble_tables(const PointDesc *__restrict__ pts, const RhsIO *
 int launch_bubble(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split,
                   cudaStream_t st) {
   (void)split;
-  k_bubble_gs<<<n_points, maxN, 0, st>>>(d_pts, d_io);
+  k_bubble_gs<<<dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0, st>>>(d_pts, d_io);
   FRG_COUNT(1);
   dim3 g(2 * maxN - 1, 2, n_points);
   k_bubble_tables<<<g, 128, 0, st>>>(d_pts, d_io);
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(128)
 
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
                         cudaStream_t st) {
-  k_bubble_gs<<<n_points, maxN, 0, st>>>(d_pts, d_io);
+  k_bubble_gs<<<dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0, st>>>(d_pts, d_io);
   FRG_COUNT(1);
   dim3 g(2 * (2 * maxN - 1) + maxN, n_points);
   if (split)
