@@ -149,10 +149,10 @@ struct Workspace;
 int launch_bubble(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, cudaStream_t st);
 int launch_contract_fp64(const PointDesc *d_pts, const RhsIO *d_io, const WorkItem *const d_work[3],
                          const int nwork[3], int mask, cudaStream_t st);
-// Propagators (one block per point), then both bubble-weight tables and the
-// self-energy rhs in one launch.
+// Propagators (16 frequencies per block), then both bubble-weight tables and
+// the self-energy rhs in one launch.
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
                         cudaStream_t st);
-int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
-                 cudaStream_t st);
+// Self-energy rhs from FP64 input alone (after launch_bubble).
+int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st);
 }  // namespace frg

@@ -141,8 +141,9 @@ __device__ __forceinline__ double2 vload(const void *gam, int N, double U, int i
 }
 
 // ------------------------------------------------------------ self-energy ----
-// dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]; one warp per w.
-template <bool SPLIT>
+// dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]; one warp per w, FP64
+// input (the allocation-free entry point; the context paths use the fused
+// k_bubble_sigma).
 __global__ void k_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int enabled) {
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
@@ -155,8 +156,8 @@ __global__ void k_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restri
   double2 acc = make_double2(0.0, 0.0);
   if (enabled) {
     for (int p = lane; p < N; p += 32) {
-      double2 a = vload<SPLIT>(o.gam, N, P.U, w, p, w);
-      double2 b = vload<SPLIT>(o.gam, N, P.U, w, p, p);
+      double2 a = vload<false>(o.gam, N, P.U, w, p, w);
+      double2 b = vload<false>(o.gam, N, P.U, w, p, p);
       double2 t = make_double2(2.0 * a.x - b.x, 2.0 * a.y - b.y);
       cfma(acc, P.S[p], t);
     }
@@ -168,18 +169,12 @@ __global__ void k_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restri
   if (lane == 0) {
     const double f = (*o.lam) * P.T;
     o.dsig[w] = make_double2(acc.x * f, acc.y * f);
-    // the contractions of this rhs have consumed the vertex bound: reset it
-    if (SPLIT && w == 0 && P.vmax) *P.vmax = 0u;
   }
 }
 
-int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
-                 cudaStream_t st) {
+int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
   dim3 g((maxN + 3) / 4, n_points);
-  if (split)
-    k_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, (mask & 8) != 0);
-  else
-    k_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, (mask & 8) != 0);
+  k_sigma<<<g, 128, 0, st>>>(d_pts, d_io, (mask & 8) != 0);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -187,7 +182,7 @@ int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int ma
 // ------------------------------------ bubble weights + self-energy, fused ----
 // Everything that needs only the propagators, in one launch after k_bubble_gs:
 // every block stages G and S of its point in shared memory (FP64 divisions are
-// slow on this part, so they are done once per point), then computes either
+// slow on this part, so they are done once per frequency), then computes either
 // one row of a bubble-weight table (blocks [0, 2(2 maxN - 1))) or one
 // self-energy entry dSigma(w)/dl (blocks beyond), with 128 threads over the
 // loop index p and a fixed-order block reduction.

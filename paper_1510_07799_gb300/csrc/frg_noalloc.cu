@@ -138,6 +138,6 @@ extern "C" int frg_rhs_noalloc(const frg_params *p, double Lambda, const void *d
   } else {
     if (launch_zero_vertex(d_pts, d_io, 1, N, st) != 0) return FRG_ECUDA;
   }
-  if (launch_sigma(d_pts, d_io, 1, N, 0, mask, st) != 0) return FRG_ECUDA;
+  if (launch_sigma(d_pts, d_io, 1, N, mask, st) != 0) return FRG_ECUDA;
   return cudaGetLastError() == cudaSuccess ? FRG_OK : FRG_ECUDA;
 }
