@@ -5,6 +5,8 @@ Each translation unit is compiled in parallel with nvcc for
 exporting the C ABI of include/frg.h.
 """
 import concurrent.futures as cf
+import contextlib
+import fcntl
 import glob
 import os
 import shutil
@@ -40,10 +42,29 @@ def up_to_date():
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+@contextlib.contextmanager
+def _build_lock():
+    """One build at a time per build directory (several processes -- ranks of a
+    multi-GPU run, parallel test workers -- may ask for the library at once)."""
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, ".lock"), "w") as f:
+        fcntl.flock(f, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(f, fcntl.LOCK_UN)
+
+
 def build(force=False, verbose=False, extra=()):
     if not force and up_to_date():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
+    with _build_lock():
+        if not force and up_to_date():  # built by another process meanwhile
+            return LIB
+        return _build(verbose, extra)
+
+
+def _build(verbose, extra):
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     nv = nvcc()
 
