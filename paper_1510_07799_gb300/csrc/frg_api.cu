@@ -410,6 +410,13 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
           !(P.kord = dalloc<unsigned char>(ctx, (size_t)2 * (2 * N - 1) * 16)))
         return bail(FRG_ENOMEM);
       if (cudaMemset(P.vmax, 0, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ECUDA);
+      // the operand maps also read rows past the valid part of each line (their
+      // products are zero through the bubble weights): keep every such element
+      // finite, the slack included
+      if (cudaMemset(P.Y32, 0, (n3 + OPERAND_SLACK) * sizeof(float2)) != cudaSuccess ||
+          cudaMemset(P.Y32W, 0, (2 * n3 + OPERAND_SLACK) * sizeof(float2)) != cudaSuccess ||
+          cudaMemset(P.Y32X, 0, (2 * n3 + OPERAND_SLACK) * sizeof(float2)) != cudaSuccess)
+        return bail(FRG_ECUDA);
       for (int j = 0; j < 7; ++j)
         if (!(P.kG[j] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
     }
@@ -564,7 +571,8 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
     if (!(u.s64 = dalloc<double2>(ctx, P.N)) || !(u.kout = dalloc<float2>(ctx, P.n3)))
       return fail(ctx, FRG_ENOMEM, "stand-alone rhs scratch");
   }
-  LK(launch_split_input(P.Y32, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, P.vmax, ctx->stream),
+  LK(launch_split_input(P.Y32, u.s64, static_cast<const double2 *>(d_gamma), o.sig, P.n3, P.N, (float)P.U, P.vmax,
+                        ctx->stream),
      "split input");
   RhsIO s = o;
   s.gam = P.Y32;

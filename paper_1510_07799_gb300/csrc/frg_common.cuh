@@ -136,6 +136,18 @@ __host__ __device__ __forceinline__ Geom geom(int ch, int N, int m) {
 
 __device__ __forceinline__ bool inbox(int N, int i) { return (unsigned)i < (unsigned)N; }
 
+// Whether the fourth frequency i1 + i2 - i3 of flat vertex index i is in the
+// box.  Where it is not, the box rule makes the vertex the bare U: the FP32
+// operand copies of the split paths store U there, so that the contraction
+// reads the box rule's value directly.
+__device__ __forceinline__ bool fourth_in_box(int i, int N) {
+  const unsigned q = (unsigned)i / (unsigned)N;
+  const int i3 = i - (int)q * N;
+  const int i1 = (int)(q / (unsigned)N);
+  const int i2 = (int)q - i1 * N;
+  return inbox(N, i1 + i2 - i3);
+}
+
 // Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).
 struct StageArgs {
   int stage;  // 0..6

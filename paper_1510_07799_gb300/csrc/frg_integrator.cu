@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
     if (SPLIT) {
       if (i < n3) {
         const float2 f = round_c64(Y);
-        P.Y32[i] = f;
+        P.Y32[i] = fourth_in_box(i, P.N) ? f : make_float2((float)P.U, 0.f);
         vm = fmaxf(vm, fmaxf(fabsf(f.x), fabsf(f.y)));
       } else {
         P.Y64[i - n3] = Y;
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict
           out = hi;
         }
       }
-      P.Y32[i] = out;
       vm = fmaxf(vm, fmaxf(fabsf(out.x), fabsf(out.y)));
+      P.Y32[i] = fourth_in_box(i, P.N) ? out : make_float2((float)P.U, 0.f);
     } else {
       double2 acc = make_double2(0.0, 0.0);
 #pragma unroll

@@ -49,12 +49,12 @@ int launch_zero_vertex(const PointDesc *d_pts, const RhsIO *d_io, int n, int max
 }
 
 __global__ void k_split_input(float2 *ys, double2 *s64, const double2 *g, const double2 *sig, int n3, int N,
-                              unsigned *vmax) {
+                              float U, unsigned *vmax) {
   float vm = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3 + N; i += gridDim.x * blockDim.x) {
     if (i < n3) {
       const float2 f = round_c64(g[i]);
-      ys[i] = f;
+      ys[i] = fourth_in_box(i, N) ? f : make_float2(U, 0.f);
       vm = fmaxf(vm, fmaxf(fabsf(f.x), fabsf(f.y)));
     } else {
       s64[i - n3] = sig ? sig[i - n3] : make_double2(0.0, 0.0);
@@ -68,9 +68,9 @@ __global__ void k_split_input(float2 *ys, double2 *s64, const double2 *g, const 
 }
 
 int launch_split_input(float2 *ysplit, double2 *s64, const double2 *gam, const double2 *sig, int n3, int N,
-                       unsigned *vmax, cudaStream_t st) {
+                       float U, unsigned *vmax, cudaStream_t st) {
   const int blocks = (n3 + N + 255) / 256 < 4096 ? (n3 + N + 255) / 256 : 4096;
-  k_split_input<<<blocks, 256, 0, st>>>(ysplit, s64, gam, sig, n3, N, vmax);
+  k_split_input<<<blocks, 256, 0, st>>>(ysplit, s64, gam, sig, n3, N, U, vmax);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

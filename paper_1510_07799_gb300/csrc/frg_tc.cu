@@ -658,8 +658,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // order of their largest bubble weight.
 // Roles: warps 0-3 epilogue (TMEM -> shuffles -> staged, coalesced stores),
 // warp 4 MMA issue, warp 5 loader (tensor-map TMA of the raw operand rows,
-// NRAW k-steps ahead), warps 6-17 transform (raw -> bubble-weighted, bare-U
-// filled, split, 64-byte-swizzled K-major operand tiles in NOP stages).  Every
+// NRAW k-steps ahead), warps 6-17 transform (raw -> bubble-weighted, split,
+// 64-byte-swizzled K-major operand tiles in NOP stages).  Every
 // wait is bounded: a wait that runs out sets the context error word and all
 // roles leave their loops.
 namespace st {
@@ -843,131 +843,127 @@ __device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__rest
 // column (right), split into hi / lo of the real and the imaginary parts.
 struct XfVals {
   float4 rh, rl, ih, il;
-  int row, g4;
+};
+// Where an item lives, fixed for all k-steps of a tile: its first raw element
+// and the byte offsets of the operand rows that take its real and imaginary
+// parts.  Complex row (or column) n occupies operand rows 2n and 2n + 1; the
+// real part takes row 2n + f, f = n & 1 for the left and (n >> 2) & 1 for the
+// right operand, so that each 16-byte store instruction of a warp covers all
+// eight bank groups of the 64-byte swizzle (rows 2n and 2n + 1 share a
+// 128-byte line).  The epilogue undoes the permutation.
+struct XfAt {
+  uint32_t re, im;
+  int src, l;
   bool valid;
 };
-// Left item t (row t / 4, k-group t % 4) of a 64 x 16 tile: Lb-weighted, and
-// for the direct channel 2A - C (first half of K) or -A (second half).
+__device__ __forceinline__ XfAt xf_left_at(int t) {
+  XfAt a;
+  const int r = t >> 2, g4 = t & 3, f = r & 1;
+  a.re = swz64(2 * r + f, g4);
+  a.im = swz64(2 * r + 1 - f, g4);
+  a.src = r * RA + 4 * g4;
+  a.l = 4 * g4;
+  a.valid = true;
+  return a;
+}
+__device__ __forceinline__ XfAt xf_right_at(int bt, int NT) {
+  XfAt a;
+  a.valid = bt < 4 * NT;
+  const int c = bt % NT, g4 = a.valid ? bt / NT : 0, f = (c >> 2) & 1;
+  a.re = swz64(2 * c + f, g4);
+  a.im = swz64(2 * c + 1 - f, g4);
+  a.src = 4 * g4 * NT + c;
+  a.l = 0;
+  return a;
+}
+__device__ __forceinline__ void split4(XfVals &o, const float re[4], const float im[4]) {
+  split_tf32(re[0], o.rh.x, o.rl.x);
+  split_tf32(re[1], o.rh.y, o.rl.y);
+  split_tf32(re[2], o.rh.z, o.rl.z);
+  split_tf32(re[3], o.rh.w, o.rl.w);
+  split_tf32(im[0], o.ih.x, o.il.x);
+  split_tf32(im[1], o.ih.y, o.il.y);
+  split_tf32(im[2], o.ih.z, o.il.z);
+  split_tf32(im[3], o.ih.w, o.il.w);
+}
+// Left item: Lb-weighted, and for the direct channel 2A - C (first half of K)
+// or -A (second half).  No masks: past the valid k of a transfer the bubble
+// weight is zero (the table holds zeros outside the box and the map's fill
+// beyond its rows), and rows past the transfer's valid rows are never stored.
 template <int CH>
-__device__ __forceinline__ void xf_left(XfVals &o, const float2 *rA, const float2 *rC, const float2 *rL, int t,
-                                        int off, const Step &q) {
-  const int r = t >> 2, g4 = t & 3;
+__device__ __forceinline__ void xf_left(XfVals &o, const float2 *rA, const float2 *rC, const float2 *rL,
+                                        const XfAt &a, int off, int half) {
   float2 v[4], c[4], L[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
-    const int kk = 4 * g4 + x;
-    v[x] = rA[r * RA + off + kk];
-    L[x] = rL[off + kk];
-    if (CH == CH_DPH) c[x] = rC[r * RA + off + kk];
+    v[x] = rA[a.src + off + x];
+    L[x] = rL[a.l + off + x];
+    if (CH == CH_DPH) c[x] = rC[a.src + off + x];
   }
   float re[4], im[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
-    const int kk = 4 * g4 + x;
     float2 u = v[x];
-    if (CH == CH_DPH) u = q.half ? make_float2(-u.x, -u.y) : make_float2(2.f * u.x - c[x].x, 2.f * u.y - c[x].y);
-    float2 a = cmulf(u, L[x]);
-    if (!(r < q.nA && kk < q.nK)) a = make_float2(0.f, 0.f);
-    re[x] = a.x;
-    im[x] = a.y;
+    if (CH == CH_DPH) u = half ? make_float2(-u.x, -u.y) : make_float2(2.f * u.x - c[x].x, 2.f * u.y - c[x].y);
+    const float2 w = cmulf(u, L[x]);
+    re[x] = w.x;
+    im[x] = w.y;
   }
-  split_tf32(re[0], o.rh.x, o.rl.x);
-  split_tf32(re[1], o.rh.y, o.rl.y);
-  split_tf32(re[2], o.rh.z, o.rl.z);
-  split_tf32(re[3], o.rh.w, o.rl.w);
-  split_tf32(im[0], o.ih.x, o.il.x);
-  split_tf32(im[1], o.ih.y, o.il.y);
-  split_tf32(im[2], o.ih.z, o.il.z);
-  split_tf32(im[3], o.ih.w, o.il.w);
-  o.row = r;
-  o.g4 = g4;
-  o.valid = true;
+  split4(o, re, im);
 }
-// Right item bt (column bt % NT, k-group bt / NT): columns whose fourth
-// frequency leaves the box take the bare U.
-template <int CH>
-__device__ __forceinline__ void xf_right(XfVals &o, const float2 *rB, int bt, const TileInfo &ti, const Step &q,
-                                         float U) {
-  o.valid = bt < 4 * ti.NT;
-  const int c = bt % ti.NT, g4 = o.valid ? bt / ti.NT : 0;
-  const int cc = ti.c0 + c;
-  const int f = CH == CH_PP ? ti.g.x - cc : (CH == CH_DPH ? cc - ti.g.x : cc + ti.g.x);
-  const bool cv = c < q.ncols, ok = (unsigned)f < (unsigned)ti.N;
-  float2 b[4];
-#pragma unroll
-  for (int x = 0; x < 4; ++x) b[x] = rB[(4 * g4 + x) * ti.NT + c];
+// Right item: the raw rows as they are.  The FP32 operand copies hold the bare
+// U wherever the fourth frequency leaves the box; rows past the valid k meet
+// zero left weights and columns past the grid are never stored.
+__device__ __forceinline__ void xf_right(XfVals &o, const float2 *rB, const XfAt &a, int NT) {
   float re[4], im[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
-    const int kk = 4 * g4 + x;
-    float2 u = ok ? b[x] : make_float2(U, 0.f);
-    if (!(cv && kk < q.nK)) u = make_float2(0.f, 0.f);
-    re[x] = u.x;
-    im[x] = u.y;
+    const float2 b = rB[a.src + x * NT];
+    re[x] = b.x;
+    im[x] = b.y;
   }
-  split_tf32(re[0], o.rh.x, o.rl.x);
-  split_tf32(re[1], o.rh.y, o.rl.y);
-  split_tf32(re[2], o.rh.z, o.rl.z);
-  split_tf32(re[3], o.rh.w, o.rl.w);
-  split_tf32(im[0], o.ih.x, o.il.x);
-  split_tf32(im[1], o.ih.y, o.il.y);
-  split_tf32(im[2], o.ih.z, o.il.z);
-  split_tf32(im[3], o.ih.w, o.il.w);
-  o.row = c;
-  o.g4 = g4;
+  split4(o, re, im);
 }
-// Operand rows 2n (real part) and 2n + 1 (imaginary part) of the hi and lo
-// slices.  Lanes with flip = 1 write the imaginary row first, so that each
-// 16-byte store instruction of a warp covers all eight bank groups of the
-// 64-byte swizzle (rows 2n and 2n + 1 share a 128-byte line).
-__device__ __forceinline__ void xf_store(uint8_t *T, int slice, const XfVals &v, int n, int g4, int flip) {
-  const int r0 = 2 * n + flip, r1 = 2 * n + 1 - flip;
-  *reinterpret_cast<float4 *>(T + swz64(r0, g4)) = flip ? v.ih : v.rh;
-  *reinterpret_cast<float4 *>(T + swz64(r1, g4)) = flip ? v.rh : v.ih;
-  *reinterpret_cast<float4 *>(T + slice + swz64(r0, g4)) = flip ? v.il : v.rl;
-  *reinterpret_cast<float4 *>(T + slice + swz64(r1, g4)) = flip ? v.rl : v.il;
+__device__ __forceinline__ void xf_store(uint8_t *T, int slice, const XfVals &v, const XfAt &a) {
+  *reinterpret_cast<float4 *>(T + a.re) = v.rh;
+  *reinterpret_cast<float4 *>(T + a.im) = v.ih;
+  *reinterpret_cast<float4 *>(T + slice + a.re) = v.rl;
+  *reinterpret_cast<float4 *>(T + slice + a.im) = v.il;
 }
 
-// Transform warps: raw rows -> bubble-weighted (left), bare-U filled (right),
-// split hi/lo, swizzled K-major operand tiles.
+// Transform warps: raw rows -> bubble-weighted (left), split hi/lo, swizzled
+// K-major operand tiles.
 template <int CH>
 __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                         const RhsIO *__restrict__ io, const StWork &w,
                                         const int *__restrict__ nt_of, uint32_t &it, int xt, int lane) {
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  const PointDesc &P = pts[ti.point];
-  const float U = (float)P.U;
-  const uint4 ord = korder_row<CH>(P, ti.N, w.m);
+  const uint4 ord = korder_row<CH>(pts[ti.point], ti.N, w.m);
+  // warps 0-7: left item xt and right item xt; warps 8-11: right items xt and xt + 128
+  const bool lr = xt < 256;
+  const XfAt a0 = lr ? xf_left_at(xt) : xf_right_at(xt, ti.NT);
+  const XfAt a1 = xf_right_at(lr ? xt : xt + 128, ti.NT);
   for (int ki = 0; ki < ti.nk; ++ki, ++it) {
     const int j = it % NRAW, s = it % NOP;
     if (!wwait(&S.raw_full[j], (it / NRAW) & 1u, S.err, S.abort_flag)) return false;
     if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
-    uint8_t *raws = S.raws, *ops = S.ops;
     const Step q = step_of<CH>(ti, kstep_at<CH>(ord, ti, ki));
     const int off = q.p0 - q.a0;
-    const uint8_t *raw = raws + j * RAW_STAGE;
+    const uint8_t *raw = S.raws + j * RAW_STAGE;
     const float2 *rA = reinterpret_cast<const float2 *>(raw);
     const float2 *rC = reinterpret_cast<const float2 *>(raw + RAW_A);
     const float2 *rB = reinterpret_cast<const float2 *>(raw + 2 * RAW_A);
     const float2 *rL = reinterpret_cast<const float2 *>(raw + 2 * RAW_A + RAW_B);
-    uint8_t *A = ops + s * OP_STAGE;
+    uint8_t *A = S.ops + s * OP_STAGE;
     uint8_t *B = A + 2 * A_SLICE;
-    if (xt < 256) {
-      // warps 0-7: left item xt and right item xt, two independent chains
-      XfVals va, vb;
-      xf_left<CH>(va, rA, rC, rL, xt, off, q);
-      xf_right<CH>(vb, rB, xt, ti, q, U);
-      xf_store(A, A_SLICE, va, xt >> 2, xt & 3, (xt >> 2) & 1);
-      if (vb.valid) xf_store(B, B_SLICE, vb, vb.row, vb.g4, (vb.row >> 2) & 1);
-    } else {
-      // warps 8-11: right items xt and xt + 128
-      XfVals va, vb;
-      xf_right<CH>(va, rB, xt, ti, q, U);
-      xf_right<CH>(vb, rB, xt + 128, ti, q, U);
-      if (va.valid) xf_store(B, B_SLICE, va, va.row, va.g4, (va.row >> 2) & 1);
-      if (vb.valid) xf_store(B, B_SLICE, vb, vb.row, vb.g4, (vb.row >> 2) & 1);
-    }
+    XfVals va, vb;
+    if (lr) xf_left<CH>(va, rA, rC, rL, a0, off, q.half);
+    else xf_right(va, rB, a0, ti.NT);
+    xf_right(vb, rB, a1, ti.NT);
+    if (lr) xf_store(A, A_SLICE, va, a0);
+    else if (a0.valid) xf_store(B, B_SLICE, va, a0);
+    if (a1.valid) xf_store(B, B_SLICE, vb, a1);
     // one arrival per warp: the generic-proxy writes are fenced for the
     // tensor cores by every writer, then the warp converges
     fence_async_smem();
@@ -1051,8 +1047,8 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
   return true;
 }
 
-// Epilogue (warps 0-3): TMEM lane 2r holds (Re a . Re b, Re a . Im b), lane
-// 2r+1 (Im a . Re b, Im a . Im b) of complex row r: the lane pair combines them
+// Epilogue (warps 0-3): TMEM lanes 2r and 2r+1 hold (Re a . Re b, Re a . Im b)
+// and (Im a . Re b, Im a . Im b) of complex row r: the lane pair combines them
 // by shuffles, the warp stages its 16 rows x 16 complex of each column chunk in
 // shared memory and stores them as whole 128-byte row segments.
 template <int CH>
@@ -1067,7 +1063,9 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   else ++tb.f0;
   tc_after();
   const int L = warp * 32 + lane;
-  const int r = L >> 1, odd = L & 1;
+  // TMEM lane L holds operand row L: complex row r = L / 2, its real part in
+  // lane 2r + (r & 1) (the transform's bank-group order)
+  const int r = L >> 1, odd = L & 1, isim = odd ^ (r & 1);
   float2 *stg = S.epi_stg + warp * (16 * EPI_PITCH);
   const uint32_t tmem = S.tmem;
   uint64_t *tempty = S.tempty;
@@ -1098,12 +1096,16 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
     float2 out[8];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const float pr = __shfl_xor_sync(0xffffffffu, v[2 * c], 1);      // partner's x.Re b
-      const float pi = __shfl_xor_sync(0xffffffffu, v[2 * c + 1], 1);  // partner's x.Im b
-      // even lane: own (ArBr, ArBi), partner (AiBr, AiBi)
-      // odd lane:  own (AiBr, AiBi), partner (ArBr, ArBi)
-      const float re = odd ? pr - v[2 * c + 1] : v[2 * c] - pi;
-      const float im = odd ? pi + v[2 * c] : v[2 * c + 1] + pr;
+      // TMEM column 2c + fb holds x.Re b of complex column c (the chunk starts
+      // at a multiple of 16 complex columns, so fb is known here)
+      const int fb = (c >> 2) & 1;
+      const float xr = v[2 * c + fb], xi = v[2 * c + 1 - fb];
+      const float pr = __shfl_xor_sync(0xffffffffu, xr, 1);  // partner's x.Re b
+      const float pi = __shfl_xor_sync(0xffffffffu, xi, 1);  // partner's x.Im b
+      // real-part lane: own (ArBr, ArBi), partner (AiBr, AiBi)
+      // imaginary-part lane: own (AiBr, AiBi), partner (ArBr, ArBi)
+      const float re = isim ? pr - xi : xr - pi;
+      const float im = isim ? pi + xr : xi + pr;
       if ((c >> 3) == odd) out[c & 7] = make_float2(re * sc, im * sc);
     }
     __syncwarp();  // the previous chunk's reads of the staging rows are done
