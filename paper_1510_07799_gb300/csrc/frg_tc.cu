@@ -670,33 +670,36 @@ __device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t parity, unsigned *
   return __all_sync(0xffffffffu, ok);
 }
 constexpr int KS = 16;                                  // complex k per step
-constexpr int ROWB = 64;                                // bytes per operand row: 16 tf32
-constexpr int A_SLICE = 128 * ROWB;                     // 8 KB
-constexpr int B_SLICE = 2 * NT_MAX * ROWB;              // 16 KB
-constexpr int OP_STAGE = 2 * (A_SLICE + B_SLICE);       // 48 KB
-constexpr int NOP = 3;
+constexpr int ROWB = 128;                               // bytes per operand row: 32 tf32 (K' = 2 KS)
+constexpr int A_SLICE = 128 * ROWB;                     // 16 KB
+constexpr int B_SLICE = NT_MAX * ROWB;                  // 16 KB
+constexpr int OP_STAGE = 2 * (A_SLICE + B_SLICE);       // 64 KB
+constexpr int NOP = 2;
 constexpr int RA = 18;                                  // complex per raw left row (aligned window)
 constexpr int RAW_A = MROWS * RA * 8;                   // 9216 B
 constexpr int RAW_B = KS * NT_MAX * 8;                  // 16 KB
 constexpr int RAW_L = 256;
 constexpr int RAW_STAGE = 2 * RAW_A + RAW_B + RAW_L;    // A, C (direct channel), B, bubble weights
 constexpr int NRAW = 2;
-constexpr int EPI_PITCH = 18;                           // complex per staged output row (16 + 2 pad)
-constexpr int EPI_STG = 16 * EPI_PITCH * 8;             // per epilogue warp: 16 rows x 16 complex
+constexpr int EPI_PITCH = 36;                           // floats per staged output row (32 + 4 pad)
+constexpr int EPI_PLANE = 16 * EPI_PITCH;               // floats: 16 rows of one component
+constexpr int EPI_STG = 2 * EPI_PLANE * 4;              // bytes per epilogue warp: Re and Im planes
 constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 4 * EPI_STG + 512;
 constexpr int EPI_W = 4, MMA_W = 4, LOAD_W = 5, XF_W0 = 6, N_XF = 12;
 constexpr int THREADS = 32 * (XF_W0 + N_XF);
 static_assert(SMEM <= 232448, "shared memory budget");
 
-__device__ __forceinline__ uint32_t swz64(int row, int ch) {
-  return (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4));
+// 128-byte swizzle: 16-byte chunk ch of row r sits at chunk ch ^ (r % 8);
+// 8-row atoms of 1024 B.
+__device__ __forceinline__ uint32_t swz128(int row, int ch) {
+  return (uint32_t)(row * 128 + ((ch ^ (row & 7)) << 4));
 }
-__device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
+__device__ __forceinline__ uint64_t sdesc128(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)(1024u >> 4) << 32;
   d |= 1ull << 46;
-  d |= 4ull << 61;
+  d |= 2ull << 61;
   return d;
 }
 __device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -779,7 +782,7 @@ struct StWork {
 // Shared pipeline state of one CTA.
 struct Pipe {
   uint8_t *ops, *raws;
-  float2 *epi_stg;
+  float *epi_stg;
   uint64_t *raw_full, *raw_empty, *op_full, *op_empty, *tfull, *tempty;
   volatile int *abort_flag;
   unsigned *err;
@@ -844,23 +847,29 @@ __device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__rest
 struct XfVals {
   float4 rh, rl, ih, il;
 };
+// Real form of the complex product (one operand row = K' = 32 values: the 16
+// k of the step for the real part, then the same 16 k for the imaginary part):
+//   left row "Re" of complex row r = [Re a | -Im a], row "Im" = [Im a | Re a],
+//   right row c = [Re b | Im b],
+// so that the accumulator rows hold Re(a b) and Im(a b) directly.  Operand row
+// of complex row r: 32 (r / 16) + (r % 16) for Re and 16 more for Im, so that
+// every 32-lane TMEM quarter (one epilogue warp) holds both parts of 16 rows.
 // Where an item lives, fixed for all k-steps of a tile: its first raw element
-// and the byte offsets of the operand rows that take its real and imaginary
-// parts.  Complex row (or column) n occupies operand rows 2n and 2n + 1; the
-// real part takes row 2n + f, f = n & 1 for the left and (n >> 2) & 1 for the
-// right operand, so that each 16-byte store instruction of a warp covers all
-// eight bank groups of the 64-byte swizzle (rows 2n and 2n + 1 share a
-// 128-byte line).  The epilogue undoes the permutation.
+// and the byte offsets of its 16-byte chunks in the k-group g4 (real half) and
+// 4 + g4 (imaginary half); lanes take consecutive rows of one k-group, so each
+// store instruction of a warp covers all eight bank groups of the swizzle.
 struct XfAt {
-  uint32_t re, im;
+  uint32_t lo_half, hi_half;
   int src, l;
   bool valid;
 };
+constexpr uint32_t IM_ROWS = 16 * ROWB;  // Im row of a complex row: 16 operand rows further
 __device__ __forceinline__ XfAt xf_left_at(int t) {
   XfAt a;
-  const int r = t >> 2, g4 = t & 3, f = r & 1;
-  a.re = swz64(2 * r + f, g4);
-  a.im = swz64(2 * r + 1 - f, g4);
+  const int r = t & 63, g4 = t >> 6;
+  const int row = 32 * (r >> 4) + (r & 15);
+  a.lo_half = swz128(row, g4);
+  a.hi_half = swz128(row, 4 + g4);
   a.src = r * RA + 4 * g4;
   a.l = 4 * g4;
   a.valid = true;
@@ -869,9 +878,9 @@ __device__ __forceinline__ XfAt xf_left_at(int t) {
 __device__ __forceinline__ XfAt xf_right_at(int bt, int NT) {
   XfAt a;
   a.valid = bt < 4 * NT;
-  const int c = bt % NT, g4 = a.valid ? bt / NT : 0, f = (c >> 2) & 1;
-  a.re = swz64(2 * c + f, g4);
-  a.im = swz64(2 * c + 1 - f, g4);
+  const int c = bt % NT, g4 = a.valid ? bt / NT : 0;
+  a.lo_half = swz128(c, g4);
+  a.hi_half = swz128(c, 4 + g4);
   a.src = 4 * g4 * NT + c;
   a.l = 0;
   return a;
@@ -886,6 +895,7 @@ __device__ __forceinline__ void split4(XfVals &o, const float re[4], const float
   split_tf32(im[2], o.ih.z, o.il.z);
   split_tf32(im[3], o.ih.w, o.il.w);
 }
+__device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 // Left item: Lb-weighted, and for the direct channel 2A - C (first half of K)
 // or -A (second half).  No masks: past the valid k of a transfer the bubble
 // weight is zero (the table holds zeros outside the box and the map's fill
@@ -924,11 +934,22 @@ __device__ __forceinline__ void xf_right(XfVals &o, const float2 *rB, const XfAt
   }
   split4(o, re, im);
 }
-__device__ __forceinline__ void xf_store(uint8_t *T, int slice, const XfVals &v, const XfAt &a) {
-  *reinterpret_cast<float4 *>(T + a.re) = v.rh;
-  *reinterpret_cast<float4 *>(T + a.im) = v.ih;
-  *reinterpret_cast<float4 *>(T + slice + a.re) = v.rl;
-  *reinterpret_cast<float4 *>(T + slice + a.im) = v.il;
+// hi slice at T, lo slice at T + slice
+__device__ __forceinline__ void xf_store_left(uint8_t *T, int slice, const XfVals &v, const XfAt &a) {
+  *reinterpret_cast<float4 *>(T + a.lo_half) = v.rh;
+  *reinterpret_cast<float4 *>(T + a.hi_half) = neg4(v.ih);
+  *reinterpret_cast<float4 *>(T + IM_ROWS + a.lo_half) = v.ih;
+  *reinterpret_cast<float4 *>(T + IM_ROWS + a.hi_half) = v.rh;
+  *reinterpret_cast<float4 *>(T + slice + a.lo_half) = v.rl;
+  *reinterpret_cast<float4 *>(T + slice + a.hi_half) = neg4(v.il);
+  *reinterpret_cast<float4 *>(T + slice + IM_ROWS + a.lo_half) = v.il;
+  *reinterpret_cast<float4 *>(T + slice + IM_ROWS + a.hi_half) = v.rl;
+}
+__device__ __forceinline__ void xf_store_right(uint8_t *T, int slice, const XfVals &v, const XfAt &a) {
+  *reinterpret_cast<float4 *>(T + a.lo_half) = v.rh;
+  *reinterpret_cast<float4 *>(T + a.hi_half) = v.ih;
+  *reinterpret_cast<float4 *>(T + slice + a.lo_half) = v.rl;
+  *reinterpret_cast<float4 *>(T + slice + a.hi_half) = v.il;
 }
 
 // Transform warps: raw rows -> bubble-weighted (left), split hi/lo, swizzled
@@ -961,9 +982,9 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     if (lr) xf_left<CH>(va, rA, rC, rL, a0, off, q.half);
     else xf_right(va, rB, a0, ti.NT);
     xf_right(vb, rB, a1, ti.NT);
-    if (lr) xf_store(A, A_SLICE, va, a0);
-    else if (a0.valid) xf_store(B, B_SLICE, va, a0);
-    if (a1.valid) xf_store(B, B_SLICE, vb, a1);
+    if (lr) xf_store_left(A, A_SLICE, va, a0);
+    else if (a0.valid) xf_store_right(B, B_SLICE, va, a0);
+    if (a1.valid) xf_store_right(B, B_SLICE, vb, a1);
     // one arrival per warp: the generic-proxy writes are fenced for the
     // tensor cores by every writer, then the warp converges
     fence_async_smem();
@@ -976,28 +997,26 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
   return true;
 }
 
-// TMEM use of consecutive tiles.  A tile's two accumulators take 2 x 2NT
-// columns: tiles with NT <= 64 alternate between the halves [0, 256) and
-// [256, 512) (the next tile's products overlap the previous tile's epilogue), a
-// wider tile takes all 512 columns.  The MMA warp and the epilogue walk the
-// same tile list and keep identical counts of the uses of each barrier.
+// TMEM use of consecutive tiles: a tile's two accumulators take NT <= 128
+// columns each; consecutive tiles alternate between the halves [0, 256) and
+// [256, 512), so that a tile's products overlap the previous tile's epilogue.
+// The MMA warp and the epilogue walk the same tile list and keep identical
+// counts of the uses of each barrier.
 struct TBuf {
   uint32_t e0 = 0u, e1 = 0u;  // completed uses of tempty[0], tempty[1]
   uint32_t f0 = 0u, f1 = 0u;  // completed uses of tfull[0], tfull[1]
   int flip = 0;
 };
 struct TSlot {
-  bool wide;
-  int b;               // 0 / 1: half of TMEM; wide tiles: 0 (barriers) and both halves
+  int b;               // half of TMEM
   uint32_t dcol, xcol; // columns of the hi*hi and the cross accumulator
 };
-__device__ __forceinline__ TSlot tslot_next(TBuf &t, int NT) {
+__device__ __forceinline__ TSlot tslot_next(TBuf &t) {
   TSlot s;
-  s.wide = 2 * NT > 128;
-  s.b = s.wide ? 0 : t.flip;
-  if (!s.wide) t.flip ^= 1;
-  s.dcol = s.wide ? 0u : 256u * s.b;
-  s.xcol = s.wide ? 256u : s.dcol + 128u;
+  s.b = t.flip;
+  t.flip ^= 1;
+  s.dcol = 256u * s.b;
+  s.xcol = s.dcol + 128u;
   return s;
 }
 
@@ -1010,18 +1029,13 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
                                          const int *__restrict__ nt_of, uint32_t &it, TBuf &tb, int lane) {
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  const TSlot ts = tslot_next(tb, ti.NT);
-  if (ts.wide || ts.b == 0) {
-    if (!wwait(&S.tempty[0], (tb.e0 & 1u) ^ 1u, S.err, S.abort_flag)) return false;
-    ++tb.e0;
-  }
-  if (ts.wide || ts.b == 1) {
-    if (!wwait(&S.tempty[1], (tb.e1 & 1u) ^ 1u, S.err, S.abort_flag)) return false;
-    ++tb.e1;
-  }
+  const TSlot ts = tslot_next(tb);
+  uint32_t &e = ts.b ? tb.e1 : tb.e0;
+  if (!wwait(&S.tempty[ts.b], (e & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+  ++e;
   tc_after();
   const uint32_t d = S.tmem + ts.dcol, dx = S.tmem + ts.xcol;
-  const uint32_t id = idesc<FRG_3XTF32>(2 * ti.NT);
+  const uint32_t id = idesc<FRG_3XTF32>(ti.NT);
   for (int kb = 0; kb < ti.nk; ++kb, ++it) {
     const int s = it % NOP;
     if (!wwait(&S.op_full[s], (it / NOP) & 1u, S.err, S.abort_flag)) return false;
@@ -1029,12 +1043,12 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
     if (lane == 0) {
       const uint32_t a0 = smem_u32(S.ops + s * OP_STAGE), b0 = a0 + 2 * A_SLICE;
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        const uint32_t o = kk * 32;
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t o = kk * 32;  // 8 tf32 of K' per instruction
         const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-        mma_tf32(d, sdesc64(a0 + o), sdesc64(b0 + o), id, first);                    // hi*hi
-        mma_tf32(dx, sdesc64(a0 + o), sdesc64(b0 + B_SLICE + o), id, first);         // hi*lo
-        mma_tf32(dx, sdesc64(a0 + A_SLICE + o), sdesc64(b0 + o), id, 1u);            // lo*hi
+        mma_tf32(d, sdesc128(a0 + o), sdesc128(b0 + o), id, first);                    // hi*hi
+        mma_tf32(dx, sdesc128(a0 + o), sdesc128(b0 + B_SLICE + o), id, first);         // hi*lo
+        mma_tf32(dx, sdesc128(a0 + A_SLICE + o), sdesc128(b0 + o), id, 1u);            // lo*hi
       }
       mma_commit(&S.op_empty[s]);
     }
@@ -1047,86 +1061,63 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
   return true;
 }
 
-// Epilogue (warps 0-3): TMEM lanes 2r and 2r+1 hold (Re a . Re b, Re a . Im b)
-// and (Im a . Re b, Im a . Im b) of complex row r: the lane pair combines them
-// by shuffles, the warp stages its 16 rows x 16 complex of each column chunk in
-// shared memory and stores them as whole 128-byte row segments.
+// Epilogue (warps 0-3): warp w reads TMEM lanes 32w..32w+31, lanes 0-15 the
+// real and lanes 16-31 the imaginary part of complex rows 16w..16w+15 (both
+// accumulators, added); the warp stages the two parts of each 32-column chunk
+// in shared memory and stores them interleaved as whole row segments.
 template <int CH>
 __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
                                          const int *__restrict__ nt_of, TBuf &tb, int warp, int lane) {
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  const TSlot ts = tslot_next(tb, ti.NT);
-  if (!wwait(&S.tfull[ts.b], (ts.b ? tb.f1 : tb.f0) & 1u, S.err, S.abort_flag)) return false;
-  if (ts.b) ++tb.f1;
-  else ++tb.f0;
+  const TSlot ts = tslot_next(tb);
+  uint32_t &f = ts.b ? tb.f1 : tb.f0;
+  if (!wwait(&S.tfull[ts.b], f & 1u, S.err, S.abort_flag)) return false;
+  ++f;
   tc_after();
-  const int L = warp * 32 + lane;
-  // TMEM lane L holds operand row L: complex row r = L / 2, its real part in
-  // lane 2r + (r & 1) (the transform's bank-group order)
-  const int r = L >> 1, odd = L & 1, isim = odd ^ (r & 1);
-  float2 *stg = S.epi_stg + warp * (16 * EPI_PITCH);
-  const uint32_t tmem = S.tmem;
-  uint64_t *tempty = S.tempty;
+  const int comp = lane >> 4, row16 = lane & 15;
+  float *plane = S.epi_stg + warp * (2 * EPI_PLANE);
   const PointDesc &P = pts[ti.point];
   const RhsIO &o = io[ti.point];
   const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
   float2 *kN = static_cast<float2 *>(o.dgam);
-  const int rr = ti.r0 + r;
+  const int rr = ti.r0 + 16 * warp + row16;
   float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int cb = 0; cb < 2 * ti.NT; cb += 32) {
+  const uint32_t tl = S.tmem + ((uint32_t)(warp * 32) << 16);
+  float *mine = plane + comp * EPI_PLANE + row16 * EPI_PITCH;
+  const int q = lane & 15;
+  for (int cb = 0; cb < ti.NT; cb += 32) {
     float v[32], vx[32];
     tmem_ld32(tl + ts.dcol + cb, v);
     tmem_ld32(tl + ts.xcol + cb, vx);
     tmem_wait_ld();
-    if (cb + 32 >= 2 * ti.NT) {
-      // all TMEM reads of this tile are done: let the next tile's MMAs start
+    if (cb + 32 >= ti.NT) {
+      // all TMEM reads of this tile are done: let the tile after next start
       tc_before();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&tempty[ts.b]);
-        if (ts.wide) mbar_arrive(&tempty[1]);
-      }
+      if (lane == 0) mbar_arrive(&S.tempty[ts.b]);
     }
+    __syncwarp();  // the previous chunk's reads of the staging planes are done
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += vx[i];
-    // even lane keeps columns 0..7 of the chunk, odd lane 8..15
-    float2 out[8];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      // TMEM column 2c + fb holds x.Re b of complex column c (the chunk starts
-      // at a multiple of 16 complex columns, so fb is known here)
-      const int fb = (c >> 2) & 1;
-      const float xr = v[2 * c + fb], xi = v[2 * c + 1 - fb];
-      const float pr = __shfl_xor_sync(0xffffffffu, xr, 1);  // partner's x.Re b
-      const float pi = __shfl_xor_sync(0xffffffffu, xi, 1);  // partner's x.Im b
-      // real-part lane: own (ArBr, ArBi), partner (AiBr, AiBi)
-      // imaginary-part lane: own (AiBr, AiBi), partner (ArBr, ArBi)
-      const float re = isim ? pr - xi : xr - pi;
-      const float im = isim ? pi + xr : xi + pr;
-      if ((c >> 3) == odd) out[c & 7] = make_float2(re * sc, im * sc);
-    }
-    __syncwarp();  // the previous chunk's reads of the staging rows are done
-    float4 *w4 = reinterpret_cast<float4 *>(stg + (lane >> 1) * EPI_PITCH + 8 * odd);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w4[j] = make_float4(out[2 * j].x, out[2 * j].y, out[2 * j + 1].x, out[2 * j + 1].y);
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<float4 *>(mine + 4 * j) =
+          make_float4((v[4 * j] + vx[4 * j]) * sc, (v[4 * j + 1] + vx[4 * j + 1]) * sc,
+                      (v[4 * j + 2] + vx[4 * j + 2]) * sc, (v[4 * j + 3] + vx[4 * j + 3]) * sc);
     __syncwarp();
-    const int q = lane & 7;
-    const int cl = cb / 2 + 2 * q;  // column (pair) within the tile
+    const int cl = cb + 2 * q;  // column (pair) within the tile
     const int cg = ti.c0 + cl;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int rho = (lane >> 3) + 4 * i;  // staged row 0..15
+    for (int i = 0; i < 8; ++i) {
+      const int rho = (lane >> 4) + 2 * i;  // staged row 0..15
       float2 *dst = reinterpret_cast<float2 *>(
-          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(orow), 2 * rho));
-      const float4 val = *reinterpret_cast<const float4 *>(stg + rho * EPI_PITCH + 2 * q);
-      if (dst && cg < ti.N && cl < ti.NT) *reinterpret_cast<float4 *>(dst + cg) = val;
+          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(orow), rho));
+      const float2 re = *reinterpret_cast<const float2 *>(plane + rho * EPI_PITCH + 2 * q);
+      const float2 im = *reinterpret_cast<const float2 *>(plane + EPI_PLANE + rho * EPI_PITCH + 2 * q);
+      if (dst && cg < ti.N && cl < ti.NT) *reinterpret_cast<float4 *>(dst + cg) = make_float4(re.x, im.x, re.y, im.y);
     }
   }
-  if (ts.wide || ts.b == 0) ++tb.e0;
-  if (ts.wide || ts.b == 1) ++tb.e1;
+  ++(ts.b ? tb.e1 : tb.e0);
   return true;
 }
 
@@ -1140,7 +1131,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   Pipe S;
   S.ops = smem;
   S.raws = S.ops + NOP * OP_STAGE;
-  S.epi_stg = reinterpret_cast<float2 *>(S.raws + NRAW * RAW_STAGE);
+  S.epi_stg = reinterpret_cast<float *>(S.raws + NRAW * RAW_STAGE);
   uint64_t *bars = reinterpret_cast<uint64_t *>(S.raws + NRAW * RAW_STAGE + 4 * EPI_STG);
   S.raw_full = bars;
   S.raw_empty = bars + NRAW;
