@@ -900,16 +900,31 @@ __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y
 // or -A (second half).  No masks: past the valid k of a transfer the bubble
 // weight is zero (the table holds zeros outside the box and the map's fill
 // beyond its rows), and rows past the transfer's valid rows are never stored.
+// Four consecutive complex values from shared memory, starting at element
+// base + off (base even, off = 0 or 1 uniform over the CTA): 16-byte loads.
+__device__ __forceinline__ void ld4c(const float2 *p, int base, int off, float2 v[4]) {
+  const float4 *q = reinterpret_cast<const float4 *>(p + base);
+  const float4 t0 = q[0], t1 = q[1];
+  if (off == 0) {
+    v[0] = make_float2(t0.x, t0.y);
+    v[1] = make_float2(t0.z, t0.w);
+    v[2] = make_float2(t1.x, t1.y);
+    v[3] = make_float2(t1.z, t1.w);
+  } else {
+    const float4 t2 = q[2];
+    v[0] = make_float2(t0.z, t0.w);
+    v[1] = make_float2(t1.x, t1.y);
+    v[2] = make_float2(t1.z, t1.w);
+    v[3] = make_float2(t2.x, t2.y);
+  }
+}
 template <int CH>
 __device__ __forceinline__ void xf_left(XfVals &o, const float2 *rA, const float2 *rC, const float2 *rL,
                                         const XfAt &a, int off, int half) {
   float2 v[4], c[4], L[4];
-#pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    v[x] = rA[a.src + off + x];
-    L[x] = rL[a.l + off + x];
-    if (CH == CH_DPH) c[x] = rC[a.src + off + x];
-  }
+  ld4c(rA, a.src, off, v);
+  ld4c(rL, a.l, off, L);
+  if (CH == CH_DPH) ld4c(rC, a.src, off, c);
   float re[4], im[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -968,7 +983,6 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
   for (int ki = 0; ki < ti.nk; ++ki, ++it) {
     const int j = it % NRAW, s = it % NOP;
     if (!wwait(&S.raw_full[j], (it / NRAW) & 1u, S.err, S.abort_flag)) return false;
-    if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
     const Step q = step_of<CH>(ti, kstep_at<CH>(ord, ti, ki));
     const int off = q.p0 - q.a0;
     const uint8_t *raw = S.raws + j * RAW_STAGE;
@@ -982,6 +996,11 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     if (lr) xf_left<CH>(va, rA, rC, rL, a0, off, q.half);
     else xf_right(va, rB, a0, ti.NT);
     xf_right(vb, rB, a1, ti.NT);
+    // the raw rows are in registers: hand the raw stage back to the loader
+    // before waiting for a free operand stage
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.raw_empty[j]);
+    if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
     if (lr) xf_store_left(A, A_SLICE, va, a0);
     else if (a0.valid) xf_store_right(B, B_SLICE, va, a0);
     if (a1.valid) xf_store_right(B, B_SLICE, vb, a1);
@@ -989,10 +1008,7 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     // tensor cores by every writer, then the warp converges
     fence_async_smem();
     __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&S.raw_empty[j]);
-      mbar_arrive(&S.op_full[s]);
-    }
+    if (lane == 0) mbar_arrive(&S.op_full[s]);
   }
   return true;
 }
