@@ -80,9 +80,11 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
 }
 
 // k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
-// (launched for every split-path rhs, also when only pp is enabled).
-__global__ void __launch_bounds__(256) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
-                                                 int mask) {
+// (launched for every split-path rhs, also when only pp is enabled).  Every
+// thread issues all 48 of its loads before the first shared-memory pass, so
+// that a block keeps 96 KB of reads in flight.
+__global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                                    int mask) {
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
@@ -91,45 +93,53 @@ __global__ void __launch_bounds__(256) k_combine(const PointDesc *__restrict__ p
   if (!t.ok) return;
   __shared__ float2 sm[TILE_SMEM];
   const int N = t.N;
+  float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
+  const float2 z = make_float2(0.f, 0.f);
+  float2 vx[16], vw[16], vk[16];
 #pragma unroll
-  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
-    const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
-    const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-    if (a < N && b < N && c < N)
-      sm[sidx(i1, i2, i3)] = (mask & 2) ? P.PX[((size_t)a * N + c) * N + b] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  if (mask & 4) {
-  #pragma unroll
-  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+  for (int u = 0; u < 16; ++u) {
+    const int n = threadIdx.x + 256 * u;
+    {
+      const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
+      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      vx[u] = ((mask & 2) && a < N && b < N && c < N) ? P.PX[((size_t)a * N + c) * N + b] : z;
+    }
+    {
       const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
       const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      if (a < N && b < N && c < N) {
-        const float2 w = P.PW[((size_t)b * N + c) * N + a];
-        float2 &v = sm[sidx(i1, i2, i3)];
-        v.x += w.x;
-        v.y += w.y;
-      }
+      vw[u] = ((mask & 4) && a < N && b < N && c < N) ? P.PW[((size_t)b * N + c) * N + a] : z;
     }
-    __syncthreads();
+    {
+      const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
+      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      vk[u] = ((mask & 1) && a < N && b < N && c < N) ? K[((size_t)a * N + b) * N + c] : z;
+    }
   }
-  float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int n = threadIdx.x + 256 * u;
+    sm[sidx(n >> 8, n & 15, (n >> 4) & 15)] = vx[u];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int n = threadIdx.x + 256 * u;
+    float2 &v = sm[sidx(n & 15, n >> 8, (n >> 4) & 15)];
+    v.x += vw[u].x;
+    v.y += vw[u].y;
+  }
+  __syncthreads();
   // the channel products of this rhs have consumed the vertex bound of the
   // stage input (BF16 slicing): reset it for the next stage
   if (blockIdx.x == 0 && threadIdx.x == 0 && P.vmax) *P.vmax = 0u;
 #pragma unroll
-  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
+  for (int u = 0; u < 16; ++u) {
+    const int n = threadIdx.x + 256 * u;
     const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
     const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
     if (a < N && b < N && c < N) {
-      const size_t at = ((size_t)a * N + b) * N + c;
-      float2 v = sm[sidx(i1, i2, i3)];
-      if (mask & 1) {
-        const float2 p = K[at];
-        v.x += p.x;
-        v.y += p.y;
-      }
-      K[at] = v;
+      const float2 v = sm[sidx(i1, i2, i3)];
+      K[((size_t)a * N + b) * N + c] = make_float2(v.x + vk[u].x, v.y + vk[u].y);
     }
   }
 }
