@@ -681,11 +681,13 @@ constexpr int RAW_B = KS * NT_MAX * 8;                  // 16 KB
 constexpr int RAW_L = 256;
 constexpr int RAW_STAGE = 2 * RAW_A + RAW_B + RAW_L;    // A, C (direct channel), B, bubble weights
 constexpr int NRAW = 2;
-constexpr int EPI_PITCH = 36;                           // floats per staged output row (32 + 4 pad)
+constexpr int EPI_COLS = 16;                            // columns per epilogue chunk
+constexpr int EPI_PITCH = EPI_COLS + 4;                 // floats per staged output row (16 + 4 pad)
 constexpr int EPI_PLANE = 16 * EPI_PITCH;               // floats: 16 rows of one component
 constexpr int EPI_STG = 2 * EPI_PLANE * 4;              // bytes per epilogue warp: Re and Im planes
-constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + 4 * EPI_STG + 512;
-constexpr int EPI_W = 4, MMA_W = 4, LOAD_W = 5, XF_W0 = 6, N_XF = 12;
+// warps 0-7 epilogue (two per TMEM lane quarter), 8 MMA, 9 loader, 10-21 transform
+constexpr int EPI_W = 8, MMA_W = 8, LOAD_W = 9, XF_W0 = 10, N_XF = 12;
+constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + EPI_W * EPI_STG + 512;
 constexpr int THREADS = 32 * (XF_W0 + N_XF);
 static_assert(SMEM <= 232448, "shared memory budget");
 
@@ -1077,10 +1079,23 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
   return true;
 }
 
-// Epilogue (warps 0-3): warp w reads TMEM lanes 32w..32w+31, lanes 0-15 the
-// real and lanes 16-31 the imaginary part of complex rows 16w..16w+15 (both
-// accumulators, added); the warp stages the two parts of each 32-column chunk
-// in shared memory and stores them interleaved as whole row segments.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue (warps 0-7): warps w and w + 4 read TMEM lanes 32w..32w+31 (lanes
+// 0-15 the real, lanes 16-31 the imaginary part of complex rows 16w..16w+15,
+// both accumulators added) and take alternate 16-column chunks of the tile;
+// a warp stages the two parts of a chunk in shared memory and stores them
+// interleaved as whole row segments.
 template <int CH>
 __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
@@ -1092,31 +1107,40 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   if (!wwait(&S.tfull[ts.b], f & 1u, S.err, S.abort_flag)) return false;
   ++f;
   tc_after();
+  const int quarter = warp & 3, half = warp >> 2;
   const int comp = lane >> 4, row16 = lane & 15;
   float *plane = S.epi_stg + warp * (2 * EPI_PLANE);
   const PointDesc &P = pts[ti.point];
   const RhsIO &o = io[ti.point];
   const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
   float2 *kN = static_cast<float2 *>(o.dgam);
-  const int rr = ti.r0 + 16 * warp + row16;
+  const int rr = ti.r0 + 16 * quarter + row16;
   float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
-  const uint32_t tl = S.tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tl = S.tmem + ((uint32_t)(quarter * 32) << 16);
   float *mine = plane + comp * EPI_PLANE + row16 * EPI_PITCH;
-  const int q = lane & 15;
-  for (int cb = 0; cb < ti.NT; cb += 32) {
-    float v[32], vx[32];
-    tmem_ld32(tl + ts.dcol + cb, v);
-    tmem_ld32(tl + ts.xcol + cb, vx);
+  const int q = lane & 7;
+  const int nch = ti.NT / EPI_COLS;
+  if (half >= nch) {
+    // no chunk for this warp: release the TMEM slot at once
+    tc_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.tempty[ts.b]);
+  }
+  for (int ci = half; ci < nch; ci += 2) {
+    const int cb = ci * EPI_COLS;
+    float v[16], vx[16];
+    tmem_ld16(tl + ts.dcol + cb, v);
+    tmem_ld16(tl + ts.xcol + cb, vx);
     tmem_wait_ld();
-    if (cb + 32 >= ti.NT) {
-      // all TMEM reads of this tile are done: let the tile after next start
+    if (ci + 2 >= nch) {
+      // all TMEM reads of this warp are done: let the tile after next start
       tc_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.tempty[ts.b]);
     }
     __syncwarp();  // the previous chunk's reads of the staging planes are done
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < 4; ++j)
       *reinterpret_cast<float4 *>(mine + 4 * j) =
           make_float4((v[4 * j] + vx[4 * j]) * sc, (v[4 * j + 1] + vx[4 * j + 1]) * sc,
                       (v[4 * j + 2] + vx[4 * j + 2]) * sc, (v[4 * j + 3] + vx[4 * j + 3]) * sc);
@@ -1124,8 +1148,8 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
     const int cl = cb + 2 * q;  // column (pair) within the tile
     const int cg = ti.c0 + cl;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int rho = (lane >> 4) + 2 * i;  // staged row 0..15
+    for (int i = 0; i < 4; ++i) {
+      const int rho = (lane >> 3) + 4 * i;  // staged row 0..15
       float2 *dst = reinterpret_cast<float2 *>(
           __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(orow), rho));
       const float2 re = *reinterpret_cast<const float2 *>(plane + rho * EPI_PITCH + 2 * q);
@@ -1148,7 +1172,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   S.ops = smem;
   S.raws = S.ops + NOP * OP_STAGE;
   S.epi_stg = reinterpret_cast<float *>(S.raws + NRAW * RAW_STAGE);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(S.raws + NRAW * RAW_STAGE + 4 * EPI_STG);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(S.raws + NRAW * RAW_STAGE + EPI_W * EPI_STG);
   S.raw_full = bars;
   S.raw_empty = bars + NRAW;
   S.op_full = bars + 2 * NRAW;
