@@ -79,8 +79,8 @@ def profiled_traffic(kind):
 def executed_tensor_flops(N, NT=128, mrows=64, ks=16):
     """Tensor-core flops the 3xTF32 kernel issues per rhs: per tile (64 complex
     rows x NT columns) and k-step of 16 complex k, 3 products of M = 128 real
-    rows x N = 2 NT x K = 16; ragged transfers padded to whole tiles and
-    k-steps (the direct channel has two K halves)."""
+    rows (real form of the left operand) x N = NT x K = 32; ragged transfers
+    padded to whole tiles and k-steps (the direct channel has two K halves)."""
     tot = 0
     for ch in range(3):
         for m in range(-(N - 1), N):
@@ -315,7 +315,7 @@ def run_ours(args):
                 "algorithmic": "8 flops x %d useful complex MACs per rhs (useful, not executed)" % macs,
                 "executed_tflops": executed_tensor_flops(N) / (ph[2] * 1e-3) / 1e12,
                 "executed_frac": executed_tensor_flops(N) / (ph[2] * 1e-3) / 1e12 / tf_peak,
-                "executed_note": "tensor-core flops issued (3 split products, real 2x2 form, whole tiles and "
+                "executed_note": "tensor-core flops issued (3 split products, real form of the complex product, whole tiles and "
                                  "k-steps), for comparison with the tensor pipe's own rate; not the roofline value"}
     roof["phases_ms"] = {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2], "combine": ph[3]}
 
