@@ -5,8 +5,8 @@ import this package.  It shares no code with the CUDA path.
 """
 from .oracle import (Model, rhs, rhs_rows, rhs_entries, flow, propagators,
                      observables, dp5_tableau, dp5_integrate, set_threads,
-                     max_threads)
+                     max_threads, MASK_TAILS, TAIL_FACTOR)
 
 __all__ = ["Model", "rhs", "rhs_rows", "rhs_entries", "flow", "propagators",
            "observables", "dp5_tableau", "dp5_integrate", "set_threads",
-           "max_threads"]
+           "max_threads", "MASK_TAILS", "TAIL_FACTOR"]

@@ -37,6 +37,14 @@
  * Every sum above is evaluated literally, entry by entry; there is no
  * transfer-major reordering and no matrix product.
  *
+ * Frequency-box tails (mask bit 4, an option beyond the paper): the internal
+ * sums above run over every p of a window of TAIL_FACTOR * N Matsubara indices
+ * centred on the box (both internal frequencies in the window) instead of the
+ * box; vertices keep the box rule (bare U as soon as an index leaves the box)
+ * and the propagators outside the box take Sigma = 0 (the flowing self-energy
+ * lives on the box only).  The window is a truncation of the infinite sum:
+ * the pp and xph bubble weights decay like 1/w^4 beyond it, S like 1/w^3.
+ *
  * The integrator is the Dormand-Prince 5(4) pair (explicit, 7 stages, first
  * same as last), the explicit stepper family the paper uses (Sec. 2; Sec. 4
  * counts seven rhs evaluations for the first step).  Its coefficients are the
@@ -64,6 +72,9 @@ typedef struct {
     int N;
 } oracle_model;
 
+#define TAIL_FACTOR 16   /* window of the internal sums with mask bit 4: 16 N indices */
+#define MASK_TAILS 16
+
 /* ---------------------------------------------------------------- model --- */
 
 static double w_of(const oracle_model *m, int i)
@@ -77,6 +88,17 @@ static cplx g0inv(const oracle_model *m, int i)
     double et = m->eps_d + 0.5 * m->U;
     double sg = (w > 0.0) ? 1.0 : -1.0;
     return I * w - et + I * m->Delta * sg;
+}
+
+/* G_L and S_L at frequency index i (any integer), self-energy sg. */
+static void propagator_at(const oracle_model *m, double L, int i, cplx sg, cplx *g_out, cplx *s_out)
+{
+    double w = w_of(m, i);
+    double thinv = 1.0 + (L * L) / (w * w);
+    cplx gi = g0inv(m, i);
+    cplx g = 1.0 / (thinv * gi - sg);
+    *g_out = g;
+    *s_out = -g * g * (2.0 * L / (w * w)) * gi;
 }
 
 /* G_L and S_L for every in-box frequency. sigma may be NULL (Sigma = 0). */
@@ -107,6 +129,9 @@ typedef struct {
     const oracle_model *m;
     const cplx *gamma;
     const cplx *G, *S;
+    /* tails: propagators on the window [lo, lo + W) of frequency indices */
+    int lo, W;
+    const cplx *Gw, *Sw;
 } vctx;
 
 static inline cplx Vget(const vctx *c, int i1, int i2, int i3)
@@ -125,6 +150,80 @@ static inline cplx Lb(const vctx *c, int a, int b)
 }
 
 static inline int inbox(int N, int i) { return i >= 0 && i < N; }
+
+static inline int inwin(const vctx *c, int i) { return i >= c->lo && i < c->lo + c->W; }
+
+/* bubble weight for window indices a, b */
+static inline cplx Lbw(const vctx *c, int a, int b)
+{
+    int x = a - c->lo, y = b - c->lo;
+    return c->Sw[x] * c->Gw[y] + c->Gw[x] * c->Sw[y];
+}
+
+/* The same channel sums with the internal loops over the window (tails). */
+static cplx rhs_entry_tails(const vctx *c, double L, int mask, int i1, int i2, int i3)
+{
+    const oracle_model *m = c->m;
+    int s = i1 + i2, t = i3 - i1, Q = i2 - i3, i4 = i1 + i2 - i3;
+    int lo = c->lo, hi = c->lo + c->W;
+    cplx pp = 0.0, dph = 0.0, xph = 0.0;
+    if (mask & 1) {
+        for (int p = lo; p < hi; ++p) {
+            int q = s - p;
+            if (!inwin(c, q)) continue;
+            pp += Vget(c, i1, i2, p) * Lbw(c, p, q) * Vget(c, p, q, i3);
+        }
+        pp *= -m->T;
+    }
+    if (mask & 2) {
+        for (int p = lo; p < hi; ++p) {
+            int r = p - t;
+            if (!inwin(c, r)) continue;
+            cplx a = Vget(c, i1, p, i3);
+            cplx term = 2.0 * a * Vget(c, r, i2, p)
+                      - Vget(c, i1, p, r) * Vget(c, r, i2, p)
+                      - a * Vget(c, r, i2, i4);
+            dph += Lbw(c, p, r) * term;
+        }
+        dph *= m->T;
+    }
+    if (mask & 4) {
+        for (int p = lo; p < hi; ++p) {
+            int r = p + Q;
+            if (!inwin(c, r)) continue;
+            xph += Vget(c, i1, r, p) * Lbw(c, p, r) * Vget(c, p, i2, i3);
+        }
+        xph *= -m->T;
+    }
+    return L * (pp + dph + xph);
+}
+
+static cplx rhs_sigma_tails(const vctx *c, double L, int i)
+{
+    cplx acc = 0.0;
+    for (int p = c->lo; p < c->lo + c->W; ++p)
+        acc += c->Sw[p - c->lo] * (2.0 * Vget(c, i, p, i) - Vget(c, i, p, p));
+    return L * c->m->T * acc;
+}
+
+/* Window propagators (tails): Sigma from the box, 0 outside. */
+static int window_setup(vctx *c, double L, const cplx *sigma, cplx **Gw, cplx **Sw)
+{
+    int N = c->m->N;
+    c->W = TAIL_FACTOR * N;
+    c->lo = -(c->W - N) / 2;
+    *Gw = malloc(sizeof(cplx) * c->W);
+    *Sw = malloc(sizeof(cplx) * c->W);
+    if (!*Gw || !*Sw) return -1;
+    for (int x = 0; x < c->W; ++x) {
+        int i = c->lo + x;
+        cplx sg = (sigma && inbox(N, i)) ? sigma[i] : 0.0;
+        propagator_at(c->m, L, i, sg, &(*Gw)[x], &(*Sw)[x]);
+    }
+    c->Gw = *Gw;
+    c->Sw = *Sw;
+    return 0;
+}
 
 /* d/dl of one vertex entry; mask bit0 pp, bit1 dph, bit2 xph */
 static cplx rhs_entry(const vctx *c, double L, int mask, int i1, int i2, int i3)
@@ -200,7 +299,13 @@ int oracle_rhs_rows(const oracle_model *m, double L, const double *gamma,
     cplx *G = malloc(sizeof(cplx) * N), *S = malloc(sizeof(cplx) * N);
     if (!G || !S) { free(G); free(S); return -1; }
     propagators(m, L, (const cplx *)sigma, G, S);
-    vctx c = {m, (const cplx *)gamma, G, S};
+    vctx c = {m, (const cplx *)gamma, G, S, 0, 0, NULL, NULL};
+    cplx *Gw = NULL, *Sw = NULL;
+    const int tails = (mask & MASK_TAILS) != 0;
+    if (tails && window_setup(&c, L, (const cplx *)sigma, &Gw, &Sw)) {
+        free(G); free(S); free(Gw); free(Sw);
+        return -1;
+    }
     cplx *dg = (cplx *)dgamma;
 #ifdef _OPENMP
     int nt = oracle_max_threads();
@@ -209,13 +314,14 @@ int oracle_rhs_rows(const oracle_model *m, double L, const double *gamma,
     for (int i1 = k1_begin; i1 < k1_end; ++i1)
         for (int i2 = 0; i2 < N; ++i2)
             for (int i3 = 0; i3 < N; ++i3)
-                dg[((size_t)i1 * N + i2) * N + i3] = rhs_entry(&c, L, mask, i1, i2, i3);
+                dg[((size_t)i1 * N + i2) * N + i3] =
+                    tails ? rhs_entry_tails(&c, L, mask, i1, i2, i3) : rhs_entry(&c, L, mask, i1, i2, i3);
     if (dsigma) {
         cplx *ds = (cplx *)dsigma;
         for (int i = 0; i < N; ++i)
-            ds[i] = (mask & 8) ? rhs_sigma(&c, L, i) : 0.0;
+            ds[i] = (mask & 8) ? (tails ? rhs_sigma_tails(&c, L, i) : rhs_sigma(&c, L, i)) : 0.0;
     }
-    free(G); free(S);
+    free(G); free(S); free(Gw); free(Sw);
     return 0;
 }
 
@@ -234,15 +340,22 @@ int oracle_rhs_entries(const oracle_model *m, double L, const double *gamma,
     cplx *G = malloc(sizeof(cplx) * N), *S = malloc(sizeof(cplx) * N);
     if (!G || !S) { free(G); free(S); return -1; }
     propagators(m, L, (const cplx *)sigma, G, S);
-    vctx c = {m, (const cplx *)gamma, G, S};
+    vctx c = {m, (const cplx *)gamma, G, S, 0, 0, NULL, NULL};
+    cplx *Gw = NULL, *Sw = NULL;
+    const int tails = (mask & MASK_TAILS) != 0;
+    if (tails && window_setup(&c, L, (const cplx *)sigma, &Gw, &Sw)) {
+        free(G); free(S); free(Gw); free(Sw);
+        return -1;
+    }
     cplx *o = (cplx *)out;
 #ifdef _OPENMP
     int nt = oracle_max_threads();
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
 #endif
     for (int j = 0; j < count; ++j)
-        o[j] = rhs_entry(&c, L, mask, idx[3 * j], idx[3 * j + 1], idx[3 * j + 2]);
-    free(G); free(S);
+        o[j] = tails ? rhs_entry_tails(&c, L, mask, idx[3 * j], idx[3 * j + 1], idx[3 * j + 2])
+                     : rhs_entry(&c, L, mask, idx[3 * j], idx[3 * j + 1], idx[3 * j + 2]);
+    free(G); free(S); free(Gw); free(Sw);
     return 0;
 }
 

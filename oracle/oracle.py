@@ -13,6 +13,12 @@ from . import build as _build
 
 _lib = None
 
+# Channel-mask bits: 1 pp, 2 dph, 4 xph, 8 self-energy flow, 16 frequency-box
+# tails (internal sums over a window of TAIL_FACTOR * N Matsubara indices
+# centred on the box, bare-U vertices and Sigma = 0 outside the box).
+MASK_TAILS = 0x10
+TAIL_FACTOR = 16
+
 
 class _Model(C.Structure):
     _fields_ = [("U", C.c_double), ("T", C.c_double), ("eps_d", C.c_double),

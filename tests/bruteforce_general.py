@@ -24,6 +24,10 @@ SU(2) decomposition gamma = V(1'2';12) d(s1',s1) d(s2',s2)
 - V(2'1';12) d(s1',s2) d(s2',s1), with V(1'2';12) = V(k1=w1, k2=w2, k3=w1')
 read from the stored array when all four frequencies are in the box and the
 bare U otherwise.  Pure-Python loops: use only on tiny grids (N <= 8).
+
+With lo != 0 the internal pair runs over the frequency window
+[lo, lo + len(G)) instead of the box (the frequency-box tail option); G and S
+are then given on that window, G[w - lo].
 """
 import numpy as np
 
@@ -55,47 +59,47 @@ class GeneralVertex:
         return val
 
 
-def general_rhs_entry(gv, G, S, T, ext):
+def general_rhs_entry(gv, G, S, T, ext, lo=0):
     """d gamma/dL at external labels ext = (s1',w1',s2',w2',s1,w1,s2,w2)."""
     s1p, w1p, s2p, w2p, s1, w1, s2, w2 = ext
-    N = gv.N
+    hi = lo + len(G)
     acc = 0.0
     for sa in (UP, DN):
         for sb in (UP, DN):
-            for wa in range(N):
+            for wa in range(lo, hi):
                 # particle-particle: 3=(sa,wa), 4=(sb,wb), wa+wb = w1+w2
                 wb = w1 + w2 - wa
-                if 0 <= wb < N:
-                    lb = S[wa] * G[wb] + G[wa] * S[wb]
+                if lo <= wb < hi:
+                    lb = S[wa - lo] * G[wb - lo] + G[wa - lo] * S[wb - lo]
                     acc += -0.5 * gv(s1p, w1p, s2p, w2p, sa, wa, sb, wb) * lb * \
                         gv(sa, wa, sb, wb, s1, w1, s2, w2)
                 # direct particle-hole: gamma(1'4;13) gamma(32';42),
                 # w1' + w4 = w1 + w3
                 wb = w1 + wa - w1p
-                if 0 <= wb < N:
-                    lb = S[wa] * G[wb] + G[wa] * S[wb]
+                if lo <= wb < hi:
+                    lb = S[wa - lo] * G[wb - lo] + G[wa - lo] * S[wb - lo]
                     acc += gv(s1p, w1p, sb, wb, s1, w1, sa, wa) * lb * \
                         gv(sa, wa, s2p, w2p, sb, wb, s2, w2)
                 # exchanged particle-hole: gamma(2'4;13) gamma(31';42),
                 # w2' + w4 = w1 + w3
                 wb = w1 + wa - w2p
-                if 0 <= wb < N:
-                    lb = S[wa] * G[wb] + G[wa] * S[wb]
+                if lo <= wb < hi:
+                    lb = S[wa - lo] * G[wb - lo] + G[wa - lo] * S[wb - lo]
                     acc -= gv(s2p, w2p, sb, wb, s1, w1, sa, wa) * lb * \
                         gv(sa, wa, s1p, w1p, sb, wb, s2, w2)
     return T * acc
 
 
-def general_sigma_entry(gv, S, T, w):
+def general_sigma_entry(gv, S, T, w, lo=0):
     """d Sigma_up(w)/dL."""
     acc = 0.0
     for sa in (UP, DN):
-        for wa in range(gv.N):
-            acc += S[wa] * gv(UP, w, sa, wa, UP, w, sa, wa)
+        for wa in range(lo, lo + len(S)):
+            acc += S[wa - lo] * gv(UP, w, sa, wa, UP, w, sa, wa)
     return T * acc
 
 
-def reduced_from_general(V, U, G, S, T, Lam):
+def reduced_from_general(V, U, G, S, T, Lam, lo=0):
     """(dV/dl, dSigma/dl) obtained from the general formula: the up-down
     component d gamma(k3 up, k4 dn; k1 up, k2 dn)/dl for every stored entry."""
     gv = GeneralVertex(V, U)
@@ -106,6 +110,6 @@ def reduced_from_general(V, U, G, S, T, Lam):
             for i3 in range(N):
                 i4 = i1 + i2 - i3
                 dV[i1, i2, i3] = Lam * general_rhs_entry(
-                    gv, G, S, T, (UP, i3, DN, i4, UP, i1, DN, i2))
-    dS = np.array([Lam * general_sigma_entry(gv, S, T, w) for w in range(N)])
+                    gv, G, S, T, (UP, i3, DN, i4, UP, i1, DN, i2), lo)
+    dS = np.array([Lam * general_sigma_entry(gv, S, T, w, lo) for w in range(N)])
     return dV, dS

@@ -372,3 +372,132 @@ def test_entry_and_row_evaluations_agree_with_full_rhs():
     assert np.array_equal(e, dg[idx[:, 0], idx[:, 1], idx[:, 2]])
     r = oracle.rhs_rows(m, 0.8, V, sig, 3, 7)
     assert np.array_equal(r[3:7], dg[3:7]) and np.all(r[:3] == 0) and np.all(r[7:] == 0)
+
+
+# ----------------------------------------------- frequency-box tails ----
+# With mask bit MASK_TAILS the internal sums run over a window of
+# TAIL_FACTOR * N Matsubara indices centred on the box (Sigma = 0 outside the
+# box, bare-U vertices as soon as an index leaves the box).
+
+TAILS = oracle.MASK_TAILS
+
+
+def window_propagators(m, Lam, sigma):
+    """(Gw, Sw, lo) on the tail window: the window's frequencies are exactly
+    those of a box of W = TAIL_FACTOR * N indices, so the oracle's propagators
+    of that larger model (with the self-energy padded by zeros) are the window's."""
+    N = m.N
+    W = oracle.TAIL_FACTOR * N
+    lo = -(W - N) // 2
+    sw = np.zeros(W, np.complex128)
+    sw[-lo:-lo + N] = sigma
+    mw = Model(U=m.U, T=m.T, eps_d=m.eps_d, Delta=m.Delta, N=W)
+    Gw, Sw = oracle.propagators(mw, Lam, sw)
+    return Gw, Sw, lo
+
+
+def tail_constants(m, Lam, sigma):
+    """Every vertex with an internal index outside the box is the bare U, so
+    the window's extra terms are U^2 times bubble sums per transfer (pp and
+    xph), 2U^2 - U^2 - U^2 = 0 for dph, and U times a sum of S for Sigma."""
+    N = m.N
+    Gw, Sw, lo = window_propagators(m, Lam, sigma)
+    W = Gw.size
+    box = lambda i: 0 <= i < N
+    win = lambda i: lo <= i < lo + W
+    lb = lambda a, b: Sw[a - lo] * Gw[b - lo] + Gw[a - lo] * Sw[b - lo]
+    cpp = np.zeros(2 * N - 1, np.complex128)
+    cxph = np.zeros(2 * N - 1, np.complex128)
+    for s in range(2 * N - 1):
+        for p in range(lo, lo + W):
+            q = s - p
+            if win(q) and not (box(p) and box(q)):
+                cpp[s] += lb(p, q)
+    for Q in range(-(N - 1), N):
+        for p in range(lo, lo + W):
+            r = p + Q
+            if win(r) and not (box(p) and box(r)):
+                cxph[Q + N - 1] += lb(p, r)
+    csig = sum(Sw[p - lo] for p in range(lo, lo + W) if not box(p))
+    return cpp, cxph, csig
+
+
+@pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4, 0x8])
+def test_tails_add_a_constant_per_transfer(mask):
+    N, U, T, Lam = 8, 1.4, 0.06, 0.45
+    m = Model(U=U, T=T, eps_d=-U / 2 + 0.35, Delta=1.0, N=N)
+    V = inputs.random_vertex(N, U, seed=11, amp=0.4)
+    sig = inputs.random_sigma(N, seed=12, amp=0.2)
+    dg0, ds0 = oracle.rhs(m, Lam, V, sig, mask)
+    dg1, ds1 = oracle.rhs(m, Lam, V, sig, mask | TAILS)
+    cpp, cxph, csig = tail_constants(m, Lam, sig)
+    s, Q = cf.transfer_indices(N)
+    ref = np.zeros((N, N, N), np.complex128)
+    if mask & 1:
+        ref += -Lam * T * U ** 2 * cpp[s]
+    if mask & 4:
+        ref += -Lam * T * U ** 2 * cxph[Q]
+    sref = np.full(N, Lam * T * U * csig if mask & 8 else 0.0, np.complex128)
+    scale = max(np.max(np.abs(dg0)), 1e-3)
+    assert np.max(np.abs((dg1 - dg0) - ref)) < 1e-13 * scale
+    assert np.max(np.abs((ds1 - ds0) - sref)) < 1e-15
+    if mask & 5:
+        assert np.max(np.abs(ref)) > 1e-3 * scale  # the tails are resolved
+    if mask & 8:
+        assert abs(csig) > 1e-6  # off particle-hole symmetry the Hartree tail is nonzero
+
+
+@pytest.mark.parametrize("N,seed,eps_shift", [(4, 21, 0.0), (6, 22, 0.5)])
+def test_tails_match_spin_resolved_general_formula(N, seed, eps_shift):
+    U, T, Lam = 1.2, 0.08, 0.3
+    m = Model(U=U, T=T, eps_d=-U / 2 + eps_shift, Delta=1.0, N=N)
+    V = inputs.random_vertex(N, U, seed=seed, amp=0.4)
+    sig = inputs.random_sigma(N, seed=seed + 100, amp=0.15)
+    dg, ds = oracle.rhs(m, Lam, V, sig, 0xF | TAILS)
+    Gw, Sw, lo = window_propagators(m, Lam, sig)
+    dgb, dsb = bf.reduced_from_general(V, U, Gw, Sw, T, Lam, lo)
+    assert rel(dg, dgb) < 1e-13
+    assert rel(ds, dsb) < 1e-13 or np.max(np.abs(ds - dsb)) < 1e-16
+
+
+@pytest.mark.parametrize("eps_shift", [0.0, 0.6])
+def test_tails_second_order_perturbation_theory(eps_shift):
+    """With the tails the O(U^2) vertex and the O(U) Hartree term take the
+    bubbles over the whole window."""
+    N, T, D, F = 8, 0.05, 1.0, oracle.TAIL_FACTOR
+    L0, Lf = 1e3, 1e-2
+    devs, sdevs = [], []
+    for U in [0.04, 0.02, 0.01]:
+        m = Model(U=U, T=T, eps_d=-U / 2 + eps_shift, Delta=D, N=N)
+        g, s, st = oracle.flow(m, Lambda0=L0, Lambda_f=Lf, rtol=1e-12, atol=1e-16, mask=0xF | TAILS)
+        assert st.status == 0
+        ref = cf.second_order_vertex_window(N, F, T, eps_shift, D, U, L0, Lf)
+        sref = cf.first_order_sigma_window(N, F, T, eps_shift, D, U, L0, Lf)
+        devs.append(np.max(np.abs(g - ref)))
+        sdevs.append(np.max(np.abs(s - sref)))
+        # the window changes the second-order result: the box-only reference misses it
+        box_ref, _, _ = cf.second_order_vertex(N, T, eps_shift, D, U, L0, Lf)
+        assert np.max(np.abs(ref - box_ref)) > 20 * devs[-1]
+    for a, b in zip(devs, devs[1:]):
+        assert 6.5 < a / b < 9.5, devs
+    if eps_shift != 0.0:
+        for a, b in zip(sdevs, sdevs[1:]):
+            assert 3.2 < a / b < 4.8, sdevs
+
+
+def test_tails_keep_the_flow_symmetries():
+    N, U = 8, 2.0
+    m = Model(U=U, T=0.05, eps_d=-U / 2 + 0.5, Delta=1.0, N=N)
+    g, s, st = oracle.flow(m, mask=0xF | TAILS)
+    assert st.status == 0
+    scale = np.max(np.abs(g))
+    assert _crossing_err(g) < 1e-12 * scale
+    mk = _aib(N)
+    rev = np.conj(g[::-1, ::-1, ::-1])
+    assert np.max(np.abs((g - rev)[mk])) < 1e-12 * scale
+    assert np.max(np.abs(s - np.conj(s[::-1]))) < 1e-14
+    mp = Model(U=U, T=0.05, eps_d=-U / 2, Delta=1.0, N=N)
+    gp, sp, st = oracle.flow(mp, mask=0xF | TAILS)
+    assert st.status == 0
+    assert np.max(np.abs(gp.imag)) < 1e-14 * np.max(np.abs(gp))
+    assert np.max(np.abs(sp.real)) < 1e-15
