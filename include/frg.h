@@ -63,6 +63,21 @@ extern "C" {
 #define FRG_CH_XPH 0x4
 #define FRG_CH_SIGMA 0x8
 #define FRG_CH_ALL 0xF
+/*
+ * Frequency-box tails (an option beyond the paper's box truncation): the
+ * internal sum of every enabled channel and of the self-energy runs over a
+ * window of FRG_TAIL_FACTOR * N_f Matsubara indices centred on the box
+ * (both internal frequencies in the window) instead of the box.  Vertices keep
+ * the box rule (bare U as soon as an index leaves the box) and the propagators
+ * outside the box take Sigma = 0.  Every vertex with an internal index
+ * outside the box is then U, so the extra terms are -Lambda T U^2 times a
+ * bubble sum per transfer for pp (s = k1 + k2) and xph (Q = k2 - k3), zero for
+ * the direct particle-hole channel, and Lambda T U sum S for the self-energy;
+ * the library evaluates them in FP64 per rhs.  Not available in
+ * frg_rhs_noalloc.
+ */
+#define FRG_TAILS 0x10
+#define FRG_TAIL_FACTOR 16
 
 typedef struct {
     double U;         /* interaction */
@@ -77,7 +92,7 @@ typedef struct {
     double h0;        /* first step in l = ln Lambda (< 0); 0 selects -0.01 */
     long max_steps;   /* step attempts before FRG_ENOTCONV; 0 selects 100000 */
     int precision;    /* FRG_FP64, FRG_3XTF32 or FRG_BF16X3 */
-    int channel_mask; /* FRG_CH_* bits; 0 selects FRG_CH_ALL */
+    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS; 0 selects FRG_CH_ALL */
 } frg_params;
 
 typedef struct frg_ctx frg_ctx;
@@ -195,8 +210,8 @@ int frg_stats(frg_ctx *ctx, frg_flow_stats *stats);
  * events on the context stream around its phases; ms[0..4] (host) receive the
  * durations of the bubble-weight (with the self-energy, which the same kernel
  * computes), operand-regather, channel-contraction and combine (scatter-add)
- * phases, and ms[4] = 0 (no separate self-energy phase); 0 for a phase the
- * path does not have.  Synchronises.
+ * phases, and ms[4] the addition of the frequency-box tails (FRG_TAILS; 0
+ * without them); 0 for a phase the path does not have.  Synchronises.
  * frg_kernel_launches returns the number of kernels this library has launched
  * in the process so far.
  */

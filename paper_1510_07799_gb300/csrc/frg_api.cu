@@ -135,7 +135,10 @@ int validate(const frg_params &p, std::string &why) {
   if (!std::isfinite(p.U) || !std::isfinite(p.eps_d)) { why = "U and eps_d must be finite"; return FRG_EINVAL; }
   if (p.h0 > 0.0) { why = "h0 must be <= 0 (the flow runs towards small Lambda)"; return FRG_EINVAL; }
   if (p.precision < FRG_FP64 || p.precision > FRG_BF16X3) { why = "unknown precision"; return FRG_EINVAL; }
-  if (p.channel_mask < 0 || p.channel_mask > 0xF) { why = "channel_mask must be within 0xF"; return FRG_EINVAL; }
+  if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS)) {
+    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS";
+    return FRG_EINVAL;
+  }
   return FRG_OK;
 }
 
@@ -161,13 +164,16 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
   if (ev) CK(cudaEventRecord(ev[0], st), "event");
   // untimed split evaluations overlap the bubble weights with the relayout
   const bool fork = !ev && ctx->split && ctx->sstream;
+  const bool tails = (ctx->mask & FRG_TAILS) != 0;
   if (fork) {
     CK(cudaEventRecord(ctx->ev_fork, st), "fork");
     CK(cudaStreamWaitEvent(ctx->sstream, ctx->ev_fork, 0), "fork");
+    if (tails) LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, ctx->sstream), "tail sums");
     LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, ctx->sstream),
        "bubble weights and self-energy");
     CK(cudaEventRecord(ctx->ev_join, ctx->sstream), "join");
   } else {
+    if (tails) LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, st), "tail sums");
     LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st),
        "bubble weights and self-energy");
   }
@@ -204,6 +210,7 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
       if (ev) CK(cudaEventRecord(ev[3], st), "event");
     }
   }
+  if (tails) LK(launch_add_tails(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "tails");
   if (ev) CK(cudaEventRecord(ev[4], st), "event");
   if (ev) CK(cudaEventRecord(ev[5], st), "event");
   return FRG_OK;
@@ -422,6 +429,12 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     }
     for (int j = 0; j < 7; ++j)
       if (!(P.kS[j] = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
+    if (p.channel_mask & FRG_TAILS) {
+      const size_t W = (size_t)FRG_TAIL_FACTOR * N;
+      if (!(P.Gw = dalloc<double2>(ctx, W)) || !(P.Sw = dalloc<double2>(ctx, W)) ||
+          !(P.tail = dalloc<double2>(ctx, 2 * (2 * (size_t)N - 1) + 1)))
+        return bail(FRG_ENOMEM);
+    }
     if (!(P.G = dalloc<double2>(ctx, N)) || !(P.S = dalloc<double2>(ctx, N)) ||
         !(P.Lpp = dalloc<double2>(ctx, (size_t)(2 * N - 1) * N)) ||
         !(P.Lph = dalloc<double2>(ctx, (size_t)(2 * N - 1) * N)))

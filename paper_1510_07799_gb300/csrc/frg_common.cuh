@@ -41,6 +41,11 @@ struct PointDesc {
   float2 *PX, *PW;          // split paths: direct (layout X) and crossed (layout W) channel outputs
   unsigned char *kord;      // split paths: per table row, its 16-wide k-chunks by increasing max |Lb| (16 each)
   unsigned *vmax;    // split paths: bits of max |Re|,|Im| over the FP32 vertex input of the current rhs
+  // frequency-box tails (null when off): propagators on the window of
+  // FRG_TAIL_FACTOR * N indices starting at -(W - N)/2 (Sigma = 0 outside the
+  // box), and per rhs the additive constants: pp transfer s at [s], xph
+  // transfer Q at [2N-1 + Q+N-1], the self-energy at [4N-2]
+  double2 *Gw, *Sw, *tail;
 };
 
 // Device-side step controller state, one per point.
@@ -148,6 +153,20 @@ __device__ __forceinline__ bool fourth_in_box(int i, int N) {
   return inbox(N, i1 + i2 - i3);
 }
 
+// Propagators at frequency index i (any integer) and scale L with self-energy
+// sg (Omega scheme): G = 1/(Theta^{-1} G0^{-1} - Sigma), Theta^{-1} = 1 + L^2/w^2,
+// S = -G^2 (2L/w^2) G0^{-1}, G0^{-1} = iw - et + i Delta sgn w.
+__device__ __forceinline__ void propagator_at(const PointDesc &P, int i, double L, double2 sg, double2 &g,
+                                              double2 &s) {
+  const double w = (2.0 * (double)(i - P.N / 2) + 1.0) * M_PI * P.T;
+  const double thinv = 1.0 + (L * L) / (w * w);
+  const double2 gi = make_double2(-P.et, w + (w > 0.0 ? P.Delta : -P.Delta));
+  const double2 den = make_double2(thinv * gi.x - sg.x, thinv * gi.y - sg.y);
+  const double nrm = den.x * den.x + den.y * den.y;
+  g = make_double2(den.x / nrm, -den.y / nrm);
+  s = cscale(cmul(cmul(g, g), gi), -2.0 * L / (w * w));
+}
+
 // Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).
 struct StageArgs {
   int stage;  // 0..6
@@ -165,6 +184,11 @@ int launch_contract_fp64(const PointDesc *d_pts, const RhsIO *d_io, const WorkIt
 // the self-energy rhs in one launch.
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
                         cudaStream_t st);
+// Frequency-box tails: window propagators, then the per-transfer constants
+// (before launch_bubble_sigma, which adds the self-energy constant) ...
+int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st);
+// ... and their addition to the vertex derivative (after the contraction).
+int launch_add_tails(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, cudaStream_t st);
 // Self-energy rhs from FP64 input alone (after launch_bubble).
 int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st);
 }  // namespace frg

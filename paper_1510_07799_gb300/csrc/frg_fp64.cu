@@ -8,6 +8,9 @@
 // Channel sums (the three one-loop diagrams of the paper, Sec. 4) are
 // evaluated as one complex product Left . Right per transfer frequency, with
 // diag(Lb) folded into Left (see Geom in frg_common.cuh for the index sets).
+#include <algorithm>
+
+#include "frg.h"
 #include "frg_common.cuh"
 #include "frg_split.cuh"
 
@@ -25,17 +28,8 @@ __global__ void k_bubble_gs(const PointDesc *__restrict__ pts, const RhsIO *__re
   const PointDesc &P = pts[pi];
   const int i = blockIdx.x * GS_PER_BLOCK + threadIdx.x;
   if (i >= P.N) return;
-  const double L = *o.lam;
-  const double w = (2.0 * (double)(i - P.N / 2) + 1.0) * M_PI * P.T;
-  const double thinv = 1.0 + (L * L) / (w * w);
-  const double2 gi = make_double2(-P.et, w + (w > 0.0 ? P.Delta : -P.Delta));
-  double2 sg = o.sig ? o.sig[i] : make_double2(0.0, 0.0);
-  // G = 1 / (thinv * gi - sigma)
-  const double2 den = make_double2(thinv * gi.x - sg.x, thinv * gi.y - sg.y);
-  const double nrm = den.x * den.x + den.y * den.y;
-  const double2 g = make_double2(den.x / nrm, -den.y / nrm);
-  const double2 g2 = cmul(g, g);
-  const double2 s = cscale(cmul(g2, gi), -2.0 * L / (w * w));
+  double2 g, s;
+  propagator_at(P, i, *o.lam, o.sig ? o.sig[i] : make_double2(0.0, 0.0), g, s);
   P.G[i] = g;
   P.S[i] = s;
 }
@@ -229,7 +223,9 @@ __global__ void __launch_bounds__(128)
       double2 t = part[0];
       for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
       const double f = L * P.T;
-      o.dsig[w] = make_double2(t.x * f, t.y * f);
+      double2 d = make_double2(t.x * f, t.y * f);
+      if (P.tail) d = cadd(d, P.tail[2 * (2 * N - 1)]);  // frequency-box tail of the self-energy
+      o.dsig[w] = d;
     }
     return;
   }
@@ -303,6 +299,114 @@ int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points,
     k_bubble_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0);
   else
     k_bubble_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ------------------------------------------------ frequency-box tails ----
+// Window of W = FRG_TAIL_FACTOR * N indices [lo, lo + W), lo = -(W - N) / 2.
+// Every vertex with an internal index outside the box is the bare U, so the
+// terms the window adds to the box sums are, per rhs and point,
+//   pp  transfer s: -L T U^2 sum_{p, s-p in window, not both in box} Lb(p, s-p)
+//   xph transfer Q: -L T U^2 sum_{p, p+Q in window, not both in box} Lb(p, p+Q)
+//   self-energy:     L T U   sum_{p in window, outside box} S(p)
+// and zero for the direct particle-hole channel (2U^2 - U^2 - U^2).
+__global__ void k_tail_gs(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  const int N = P.N, W = FRG_TAIL_FACTOR * N, lo = -(W - N) / 2;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!P.Gw || x >= W) return;
+  const int i = lo + x;
+  double2 g, s;
+  propagator_at(P, i, *o.lam, (o.sig && inbox(N, i)) ? o.sig[i] : make_double2(0.0, 0.0), g, s);
+  P.Gw[x] = g;
+  P.Sw[x] = s;
+}
+
+// blocks [0, 2 maxN - 1): pp transfers; the next 2 maxN - 1: xph transfers;
+// the last one: the self-energy constant.  128 threads, fixed-order reduction.
+__global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                                   int maxN, int mask) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  if (!P.tail) return;
+  const int N = P.N, nrow = 2 * N - 1, nrow_max = 2 * maxN - 1;
+  const int b = blockIdx.x;
+  const int which = b < nrow_max ? 0 : (b < 2 * nrow_max ? 1 : 2);
+  const int row = which == 2 ? 0 : b - which * nrow_max;
+  if (which < 2 && row >= nrow) return;
+  const int W = FRG_TAIL_FACTOR * N, lo = -(W - N) / 2;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    const int p = lo + x;
+    if (which == 2) {
+      if (!inbox(N, p)) acc = cadd(acc, P.Sw[x]);
+      continue;
+    }
+    const int q = which == 0 ? row - p : p + (row - (N - 1));
+    const int y = q - lo;
+    if ((unsigned)y >= (unsigned)W || (inbox(N, p) && inbox(N, q))) continue;
+    acc = cadd(acc, cadd(cmul(P.Sw[x], P.Gw[y]), cmul(P.Gw[x], P.Sw[y])));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  __shared__ double2 part[4];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = part[0];
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
+    const double L = *o.lam;
+    if (which == 0) P.tail[row] = (mask & 1) ? cscale(t, -L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
+    else if (which == 1) P.tail[nrow + row] = (mask & 4) ? cscale(t, -L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
+    else P.tail[2 * nrow] = (mask & 8) ? cscale(t, L * P.T * P.U) : make_double2(0.0, 0.0);
+  }
+}
+
+// dGamma(k1,k2,k3) += tail_pp[k1 + k2] + tail_xph[k2 - k3]; FP32 or FP64 output.
+__global__ void __launch_bounds__(256) k_add_tails(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
+  const int pi = blockIdx.y;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  if (!P.tail) return;
+  const int N = P.N, nrow = 2 * N - 1;
+  __shared__ double2 tab[2 * (2 * FRG_MAX_N - 1)];
+  for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x) tab[j] = P.tail[j];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n3; i += gridDim.x * blockDim.x) {
+    const int q = i / N, i3 = i - q * N, i1 = q / N, i2 = q - i1 * N;
+    const double2 a = cadd(tab[i1 + i2], tab[nrow + i2 - i3 + N - 1]);
+    if (o.out_f32) {
+      float2 &d = static_cast<float2 *>(o.dgam)[i];
+      d = make_float2(d.x + (float)a.x, d.y + (float)a.y);
+    } else {
+      double2 &d = static_cast<double2 *>(o.dgam)[i];
+      d = cadd(d, a);
+    }
+  }
+}
+
+int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
+  const int W = FRG_TAIL_FACTOR * maxN;
+  k_tail_gs<<<dim3((W + 127) / 128, n_points), 128, 0, st>>>(d_pts, d_io);
+  FRG_COUNT(1);
+  k_tail_sums<<<dim3(2 * (2 * maxN - 1) + 1, n_points), 128, 0, st>>>(d_pts, d_io, maxN, mask);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_add_tails(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, cudaStream_t st) {
+  const long n3 = (long)maxN * maxN * maxN;
+  const int blocks = (int)std::min<long>((n3 + 255) / 256, 1024);
+  k_add_tails<<<dim3(blocks, n_points), 256, 0, st>>>(d_pts, d_io);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

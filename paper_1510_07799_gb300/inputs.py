@@ -39,7 +39,11 @@ SIAM_N128 = Workload("siam_N128_U3_T0.005_ph", N=128, U=3.0, T=0.005, eps_d=-1.5
 SIAM_N256 = Workload("siam_N256_U3_T0.002_asym0.25", N=256, U=3.0, T=0.002,
                      eps_d=-1.5 + 0.25)
 
-WORKLOADS = {w.name: w for w in (SIAM_N16, SIAM_N64, SIAM_N128, SIAM_N256)}
+# Small flow off particle-hole symmetry (eps_d = -U/2 + 0.3), used with the
+# frequency-box tail option (whose self-energy tail vanishes at ph symmetry).
+SIAM_N16_ASYM = Workload("siam_N16_U1_T0.05_asym0.3", N=16, U=1.0, T=0.05, eps_d=-0.5 + 0.3)
+
+WORKLOADS = {w.name: w for w in (SIAM_N16, SIAM_N64, SIAM_N128, SIAM_N256, SIAM_N16_ASYM)}
 
 BATCH_SEED = 1510077
 BATCH_SIZES = (32, 48, 64, 96)

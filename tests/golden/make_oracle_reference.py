@@ -6,7 +6,9 @@ vertex, the whole self-energy, the observables, the norms needed for normwise
 relative errors, and the integrator statistics.  Nothing here touches the CUDA
 path.
 
-usage: python tests/golden/make_oracle_reference.py <workload-name> [samples]
+usage: python tests/golden/make_oracle_reference.py <workload-name> [samples] [mask]
+(mask: the channel mask in hex, default 0xF; a mask other than 0xF is part of
+the output file's name)
 """
 import json
 import os
@@ -38,11 +40,12 @@ def sample_indices(N, count, seed=SAMPLE_SEED):
 def main():
     name = sys.argv[1]
     count = int(sys.argv[2]) if len(sys.argv) > 2 else 2048
+    mask = int(sys.argv[3], 16) if len(sys.argv) > 3 else 0xF
     w = inputs.WORKLOADS[name]
     m = oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
     t0 = time.time()
     g, s, st = oracle.flow(m, Lambda0=w.Lambda0, Lambda_f=w.Lambda_f, rtol=w.rtol,
-                           atol=w.atol)
+                           atol=w.atol, mask=mask)
     wall = time.time() - t0
     if st.status != 0:
         raise SystemExit("oracle flow failed: %s" % st)
@@ -51,6 +54,7 @@ def main():
     obs = oracle.observables(m, w.Lambda_f, g, s)
     out = {
         "workload": name,
+        "mask": mask,
         "what": "oracle FP64 flow from Lambda0 to Lambda_f; sampled final vertex",
         "params": {"N": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d, "Delta": w.Delta,
                    "Lambda0": w.Lambda0, "Lambda_f": w.Lambda_f, "rtol": w.rtol,
@@ -71,7 +75,7 @@ def main():
                         "n": obs["n"]},
     }
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                        "oracle_flow_%s.json" % name)
+                        "oracle_flow_%s%s.json" % (name, "" if mask == 0xF else "_mask%x" % mask))
     with open(path, "w") as f:
         json.dump(out, f, indent=0, separators=(",", ":"))
         f.write("\n")
