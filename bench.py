@@ -176,7 +176,7 @@ def reduce_over_ranks(ms, evals, device=None):
     return float(t.item()), float(ev.item())
 
 
-def cpu_baseline(N_rows, seconds=12.0):
+def cpu_baseline(N_rows, seconds=12.0, mask=0xF):
     """The FP64 oracle as it stands on the host cores, on whole rows i1 of the
     N=128 vertex (a bounded sample), scaled to rhs evaluations per second."""
     import numpy as np
@@ -190,15 +190,15 @@ def cpu_baseline(N_rows, seconds=12.0):
     i = 0
     while True:
         a = (i * N_rows) % w.N
-        oracle.rhs_rows(m, 0.02, V, sig, a, a + N_rows)
+        oracle.rhs_rows(m, 0.02, V, sig, a, a + N_rows, mask=mask)
         rows += N_rows
         i += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     return {"value": (rows / w.N) / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d, repeated for %.1f s; "
-                      "scaled by rows/N" % (rows, w.N, w.N, el)}
+            "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d (channel mask 0x%x), repeated "
+                      "for %.1f s; scaled by rows/N" % (rows, w.N, w.N, mask, el)}
 
 
 def run_reference(args):
@@ -251,7 +251,8 @@ def run_ours(args):
     w = inputs.SIAM_N128
     N = w.N
     prec = args.precision
-    ctx = frg.Context([w], precision=prec)
+    mask = frg.CH_ALL | (frg.TAILS if args.tails else 0)
+    ctx = frg.Context([w], precision=prec, channel_mask=mask)
     tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
 
@@ -318,6 +319,8 @@ def run_ours(args):
                 "executed_note": "tensor-core flops issued (3 split products, real form of the complex product, whole tiles and "
                                  "k-steps), for comparison with the tensor pipe's own rate; not the roofline value"}
     roof["phases_ms"] = {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2], "combine": ph[3]}
+    if args.tails:
+        roof["phases_ms"]["tails_add"] = ph[4]
 
     # ---- end to end through the host-buffer entry point: pinned host buffers,
     # the pipelined call (input copy, evaluation and output copy of successive
@@ -343,7 +346,7 @@ def run_ours(args):
     # the plain FP64 GPU path on the same state (the metric's comparison arm)
     fp64_gpu = None
     if prec != "fp64":
-        with frg.Context([w], precision="fp64") as c64:
+        with frg.Context([w], precision="fp64", channel_mask=mask) as c64:
             for _ in range(2):
                 c64.rhs_timed(0, lam, g, s, dg, ds)
             torch.cuda.synchronize()
@@ -359,7 +362,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
-            "config": {"workload": w.name, "N_f": N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
+            "config": {"workload": w.name + ("+tails" if args.tails else ""), "N_f": N, "U": w.U, "T": w.T,
+                       "eps_d": w.eps_d, "channel_mask": mask,
                        "precision": prec, "rhs_evals_timed": evals, "step_attempts_timed": attempts,
                        "step": "one Dormand-Prince step attempt of the flow (6 rhs + FP64 stage sums + "
                                "error norm + controller)",
@@ -369,7 +373,7 @@ def run_ours(args):
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "fp64_gpu": fp64_gpu}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(8, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(2 if args.tails else 8, seconds=args.cpu_seconds, mask=mask)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -574,6 +578,8 @@ def main():
     ap.add_argument("--workload", default="siam_N128", choices=["siam_N128", "batch64", "siam_N256", "siam_N64"])
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--tails", action="store_true",
+                    help="headline workload with the frequency-box tail option (channel_mask | FRG_TAILS)")
     args = ap.parse_args()
     args.precision_explicit = args.precision is not None
     if args.precision is None:

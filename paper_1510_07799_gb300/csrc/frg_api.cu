@@ -60,7 +60,7 @@ struct frg_ctx {
   // split paths: the bubble weights and the self-energy run on a side stream
   // while the stage input is relaid (fork / join by events)
   cudaStream_t sstream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tails = nullptr;
   // pipelined host-buffer evaluations: copy-in and copy-out streams, two device
   // slots per point, per-slot events (input copied, compute done, output read)
   cudaStream_t cin = nullptr, cout = nullptr;
@@ -168,10 +168,15 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
   if (fork) {
     CK(cudaEventRecord(ctx->ev_fork, st), "fork");
     CK(cudaStreamWaitEvent(ctx->sstream, ctx->ev_fork, 0), "fork");
-    if (tails) LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, ctx->sstream), "tail sums");
     LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, ctx->sstream),
        "bubble weights and self-energy");
     CK(cudaEventRecord(ctx->ev_join, ctx->sstream), "join");
+    // the tail constants are needed only after the contraction: they run on
+    // the side stream while the main stream regathers and contracts
+    if (tails) {
+      LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, ctx->sstream), "tail sums");
+      CK(cudaEventRecord(ctx->ev_tails, ctx->sstream), "tails");
+    }
   } else {
     if (tails) LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, st), "tail sums");
     LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st),
@@ -201,7 +206,7 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
   } else {
     if (chmask) {
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
-                ctx->maxN, fork ? ctx->ev_join : nullptr),
+                ctx->maxN, fork ? ctx->ev_join : nullptr, tails, fork ? ctx->ev_tails : nullptr),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
@@ -210,7 +215,11 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
       if (ev) CK(cudaEventRecord(ev[3], st), "event");
     }
   }
-  if (tails) LK(launch_add_tails(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "tails");
+  // the split contraction's combine adds the tails itself
+  if (tails && !(ctx->split && chmask)) {
+    if (fork) CK(cudaStreamWaitEvent(st, ctx->ev_tails, 0), "tails");
+    LK(launch_add_tails(ctx->d_pts, d_io, ctx->n, ctx->maxN, st), "tails");
+  }
   if (ev) CK(cudaEventRecord(ev[4], st), "event");
   if (ev) CK(cudaEventRecord(ev[5], st), "event");
   return FRG_OK;
@@ -369,6 +378,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_tails, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return bail(FRG_ECUDA);
@@ -539,6 +549,7 @@ void frg_destroy(frg_ctx *ctx) {
     if (ctx->aev_odone[b]) cudaEventDestroy(ctx->aev_odone[b]);
   }
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_tails) cudaEventDestroy(ctx->ev_tails);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->tc) tc_plan_destroy(ctx->tc);

@@ -223,9 +223,7 @@ __global__ void __launch_bounds__(128)
       double2 t = part[0];
       for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
       const double f = L * P.T;
-      double2 d = make_double2(t.x * f, t.y * f);
-      if (P.tail) d = cadd(d, P.tail[2 * (2 * N - 1)]);  // frequency-box tail of the self-energy
-      o.dsig[w] = d;
+      o.dsig[w] = make_double2(t.x * f, t.y * f);
     }
     return;
   }
@@ -370,26 +368,57 @@ __global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__
   }
 }
 
-// dGamma(k1,k2,k3) += tail_pp[k1 + k2] + tail_xph[k2 - k3]; FP32 or FP64 output.
-__global__ void __launch_bounds__(256) k_add_tails(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io) {
+// dGamma(k1,k2,k3) += tail_pp[k1 + k2] + tail_xph[k2 - k3] (FP32 or FP64
+// output, the constants rounded to the output's precision), dSigma += its
+// tail.  A block takes TAIL_ROWS rows (k1, k2); thread k3 walks them.
+constexpr int TAIL_ROWS = 16;
+__global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__restrict__ pts,
+                                                         const RhsIO *__restrict__ io) {
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
   const PointDesc &P = pts[pi];
   if (!P.tail) return;
   const int N = P.N, nrow = 2 * N - 1;
+  const int r0 = blockIdx.x * TAIL_ROWS;
+  if (r0 >= N * N) return;
   __shared__ double2 tab[2 * (2 * FRG_MAX_N - 1)];
-  for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x) tab[j] = P.tail[j];
+  __shared__ float2 tabf[2 * (2 * FRG_MAX_N - 1)];
+  for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x) {
+    tab[j] = P.tail[j];
+    tabf[j] = make_float2((float)tab[j].x, (float)tab[j].y);
+  }
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n3; i += gridDim.x * blockDim.x) {
-    const int q = i / N, i3 = i - q * N, i1 = q / N, i2 = q - i1 * N;
-    const double2 a = cadd(tab[i1 + i2], tab[nrow + i2 - i3 + N - 1]);
-    if (o.out_f32) {
-      float2 &d = static_cast<float2 *>(o.dgam)[i];
-      d = make_float2(d.x + (float)a.x, d.y + (float)a.y);
-    } else {
-      double2 &d = static_cast<double2 *>(o.dgam)[i];
-      d = cadd(d, a);
+  if (blockIdx.x == 0 && threadIdx.x < N && o.dsig)
+    o.dsig[threadIdx.x] = cadd(o.dsig[threadIdx.x], P.tail[2 * nrow]);
+  const int i3 = threadIdx.x;
+  if (i3 >= N) return;
+  const int nr = min(TAIL_ROWS, N * N - r0);
+  // all loads of the thread first, then the updates (one round trip)
+  if (o.out_f32) {
+    float2 *d = static_cast<float2 *>(o.dgam) + (size_t)r0 * N + i3;
+    float2 v[TAIL_ROWS];
+#pragma unroll
+    for (int k = 0; k < TAIL_ROWS; ++k)
+      if (k < nr) v[k] = d[(size_t)k * N];
+#pragma unroll
+    for (int k = 0; k < TAIL_ROWS; ++k) {
+      if (k >= nr) break;
+      const int r = r0 + k, i1 = r / N, i2 = r - i1 * N;
+      const float2 ta = tabf[i1 + i2], tb = tabf[nrow + i2 - i3 + N - 1];
+      d[(size_t)k * N] = make_float2(v[k].x + (ta.x + tb.x), v[k].y + (ta.y + tb.y));
+    }
+  } else {
+    double2 *d = static_cast<double2 *>(o.dgam) + (size_t)r0 * N + i3;
+    double2 v[TAIL_ROWS];
+#pragma unroll
+    for (int k = 0; k < TAIL_ROWS; ++k)
+      if (k < nr) v[k] = d[(size_t)k * N];
+#pragma unroll
+    for (int k = 0; k < TAIL_ROWS; ++k) {
+      if (k >= nr) break;
+      const int r = r0 + k, i1 = r / N, i2 = r - i1 * N;
+      d[(size_t)k * N] = cadd(v[k], cadd(tab[i1 + i2], tab[nrow + i2 - i3 + N - 1]));
     }
   }
 }
@@ -404,9 +433,9 @@ int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, in
 }
 
 int launch_add_tails(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, cudaStream_t st) {
-  const long n3 = (long)maxN * maxN * maxN;
-  const int blocks = (int)std::min<long>((n3 + 255) / 256, 1024);
-  k_add_tails<<<dim3(blocks, n_points), 256, 0, st>>>(d_pts, d_io);
+  const int blocks = (maxN * maxN + TAIL_ROWS - 1) / TAIL_ROWS;
+  const int threads = std::max(32, (maxN + 31) / 32 * 32);
+  k_add_tails<<<dim3(blocks, n_points), threads, 0, st>>>(d_pts, d_io);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

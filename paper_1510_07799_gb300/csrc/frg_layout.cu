@@ -13,6 +13,7 @@
 // input; k_combine adds the three channel outputs into the natural layout.
 // Both move 16^3 tiles through shared memory so that every global access is a
 // 128-byte row.
+#include "frg.h"
 #include "frg_common.cuh"
 #include "frg_layout.cuh"
 
@@ -80,9 +81,10 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
 }
 
 // k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
-// (launched for every split-path rhs, also when only pp is enabled).  Every
-// thread issues all 48 of its loads before the first shared-memory pass, so
-// that a block keeps 96 KB of reads in flight.
+// (launched for every split-path rhs, also when only pp is enabled), plus the
+// frequency-box tail constants when mask has FRG_TAILS (block 0 of a point also
+// adds the self-energy's).  Every thread issues all 48 of its loads before the
+// first shared-memory pass, so that a block keeps 96 KB of reads in flight.
 __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                                     int mask) {
   const int pi = blockIdx.y;
@@ -92,7 +94,17 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
   const Tile t = tile_of(P);
   if (!t.ok) return;
   __shared__ float2 sm[TILE_SMEM];
-  const int N = t.N;
+  __shared__ float2 ttab[2 * (2 * FRG_MAX_N - 1)];
+  const int N = t.N, nrow = 2 * N - 1;
+  const bool tails = (mask & FRG_TAILS) && P.tail;
+  if (tails) {
+    for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x)
+      ttab[j] = make_float2((float)P.tail[j].x, (float)P.tail[j].y);
+    if (blockIdx.x == 0 && threadIdx.x < N && o.dsig) {
+      const double2 a = o.dsig[threadIdx.x], b = P.tail[2 * nrow];
+      o.dsig[threadIdx.x] = make_double2(a.x + b.x, a.y + b.y);
+    }
+  }
   float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
   const float2 z = make_float2(0.f, 0.f);
   float2 vx[16], vw[16], vk[16];
@@ -138,7 +150,11 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
     const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
     const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
     if (a < N && b < N && c < N) {
-      const float2 v = sm[sidx(i1, i2, i3)];
+      float2 v = sm[sidx(i1, i2, i3)];
+      if (tails) {
+        const float2 ta = ttab[a + b], tb = ttab[nrow + b - c + N - 1];
+        v = make_float2(v.x + (ta.x + tb.x), v.y + (ta.y + tb.y));
+      }
       K[((size_t)a * N + b) * N + c] = make_float2(v.x + vk[u].x, v.y + vk[u].y);
     }
   }

@@ -44,6 +44,7 @@
 
 #include <cuda_bf16.h>
 
+#include "frg.h"
 #include "frg_layout.cuh"
 #include "frg_tc.cuh"
 
@@ -1542,7 +1543,8 @@ static void launch_one(int ch, int grid, cudaStream_t st, const PointDesc *d_pts
 }
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
-           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before) {
+           cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
+           int tails, cudaEvent_t wait_tails) {
   if (chmask & 6) {
     if (launch_relayout(d_pts, d_io, n_points, maxN, 1, (chmask & 2) != 0, st) != 0) return -3;
   }
@@ -1577,9 +1579,11 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
     }
   }
   if (ev_contract && cudaEventRecord(ev_contract, st) != cudaSuccess) return -3;
-  // channel outputs in their own layouts -> natural layout (the scatter-add);
-  // also resets the vertex bound that the BF16 slicing read
-  if (launch_combine(d_pts, d_io, n_points, maxN, chmask, st) != 0) return -3;
+  // channel outputs in their own layouts -> natural layout (the scatter-add,
+  // with the frequency-box tail constants when enabled); also resets the
+  // vertex bound that the BF16 slicing read
+  if (tails && wait_tails && cudaStreamWaitEvent(st, wait_tails, 0) != cudaSuccess) return -3;
+  if (launch_combine(d_pts, d_io, n_points, maxN, chmask | (tails ? FRG_TAILS : 0), st) != 0) return -3;
   return 0;
 }
 

@@ -33,5 +33,5 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // (optional: the bubble weights computed on another stream).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
-           cudaEvent_t wait_before = nullptr);
+           cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_tails = nullptr);
 }  // namespace frg
