@@ -76,14 +76,14 @@ def profiled_traffic(kind):
         return None
 
 
-def executed_tensor_flops(N, NT=128, mrows=64, ks=16):
+def executed_tensor_flops(N, NT=128, mrows=64, ks=16, half=False):
     """Tensor-core flops the 3xTF32 kernel issues per rhs: per tile (64 complex
     rows x NT columns) and k-step of 16 complex k, 3 products of M = 128 real
     rows (real form of the left operand) x N = NT x K = 32; ragged transfers
     padded to whole tiles and k-steps (the direct channel has two K halves)."""
     tot = 0
     for ch in range(3):
-        for m in range(-(N - 1), N):
+        for m in range(-(N - 1), 1 if half else N):
             D = N - abs(m)
             nk = (2 if ch == 1 else 1) * -(-D // ks)
             tiles = -(-D // mrows) * -(-N // min(NT, -(-N // 16) * 16))
@@ -91,11 +91,12 @@ def executed_tensor_flops(N, NT=128, mrows=64, ks=16):
     return tot
 
 
-def contraction_macs(N):
+def contraction_macs(N, half=False):
     """Useful complex multiply-adds of the three channel contractions per rhs:
     4 N sum_m D_m^2 with D_m = N - |m| (pp: D x D x N, dph: D x 2D x N,
-    xph: D x D x N per transfer)."""
-    return 4 * N * sum((N - abs(m)) ** 2 for m in range(-(N - 1), N))
+    xph: D x D x N per transfer); with the reversal reduction only the
+    transfers m <= 0 (about half) are contracted."""
+    return 4 * N * sum((N - abs(m)) ** 2 for m in range(-(N - 1), 1 if half else N))
 
 
 class Clocks:
@@ -251,7 +252,7 @@ def run_ours(args):
     w = inputs.SIAM_N128
     N = w.N
     prec = args.precision
-    mask = frg.CH_ALL | (frg.TAILS if args.tails else 0)
+    mask = frg.CH_ALL | (frg.TAILS if args.tails else 0) | (frg.REVERSAL if args.reversal else 0)
     ctx = frg.Context([w], precision=prec, channel_mask=mask)
     tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
@@ -294,7 +295,7 @@ def run_ours(args):
     phases = np.array([ctx.rhs_timed(0, lam, g, s, dg, ds) for _ in range(args.rhs_reps)])
     ph = phases.mean(axis=0)
     pk = peaks()
-    macs = contraction_macs(N)
+    macs = contraction_macs(N, half=args.reversal)
     if prec == "fp64":
         flops = 8.0 * macs
         achieved = flops / (ph[2] * 1e-3) / 1e12
@@ -309,13 +310,13 @@ def run_ours(args):
         achieved = flops / (ph[2] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
                 "frac": achieved / tf_peak,
-                "traffic": profiled_traffic("tf32") if prec == "3xtf32" else None,
+                "traffic": profiled_traffic("tf32") if prec == "3xtf32" and not args.reversal else None,
                 "traffic_unit": "DRAM bytes per rhs (contraction launch, ncu, cold cache)",
                 "kernel": "tcgen05 channel contractions of one rhs",
                 "peak_source": "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)" % pk["_source"],
                 "algorithmic": "8 flops x %d useful complex MACs per rhs (useful, not executed)" % macs,
-                "executed_tflops": executed_tensor_flops(N) / (ph[2] * 1e-3) / 1e12,
-                "executed_frac": executed_tensor_flops(N) / (ph[2] * 1e-3) / 1e12 / tf_peak,
+                "executed_tflops": executed_tensor_flops(N, half=args.reversal) / (ph[2] * 1e-3) / 1e12,
+                "executed_frac": executed_tensor_flops(N, half=args.reversal) / (ph[2] * 1e-3) / 1e12 / tf_peak,
                 "executed_note": "tensor-core flops issued (3 split products, real form of the complex product, whole tiles and "
                                  "k-steps), for comparison with the tensor pipe's own rate; not the roofline value"}
     roof["phases_ms"] = {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2], "combine": ph[3]}
@@ -362,7 +363,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
-            "config": {"workload": w.name + ("+tails" if args.tails else ""), "N_f": N, "U": w.U, "T": w.T,
+            "config": {"workload": w.name + ("+tails" if args.tails else "") + ("+reversal" if args.reversal else ""),
+                       "N_f": N, "U": w.U, "T": w.T,
                        "eps_d": w.eps_d, "channel_mask": mask,
                        "precision": prec, "rhs_evals_timed": evals, "step_attempts_timed": attempts,
                        "step": "one Dormand-Prince step attempt of the flow (6 rhs + FP64 stage sums + "
@@ -373,7 +375,7 @@ def run_ours(args):
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "fp64_gpu": fp64_gpu}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(2 if args.tails else 8, seconds=args.cpu_seconds, mask=mask)
+        line["cpu_baseline"] = cpu_baseline(2 if args.tails else 8, seconds=args.cpu_seconds, mask=mask & 0x1F)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -580,6 +582,9 @@ def main():
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--tails", action="store_true",
                     help="headline workload with the frequency-box tail option (channel_mask | FRG_TAILS)")
+    ap.add_argument("--reversal", action="store_true",
+                    help="headline workload with the frequency-reversal reduction (channel_mask | FRG_REVERSAL): "
+                         "the contraction computes half of the transfers of each channel")
     args = ap.parse_args()
     args.precision_explicit = args.precision is not None
     if args.precision is None:

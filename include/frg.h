@@ -78,6 +78,20 @@ extern "C" {
  */
 #define FRG_TAILS 0x10
 #define FRG_TAIL_FACTOR 16
+/*
+ * Frequency-reversal reduction (split precisions; FRG_FP64 accepts the bit
+ * and computes everything).  The caller asserts that every vertex and
+ * self-energy handed to the context is reversal-symmetric,
+ *   V(N-1-i1, N-1-i2, N-1-i3) = conj V(i1, i2, i3),  Sigma(N-1-i) = conj Sigma(i)
+ * (index i = n + N/2, i.e. n -> -n-1 with complex conjugation), which every
+ * flow from the bare vertex keeps exactly.  The rhs then has the same symmetry
+ * channel by channel, transfer m of each channel (m = s, t + N - 1 or Q + N - 1)
+ * mapping to 2N - 2 - m: the contraction computes the transfers m <= N - 1
+ * only (about half of the tensor-core work) and the scatter-add takes the
+ * others from the mirrored entries.  For inputs without the symmetry the
+ * result is the symmetric part's rhs, not the input's.
+ */
+#define FRG_REVERSAL 0x20
 
 typedef struct {
     double U;         /* interaction */

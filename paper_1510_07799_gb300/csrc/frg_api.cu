@@ -135,8 +135,8 @@ int validate(const frg_params &p, std::string &why) {
   if (!std::isfinite(p.U) || !std::isfinite(p.eps_d)) { why = "U and eps_d must be finite"; return FRG_EINVAL; }
   if (p.h0 > 0.0) { why = "h0 must be <= 0 (the flow runs towards small Lambda)"; return FRG_EINVAL; }
   if (p.precision < FRG_FP64 || p.precision > FRG_BF16X3) { why = "unknown precision"; return FRG_EINVAL; }
-  if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS)) {
-    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS";
+  if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL)) {
+    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL";
     return FRG_EINVAL;
   }
   return FRG_OK;
@@ -419,6 +419,8 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
           !(P.Y32X = dalloc<float2>(ctx, 2 * n3 + OPERAND_SLACK)) || !(P.PX = dalloc<float2>(ctx, n3)) ||
           !(P.PW = dalloc<float2>(ctx, n3)))
         return bail(FRG_ENOMEM);
+      // reversal reduction: the pp channel's computed half in its own buffer
+      if ((p.channel_mask & FRG_REVERSAL) && !(P.PN = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
       for (int b = 0; b < 2; ++b)
         if (!(P.yhi[b] = dalloc<float2>(ctx, n3)) || !(P.ylo[b] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
       if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||

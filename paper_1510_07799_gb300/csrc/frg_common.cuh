@@ -39,6 +39,7 @@ struct PointDesc {
   float2 *yhi[2], *ylo[2];  // split paths: vertex part of ybuf[] as float pairs (hi + lo)
   float2 *Y32W, *Y32X;      // split paths: FP32 stage input in the layouts [i2][i3][i1] and [i1][i3][i2]
   float2 *PX, *PW;          // split paths: direct (layout X) and crossed (layout W) channel outputs
+  float2 *PN;               // split paths with the reversal reduction: pp channel output (natural layout)
   unsigned char *kord;      // split paths: per table row, its 16-wide k-chunks by increasing max |Lb| (16 each)
   unsigned *vmax;    // split paths: bits of max |Re|,|Im| over the FP32 vertex input of the current rhs
   // frequency-box tails (null when off): propagators on the window of

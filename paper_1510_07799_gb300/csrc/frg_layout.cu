@@ -83,8 +83,13 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
 // k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
 // (launched for every split-path rhs, also when only pp is enabled), plus the
 // frequency-box tail constants when mask has FRG_TAILS (block 0 of a point also
-// adds the self-energy's).  Every thread issues all 48 of its loads before the
-// first shared-memory pass, so that a block keeps 96 KB of reads in flight.
+// adds the self-energy's).  With FRG_REVERSAL each channel holds only its
+// transfers m <= N - 1 (pp in PN): an entry whose transfer lies beyond takes the
+// conjugate of the channel's value at the mirrored entry (N-1-i1, N-1-i2,
+// N-1-i3); on the self-mirrored transfer m = N - 1 the entry of each mirror pair
+// with the smaller leading index keeps its own value and the other takes its
+// conjugate, so that the result is exactly reversal-symmetric.  Every thread issues all 48 of its loads before the first
+// shared-memory pass, so that a block keeps 96 KB of reads in flight.
 __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                                     int mask) {
   const int pi = blockIdx.y;
@@ -107,24 +112,39 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
   }
   float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
   const float2 z = make_float2(0.f, 0.f);
+  const bool rev = (mask & FRG_REVERSAL) && P.PN;
+  const float2 *__restrict__ src_pp = rev ? P.PN : K;
+  const int M = N - 1;  // mirror: i -> M - i
   float2 vx[16], vw[16], vk[16];
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int n = threadIdx.x + 256 * u;
     {
+      // dph, layout X [a][c][b]; transfer t = c - a computed for t <= 0
       const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
       const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      vx[u] = ((mask & 2) && a < N && b < N && c < N) ? P.PX[((size_t)a * N + c) * N + b] : z;
+      const bool own = !rev || c < a || (c == a && 2 * a < M);
+      const size_t at = own ? ((size_t)a * N + c) * N + b : ((size_t)(M - a) * N + (M - c)) * N + (M - b);
+      vx[u] = ((mask & 2) && a < N && b < N && c < N) ? P.PX[at] : z;
+      if (!own) vx[u].y = -vx[u].y;
     }
     {
+      // xph, layout W [b][c][a]; transfer Q = b - c computed for Q <= 0
       const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
       const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      vw[u] = ((mask & 4) && a < N && b < N && c < N) ? P.PW[((size_t)b * N + c) * N + a] : z;
+      const bool own = !rev || b < c || (b == c && 2 * b < M);
+      const size_t at = own ? ((size_t)b * N + c) * N + a : ((size_t)(M - b) * N + (M - c)) * N + (M - a);
+      vw[u] = ((mask & 4) && a < N && b < N && c < N) ? P.PW[at] : z;
+      if (!own) vw[u].y = -vw[u].y;
     }
     {
+      // pp, natural layout; transfer s = a + b computed for s <= N - 1
       const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
       const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      vk[u] = ((mask & 1) && a < N && b < N && c < N) ? K[((size_t)a * N + b) * N + c] : z;
+      const bool own = !rev || a + b < M || (a + b == M && 2 * a < M);
+      const size_t at = own ? ((size_t)a * N + b) * N + c : ((size_t)(M - a) * N + (M - b)) * N + (M - c);
+      vk[u] = ((mask & 1) && a < N && b < N && c < N) ? src_pp[at] : z;
+      if (!own) vk[u].y = -vk[u].y;
     }
   }
 #pragma unroll

@@ -323,7 +323,7 @@ __device__ __forceinline__ float2 *out_row(const PointDesc &P, float2 *kN, const
   const Geom &g = ti.g;
   if (CH == CH_PP) {
     const int a = g.row_lo + rr;
-    return kN + ((size_t)a * N + (g.x - a)) * N;
+    return (P.PN ? P.PN : kN) + ((size_t)a * N + (g.x - a)) * N;
   } else if (CH == CH_DPH) {
     const int k1 = g.row_lo + rr;
     return P.PX + ((size_t)k1 * N + (k1 + g.x)) * N;
@@ -1284,6 +1284,7 @@ struct TcPlan {
   int nall[3] = {0, 0, 0};
   tc::TcWork *d_pt[3] = {nullptr, nullptr, nullptr};
   std::vector<int> off[3];
+  bool half = false;  // reversal reduction: transfers m <= N - 1 only
   // 3xTF32: one launch for all enabled channels; schedule [0] covers every
   // point, [1 + i] point i alone
   struct Sched {
@@ -1308,7 +1309,7 @@ static bool build_sched(TcPlan *p, const std::vector<PointDesc> &pts, const std:
     const int N = pts[i].N;
     for (int ch = 0; ch < 3; ++ch) {
       if (!(p->mask & (1 << ch))) continue;
-      for (int m = 0; m < 2 * N - 1; ++m) {
+      for (int m = 0; m < (p->half ? N : 2 * N - 1); ++m) {
         const Geom g = geom(ch, N, m);
         const int nk = (ch == CH_DPH ? 2 : 1) * ((g.D + tc::KSTEP - 1) / tc::KSTEP);
         for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
@@ -1453,6 +1454,8 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
     return FRG_EINVAL;
   }
   p->tune = tune;
+  // reversal reduction: transfers m <= N - 1 only (the others by symmetry)
+  p->half = !params.empty() && (params[0].channel_mask & FRG_REVERSAL) != 0;
   std::vector<int> nt(p->n);
   for (int i = 0; i < p->n; ++i) nt[i] = std::min(tune.nt_cap, (pts[i].N + 15) / 16 * 16);
   bool ok = cudaMalloc(&p->d_nt, sizeof(int) * p->n) == cudaSuccess &&
@@ -1464,7 +1467,7 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
     for (int i = 0; i < p->n; ++i) {
       one.clear();
       const int N = pts[i].N;
-      for (int m = 0; m < 2 * N - 1; ++m) {
+      for (int m = 0; m < (p->half ? N : 2 * N - 1); ++m) {
         Geom g = geom(ch, N, m);
         const int nk = (g.K + tc::KSTEP - 1) / tc::KSTEP;
         for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
@@ -1583,7 +1586,8 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   // with the frequency-box tail constants when enabled); also resets the
   // vertex bound that the BF16 slicing read
   if (tails && wait_tails && cudaStreamWaitEvent(st, wait_tails, 0) != cudaSuccess) return -3;
-  if (launch_combine(d_pts, d_io, n_points, maxN, chmask | (tails ? FRG_TAILS : 0), st) != 0) return -3;
+  const int cmask = chmask | (tails ? FRG_TAILS : 0) | (p->half ? FRG_REVERSAL : 0);
+  if (launch_combine(d_pts, d_io, n_points, maxN, cmask, st) != 0) return -3;
   return 0;
 }
 

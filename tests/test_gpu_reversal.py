@@ -1,0 +1,123 @@
+"""GPU parity of the frequency-reversal reduction (channel_mask | FRG_REVERSAL)
+against the FP64 CPU oracle, through the C ABI.
+
+With the bit set the split contraction computes the transfers m <= N - 1 of
+each channel and the scatter-add takes the others from the mirrored entries,
+which is exact for reversal-symmetric states (every flow from the bare
+vertex).  Tolerances are those of the split paths."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_07799_gb300 import frg, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+RHS_TOL = {frg.FP64: 1e-12, frg.TF32X3: 2e-6, frg.BF16X3: 5e-5}
+FLOW_TOL = 1e-6
+REV = frg.REVERSAL
+
+
+def nrel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def model(w):
+    return oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+
+
+def symmetric_state(N, U, seed):
+    V = inputs.random_vertex(N, U, seed=seed)
+    V = 0.5 * (V + np.conj(V[::-1, ::-1, ::-1]))
+    s = inputs.random_sigma(N, seed=seed + 1)
+    return V, 0.5 * (s + np.conj(s[::-1]))
+
+
+def gpu_rhs(ctx, Lam, V, sig):
+    g = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    s = torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+    dg = torch.full_like(g, complex(np.nan, np.nan))
+    ds = torch.full_like(s, complex(np.nan, np.nan))
+    ctx.rhs(0, Lam, g, s, dg, ds)
+    torch.cuda.synchronize()
+    return dg.cpu().numpy(), ds.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [frg.TF32X3, frg.BF16X3, frg.FP64])
+@pytest.mark.parametrize("N", [2, 4, 16, 34, 100])
+@pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4, 0xF | frg.TAILS])
+def test_reversal_rhs_matches_oracle(prec, N, mask):
+    """The reduction adds no error beyond the path's own: within the path's rhs
+    bound of the oracle, or within 1.5x the error of the same path computing
+    every transfer (a channel alone can be a small difference of large terms)."""
+    if N == 100 and prec == frg.FP64:
+        pytest.skip("the FP64 path computes every transfer; covered at smaller N")
+    w = inputs.Workload("t", N=N, U=1.7, T=0.03, eps_d=-0.85 + 0.3)
+    V, sig = symmetric_state(N, w.U, seed=7 * N + mask)
+    with frg.Context([w], precision=prec, channel_mask=mask | REV) as ctx, \
+            frg.Context([w], precision=prec, channel_mask=mask) as full:
+        for Lam in (0.01, 0.4, 7.0):
+            dg, ds = gpu_rhs(ctx, Lam, V, sig)
+            fg, fs = gpu_rhs(full, Lam, V, sig)
+            rg, rs = oracle.rhs(model(w), Lam, V, sig, mask=mask)
+            e, ef = nrel(dg, rg), nrel(fg, rg)
+            assert e < max(RHS_TOL[prec], 1.5 * ef), (Lam, e, ef)
+            assert nrel(ds, rs) < RHS_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [frg.TF32X3, frg.BF16X3])
+def test_reversal_output_is_exactly_symmetric(prec):
+    """Without tails every mirrored entry is the exact conjugate of the
+    computed one (same summation order on both sides)."""
+    N = 34
+    w = inputs.Workload("t", N=N, U=1.7, T=0.03, eps_d=-0.85 + 0.3)
+    V, sig = symmetric_state(N, w.U, seed=3)
+    with frg.Context([w], precision=prec, channel_mask=0xF | REV) as ctx:
+        dg, _ = gpu_rhs(ctx, 0.4, V, sig)
+    assert np.array_equal(dg, np.conj(dg[::-1, ::-1, ::-1]))
+
+
+@pytest.mark.parametrize("name", ["siam_N16_U1_T0.05_ph", "siam_N64_U2_T0.01_asym0.5",
+                                  "siam_N128_U3_T0.005_ph"])
+def test_reversal_flow_matches_oracle_reference(name):
+    with open(os.path.join(HERE, "golden", "oracle_flow_%s.json" % name)) as f:
+        ref = json.load(f)
+    w = inputs.WORKLOADS[name]
+    with frg.Context([w], precision=frg.TF32X3, channel_mask=0xF | REV) as ctx:
+        st = ctx.flow()[0]
+        g, s, _, _ = ctx.get_state(0)
+        obs = ctx.observables(0)
+    assert st.status == 0 and st.done == 1
+    g = g.cpu().numpy()
+    # the state stays exactly reversal-symmetric along the flow
+    assert np.array_equal(g, np.conj(g[::-1, ::-1, ::-1]))
+    idx = np.array(ref["sample_idx"])
+    rv = np.array(ref["sample_re"]) + 1j * np.array(ref["sample_im"])
+    eg = np.max(np.abs(g[idx[:, 0], idx[:, 1], idx[:, 2]] - rv)) / ref["gamma_norm_inf"]
+    rsig = np.array(ref["sigma_re"]) + 1j * np.array(ref["sigma_im"])
+    es = nrel(s.cpu().numpy(), rsig)
+    ru = complex(*ref["observables"]["U_eff"])
+    eu = abs(obs["U_eff"] - ru) / abs(ru)
+    print("reversal flow %s errors gamma %.3e sigma %.3e ueff %.3e evals %d vs %d" % (
+        name, eg, es, eu, st.rhs_evals, ref["stats"]["rhs_evals"]))
+    assert eg < FLOW_TOL and es < FLOW_TOL and eu < FLOW_TOL
+
+
+def test_reversal_in_a_mixed_size_batch_equals_single_point_runs():
+    pts = [inputs.Workload("a", N=16, U=1.2, T=0.04, eps_d=-0.6 + 0.2),
+           inputs.Workload("b", N=34, U=2.0, T=0.03, eps_d=-1.0 - 0.4)]
+    with frg.Context(pts, precision=frg.TF32X3, channel_mask=0xF | REV) as ctx:
+        stb = ctx.advance(4)
+        batched = [ctx.get_state(i)[:2] for i in range(len(pts))]
+    for i, w in enumerate(pts):
+        with frg.Context([w], precision=frg.TF32X3, channel_mask=0xF | REV) as ctx:
+            st = ctx.advance(4)[0]
+            g, s, _, _ = ctx.get_state(0)
+        assert torch.equal(g, batched[i][0]) and torch.equal(s, batched[i][1])
+        assert st.rhs_evals == stb[i].rhs_evals

@@ -501,3 +501,29 @@ def test_tails_keep_the_flow_symmetries():
     assert st.status == 0
     assert np.max(np.abs(gp.imag)) < 1e-14 * np.max(np.abs(gp))
     assert np.max(np.abs(sp.real)) < 1e-15
+
+
+# ------------------------------------------------- frequency reversal ----
+
+@pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4, 0x8, 0xF | TAILS])
+def test_rhs_keeps_the_reversal_symmetry_on_every_entry(mask):
+    """For V(N-1-i1, N-1-i2, N-1-i3) = conj V(i1, i2, i3) and
+    Sigma(N-1-i) = conj Sigma(i) the rhs has the same symmetry, channel by
+    channel, on every stored entry (also those whose fourth index leaves the
+    box): what the library's reversal reduction rests on."""
+    N, U = 10, 1.3
+    m = Model(U=U, T=0.05, eps_d=-U / 2 + 0.4, Delta=1.0, N=N)
+    V = inputs.random_vertex(N, U, seed=31)
+    V = 0.5 * (V + np.conj(V[::-1, ::-1, ::-1]))
+    s = inputs.random_sigma(N, seed=32)
+    s = 0.5 * (s + np.conj(s[::-1]))
+    dg, ds = oracle.rhs(m, 0.3, V, s, mask)
+    if mask & 7:
+        assert rel(dg, np.conj(dg[::-1, ::-1, ::-1])) < 1e-14
+        assert np.max(np.abs(dg)) > 1e-3
+    if mask & 8:
+        assert np.max(np.abs(ds - np.conj(ds[::-1]))) < 1e-14 * max(np.max(np.abs(ds)), 1e-3)
+    # a vertex without the symmetry gives an rhs without it
+    W = inputs.random_vertex(N, U, seed=33)
+    dw, _ = oracle.rhs(m, 0.3, W, s, 0xF)
+    assert rel(dw, np.conj(dw[::-1, ::-1, ::-1])) > 1e-3
