@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
 // with the smaller leading index keeps its own value and the other takes its
 // conjugate, so that the result is exactly reversal-symmetric.  Every thread issues all 48 of its loads before the first
 // shared-memory pass, so that a block keeps 96 KB of reads in flight.
+template <bool REV>
 __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                                     int mask) {
   const int pi = blockIdx.y;
@@ -112,39 +113,55 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
   }
   float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
   const float2 z = make_float2(0.f, 0.f);
-  const bool rev = (mask & FRG_REVERSAL) && P.PN;
-  const float2 *__restrict__ src_pp = rev ? P.PN : K;
+  const float2 *__restrict__ src_pp = REV ? P.PN : K;
   const int M = N - 1;  // mirror: i -> M - i
   float2 vx[16], vw[16], vk[16];
+  // REV: bit u of flip{x,w,k} marks a value taken from the mirrored entry
+  unsigned flipx = 0u, flipw = 0u, flipk = 0u;
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int n = threadIdx.x + 256 * u;
     {
-      // dph, layout X [a][c][b]; transfer t = c - a computed for t <= 0
+      // dph, layout X [a][c][b]; REV: transfer t = c - a computed for t <= 0
       const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
-      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool own = !rev || c < a || (c == a && 2 * a < M);
-      const size_t at = own ? ((size_t)a * N + c) * N + b : ((size_t)(M - a) * N + (M - c)) * N + (M - b);
-      vx[u] = ((mask & 2) && a < N && b < N && c < N) ? P.PX[at] : z;
-      if (!own) vx[u].y = -vx[u].y;
+      int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      const bool ok = (mask & 2) && a < N && b < N && c < N;
+      if (REV && !(c < a || (c == a && 2 * a < M))) {
+        a = M - a, b = M - b, c = M - c;
+        flipx |= 1u << u;
+      }
+      vx[u] = ok ? P.PX[((size_t)a * N + c) * N + b] : z;
     }
     {
-      // xph, layout W [b][c][a]; transfer Q = b - c computed for Q <= 0
+      // xph, layout W [b][c][a]; REV: transfer Q = b - c computed for Q <= 0
       const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
-      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool own = !rev || b < c || (b == c && 2 * b < M);
-      const size_t at = own ? ((size_t)b * N + c) * N + a : ((size_t)(M - b) * N + (M - c)) * N + (M - a);
-      vw[u] = ((mask & 4) && a < N && b < N && c < N) ? P.PW[at] : z;
-      if (!own) vw[u].y = -vw[u].y;
+      int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      const bool ok = (mask & 4) && a < N && b < N && c < N;
+      if (REV && !(b < c || (b == c && 2 * b < M))) {
+        a = M - a, b = M - b, c = M - c;
+        flipw |= 1u << u;
+      }
+      vw[u] = ok ? P.PW[((size_t)b * N + c) * N + a] : z;
     }
     {
-      // pp, natural layout; transfer s = a + b computed for s <= N - 1
+      // pp, natural layout; REV: transfer s = a + b computed for s <= N - 1
       const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
-      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool own = !rev || a + b < M || (a + b == M && 2 * a < M);
-      const size_t at = own ? ((size_t)a * N + b) * N + c : ((size_t)(M - a) * N + (M - b)) * N + (M - c);
-      vk[u] = ((mask & 1) && a < N && b < N && c < N) ? src_pp[at] : z;
-      if (!own) vk[u].y = -vk[u].y;
+      int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
+      const bool ok = (mask & 1) && a < N && b < N && c < N;
+      if (REV && !(a + b < M || (a + b == M && 2 * a < M))) {
+        a = M - a, b = M - b, c = M - c;
+        flipk |= 1u << u;
+      }
+      vk[u] = ok ? src_pp[((size_t)a * N + b) * N + c] : z;
+    }
+  }
+  if (REV) {
+    // mirrored values enter as complex conjugates
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      if (flipx >> u & 1u) vx[u].y = -vx[u].y;
+      if (flipw >> u & 1u) vw[u].y = -vw[u].y;
+      if (flipk >> u & 1u) vk[u].y = -vk[u].y;
     }
   }
 #pragma unroll
@@ -193,7 +210,10 @@ int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int
 }
 
 int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
-  k_combine<<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, mask);
+  if (mask & FRG_REVERSAL)
+    k_combine<true><<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, mask);
+  else
+    k_combine<false><<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, mask);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
