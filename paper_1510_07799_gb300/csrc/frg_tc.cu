@@ -1000,7 +1000,11 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     else xf_right(va, rB, a0, ti.NT);
     xf_right(vb, rB, a1, ti.NT);
     // the raw rows are in registers: hand the raw stage back to the loader
-    // before waiting for a free operand stage
+    // before waiting for a free operand stage.  The loader's next tensor-map
+    // copy into this stage is an async-proxy write: the proxy fence orders
+    // the generic-proxy reads above before it (without it the copy was seen
+    // to overtake them when other kernels shared the SMs)
+    fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.raw_empty[j]);
     if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;

@@ -121,3 +121,28 @@ def test_tails_in_a_mixed_size_batch_equal_single_point_runs():
             g, s, _, _ = ctx.get_state(0)
         assert torch.equal(g, batched[i][0]) and torch.equal(s, batched[i][1])
         assert st.rhs_evals == stb[i].rhs_evals
+
+
+def test_concurrent_tail_kernels_leave_the_contraction_intact():
+    """With the tails the tail kernels share the SMs with the contraction; the
+    rhs must equal the in-order evaluation (frg_rhs_timed, no side stream)
+    bit for bit.  Idle pauses between calls change the relative timing of the
+    two streams (a missing proxy fence once let a tensor-map copy overtake the
+    transform's reads of its raw stage in exactly this setting)."""
+    import time
+    N = 100
+    w = inputs.Workload("t", N=N, U=1.7, T=0.03, eps_d=-0.85 + 0.3)
+    V = inputs.random_vertex(N, w.U, seed=717)
+    sig = inputs.random_sigma(N, seed=718)
+    g = torch.from_numpy(V).cuda()
+    s = torch.from_numpy(sig).cuda()
+    with frg.Context([w], precision=frg.TF32X3, channel_mask=0x1F) as ctx:
+        for Lam in (0.01, 0.4, 7.0, 0.4, 7.0, 0.01):
+            time.sleep(0.7)
+            a, sa = torch.empty_like(g), torch.empty_like(s)
+            b, sb = torch.empty_like(g), torch.empty_like(s)
+            ctx.rhs(0, Lam, g, s, a, sa)
+            torch.cuda.synchronize()
+            ctx.rhs_timed(0, Lam, g, s, b, sb)
+            torch.cuda.synchronize()
+            assert torch.equal(a, b) and torch.equal(sa, sb), Lam
