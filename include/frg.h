@@ -93,6 +93,21 @@ extern "C" {
  */
 #define FRG_REVERSAL 0x20
 
+/*
+ * Cutoff schemes (frg_params.cutoff).  Both regularise the bare propagator as
+ * G0_L = Theta_L G0 and flow in l = ln Lambda from Lambda0 down to Lambda_f:
+ *   FRG_CUTOFF_OMEGA        Theta = w^2 / (w^2 + Lambda^2); Lambda_f -> 0 is
+ *                           the full model.
+ *   FRG_CUTOFF_INTERACTION  the interaction flow: Theta = 1 / sqrt(Lambda),
+ *                           i.e. G0_g = sqrt(g) G0 with g = 1 / Lambda, so that
+ *                           the model at Lambda has the interaction U / Lambda
+ *                           (after rescaling); Lambda = 1 (g = 1) is the full
+ *                           model, Lambda0 = 1 / g0 >> 1 the start at V = U,
+ *                           Sigma = 0.
+ */
+#define FRG_CUTOFF_OMEGA 0
+#define FRG_CUTOFF_INTERACTION 1
+
 typedef struct {
     double U;         /* interaction */
     double T;         /* temperature (> 0) */
@@ -106,7 +121,8 @@ typedef struct {
     double h0;        /* first step in l = ln Lambda (< 0); 0 selects -0.01 */
     long max_steps;   /* step attempts before FRG_ENOTCONV; 0 selects 100000 */
     int precision;    /* FRG_FP64, FRG_3XTF32 or FRG_BF16X3 */
-    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS; 0 selects FRG_CH_ALL */
+    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS | FRG_REVERSAL; 0 selects FRG_CH_ALL */
+    int cutoff;       /* FRG_CUTOFF_OMEGA (default) or FRG_CUTOFF_INTERACTION */
 } frg_params;
 
 typedef struct frg_ctx frg_ctx;

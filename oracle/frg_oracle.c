@@ -15,9 +15,12 @@
  * in the paper; the reading used here is:
  *
  *   G0^{-1}(iw) = iw - et + i Delta sgn(w),  et = eps_d + U/2  (Hartree U/2 absorbed)
- *   Theta_L(w)  = w^2 / (w^2 + L^2)
+ *   Theta_L(w)  = w^2 / (w^2 + L^2)          (Omega scheme)
+ *   Theta_L     = 1 / sqrt(L)                (interaction flow, cutoff = 1: the bare
+ *                 propagator sqrt(g) G0 with g = 1/L; L = 1 is the full model)
  *   G_L(w)      = 1 / (Theta^{-1} G0^{-1} - Sigma)
- *   S_L(w)      = dG/dL at fixed Sigma = -G^2 (2L/w^2) G0^{-1}
+ *   S_L(w)      = dG/dL at fixed Sigma = -G^2 (d Theta^{-1}/dL) G0^{-1}
+ *               (Omega: -G^2 (2L/w^2) G0^{-1}; interaction flow: -G^2 G0^{-1} / (2 sqrt L))
  *   Lb(a,b)     = S(a) G(b) + G(a) S(b)                      (bubble weight)
  *
  * V(k1,k2,k3) is the up-down vertex (k1 up-in, k2 down-in, k3 up-out,
@@ -70,6 +73,7 @@ typedef double complex cplx;
 typedef struct {
     double U, T, eps_d, Delta;
     int N;
+    int cutoff;  /* 0: Omega scheme; 1: interaction flow */
 } oracle_model;
 
 #define TAIL_FACTOR 16   /* window of the internal sums with mask bit 4: 16 N indices */
@@ -94,11 +98,12 @@ static cplx g0inv(const oracle_model *m, int i)
 static void propagator_at(const oracle_model *m, double L, int i, cplx sg, cplx *g_out, cplx *s_out)
 {
     double w = w_of(m, i);
-    double thinv = 1.0 + (L * L) / (w * w);
+    double thinv = m->cutoff ? sqrt(L) : 1.0 + (L * L) / (w * w);
+    double dthinv = m->cutoff ? 0.5 / sqrt(L) : 2.0 * L / (w * w);
     cplx gi = g0inv(m, i);
     cplx g = 1.0 / (thinv * gi - sg);
     *g_out = g;
-    *s_out = -g * g * (2.0 * L / (w * w)) * gi;
+    *s_out = -g * g * dthinv * gi;
 }
 
 /* G_L and S_L for every in-box frequency. sigma may be NULL (Sigma = 0). */
@@ -107,12 +112,13 @@ static void propagators(const oracle_model *m, double L, const cplx *sigma,
 {
     for (int i = 0; i < m->N; ++i) {
         double w = w_of(m, i);
-        double thinv = 1.0 + (L * L) / (w * w);
+        double thinv = m->cutoff ? sqrt(L) : 1.0 + (L * L) / (w * w);
+        double dthinv = m->cutoff ? 0.5 / sqrt(L) : 2.0 * L / (w * w);
         cplx gi = g0inv(m, i);
         cplx sg = sigma ? sigma[i] : 0.0;
         cplx g = 1.0 / (thinv * gi - sg);
         G[i] = g;
-        S[i] = -g * g * (2.0 * L / (w * w)) * gi;
+        S[i] = -g * g * dthinv * gi;
     }
 }
 

@@ -22,7 +22,7 @@ TAIL_FACTOR = 16
 
 class _Model(C.Structure):
     _fields_ = [("U", C.c_double), ("T", C.c_double), ("eps_d", C.c_double),
-                ("Delta", C.c_double), ("N", C.c_int)]
+                ("Delta", C.c_double), ("N", C.c_int), ("cutoff", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -65,15 +65,17 @@ def _load():
 @dataclasses.dataclass(frozen=True)
 class Model:
     """SIAM parameters: interaction U, temperature T, level eps_d,
-    hybridisation Delta, N fermionic frequencies per axis (N even)."""
+    hybridisation Delta, N fermionic frequencies per axis (N even); cutoff 0
+    for the Omega scheme, 1 for the interaction flow."""
     U: float
     T: float
     eps_d: float
     Delta: float
     N: int
+    cutoff: int = 0
 
     def c(self):
-        return _Model(self.U, self.T, self.eps_d, self.Delta, self.N)
+        return _Model(self.U, self.T, self.eps_d, self.Delta, self.N, self.cutoff)
 
 
 def _dp(a):

@@ -135,6 +135,7 @@ int validate(const frg_params &p, std::string &why) {
   if (!std::isfinite(p.U) || !std::isfinite(p.eps_d)) { why = "U and eps_d must be finite"; return FRG_EINVAL; }
   if (p.h0 > 0.0) { why = "h0 must be <= 0 (the flow runs towards small Lambda)"; return FRG_EINVAL; }
   if (p.precision < FRG_FP64 || p.precision > FRG_BF16X3) { why = "unknown precision"; return FRG_EINVAL; }
+  if (p.cutoff != FRG_CUTOFF_OMEGA && p.cutoff != FRG_CUTOFF_INTERACTION) { why = "unknown cutoff"; return FRG_EINVAL; }
   if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL)) {
     why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL";
     return FRG_EINVAL;
@@ -395,6 +396,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     const size_t n3 = (size_t)N * N * N, nc = n3 + N;
     P.N = N;
     P.n3 = (int)n3;
+    P.cutoff = p.cutoff;
     P.U = p.U;
     P.T = p.T;
     P.et = p.eps_d + 0.5 * p.U;
@@ -914,7 +916,7 @@ int frg_observables(frg_ctx *ctx, int point, frg_obs *out) {
   double n = 0.5;
   for (int i = 0; i < N; ++i) {
     const double w = (2.0 * (i - hN) + 1.0) * M_PI * T;
-    const double thinv = 1.0 + L * L / (w * w);
+    const double thinv = P.cutoff ? std::sqrt(L) : 1.0 + L * L / (w * w);
     const double dr = -thinv * P.et - sig[i].x;
     const double di = thinv * (w + (w > 0 ? P.Delta : -P.Delta)) - sig[i].y;
     n += T * dr / (dr * dr + di * di);  // Re of 1/(dr + i di)

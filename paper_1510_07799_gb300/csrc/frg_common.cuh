@@ -22,6 +22,7 @@ enum Channel { CH_PP = 0, CH_DPH = 1, CH_XPH = 2 };
 struct PointDesc {
   int N;
   int n3;                 // N^3
+  int cutoff;             // FRG_CUTOFF_OMEGA (0) or FRG_CUTOFF_INTERACTION (1)
   double U, T, et, Delta; // et = eps_d + U/2
   double l0, l_end;       // ln Lambda0, ln Lambda_f
   double rtol, atol, h0;
@@ -155,17 +156,19 @@ __device__ __forceinline__ bool fourth_in_box(int i, int N) {
 }
 
 // Propagators at frequency index i (any integer) and scale L with self-energy
-// sg (Omega scheme): G = 1/(Theta^{-1} G0^{-1} - Sigma), Theta^{-1} = 1 + L^2/w^2,
-// S = -G^2 (2L/w^2) G0^{-1}, G0^{-1} = iw - et + i Delta sgn w.
+// sg: G = 1/(Theta^{-1} G0^{-1} - Sigma), S = dG/dL at fixed Sigma
+// = -G^2 (d Theta^{-1}/dL) G0^{-1}, G0^{-1} = iw - et + i Delta sgn w, with
+// Theta^{-1} = 1 + L^2/w^2 (Omega scheme) or sqrt(L) (interaction flow).
 __device__ __forceinline__ void propagator_at(const PointDesc &P, int i, double L, double2 sg, double2 &g,
                                               double2 &s) {
   const double w = (2.0 * (double)(i - P.N / 2) + 1.0) * M_PI * P.T;
-  const double thinv = 1.0 + (L * L) / (w * w);
+  const double rl = P.cutoff ? sqrt(L) : 0.0;
+  const double thinv = P.cutoff ? rl : 1.0 + (L * L) / (w * w);
   const double2 gi = make_double2(-P.et, w + (w > 0.0 ? P.Delta : -P.Delta));
   const double2 den = make_double2(thinv * gi.x - sg.x, thinv * gi.y - sg.y);
   const double nrm = den.x * den.x + den.y * den.y;
   g = make_double2(den.x / nrm, -den.y / nrm);
-  s = cscale(cmul(cmul(g, g), gi), -2.0 * L / (w * w));
+  s = cscale(cmul(cmul(g, g), gi), P.cutoff ? -0.5 / rl : -2.0 * L / (w * w));
 }
 
 // Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).

@@ -97,6 +97,7 @@ extern "C" int frg_rhs_noalloc(const frg_params *p, double Lambda, const void *d
     return FRG_EINVAL;
   const int mask = p->channel_mask == 0 ? FRG_CH_ALL : p->channel_mask;
   if (mask < 0 || mask > 0xF) return FRG_EINVAL;
+  if (p->cutoff != FRG_CUTOFF_OMEGA && p->cutoff != FRG_CUTOFF_INTERACTION) return FRG_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return FRG_ECUDA;
   unsigned char *base;
@@ -113,6 +114,7 @@ extern "C" int frg_rhs_noalloc(const frg_params *p, double Lambda, const void *d
   PointDesc pd = {};
   pd.N = N;
   pd.n3 = N * N * N;
+  pd.cutoff = p->cutoff;
   pd.U = p->U;
   pd.T = p->T;
   pd.et = p->eps_d + 0.5 * p->U;

@@ -19,6 +19,7 @@ PRECISIONS = {"fp64": FP64, "3xtf32": TF32X3, "bf16x3": BF16X3}
 CH_PP, CH_DPH, CH_XPH, CH_SIGMA, CH_ALL = 0x1, 0x2, 0x4, 0x8, 0xF
 TAILS, TAIL_FACTOR = 0x10, 16  # frequency-box tails option of channel_mask (FRG_TAILS)
 REVERSAL = 0x20  # frequency-reversal reduction for reversal-symmetric states (FRG_REVERSAL)
+CUTOFF_OMEGA, CUTOFF_INTERACTION = 0, 1  # frg_params.cutoff
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOTCONV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 ERRNAMES = {EINVAL: "FRG_EINVAL", ENOMEM: "FRG_ENOMEM", ECUDA: "FRG_ECUDA",
@@ -41,7 +42,7 @@ class _Params(C.Structure):
                 ("Delta", C.c_double), ("N_f", C.c_int), ("Lambda0", C.c_double),
                 ("Lambda_f", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
                 ("h0", C.c_double), ("max_steps", C.c_long), ("precision", C.c_int),
-                ("channel_mask", C.c_int)]
+                ("channel_mask", C.c_int), ("cutoff", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -74,11 +75,12 @@ class Params:
     atol: float = 1e-10
     h0: float = -0.01
     max_steps: int = 100000
+    cutoff: int = 0  # CUTOFF_OMEGA or CUTOFF_INTERACTION
 
     @classmethod
     def from_workload(cls, w):
         return cls(U=w.U, T=w.T, eps_d=w.eps_d, N_f=w.N, Delta=w.Delta, Lambda0=w.Lambda0,
-                   Lambda_f=w.Lambda_f, rtol=w.rtol, atol=w.atol)
+                   Lambda_f=w.Lambda_f, rtol=w.rtol, atol=w.atol, cutoff=getattr(w, "cutoff", 0))
 
 
 @dataclasses.dataclass
@@ -150,7 +152,7 @@ def rhs_noalloc(params, Lambda, gamma, sigma, dgamma, dsigma, channel_mask=CH_AL
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     cp = _Params(p.U, p.T, p.eps_d, p.Delta, p.N_f, p.Lambda0, p.Lambda_f, p.rtol, p.atol, p.h0,
-                 p.max_steps, FP64, channel_mask)
+                 p.max_steps, FP64, channel_mask, getattr(p, "cutoff", 0))
     rc = lib.frg_rhs_noalloc(C.byref(cp), Lambda, _ptr(gamma), _ptr(sigma), _ptr(dgamma),
                              _ptr(dsigma), C.c_void_p(stream))
     if rc != OK:
@@ -184,7 +186,7 @@ class Context:
         arr = (_Params * len(pts))()
         for i, p in enumerate(pts):
             arr[i] = _Params(p.U, p.T, p.eps_d, p.Delta, p.N_f, p.Lambda0, p.Lambda_f, p.rtol,
-                             p.atol, p.h0, p.max_steps, precision, channel_mask)
+                             p.atol, p.h0, p.max_steps, precision, channel_mask, p.cutoff)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream

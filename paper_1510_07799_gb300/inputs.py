@@ -27,6 +27,7 @@ class Workload:
     Lambda_f: float = 1e-3
     rtol: float = 1e-8
     atol: float = 1e-10
+    cutoff: int = 0  # 0: Omega scheme; 1: interaction flow (Lambda = 1/g from Lambda0 down to 1)
 
 
 # Plain FP64 single flow, particle-hole symmetric.
@@ -43,7 +44,15 @@ SIAM_N256 = Workload("siam_N256_U3_T0.002_asym0.25", N=256, U=3.0, T=0.002,
 # frequency-box tail option (whose self-energy tail vanishes at ph symmetry).
 SIAM_N16_ASYM = Workload("siam_N16_U1_T0.05_asym0.3", N=16, U=1.0, T=0.05, eps_d=-0.5 + 0.3)
 
-WORKLOADS = {w.name: w for w in (SIAM_N16, SIAM_N64, SIAM_N128, SIAM_N256, SIAM_N16_ASYM)}
+# Interaction flow (cutoff 1): Lambda = 1/g from 1e12 down to 1, the full model;
+# off particle-hole symmetry.
+SIAM_N16_IFLOW = Workload("siam_N16_U1_T0.05_asym0.3_iflow", N=16, U=1.0, T=0.05, eps_d=-0.5 + 0.3,
+                          Lambda0=1e12, Lambda_f=1.0, cutoff=1)
+SIAM_N64_IFLOW = Workload("siam_N64_U2_T0.01_asym0.5_iflow", N=64, U=2.0, T=0.01, eps_d=-1.0 + 0.5,
+                          Lambda0=1e12, Lambda_f=1.0, cutoff=1)
+
+WORKLOADS = {w.name: w for w in (SIAM_N16, SIAM_N64, SIAM_N128, SIAM_N256, SIAM_N16_ASYM, SIAM_N16_IFLOW,
+                                 SIAM_N64_IFLOW)}
 
 BATCH_SEED = 1510077
 BATCH_SIZES = (32, 48, 64, 96)

@@ -13,9 +13,11 @@ def freqs(N, T):
     return (2 * n + 1) * np.pi * T
 
 
-def g_free(N, T, et, Delta, Lam):
+def g_free(N, T, et, Delta, Lam, cutoff=0):
+    """Free propagator; cutoff 0: Omega scheme, 1: interaction flow
+    (Theta = 1/sqrt(Lambda), Lambda = 1/g)."""
     w = freqs(N, T)
-    th = w ** 2 / (w ** 2 + Lam ** 2)
+    th = 1.0 / np.sqrt(Lam) if cutoff else w ** 2 / (w ** 2 + Lam ** 2)
     return th / (1j * w - et + 1j * Delta * np.sign(w))
 
 
@@ -50,18 +52,18 @@ def transfer_indices(N):
     return s, Q
 
 
-def second_order_vertex(N, T, et, Delta, U, Lam0, Lamf):
-    G0 = g_free(N, T, et, Delta, Lam0)
-    G1 = g_free(N, T, et, Delta, Lamf)
+def second_order_vertex(N, T, et, Delta, U, Lam0, Lamf, cutoff=0):
+    G0 = g_free(N, T, et, Delta, Lam0, cutoff)
+    G1 = g_free(N, T, et, Delta, Lamf, cutoff)
     dBpp = bubble_pp(G1, T) - bubble_pp(G0, T)
     dBph = bubble_ph(G1, T) - bubble_ph(G0, T)
     s, Q = transfer_indices(N)
     return U - U ** 2 * dBpp[s] - U ** 2 * dBph[Q], dBpp[s], dBph[Q]
 
 
-def first_order_sigma(N, T, et, Delta, U, Lam0, Lamf):
-    G0 = g_free(N, T, et, Delta, Lam0)
-    G1 = g_free(N, T, et, Delta, Lamf)
+def first_order_sigma(N, T, et, Delta, U, Lam0, Lamf, cutoff=0):
+    G0 = g_free(N, T, et, Delta, Lam0, cutoff)
+    G1 = g_free(N, T, et, Delta, Lamf, cutoff)
     return np.full(N, U * T * np.sum(G1 - G0), np.complex128)
 
 

@@ -42,7 +42,7 @@ def main():
     count = int(sys.argv[2]) if len(sys.argv) > 2 else 2048
     mask = int(sys.argv[3], 16) if len(sys.argv) > 3 else 0xF
     w = inputs.WORKLOADS[name]
-    m = oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+    m = oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N, cutoff=w.cutoff)
     t0 = time.time()
     g, s, st = oracle.flow(m, Lambda0=w.Lambda0, Lambda_f=w.Lambda_f, rtol=w.rtol,
                            atol=w.atol, mask=mask)
@@ -58,7 +58,7 @@ def main():
         "what": "oracle FP64 flow from Lambda0 to Lambda_f; sampled final vertex",
         "params": {"N": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d, "Delta": w.Delta,
                    "Lambda0": w.Lambda0, "Lambda_f": w.Lambda_f, "rtol": w.rtol,
-                   "atol": w.atol},
+                   "atol": w.atol, "cutoff": w.cutoff},
         "stats": {"accepted": st.accepted, "rejected": st.rejected,
                   "rhs_evals": st.rhs_evals, "first_step_evals": st.first_step_evals,
                   "wall_s": wall, "threads": oracle.max_threads()},

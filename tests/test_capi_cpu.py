@@ -49,7 +49,7 @@ def test_library_is_sm103a(lib):
 
 def _params(**kw):
     d = dict(U=1.0, T=0.05, eps_d=-0.5, Delta=1.0, N_f=16, Lambda0=1e3, Lambda_f=1e-3,
-             rtol=1e-8, atol=1e-10, h0=-0.01, max_steps=1000, precision=0, channel_mask=0xF)
+             rtol=1e-8, atol=1e-10, h0=-0.01, max_steps=1000, precision=0, channel_mask=0xF, cutoff=0)
     d.update(kw)
     return frg._Params(**d)
 
@@ -57,7 +57,7 @@ def _params(**kw):
 @pytest.mark.parametrize("bad", [dict(N_f=15), dict(N_f=0), dict(N_f=258), dict(T=0.0),
                                  dict(T=-1.0), dict(Delta=0.0), dict(rtol=0.0),
                                  dict(Lambda_f=2e3), dict(Lambda_f=0.0), dict(h0=0.5),
-                                 dict(precision=7), dict(channel_mask=0x40), dict(channel_mask=-1),
+                                 dict(precision=7), dict(channel_mask=0x40), dict(channel_mask=-1), dict(cutoff=2),
                                  dict(U=float("nan"))])
 def test_init_rejects_invalid_parameters_without_device(lib, bad):
     arr = (frg._Params * 1)(_params(**bad))

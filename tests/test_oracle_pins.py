@@ -527,3 +527,88 @@ def test_rhs_keeps_the_reversal_symmetry_on_every_entry(mask):
     W = inputs.random_vertex(N, U, seed=33)
     dw, _ = oracle.rhs(m, 0.3, W, s, 0xF)
     assert rel(dw, np.conj(dw[::-1, ::-1, ::-1])) > 1e-3
+
+
+# ------------------------------------------------------ interaction flow ----
+# cutoff = 1: Theta = 1/sqrt(Lambda) (the bare propagator sqrt(g) G0, g = 1/Lambda),
+# flowing from Lambda0 = 1/g0 >> 1 down to Lambda = 1, the full model.
+IF_L0, IF_LF = 1e12, 1.0
+
+
+@pytest.mark.parametrize("Lam", [1e6, 40.0, 1.0, 0.3])
+def test_interaction_flow_single_scale_is_scale_derivative(Lam):
+    m = Model(U=1.5, T=0.04, eps_d=-0.2, Delta=1.0, N=12, cutoff=1)
+    sig = inputs.random_sigma(m.N, seed=13, amp=0.2)
+    G, S = oracle.propagators(m, Lam, sig)
+    h = 1e-5 * Lam
+    Gp, _ = oracle.propagators(m, Lam + h, sig)
+    Gm, _ = oracle.propagators(m, Lam - h, sig)
+    assert rel(S, (Gp - Gm) / (2 * h)) < 1e-8
+    # at Lambda = 1 the regulated propagator is the full one
+    if Lam == 1.0:
+        w = cf.freqs(m.N, m.T)
+        full = 1.0 / (1j * w - (m.eps_d + m.U / 2) + 1j * m.Delta * np.sign(w) - sig)
+        assert rel(G, full) < 1e-14
+
+
+@pytest.mark.parametrize("eps_shift", [0.0, 0.6])
+def test_interaction_flow_second_order_perturbation_theory(eps_shift):
+    N, T, D = 8, 0.05, 1.0
+    devs, sdevs = [], []
+    for U in [0.04, 0.02, 0.01]:
+        m = Model(U=U, T=T, eps_d=-U / 2 + eps_shift, Delta=D, N=N, cutoff=1)
+        g, s, st = oracle.flow(m, Lambda0=IF_L0, Lambda_f=IF_LF, rtol=1e-12, atol=1e-16)
+        assert st.status == 0
+        ref, _, _ = cf.second_order_vertex(N, T, eps_shift, D, U, IF_L0, IF_LF, cutoff=1)
+        sref = cf.first_order_sigma(N, T, eps_shift, D, U, IF_L0, IF_LF, cutoff=1)
+        devs.append(np.max(np.abs(g - ref)))
+        sdevs.append(np.max(np.abs(s - sref)))
+    _, dBpp, dBph = cf.second_order_vertex(N, T, eps_shift, D, 1.0, IF_L0, IF_LF, cutoff=1)
+    assert np.max(np.abs(dBpp)) > 1e-2 and np.max(np.abs(dBph)) > 1e-2
+    for a, b in zip(devs, devs[1:]):
+        assert 6.5 < a / b < 9.5, devs
+    if eps_shift != 0.0:
+        for a, b in zip(sdevs, sdevs[1:]):
+            assert 3.2 < a / b < 4.8, sdevs
+
+
+def test_interaction_flow_pp_ladder_closed_form():
+    N, T, D, U = 10, 0.05, 1.0, 2.5
+    m = Model(U=U, T=T, eps_d=-U / 2 + 0.4, Delta=D, N=N, cutoff=1)
+    g, s, st = oracle.flow(m, mask=0x1, Lambda0=IF_L0, Lambda_f=IF_LF, rtol=1e-11, atol=1e-14)
+    assert st.status == 0 and np.max(np.abs(s)) == 0.0
+    _, dBpp, _ = cf.second_order_vertex(N, T, 0.4, D, 1.0, IF_L0, IF_LF, cutoff=1)
+    ref = U / (1 + U * dBpp)
+    mk = _aib(N)
+    assert rel(g[mk], ref[mk]) < 2e-8
+    assert rel(ref[mk], U) > 0.05
+
+
+def test_interaction_and_omega_schemes_agree_to_second_order():
+    """Both cutoffs end at the full propagator, so their final vertex and
+    self-energy coincide through O(U^2) (perturbation theory does not know the
+    regulator); the one-loop truncation makes them differ at O(U^3)."""
+    dg, ds = [], []
+    for U in [0.5, 0.25, 0.125]:
+        kw = dict(U=U, T=0.05, eps_d=-U / 2 + 0.3, Delta=1.0, N=8)
+        gi, si, st1 = oracle.flow(Model(cutoff=1, **kw), Lambda0=IF_L0, Lambda_f=IF_LF, rtol=1e-11, atol=1e-15)
+        go, so, st2 = oracle.flow(Model(cutoff=0, **kw), Lambda0=1e8, Lambda_f=1e-8, rtol=1e-11, atol=1e-15)
+        assert st1.status == 0 and st2.status == 0
+        dg.append(np.max(np.abs(gi - go)))
+        ds.append(np.max(np.abs(si - so)))
+        assert np.max(np.abs(gi - U)) > 20 * dg[-1]  # the vertex did flow
+    for a, b in zip(dg, dg[1:]):
+        assert 6.5 < a / b < 9.5, dg
+    for a, b in zip(ds, ds[1:]):
+        assert 6.0 < a / b < 10.0, ds
+
+
+def test_interaction_flow_rhs_matches_spin_resolved_general_formula():
+    N, U, T, Lam = 6, 1.3, 0.07, 3.7
+    m = Model(U=U, T=T, eps_d=-U / 2 + 0.4, Delta=1.0, N=N, cutoff=1)
+    V = inputs.random_vertex(N, U, seed=41, amp=0.4)
+    sig = inputs.random_sigma(N, seed=42, amp=0.15)
+    dg, ds = oracle.rhs(m, Lam, V, sig)
+    G, S = oracle.propagators(m, Lam, sig)
+    dgb, dsb = bf.reduced_from_general(V, U, G, S, T, Lam)
+    assert rel(dg, dgb) < 1e-13 and rel(ds, dsb) < 1e-13
