@@ -24,6 +24,10 @@ headline):
   siam_N64   full flows per second at N_f = 64 (off particle-hole symmetry):
              the plain FP64 GPU path and the 3xTF32 path, next to the oracle's
              flow on the host cores (one flow, --no-oracle skips it)
+  siam_N64_iflow  the same with the interaction-flow cutoff (Lambda = 1/g from
+             1e12 down to the full model at 1)
+Options of the headline workload: --tails (frequency-box tails), --reversal
+(frequency-reversal reduction).
 """
 import argparse
 import json
@@ -522,7 +526,7 @@ def run_n64(args):
     from paper_1510_07799_gb300 import build as cuda_build
     cuda_build.build()
     from paper_1510_07799_gb300 import frg, inputs
-    w = inputs.SIAM_N64
+    w = inputs.SIAM_N64_IFLOW if args.workload == "siam_N64_iflow" else inputs.SIAM_N64
     res = {}
     finals = {}
     for prec in ("fp64", "3xtf32"):
@@ -541,12 +545,14 @@ def run_n64(args):
                 finals[prec] = g.cpu().numpy()
         t = sum(times) / len(times)
         res[prec] = {"flows_per_s": 1.0 / t, "rhs_evals_per_s": evals[-1] / t, "rhs_evals": evals[-1]}
-    line = {"metric": "full flows/s at N_f=64 (off particle-hole symmetry)", "value": res["fp64"]["flows_per_s"],
+    scheme = "interaction flow, Lambda = 1/g 1e12 -> 1" if w.cutoff else "Omega scheme, Lambda 1e3 -> 1e-3"
+    line = {"metric": "full flows/s at N_f=64 (off particle-hole symmetry%s)" % (", interaction flow" if w.cutoff else ""),
+            "value": res["fp64"]["flows_per_s"],
             "unit": "flows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / res["fp64"]["flows_per_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "N_f": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
-                       "step": "one full flow (Lambda 1e3 -> 1e-3, rtol 1e-8)"},
+                       "cutoff": w.cutoff, "step": "one full flow (%s, rtol 1e-8)" % scheme},
             "fp64_gpu": res["fp64"], "tf32x3_gpu": res["3xtf32"],
             "tf32x3_vs_fp64_gamma": float(np.max(np.abs(finals["3xtf32"] - finals["fp64"]))
                                           / np.max(np.abs(finals["fp64"])))}
@@ -554,9 +560,9 @@ def run_n64(args):
         import oracle as orc
         from oracle import build as oracle_build
         oracle_build.build()
-        m = orc.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
+        m = orc.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N, cutoff=w.cutoff)
         t0 = time.perf_counter()
-        g0, _, st0 = orc.flow(m)
+        g0, _, st0 = orc.flow(m, Lambda0=w.Lambda0, Lambda_f=w.Lambda_f, rtol=w.rtol, atol=w.atol)
         dt = time.perf_counter() - t0
         line["oracle_cpu"] = {"flows_per_s": 1.0 / dt, "rhs_evals_per_s": st0.rhs_evals / dt,
                               "rhs_evals": int(st0.rhs_evals), "cores": orc.max_threads(), "kind": "oracle",
@@ -577,7 +583,8 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="siam_N128", choices=["siam_N128", "batch64", "siam_N256", "siam_N64"])
+    ap.add_argument("--workload", default="siam_N128",
+                    choices=["siam_N128", "batch64", "siam_N256", "siam_N64", "siam_N64_iflow"])
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--tails", action="store_true",
@@ -597,7 +604,7 @@ def main():
         return run_batch(args)
     if args.workload == "siam_N256":
         return run_n256(args)
-    if args.workload == "siam_N64":
+    if args.workload in ("siam_N64", "siam_N64_iflow"):
         return run_n64(args)
     return run_ours(args)
 
