@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict
         float sr = 0.f, srl = 0.f, si = 0.f, sil = 0.f;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
+          if (S == 6 && j == 1) continue;  // the fifth-order weight of k2 is zero: no read
           const float2 k = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
           ff_mac(sr, srl, fAh[S][j], fAl[S][j], k.x);
           ff_mac(si, sil, fAh[S][j], fAl[S][j], k.y);
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict
       float er = 0.f, erl = 0.f, ei = 0.f, eil = 0.f;
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
+        if (j == 1) continue;  // b2 = bstar2 = 0: no read
         const float2 k = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
         ff_mac(er, erl, fEh[j], fEl[j], k.x);
         ff_mac(ei, eil, fEh[j], fEl[j], k.y);
