@@ -183,16 +183,14 @@ __device__ __forceinline__ void block_max_to(float v, unsigned *dst) {
 }
 
 // ---------------------------------------------------------- stage sums ----
-// Y_s = y + h sum_{j<s} a_sj k_j, FP64.  Stage 6 (the seventh) is the fifth-order
-// candidate and is also kept in FP64 as ynew.  Split paths: the vertex part of
-// Y_s is stored rounded to FP32 for the contraction, the self-energy part in FP64.
-template <bool SPLIT>
+// Y_s = y + h sum_{j<s} a_sj k_j, FP64 path.  Stage 6 (the seventh) is the
+// fifth-order candidate, kept as ynew.  (The split paths use k_stage_split.)
 __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
                                                SegTable seg, int s, RhsIO *__restrict__ io) {
   const int b = blockIdx.x;
   const int pi = seg.point[b];
   // the first block of the point also writes the stage's rhs IO record
-  if (io && seg.base[b] == 0 && threadIdx.x == 0) write_stage_io(pts[pi], ctl[pi], io + pi, s, SPLIT);
+  if (io && seg.base[b] == 0 && threadIdx.x == 0) write_stage_io(pts[pi], ctl[pi], io + pi, s, 0);
   const Ctl &c = ctl[pi];
   if (c.done) return;
   const PointDesc &P = pts[pi];
@@ -204,55 +202,25 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
   double a[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) a[j] = dA[s][j];
-  float vm = 0.f;
   for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
     const int i = base + e;
     if (i >= n) break;
     double2 acc = make_double2(0.0, 0.0);
-    if (i < n3) {
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (j < s) {
-          double2 k;
-          if (SPLIT) {
-            float2 kf = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
-            k = make_double2((double)kf.x, (double)kf.y);
-          } else {
-            k = static_cast<const double2 *>(P.kG[c.kslot[j]])[i];
-          }
-          acc.x += a[j] * k.x;
-          acc.y += a[j] * k.y;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (j < s) {
-          const double2 k = P.kS[c.kslot[j]][i - n3];
-          acc.x += a[j] * k.x;
-          acc.y += a[j] * k.y;
-        }
+    for (int j = 0; j < 6; ++j) {
+      if (j < s) {
+        const double2 k = i < n3 ? static_cast<const double2 *>(P.kG[c.kslot[j]])[i] : P.kS[c.kslot[j]][i - n3];
+        acc.x += a[j] * k.x;
+        acc.y += a[j] * k.y;
       }
     }
     const double2 yi = y[i];
     const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
-    if (SPLIT) {
-      if (i < n3) {
-        const float2 f = round_c64(Y);
-        P.Y32[i] = fourth_in_box(i, P.N) ? f : make_float2((float)P.U, 0.f);
-        vm = fmaxf(vm, fmaxf(fabsf(f.x), fabsf(f.y)));
-      } else {
-        P.Y64[i - n3] = Y;
-      }
-      if (s == 6) ynew[i] = Y;
-    } else {
-      if (s < 6)
-        P.Y64[i] = Y;
-      else
-        ynew[i] = Y;
-    }
+    if (s < 6)
+      P.Y64[i] = Y;
+    else
+      ynew[i] = Y;
   }
-  if (SPLIT) block_max_to(vm, P.vmax);
 }
 
 // ------------------------------------------------- split-path stages ----
@@ -442,7 +410,7 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-template <bool SPLIT>
+// Error norm of the FP64 path (the split paths use k_error_split).
 __global__ void __launch_bounds__(256) k_error(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
                                                SegTable seg) {
   const int b = blockIdx.x;
@@ -463,17 +431,7 @@ __global__ void __launch_bounds__(256) k_error(const PointDesc *__restrict__ pts
     double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
-      double2 k;
-      if (i < n3) {
-        if (SPLIT) {
-          float2 kf = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
-          k = make_double2((double)kf.x, (double)kf.y);
-        } else {
-          k = static_cast<const double2 *>(P.kG[c.kslot[j]])[i];
-        }
-      } else {
-        k = P.kS[c.kslot[j]][i - n3];
-      }
+      const double2 k = i < n3 ? static_cast<const double2 *>(P.kG[c.kslot[j]])[i] : P.kS[c.kslot[j]][i - n3];
       acc.x += dE[j] * k.x;
       acc.y += dE[j] * k.y;
     }
@@ -593,7 +551,7 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
       default: k_stage_split<6><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
     }
   } else {
-    k_stage<false><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);
+    k_stage<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);
   }
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
@@ -603,7 +561,7 @@ int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
   if (split)
     k_error_split<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
   else
-    k_error<false><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
+    k_error<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
