@@ -6,6 +6,8 @@ Runs `repeats` rhs evaluations (default 2) of a seeded vertex at N (default
 last one; with a fourth argument `steps` > 0 it then advances a flow of the
 same workload by that many Dormand-Prince step attempts (one captured graph
 per step), so that a launch list shows the kernels of the flow step.
+With N = batch64 it advances the 64-point batch context by `steps` attempts
+(no single-point evaluations) and prints the time of the last 10.
 """
 import sys
 
@@ -14,8 +16,25 @@ import torch
 from . import build, frg, inputs
 
 
+def batch(prec, steps):
+    build.build()
+    ctx = frg.Context(inputs.batch_points(), precision=prec)
+    ctx.advance(max(steps - 10, 0))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.advance(min(steps, 10))
+    e1.record()
+    torch.cuda.synchronize()
+    print("batch64: %d step attempts in %.3f ms" % (min(steps, 10), e0.elapsed_time(e1)))
+    ctx.close()
+
+
 def main():
     prec = sys.argv[1] if len(sys.argv) > 1 else "3xtf32"
+    if len(sys.argv) > 2 and sys.argv[2] == "batch64":
+        batch(prec, int(sys.argv[4]) if len(sys.argv) > 4 else 14)
+        return
     N = int(sys.argv[2]) if len(sys.argv) > 2 else 128
     reps = int(sys.argv[3]) if len(sys.argv) > 3 else 2
     steps = int(sys.argv[4]) if len(sys.argv) > 4 else 0
