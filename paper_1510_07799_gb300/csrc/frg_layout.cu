@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
 // conjugate of the channel's value at the mirrored entry (N-1-i1, N-1-i2,
 // N-1-i3); on the self-mirrored transfer m = N - 1 the entry of each mirror pair
 // with the smaller leading index keeps its own value and the other takes its
-// conjugate, so that the result is exactly reversal-symmetric.  Every thread issues all 48 of its loads before the first
-// shared-memory pass, so that a block keeps 96 KB of reads in flight.
+// conjugate, so that the result is exactly reversal-symmetric.  Every thread
+// issues all 48 of its loads before the first shared-memory pass, so that a
+// block keeps 96 KB of reads in flight.
 template <bool REV>
 __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                                     int mask) {
@@ -189,7 +190,23 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
     if (a < N && b < N && c < N) {
       float2 v = sm[sidx(i1, i2, i3)];
       if (tails) {
-        const float2 ta = ttab[a + b], tb = ttab[nrow + b - c + N - 1];
+        float2 ta = ttab[a + b], tb = ttab[nrow + b - c + N - 1];
+        if (REV) {
+          // the constants of mirrored transfers as exact conjugates, so that
+          // the sum stays exactly reversal-symmetric
+          if (a + b > M) {
+            ta = ttab[2 * M - (a + b)];
+            ta.y = -ta.y;
+          } else if (a + b == M) {
+            ta.y = 0.f;
+          }
+          if (b > c) {
+            tb = ttab[nrow + c - b + N - 1];
+            tb.y = -tb.y;
+          } else if (b == c) {
+            tb.y = 0.f;
+          }
+        }
         v = make_float2(v.x + (ta.x + tb.x), v.y + (ta.y + tb.y));
       }
       K[((size_t)a * N + b) * N + c] = make_float2(v.x + vk[u].x, v.y + vk[u].y);

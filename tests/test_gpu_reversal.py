@@ -121,3 +121,23 @@ def test_reversal_in_a_mixed_size_batch_equals_single_point_runs():
             g, s, _, _ = ctx.get_state(0)
         assert torch.equal(g, batched[i][0]) and torch.equal(s, batched[i][1])
         assert st.rhs_evals == stb[i].rhs_evals
+
+
+@pytest.mark.parametrize("cutoff", [0, 1])
+def test_all_options_together_match_the_fp64_path(cutoff):
+    """3xTF32 with the reversal reduction and the tails, on either cutoff,
+    against the FP64 path with the tails (itself at 1e-15 of the oracle):
+    a full N = 16 flow off particle-hole symmetry within the 1e-6 bar."""
+    kw = dict(Lambda0=1e12, Lambda_f=1.0) if cutoff else {}
+    w = inputs.Workload("t", N=16, U=1.0, T=0.05, eps_d=-0.5 + 0.3, cutoff=cutoff, **kw)
+    with frg.Context([w], precision=frg.FP64, channel_mask=0xF | frg.TAILS) as c64:
+        st64 = c64.flow()[0]
+        g64, s64, _, _ = c64.get_state(0)
+    with frg.Context([w], precision=frg.TF32X3, channel_mask=0xF | frg.TAILS | REV) as c:
+        st = c.flow()[0]
+        g, s, _, _ = c.get_state(0)
+    assert st64.status == 0 and st.status == 0
+    assert nrel(g.cpu().numpy(), g64.cpu().numpy()) < FLOW_TOL
+    assert nrel(s.cpu().numpy(), s64.cpu().numpy()) < FLOW_TOL
+    gn = g.cpu().numpy()
+    assert nrel(gn, np.conj(gn[::-1, ::-1, ::-1])) < 1e-15
