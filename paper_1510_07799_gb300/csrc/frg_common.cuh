@@ -162,13 +162,22 @@ __device__ __forceinline__ bool fourth_in_box(int i, int N) {
 __device__ __forceinline__ void propagator_at(const PointDesc &P, int i, double L, double2 sg, double2 &g,
                                               double2 &s) {
   const double w = (2.0 * (double)(i - P.N / 2) + 1.0) * M_PI * P.T;
-  const double rl = P.cutoff ? sqrt(L) : 0.0;
-  const double thinv = P.cutoff ? rl : 1.0 + (L * L) / (w * w);
+  // two separate branches (a select would evaluate the FP64 square root and
+  // division of the interaction flow on every call)
+  double thinv, dthinv;
+  if (P.cutoff) {
+    const double rl = sqrt(L);
+    thinv = rl;
+    dthinv = 0.5 / rl;
+  } else {
+    thinv = 1.0 + (L * L) / (w * w);
+    dthinv = 2.0 * L / (w * w);
+  }
   const double2 gi = make_double2(-P.et, w + (w > 0.0 ? P.Delta : -P.Delta));
   const double2 den = make_double2(thinv * gi.x - sg.x, thinv * gi.y - sg.y);
   const double nrm = den.x * den.x + den.y * den.y;
   g = make_double2(den.x / nrm, -den.y / nrm);
-  s = cscale(cmul(cmul(g, g), gi), P.cutoff ? -0.5 / rl : -2.0 * L / (w * w));
+  s = cscale(cmul(cmul(g, g), gi), -dthinv);
 }
 
 // Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).
