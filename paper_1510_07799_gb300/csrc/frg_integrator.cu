@@ -230,9 +230,44 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
 // float-float, and rounded once.  The seventh stage (the candidate that becomes
 // the state) is formed in FP64: ynew = y + h S with S the float-float sum
 // widened to FP64.  Stage 0 only prepares the float pairs of y.  The
-// self-energy part stays in FP64 throughout.
+// self-energy part stays in FP64 throughout.  The vertex part moves two
+// complex elements (one 16-byte access per array) per thread and pass: N is
+// even, so a segment's vertex range holds whole pairs.  Eight blocks of 256
+// threads per SM (32 registers; a few bytes of spills at stages 0, 5 and 6)
+// keep every segment of an N = 128 state in one wave: measured faster than the
+// unbounded 40-48 registers (two waves) and than 8-byte accesses.
+
+// y + h S rounded once to FP32, y = yh + yl, h = h_hi + h_lo, S = Sh + Sl.
+__device__ __forceinline__ float stage_round(float yh, float yl, float Sh, float Sl, float h_hi, float h_lo) {
+  const float p = __fmul_rn(h_hi, Sh);
+  const float pe = __fmaf_rn(h_hi, Sh, -p);
+  const float rest = __fmaf_rn(h_hi, Sl, __fmul_rn(h_lo, Sh));
+  float s0, e0;
+  two_sum(yh, p, s0, e0);
+  return __fadd_rn(s0, __fadd_rn(__fadd_rn(yl, e0), __fadd_rn(pe, rest)));
+}
+__device__ __forceinline__ void f4_set(float4 &v, int q, float x) {
+  if (q == 0) v.x = x;
+  else if (q == 1) v.y = x;
+  else if (q == 2) v.z = x;
+  else v.w = x;
+}
+__device__ __forceinline__ float f4_get(const float4 &v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+// FP32 hi / lo parts of two complex FP64 values, component by component.
+__device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, float4 &hi, float4 &lo) {
+  const double yv[4] = {y0.x, y0.y, y1.x, y1.y};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float h = d2f(yv[q]);
+    f4_set(hi, q, h);
+    f4_set(lo, q, d2f(yv[q] - f2d(h)));
+  }
+}
+
 template <int S>
-__global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+__global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
                                                      SegTable seg, RhsIO *__restrict__ io) {
   const int b = blockIdx.x;
   const int pi = seg.point[b];
@@ -246,67 +281,60 @@ __global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict
   const int ys = c.yslot;
   const double h = c.h;
   const float h_hi = d2f(h), h_lo = d2f(h - f2d(h_hi));
+  const float U = (float)P.U;
   float vm = 0.f;
-  for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
-    const int i = base + e;
-    if (i >= n) break;
-    if (i < n3) {
-      float2 out;
-      if (S == 0) {
-        const double2 y = P.ybuf[ys][i];
-        const float2 hi = make_float2(d2f(y.x), d2f(y.y));
-        P.yhi[ys][i] = hi;
-        P.ylo[ys][i] = make_float2(d2f(y.x - f2d(hi.x)), d2f(y.y - f2d(hi.y)));
-        out = hi;
-      } else {
-        float sr = 0.f, srl = 0.f, si = 0.f, sil = 0.f;
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-          if (S == 6 && j == 1) continue;  // the fifth-order weight of k2 is zero: no read
-          const float2 k = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
-          ff_mac(sr, srl, fAh[S][j], fAl[S][j], k.x);
-          ff_mac(si, sil, fAh[S][j], fAl[S][j], k.y);
-        }
-        if (S < 6) {
-          const float2 yh = P.yhi[ys][i], yl = P.ylo[ys][i];
-          float res[2];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float Sh = q ? si : sr, Sl = q ? sil : srl;
-            const float p = __fmul_rn(h_hi, Sh);
-            const float pe = __fmaf_rn(h_hi, Sh, -p);
-            const float rest = __fmaf_rn(h_hi, Sl, __fmul_rn(h_lo, Sh));
-            float s0, e0;
-            two_sum(q ? yh.y : yh.x, p, s0, e0);
-            res[q] = __fadd_rn(s0, __fadd_rn(__fadd_rn(q ? yl.y : yl.x, e0), __fadd_rn(pe, rest)));
-          }
-          out = make_float2(res[0], res[1]);
-        } else {
-          const double2 y = P.ybuf[ys][i];
-          const double Sr = f2d(sr) + f2d(srl), Si = f2d(si) + f2d(sil);
-          const double2 yn = make_double2(fma(h, Sr, y.x), fma(h, Si, y.y));
-          P.ybuf[ys ^ 1][i] = yn;
-          const float2 hi = make_float2(d2f(yn.x), d2f(yn.y));
-          P.yhi[ys ^ 1][i] = hi;
-          P.ylo[ys ^ 1][i] = make_float2(d2f(yn.x - f2d(hi.x)), d2f(yn.y - f2d(hi.y)));
-          out = hi;
-        }
-      }
-      vm = fmaxf(vm, fmaxf(fabsf(out.x), fabsf(out.y)));
-      P.Y32[i] = fourth_in_box(i, P.N) ? out : make_float2((float)P.U, 0.f);
+  const int vend = min(base + SEG_ELEMS, n3);
+  for (int i = base + 2 * (int)threadIdx.x; i < vend; i += 2 * (int)blockDim.x) {
+    float4 out;
+    if (S == 0) {
+      float4 lo;
+      split_pair(P.ybuf[ys][i], P.ybuf[ys][i + 1], out, lo);
+      *reinterpret_cast<float4 *>(P.yhi[ys] + i) = out;
+      *reinterpret_cast<float4 *>(P.ylo[ys] + i) = lo;
     } else {
-      double2 acc = make_double2(0.0, 0.0);
+      float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int j = 0; j < (S < 6 ? S : 6); ++j) {
-        const double2 k = P.kS[c.kslot[j]][i - n3];
-        acc.x += dA[S][j] * k.x;
-        acc.y += dA[S][j] * k.y;
+      for (int j = 0; j < S; ++j) {
+        if (S == 6 && j == 1) continue;  // the fifth-order weight of k2 is zero: no read
+        const float4 k = *reinterpret_cast<const float4 *>(static_cast<const float2 *>(P.kG[c.kslot[j]]) + i);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ff_mac(sh[q], sl[q], fAh[S][j], fAl[S][j], f4_get(k, q));
       }
-      const double2 yi = P.ybuf[ys][i];
-      const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
-      P.Y64[i - n3] = Y;
-      if (S == 6) P.ybuf[ys ^ 1][i] = Y;
+      if (S < 6) {
+        const float4 yh = *reinterpret_cast<const float4 *>(P.yhi[ys] + i);
+        const float4 yl = *reinterpret_cast<const float4 *>(P.ylo[ys] + i);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f4_set(out, q, stage_round(f4_get(yh, q), f4_get(yl, q), sh[q], sl[q], h_hi, h_lo));
+      } else {
+        const double2 y0 = P.ybuf[ys][i], y1 = P.ybuf[ys][i + 1];
+        const double2 yn0 = make_double2(fma(h, f2d(sh[0]) + f2d(sl[0]), y0.x), fma(h, f2d(sh[1]) + f2d(sl[1]), y0.y));
+        const double2 yn1 = make_double2(fma(h, f2d(sh[2]) + f2d(sl[2]), y1.x), fma(h, f2d(sh[3]) + f2d(sl[3]), y1.y));
+        P.ybuf[ys ^ 1][i] = yn0;
+        P.ybuf[ys ^ 1][i + 1] = yn1;
+        float4 lo;
+        split_pair(yn0, yn1, out, lo);
+        *reinterpret_cast<float4 *>(P.yhi[ys ^ 1] + i) = out;
+        *reinterpret_cast<float4 *>(P.ylo[ys ^ 1] + i) = lo;
+      }
     }
+    vm = fmaxf(vm, fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))));
+    const bool in0 = fourth_in_box(i, P.N), in1 = fourth_in_box(i + 1, P.N);
+    *reinterpret_cast<float4 *>(P.Y32 + i) =
+        make_float4(in0 ? out.x : U, in0 ? out.y : 0.f, in1 ? out.z : U, in1 ? out.w : 0.f);
+  }
+  // self-energy part
+  for (int i = max(base, n3) + (int)threadIdx.x; i < min(base + SEG_ELEMS, n); i += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < (S < 6 ? S : 6); ++j) {
+      const double2 k = P.kS[c.kslot[j]][i - n3];
+      acc.x += dA[S][j] * k.x;
+      acc.y += dA[S][j] * k.y;
+    }
+    const double2 yi = P.ybuf[ys][i];
+    const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
+    P.Y64[i - n3] = Y;
+    if (S == 6) P.ybuf[ys ^ 1][i] = Y;
   }
   block_max_to(vm, P.vmax);
 }
@@ -314,7 +342,8 @@ __global__ void __launch_bounds__(256) k_stage_split(const PointDesc *__restrict
 // Error estimate of the split paths: e = h sum_j (b_j - bstar_j) k_j with the
 // FP32 k_j summed in float-float; the scaled ratio |e| / (atol + rtol max(|y|,
 // |ynew|)) of every vertex component in FP32, of the self-energy in FP64.
-__global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+// Bounded to eight blocks per SM like the stage kernels.
+__global__ void __launch_bounds__(256, 8) k_error_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
                                                      SegTable seg) {
   const int b = blockIdx.x;
   const int pi = seg.point[b];
@@ -333,43 +362,46 @@ __global__ void __launch_bounds__(256) k_error_split(const PointDesc *__restrict
   float fmax_ = 0.f, ym = 0.f;
   double dmax = 0.0, sm = 0.0;
   int bad = 0;
-  for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
-    const int i = base + e;
-    if (i >= n) break;
-    if (i < n3) {
-      float er = 0.f, erl = 0.f, ei = 0.f, eil = 0.f;
+  // vertex part: two complex elements per thread and pass (16-byte accesses)
+  const int vend = min(base + SEG_ELEMS, n3);
+  for (int i = base + 2 * (int)threadIdx.x; i < vend; i += 2 * (int)blockDim.x) {
+    float eh[4] = {0.f, 0.f, 0.f, 0.f}, el[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        if (j == 1) continue;  // b2 = bstar2 = 0: no read
-        const float2 k = static_cast<const float2 *>(P.kG[c.kslot[j]])[i];
-        ff_mac(er, erl, fEh[j], fEl[j], k.x);
-        ff_mac(ei, eil, fEh[j], fEl[j], k.y);
-      }
-      const float2 y = P.yhi[ys][i], yn = P.yhi[ys ^ 1][i];
-      const float mx = fmaxf(fabsf(y.x), fabsf(yn.x)), my = fmaxf(fabsf(y.y), fabsf(yn.y));
-      ym = fmaxf(ym, fmaxf(mx, my));
+    for (int j = 0; j < 7; ++j) {
+      if (j == 1) continue;  // b2 = bstar2 = 0: no read
+      const float4 k = *reinterpret_cast<const float4 *>(static_cast<const float2 *>(P.kG[c.kslot[j]]) + i);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ff_mac(eh[q], el[q], fEh[j], fEl[j], f4_get(k, q));
+    }
+    const float4 y = *reinterpret_cast<const float4 *>(P.yhi[ys] + i);
+    const float4 yn = *reinterpret_cast<const float4 *>(P.yhi[ys ^ 1] + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float m = fmaxf(fabsf(f4_get(y, q)), fabsf(f4_get(yn, q)));
+      ym = fmaxf(ym, m);
       // the ratio only decides accept / reject and the step factor: a fast
       // division (a few ulp) is enough
-      const float rx = __fdividef(fabsf(hf * __fadd_rn(er, erl)), atolf + rtolf * fmaxf(mx, yfl));
-      const float ry = __fdividef(fabsf(hf * __fadd_rn(ei, eil)), atolf + rtolf * fmaxf(my, yfl));
-      if (!isfinite(rx) || !isfinite(ry) || !isfinite(yn.x) || !isfinite(yn.y)) bad = 1;
-      else fmax_ = fmaxf(fmax_, fmaxf(rx, ry));
-    } else {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        const double2 k = P.kS[c.kslot[j]][i - n3];
-        acc.x += dE[j] * k.x;
-        acc.y += dE[j] * k.y;
-      }
-      const double2 yi = P.ybuf[ys][i], yni = P.ybuf[ys ^ 1][i];
-      const double mx = fmax(fabs(yi.x), fabs(yni.x)), my = fmax(fabs(yi.y), fabs(yni.y));
-      sm = fmax(sm, fmax(mx, my));
-      const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(mx, sfl));
-      const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(my, sfl));
-      if (!isfinite(rx) || !isfinite(ry) || !isfinite(yni.x) || !isfinite(yni.y)) bad = 1;
-      else dmax = fmax(dmax, fmax(rx, ry));
+      const float r = __fdividef(fabsf(hf * __fadd_rn(eh[q], el[q])), atolf + rtolf * fmaxf(m, yfl));
+      if (!isfinite(r) || !isfinite(f4_get(yn, q))) bad = 1;
+      else fmax_ = fmaxf(fmax_, r);
     }
+  }
+  // self-energy part
+  for (int i = max(base, n3) + (int)threadIdx.x; i < min(base + SEG_ELEMS, n); i += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const double2 k = P.kS[c.kslot[j]][i - n3];
+      acc.x += dE[j] * k.x;
+      acc.y += dE[j] * k.y;
+    }
+    const double2 yi = P.ybuf[ys][i], yni = P.ybuf[ys ^ 1][i];
+    const double mx = fmax(fabs(yi.x), fabs(yni.x)), my = fmax(fabs(yi.y), fabs(yni.y));
+    sm = fmax(sm, fmax(mx, my));
+    const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(mx, sfl));
+    const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(my, sfl));
+    if (!isfinite(rx) || !isfinite(ry) || !isfinite(yni.x) || !isfinite(yni.y)) bad = 1;
+    else dmax = fmax(dmax, fmax(rx, ry));
   }
   double emax = fmax(dmax, f2d(fmax_));
   double ymd = f2d(ym);
