@@ -201,9 +201,26 @@ def cpu_baseline(N_rows, seconds=12.0, mask=0xF):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": (rows / w.N) / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d (channel mask 0x%x), repeated "
-                      "for %.1f s; scaled by rows/N" % (rows, w.N, w.N, mask, el)}
+    res = {"value": (rows / w.N) / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+           "host_cpus": os.cpu_count(),
+           "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d (channel mask 0x%x), repeated "
+                     "for %.1f s; scaled by rows/N" % (rows, w.N, w.N, mask, el)}
+    # the same sample on one thread (a quarter of the time budget)
+    oracle.set_threads(1)
+    try:
+        rows1, t0 = 0, time.perf_counter()
+        while True:
+            a = rows1 % w.N
+            oracle.rhs_rows(m, 0.02, V, sig, a, a + 1, mask=mask)
+            rows1 += 1
+            el1 = time.perf_counter() - t0
+            if el1 >= seconds / 4:
+                break
+    finally:
+        oracle.set_threads(0)  # back to the OpenMP default
+    res["value_1thread"] = (rows1 / w.N) / el1
+    res["sample_1thread"] = "%d vertex rows on one thread in %.1f s" % (rows1, el1)
+    return res
 
 
 def run_reference(args):
