@@ -89,7 +89,12 @@ extern "C" {
  * mapping to 2N - 2 - m: the contraction computes the transfers m <= N - 1
  * only (about half of the tensor-core work) and the scatter-add takes the
  * others from the mirrored entries.  For inputs without the symmetry the
- * result is the symmetric part's rhs, not the input's.
+ * result is the symmetric part's rhs, not the input's.  In a flow the split
+ * precisions also store half of the vertex: the stage derivatives and the
+ * float-pair copy of the state hold the entries with i1 < N/2 only, the stage
+ * sums and the error norm run over those, and every other entry of the state
+ * is written as the conjugate of its mirror (so a state set with
+ * frg_set_state enters the flow through its entries with i1 < N/2).
  */
 #define FRG_REVERSAL 0x20
 

@@ -397,6 +397,9 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     P.N = N;
     P.n3 = (int)n3;
     P.cutoff = p.cutoff;
+    P.rev_half = ctx->split && (p.channel_mask & FRG_REVERSAL) ? 1 : 0;
+    // vertex elements of the flow's stage derivatives and float-pair state
+    const size_t nv = P.rev_half ? n3 / 2 : n3;
     P.U = p.U;
     P.T = p.T;
     P.et = p.eps_d + 0.5 * p.U;
@@ -424,7 +427,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       // reversal reduction: the pp channel's computed half in its own buffer
       if ((p.channel_mask & FRG_REVERSAL) && !(P.PN = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
       for (int b = 0; b < 2; ++b)
-        if (!(P.yhi[b] = dalloc<float2>(ctx, n3)) || !(P.ylo[b] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
+        if (!(P.yhi[b] = dalloc<float2>(ctx, nv)) || !(P.ylo[b] = dalloc<float2>(ctx, nv))) return bail(FRG_ENOMEM);
       if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
           !(P.Lph32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
           !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 1)) ||
@@ -439,7 +442,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
           cudaMemset(P.Y32X, 0, (2 * n3 + OPERAND_SLACK) * sizeof(float2)) != cudaSuccess)
         return bail(FRG_ECUDA);
       for (int j = 0; j < 7; ++j)
-        if (!(P.kG[j] = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
+        if (!(P.kG[j] = dalloc<float2>(ctx, nv))) return bail(FRG_ENOMEM);
     }
     for (int j = 0; j < 7; ++j)
       if (!(P.kS[j] = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
@@ -505,7 +508,20 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
   {
     std::vector<int> sp, sb;
     for (int i = 0; i < n_points; ++i) {
-      const int nc = ctx->hpts[i].n3 + ctx->hpts[i].N;
+      const PointDesc &P = ctx->hpts[i];
+      if (P.rev_half) {
+        // the vertex entries i < n3/2, then the self-energy
+        for (int b = 0; b < P.n3 / 2; b += SEG_ELEMS) {
+          sp.push_back(i);
+          sb.push_back(b);
+        }
+        for (int b = P.n3; b < P.n3 + P.N; b += SEG_ELEMS) {
+          sp.push_back(i);
+          sb.push_back(b);
+        }
+        continue;
+      }
+      const int nc = P.n3 + P.N;
       for (int b = 0; b < nc; b += SEG_ELEMS) {
         sp.push_back(i);
         sb.push_back(b);
@@ -585,6 +601,7 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
   o.lam = nullptr;
   o.active = 1;
   o.out_f32 = 0;
+  o.canon = 0;
   if (!ctx->split) {
     LK(launch_set_user_io(ctx->d_io_user, ctx->d_ctl, ctx->n, point, o, Lambda, ctx->stream), "user io");
     return run_rhs(ctx, ctx->d_io_user, point, ev);

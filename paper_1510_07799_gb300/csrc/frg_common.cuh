@@ -23,6 +23,11 @@ struct PointDesc {
   int N;
   int n3;                 // N^3
   int cutoff;             // FRG_CUTOFF_OMEGA (0) or FRG_CUTOFF_INTERACTION (1)
+  // split paths with the reversal reduction: the flow keeps the vertex part of
+  // the stage derivatives and of the float-pair state for the entries i < n3/2
+  // (i1 < N/2) only; entry n3-1-i is the conjugate of entry i (kG, yhi, ylo
+  // hold n3/2 elements, ybuf stays whole and symmetric)
+  int rev_half;
   double U, T, et, Delta; // et = eps_d + U/2
   double l0, l_end;       // ln Lambda0, ln Lambda_f
   double rtol, atol, h0;
@@ -77,6 +82,7 @@ struct RhsIO {
   const double *lam;   // scale (device)
   int active;          // 0: skip this point
   int out_f32;         // vertex output as float2
+  int canon;           // 1: only the entries i < n3/2 of the vertex output are wanted (dgam holds n3/2)
 };
 
 // One CTA of a channel contraction.

@@ -392,8 +392,10 @@ __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__rest
   if (blockIdx.x == 0 && threadIdx.x < N && o.dsig)
     o.dsig[threadIdx.x] = cadd(o.dsig[threadIdx.x], P.tail[2 * nrow]);
   const int i3 = threadIdx.x;
-  if (i3 >= N) return;
-  const int nr = min(TAIL_ROWS, N * N - r0);
+  // half storage: the rows (i1, i2) with i1 < N/2 only
+  const int nrows = o.canon ? N * N / 2 : N * N;
+  if (i3 >= N || r0 >= nrows) return;
+  const int nr = min(TAIL_ROWS, nrows - r0);
   // all loads of the thread first, then the updates (one round trip)
   if (o.out_f32) {
     float2 *d = static_cast<float2 *>(o.dgam) + (size_t)r0 * N + i3;

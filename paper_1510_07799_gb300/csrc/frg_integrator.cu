@@ -86,6 +86,8 @@ __global__ void k_fill_bare(const PointDesc *__restrict__ pts, SegTable seg) {
   for (int e = threadIdx.x; e < SEG_ELEMS; e += blockDim.x) {
     const int i = base + e;
     if (i < n) y[i] = make_double2(i < P.n3 ? P.U : 0.0, 0.0);
+    // half-storage segments cover the entries i < n3/2: their mirrors too
+    if (P.rev_half && i < P.n3 / 2) y[P.n3 - 1 - i] = make_double2(P.U, 0.0);
   }
 }
 
@@ -122,6 +124,7 @@ __device__ __forceinline__ void write_stage_io(const PointDesc &P, Ctl &c, RhsIO
   o.dgam = P.kG[c.kslot[stage]];
   o.dsig = P.kS[c.kslot[stage]];
   o.out_f32 = split;
+  o.canon = split ? P.rev_half : 0;
   *io = o;
 }
 
@@ -232,7 +235,11 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
 // widened to FP64.  Stage 0 only prepares the float pairs of y.  The
 // self-energy part stays in FP64 throughout.  The vertex part moves two
 // complex elements (one 16-byte access per array) per thread and pass: N is
-// even, so a segment's vertex range holds whole pairs.  Eight blocks of 256
+// even, so a segment's vertex range holds whole pairs.  With half storage
+// (reversal reduction) the kernel forms the entries i < n3/2 and writes their
+// conjugates to the mirrored entries n3-1-i of the FP32 stage input (and of the
+// FP64 state at the seventh stage); the two entries of a pair mirror to the
+// pair starting at n3-2-i, in swapped order.  Eight blocks of 256
 // threads per SM (32 registers; a few bytes of spills at stages 0, 5 and 6)
 // keep every segment of an N = 128 state in one wave: measured faster than the
 // unbounded 40-48 registers (two waves) and than 8-byte accesses.
@@ -282,8 +289,9 @@ __global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restr
   const double h = c.h;
   const float h_hi = d2f(h), h_lo = d2f(h - f2d(h_hi));
   const float U = (float)P.U;
+  const bool half = P.rev_half != 0;
   float vm = 0.f;
-  const int vend = min(base + SEG_ELEMS, n3);
+  const int vend = min(base + SEG_ELEMS, half ? n3 / 2 : n3);
   for (int i = base + 2 * (int)threadIdx.x; i < vend; i += 2 * (int)blockDim.x) {
     float4 out;
     if (S == 0) {
@@ -311,6 +319,10 @@ __global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restr
         const double2 yn1 = make_double2(fma(h, f2d(sh[2]) + f2d(sl[2]), y1.x), fma(h, f2d(sh[3]) + f2d(sl[3]), y1.y));
         P.ybuf[ys ^ 1][i] = yn0;
         P.ybuf[ys ^ 1][i + 1] = yn1;
+        if (half) {
+          P.ybuf[ys ^ 1][n3 - 1 - i] = make_double2(yn0.x, -yn0.y);
+          P.ybuf[ys ^ 1][n3 - 2 - i] = make_double2(yn1.x, -yn1.y);
+        }
         float4 lo;
         split_pair(yn0, yn1, out, lo);
         *reinterpret_cast<float4 *>(P.yhi[ys ^ 1] + i) = out;
@@ -321,6 +333,10 @@ __global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restr
     const bool in0 = fourth_in_box(i, P.N), in1 = fourth_in_box(i + 1, P.N);
     *reinterpret_cast<float4 *>(P.Y32 + i) =
         make_float4(in0 ? out.x : U, in0 ? out.y : 0.f, in1 ? out.z : U, in1 ? out.w : 0.f);
+    // the box rule is reversal-symmetric: a mirrored entry is in the box iff its image is
+    if (half)
+      *reinterpret_cast<float4 *>(P.Y32 + (n3 - 2 - i)) =
+          make_float4(in1 ? out.z : U, in1 ? -out.w : 0.f, in0 ? out.x : U, in0 ? -out.y : 0.f);
   }
   // self-energy part
   for (int i = max(base, n3) + (int)threadIdx.x; i < min(base + SEG_ELEMS, n); i += blockDim.x) {
@@ -362,8 +378,9 @@ __global__ void __launch_bounds__(256, 8) k_error_split(const PointDesc *__restr
   float fmax_ = 0.f, ym = 0.f;
   double dmax = 0.0, sm = 0.0;
   int bad = 0;
-  // vertex part: two complex elements per thread and pass (16-byte accesses)
-  const int vend = min(base + SEG_ELEMS, n3);
+  // vertex part: two complex elements per thread and pass (16-byte accesses);
+  // with half storage the entries i < n3/2 (their mirrors have the same moduli)
+  const int vend = min(base + SEG_ELEMS, P.rev_half ? n3 / 2 : n3);
   for (int i = base + 2 * (int)threadIdx.x; i < vend; i += 2 * (int)blockDim.x) {
     float eh[4] = {0.f, 0.f, 0.f, 0.f}, el[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll

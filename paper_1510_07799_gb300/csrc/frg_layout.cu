@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
 // conjugate of the channel's value at the mirrored entry (N-1-i1, N-1-i2,
 // N-1-i3); on the self-mirrored transfer m = N - 1 the entry of each mirror pair
 // with the smaller leading index keeps its own value and the other takes its
-// conjugate, so that the result is exactly reversal-symmetric.  Every thread
+// conjugate, so that the result is exactly reversal-symmetric.  With half
+// storage (RhsIO.canon) only the entries with i1 < N/2 are formed and written:
+// tiles that start at i1 >= N/2 leave after block 0's self-energy tail.  Every thread
 // issues all 48 of its loads before the first shared-memory pass, so that a
 // block keeps 96 KB of reads in flight.
 template <bool REV>
@@ -112,6 +114,9 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
       o.dsig[threadIdx.x] = make_double2(a.x + b.x, a.y + b.y);
     }
   }
+  // half storage: entries with i1 >= hN are not wanted (and have no room in K)
+  const int hN = (REV && o.canon) ? N / 2 : N;
+  if (t.g1 >= hN) return;
   float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
   const float2 z = make_float2(0.f, 0.f);
   const float2 *__restrict__ src_pp = REV ? P.PN : K;
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
       // dph, layout X [a][c][b]; REV: transfer t = c - a computed for t <= 0
       const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
       int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool ok = (mask & 2) && a < N && b < N && c < N;
+      const bool ok = (mask & 2) && a < hN && b < N && c < N;
       if (REV && !(c < a || (c == a && 2 * a < M))) {
         a = M - a, b = M - b, c = M - c;
         flipx |= 1u << u;
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
       // xph, layout W [b][c][a]; REV: transfer Q = b - c computed for Q <= 0
       const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
       int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool ok = (mask & 4) && a < N && b < N && c < N;
+      const bool ok = (mask & 4) && a < hN && b < N && c < N;
       if (REV && !(b < c || (b == c && 2 * b < M))) {
         a = M - a, b = M - b, c = M - c;
         flipw |= 1u << u;
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
       // pp, natural layout; REV: transfer s = a + b computed for s <= N - 1
       const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
       int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool ok = (mask & 1) && a < N && b < N && c < N;
+      const bool ok = (mask & 1) && a < hN && b < N && c < N;
       if (REV && !(a + b < M || (a + b == M && 2 * a < M))) {
         a = M - a, b = M - b, c = M - c;
         flipk |= 1u << u;
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict_
     const int n = threadIdx.x + 256 * u;
     const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
     const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-    if (a < N && b < N && c < N) {
+    if (a < hN && b < N && c < N) {
       float2 v = sm[sidx(i1, i2, i3)];
       if (tails) {
         float2 ta = ttab[a + b], tb = ttab[nrow + b - c + N - 1];

@@ -32,7 +32,7 @@ __global__ void k_zero_vertex(const PointDesc *pts, const RhsIO *io) {
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
-  const int n3 = pts[pi].n3;
+  const int n3 = o.canon ? pts[pi].n3 / 2 : pts[pi].n3;  // half storage: the entries i < n3/2
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
     if (o.out_f32)
       static_cast<float2 *>(o.dgam)[i] = make_float2(0.f, 0.f);
