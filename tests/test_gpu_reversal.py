@@ -141,3 +141,45 @@ def test_all_options_together_match_the_fp64_path(cutoff):
     assert nrel(s.cpu().numpy(), s64.cpu().numpy()) < FLOW_TOL
     gn = g.cpu().numpy()
     assert nrel(gn, np.conj(gn[::-1, ::-1, ::-1])) < 1e-15
+
+
+@pytest.mark.parametrize("prec", [frg.TF32X3, frg.BF16X3])
+@pytest.mark.parametrize("mask", [0xF, 0x8, 0x8 | frg.TAILS, 0xF | frg.TAILS])
+def test_half_storage_flow_matches_full_storage(prec, mask):
+    """In a flow the reversal reduction keeps half of the vertex (stage
+    derivatives and float-pair state for i1 < N/2) and writes the other half as
+    conjugates.  Against the same flow without the reduction (whole storage,
+    every transfer): the final state agrees within the split
+    paths' bound and is exactly symmetric, also when no vertex channel is on
+    (the zero-vertex and tail-addition kernels then write the derivatives)."""
+    w = inputs.Workload("t", N=16, U=1.3, T=0.04, eps_d=-0.65 + 0.25)
+    with frg.Context([w], precision=prec, channel_mask=mask | REV) as ch, \
+            frg.Context([w], precision=prec, channel_mask=mask) as cf:
+        sh = ch.flow()[0]
+        sf = cf.flow()[0]
+        gh, s_h, lh, _ = ch.get_state(0)
+        gf, s_f, lf, _ = cf.get_state(0)
+    assert sh.status == 0 and sf.status == 0 and sh.done == 1 and sf.done == 1 and lh == lf
+    gh, gf = gh.cpu().numpy(), gf.cpu().numpy()
+    assert np.array_equal(gh, np.conj(gh[::-1, ::-1, ::-1]))
+    assert nrel(gh, gf) < FLOW_TOL and nrel(s_h.cpu().numpy(), s_f.cpu().numpy()) < FLOW_TOL
+
+
+def test_half_storage_symmetrises_a_state_from_its_canonical_half():
+    """A state set with frg_set_state enters a reduced flow through its entries
+    with i1 < N/2: an asymmetric state flows like its canonical half's
+    symmetric completion."""
+    N = 16
+    w = inputs.Workload("t", N=N, U=1.0, T=0.05, eps_d=-0.5 + 0.2)
+    V, sig = symmetric_state(N, w.U, seed=41)
+    V = 0.2 * (V - w.U) + w.U  # a mild perturbation of the bare vertex
+    Va = V.copy()
+    Va[N // 2:] += 0.05  # break the symmetry in the mirrored half only
+    out = []
+    for state in (V, Va):
+        with frg.Context([w], precision=frg.TF32X3, channel_mask=0xF | REV) as c:
+            c.set_state(0, torch.from_numpy(state).cuda(), torch.from_numpy(sig).cuda(), 20.0)
+            st = c.advance(3)[0]
+            assert st.status == 0 and st.accepted >= 1
+            out.append(c.get_state(0)[0].cpu().numpy())
+    assert np.array_equal(out[0], out[1])
