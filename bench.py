@@ -80,18 +80,19 @@ def profiled_traffic(kind):
         return None
 
 
-def executed_tensor_flops(N, NT=128, mrows=64, ks=16, half=False):
-    """Tensor-core flops the 3xTF32 kernel issues per rhs: per tile (64 complex
-    rows x NT columns) and k-step of 16 complex k, 3 products of M = 128 real
-    rows (real form of the left operand) x N = NT x K = 32; ragged transfers
-    padded to whole tiles and k-steps (the direct channel has two K halves)."""
+def executed_tensor_flops(N, NT=128, mrows=64, ks=16, half=False, products=3):
+    """Tensor-core flops the split kernel issues per rhs: per tile (64 complex
+    rows x NT columns) and k-step of 16 complex k, `products` slice products
+    (3xTF32: 3, BF16x3: 6) of M = 128 real rows (real form of the left operand)
+    x N = NT x K = 32; ragged transfers padded to whole tiles and k-steps (the
+    direct channel has two K halves)."""
     tot = 0
     for ch in range(3):
         for m in range(-(N - 1), 1 if half else N):
             D = N - abs(m)
             nk = (2 if ch == 1 else 1) * -(-D // ks)
             tiles = -(-D // mrows) * -(-N // min(NT, -(-N // 16) * 16))
-            tot += tiles * nk * 3 * 2 * 128 * (2 * min(NT, -(-N // 16) * 16)) * ks
+            tot += tiles * nk * products * 2 * 128 * (2 * min(NT, -(-N // 16) * 16)) * ks
     return tot
 
 
@@ -327,19 +328,25 @@ def run_ours(args):
                 "algorithmic": "8 flops x %d useful complex MACs per rhs" % macs}
     else:
         flops = 8.0 * macs
-        tf_peak = pk["bf16_tflops"] * 0.5  # TF32 dense = half the bf16 rate
+        bf = prec == "bf16x3"
+        # the products run in the slices' own type: BF16 at the measured bf16
+        # rate, TF32 at half of it (nominal tf32/bf16 ratio)
+        tc_peak = pk["bf16_tflops"] * (1.0 if bf else 0.5)
+        nprod = 6 if bf else 3
         achieved = flops / (ph[2] * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf_peak,
+        executed = executed_tensor_flops(N, half=args.reversal, products=nprod) / (ph[2] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                "frac": achieved / tc_peak,
                 "traffic": profiled_traffic("tf32") if prec == "3xtf32" and not args.reversal else None,
                 "traffic_unit": "DRAM bytes per rhs (contraction launch, ncu, cold cache)",
                 "kernel": "tcgen05 channel contractions of one rhs",
-                "peak_source": "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)" % pk["_source"],
+                "peak_source": ("%s bf16 burst" if bf else "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)") % pk["_source"],
                 "algorithmic": "8 flops x %d useful complex MACs per rhs (useful, not executed)" % macs,
-                "executed_tflops": executed_tensor_flops(N, half=args.reversal) / (ph[2] * 1e-3) / 1e12,
-                "executed_frac": executed_tensor_flops(N, half=args.reversal) / (ph[2] * 1e-3) / 1e12 / tf_peak,
-                "executed_note": "tensor-core flops issued (3 split products, real form of the complex product, whole tiles and "
-                                 "k-steps), for comparison with the tensor pipe's own rate; not the roofline value"}
+                "executed_tflops": executed,
+                "executed_frac": executed / tc_peak,
+                "executed_note": "tensor-core flops issued (%d slice products, real form of the complex product, whole tiles "
+                                 "and k-steps), for comparison with the tensor pipe's own rate; not the roofline value"
+                                 % nprod}
     roof["phases_ms"] = {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2], "combine": ph[3]}
     if args.tails:
         roof["phases_ms"]["tails_add"] = ph[4]
@@ -511,7 +518,8 @@ def run_n256(args):
 
     pk = peaks()
     macs = contraction_macs(w.N)
-    tf_peak = 0.5 * pk["bf16_tflops"]
+    bf = prec == "bf16x3"
+    tc_peak = pk["bf16_tflops"] * (1.0 if bf else 0.5)
     achieved = 8.0 * macs / (ph[2] * 1e-3) / 1e12
     line = {"metric": "vertex-rhs evals/s at N_f=256 (largest single flow)", "value": evals / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -520,10 +528,10 @@ def run_n256(args):
             "data": "synthetic",
             "config": {"workload": w.name, "N_f": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
                        "precision": prec, "rhs_evals_timed": evals, "autotune": tune},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
-                         "frac": achieved / tf_peak, "kernel": "tcgen05 channel contractions of one rhs",
-                         "executed_tflops": executed_tensor_flops(w.N) / (ph[2] * 1e-3) / 1e12,
-                         "peak_source": "%s bf16 burst x 0.5" % pk["_source"],
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": achieved / tc_peak, "kernel": "tcgen05 channel contractions of one rhs",
+                         "executed_tflops": executed_tensor_flops(w.N, products=6 if bf else 3) / (ph[2] * 1e-3) / 1e12,
+                         "peak_source": ("%s bf16 burst" if bf else "%s bf16 burst x 0.5") % pk["_source"],
                          "phases_ms": {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2],
                                        "combine": ph[3]}},
             "error_vs_fp64_gpu": {"gamma": nrel(dg, fg), "sigma": nrel(ds, fs),

@@ -7,31 +7,28 @@
 // index sets in frg_common.cuh).  A CTA tile is 64 complex rows x NT complex
 // columns; the complex product runs as real products on the tensor cores.
 //
-// Two kernels:
-//  * st::k_contract_tf32 (3xTF32, the headline precision): one persistent
-//    launch per rhs over the tiles of all channels and points, tensor-map TMA
-//    loader, transform warps, MMA warp, epilogue warps (see namespace st below).
-//    Split: x = hi + lo with hi = tf32(x), lo = tf32(x - hi); hi*hi in one TMEM
-//    accumulator, hi*lo + lo*hi in another, added in the epilogue.
-//  * k_contract_tc<CH, FRG_BF16X3>: one launch per channel.  Real form on the
-//    left operand, A' rows 0..63 = [Re a | -Im a], rows 64..127 = [Im a | Re a],
-//    B' row c = [Re b | Im b] (K-major), so that (A' B'^T)[r] = Re(a b)[r] and
-//    [r + 64] = Im(a b)[r].  Every operand is scaled by a power of two 2^-e
-//    with 2^e above a bound on its magnitude (the vertex maximum for Right;
-//    that times the bubble-weight row maximum, x3 for the direct particle-hole
-//    combination, for Left) and cut into three 8-bit slices on the fixed grids
-//    2^-7, 2^-15, 2^-23:
+// One persistent launch per rhs over the tiles of all channels and points
+// (tiles sorted heavy-first and dealt to the CTAs by least load, the paper's
+// Sec. 5.1 static distribution taken further): tensor-map TMA loader,
+// transform warps, MMA warp, epilogue warps (namespace st below), in two
+// precisions that share the pipeline and differ in the operand slices:
+//  * st::k_contract_tf32 (3xTF32, the headline precision): x = hi + lo with
+//    hi = tf32(x), lo = tf32(x - hi); hi*hi in one TMEM accumulator,
+//    hi*lo + lo*hi in another, added in the epilogue.
+//  * st::k_contract_bf16x3 (BF16x3): every operand is scaled by a power of two
+//    2^-e with 2^e above a bound on its magnitude (the vertex maximum for the
+//    right operand; that times the transfer's bubble-weight maximum, x3 for
+//    the direct particle-hole combination, x2 for a complex product's parts,
+//    for the left one) and cut into three 8-bit slices on fixed grids:
 //      s1 = rint(2^7 x)/2^7, s2 = rint(2^15 (x - s1))/2^15, s3 = rint(2^23 (x-s1-s2))/2^23.
 //    Products of first slices are integers times 2^(eA+eB-14) bounded by 2^14,
 //    so their sum over K' <= 1024 terms is exact in the FP32 accumulator
-//    whatever the accumulator's rounding (group 0); the five products of order
-//    <= 4 beyond it go to group 1 (the error-free splitting idea of Ozaki et
-//    al. with bf16 slices).  Roles: warps 0-3 epilogue, warp 4 TMEM allocation
-//    and MMA issue, warps 5-20 producers in two groups that take alternate
-//    k-steps (load the operand rows from the FP32 vertex layouts, fold in
-//    diag(Lb), slice, write swizzled K-major tiles); tiles in a static strided
-//    order over a list sorted heavy-first (the strided static distribution of
-//    the paper's Sec. 5.1).
+//    whatever the accumulator's rounding (first accumulator); the five
+//    products of order <= 4 beyond it go to the second (the error-free
+//    splitting idea of Ozaki et al. with bf16 slices).
+// Real form on the left operand in both: operand rows [Re a | -Im a] and
+// [Im a | Re a], B' row c = [Re b | Im b] (K-major), so that the accumulator
+// rows are Re and Im of the complex product.
 // Every wait is bounded; a wait that runs out sets the context error word, and
 // all roles then leave their loops.
 #include <cuda.h>
@@ -55,32 +52,21 @@ namespace tc {
 constexpr int NT_MAX = 128;         // complex columns per tile
 constexpr int MROWS = 64;           // complex rows per tile (128 real rows)
 constexpr int KSTEP = 16;           // complex k per pipeline stage (32 real K')
-constexpr int STAGING_BYTES = MROWS * 33 * 8;   // 64 rows x 32 cols float2, row pitch 33
-constexpr int N_EPI_WARPS = 4, MMA_WARP = 4, N_PROD_WARPS = 16;
-constexpr int THREADS = 32 * (N_EPI_WARPS + 1 + N_PROD_WARPS);
-constexpr int PROD_THREADS = 32 * N_PROD_WARPS;
-constexpr int GROUP_THREADS = PROD_THREADS / 2;  // producers of one k-step parity
 constexpr int TMEM_COLS = 512;      // 2 buffers x 2 groups x 128 columns
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
-// Per-precision layout of one pipeline stage.  K' = 32 real values per row:
-// 128 B rows (TF32, 128-byte swizzle) or 64 B rows (BF16, 64-byte swizzle).
+// Per-precision operand format.  K' = 32 real values per row: 128 B rows
+// (TF32, 128-byte swizzle) or 64 B rows (BF16, 64-byte swizzle); the slices
+// of the split and the shared-memory descriptor's swizzle mode and atom size.
 template <int PREC>
 struct Tr;
 template <>
 struct Tr<FRG_3XTF32> {
-  static constexpr int SLICES = 2, ROWB = 128, NSTAGE = 3, SWZ_MODE = 2, ATOM = 1024, KINSTR = 8;
+  static constexpr int SLICES = 2, ROWB = 128, SWZ_MODE = 2, ATOM = 1024;
 };
 template <>
 struct Tr<FRG_BF16X3> {
-  static constexpr int SLICES = 3, ROWB = 64, NSTAGE = 4, SWZ_MODE = 4, ATOM = 512, KINSTR = 16;
-};
-template <int PREC>
-struct Lay {
-  static constexpr int A_SLICE = 128 * Tr<PREC>::ROWB;
-  static constexpr int B_SLICE = NT_MAX * Tr<PREC>::ROWB;
-  static constexpr int STAGE = Tr<PREC>::SLICES * (A_SLICE + B_SLICE);
-  static constexpr int SMEM = 1024 + Tr<PREC>::NSTAGE * STAGE + STAGING_BYTES + 256;
+  static constexpr int SLICES = 3, ROWB = 64, SWZ_MODE = 4, ATOM = 512;
 };
 
 struct TcWork {
@@ -150,28 +136,11 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
-}
-__device__ __forceinline__ void named_bar(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Shared-memory matrix descriptor (K-major, swizzled): start address, stride
@@ -207,114 +176,15 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
     mma_bf16(d, a, b, id, acc);
 }
 
-// Byte offset of 16-byte chunk `ch` of row `row` in a swizzled K-major tile:
-// 128-byte rows: chunk ^= row % 8 (8-row atoms of 1024 B);
-// 64-byte rows:  chunk ^= (row / 2) % 4 (8-row atoms of 512 B).
-template <int PREC>
-__device__ __forceinline__ uint32_t swz(int row, int ch) {
-  if (PREC == FRG_3XTF32) return (uint32_t)(row * 128 + ((ch ^ (row & 7)) << 4));
-  return (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4));
-}
-
 // ----------------------------------------------------------- operands ----
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// Operand rows of the FP32 vertex layouts (see frg_layout.cu for the table).
-struct Srcs {
-  const float2 *YN, *YW, *YX;
-};
-
 struct TileInfo {
   int point, N, NT, nk, r0, c0, D16;
   Geom g;
 };
-
-// Left operand, K indices kq..kq+3 (never across a dph half), local row r.
-template <int CH>
-__device__ __forceinline__ void fetch_left(const PointDesc &P, const Srcs &S, const TileInfo &ti, int r, int kq,
-                                           float2 out[4]) {
-  const int N = ti.N;
-  const Geom &g = ti.g;
-  const int rr = ti.r0 + r;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) out[j] = make_float2(0.f, 0.f);
-  if (rr >= g.D) return;
-  if (CH == CH_PP) {
-    const int a = g.row_lo + rr, s = g.x;
-    const float2 *row = S.YN + ((size_t)a * N + (s - a)) * N;
-    const float2 *L = P.Lpp32 + (size_t)s * N;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = kq + j;
-      if (k < g.D) out[j] = cmulf(__ldg(row + g.p_lo + k), __ldg(L + g.p_lo + k));
-    }
-  } else if (CH == CH_XPH) {
-    const int k3 = g.row_lo + rr, Q = g.x;
-    const float2 *row = S.YW + ((size_t)(k3 + Q) * N + k3) * N;
-    const float2 *L = P.Lph32 + (size_t)(Q + N - 1) * N;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = kq + j;
-      if (k < g.D) out[j] = cmulf(__ldg(row + g.p_lo + k), __ldg(L + g.p_lo + k));
-    }
-  } else {
-    const int k1 = g.row_lo + rr, t = g.x;
-    const int half = kq >= ti.D16;
-    const int kl = kq - (half ? ti.D16 : 0);
-    const size_t ro = ((size_t)k1 * N + (k1 + t)) * N;
-    const float2 *rowA = S.YX + ro, *rowC = S.YW + ro;
-    const float2 *L = P.Lph32 + (size_t)(-t + N - 1) * N;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = kl + j;
-      if (k < g.D) {
-        const int p = g.p_lo + k;
-        const float2 A = __ldg(rowA + p), Lv = __ldg(L + p);
-        if (!half) {
-          const float2 C = __ldg(rowC + p);
-          out[j] = cmulf(make_float2(2.f * A.x - C.x, 2.f * A.y - C.y), Lv);
-        } else {
-          out[j] = cmulf(make_float2(-A.x, -A.y), Lv);
-        }
-      }
-    }
-  }
-}
-
-// Right operand, K indices kq..kq+3, absolute columns cc and cc+1 (cc even).
-template <int CH>
-__device__ __forceinline__ void fetch_right(const Srcs &S, const TileInfo &ti, float U, int kq, int cc, float2 v0[4],
-                                            float2 v1[4]) {
-  const int N = ti.N;
-  const Geom &g = ti.g;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) v0[j] = v1[j] = make_float2(0.f, 0.f);
-  if (cc >= N) return;  // N even: cc + 1 < N as well
-  // columns whose fourth frequency leaves the box take the bare U
-  const int f0 = CH == CH_PP ? g.x - cc : (CH == CH_DPH ? cc - g.x : cc + g.x);
-  const int f1 = CH == CH_PP ? f0 - 1 : f0 + 1;
-  const bool ok0 = (unsigned)f0 < (unsigned)N, ok1 = (unsigned)f1 < (unsigned)N;
-  const int half = CH == CH_DPH ? (kq >= ti.D16) : 0;
-  const int kl = kq - (half ? ti.D16 : 0);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int k = kl + j;
-    if (k >= g.D) continue;
-    const int p = g.p_lo + k;
-    const float2 *row;
-    if (CH == CH_PP)
-      row = S.YN + ((size_t)p * N + (g.x - p)) * N;
-    else if (CH == CH_XPH)
-      row = S.YW + ((size_t)(p + g.x) * N + p) * N;
-    else
-      row = (half ? S.YW : S.YX) + ((size_t)(p - g.x) * N + p) * N;
-    const float4 x = __ldg(reinterpret_cast<const float4 *>(row + cc));
-    v0[j] = ok0 ? make_float2(x.x, x.y) : make_float2(U, 0.f);
-    v1[j] = ok1 ? make_float2(x.z, x.w) : make_float2(U, 0.f);
-  }
-}
 
 // Output row pointer (channel layout) of local row rr.
 template <int CH>
@@ -388,281 +258,25 @@ __device__ __forceinline__ bool tile_info(const PointDesc *__restrict__ pts, con
   return io[w.point].active != 0;
 }
 
-// Write 4 consecutive K' values (positions 4*g4 .. 4*g4+3 of a 32-wide row) of
-// every slice of one operand row.
-template <int PREC>
-struct Emit;
-template <>
-struct Emit<FRG_3XTF32> {
-  static constexpr int SL = 2;
-  float4 v[2];
-  __device__ __forceinline__ void make(const float x[4], float, float) {
-    split_tf32(x[0], v[0].x, v[1].x);
-    split_tf32(x[1], v[0].y, v[1].y);
-    split_tf32(x[2], v[0].z, v[1].z);
-    split_tf32(x[3], v[0].w, v[1].w);
-  }
-  __device__ __forceinline__ void neg() {
-    for (int i = 0; i < 2; ++i) v[i] = make_float4(-v[i].x, -v[i].y, -v[i].z, -v[i].w);
-  }
-  __device__ __forceinline__ void store(uint8_t *tile, int slice_bytes, int row, int g4) const {
-    for (int i = 0; i < 2; ++i)
-      *reinterpret_cast<float4 *>(tile + i * slice_bytes + swz<FRG_3XTF32>(row, g4)) = v[i];
-  }
-};
-template <>
-struct Emit<FRG_BF16X3> {
-  static constexpr int SL = 3;
-  uint2 v[3];
-  __device__ __forceinline__ void make(const float x[4], float inv, float sc) {
-    __nv_bfloat16 s[3][4];
-    for (int j = 0; j < 4; ++j) slice3(x[j], inv, sc, s[0][j], s[1][j], s[2][j]);
-    for (int i = 0; i < 3; ++i) {
-      __nv_bfloat162 lo = __halves2bfloat162(s[i][0], s[i][1]);
-      __nv_bfloat162 hi = __halves2bfloat162(s[i][2], s[i][3]);
-      v[i] = make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
-    }
-  }
-  __device__ __forceinline__ void neg() {
-    for (int i = 0; i < 3; ++i) v[i] = make_uint2(v[i].x ^ 0x80008000u, v[i].y ^ 0x80008000u);
-  }
-  __device__ __forceinline__ void store(uint8_t *tile, int slice_bytes, int row, int g4) const {
-    for (int i = 0; i < 3; ++i)
-      *reinterpret_cast<uint2 *>(tile + i * slice_bytes + swz<FRG_BF16X3>(row, g4 >> 1) + (g4 & 1) * 8) = v[i];
-  }
-};
-
-// ------------------------------------------------------------- kernel ----
-template <int CH, int PREC>
-__global__ void __launch_bounds__(THREADS, 1)
-    k_contract_tc(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const TcWork *__restrict__ work,
-                  int nwork, const int *__restrict__ nt_of, unsigned *__restrict__ err) {
-  using T = Tr<PREC>;
-  using LY = Lay<PREC>;
-  constexpr int NSTAGE = T::NSTAGE;
-  extern __shared__ uint8_t smem_raw[];
-  // offset the shared array itself (keeps the shared state space for ld/st.shared)
-  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t *stages = smem;
-  float2 *staging = reinterpret_cast<float2 *>(smem + NSTAGE * LY::STAGE);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NSTAGE * LY::STAGE + STAGING_BYTES);
-  uint64_t *full = bars, *empty = bars + NSTAGE, *tfull = bars + 2 * NSTAGE, *tempty = bars + 2 * NSTAGE + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 4);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full[s], GROUP_THREADS);
-      mbar_init(&empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 32 * N_EPI_WARPS);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == MMA_WARP) tmem_alloc(tmem_slot, TMEM_COLS);
-  tc_before();
-  __syncthreads();
-  tc_after();
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp >= MMA_WARP + 1) {
-    // ------------------------------------------------------ producers ----
-    const int ptid = tid - 32 * (MMA_WARP + 1);
-    const uint32_t parity = ptid / GROUP_THREADS;
-    const int lt = ptid % GROUP_THREADS;
-    uint32_t it = 0;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      const bool active = tile_info<CH>(pts, io, work[wi], nt_of, ti);
-      if (!active) continue;
-      const PointDesc &P = pts[ti.point];
-      const Srcs S = {static_cast<const float2 *>(io[ti.point].gam), P.Y32W, P.Y32X};
-      const float U = (float)P.U;
-      float invA = 1.f, scA = 1.f, invB = 1.f, scB = 1.f;
-      if (PREC == FRG_BF16X3) {
-        const float vb = fmaxf(__uint_as_float(*P.vmax), fabsf(U));
-        const int m = work[wi].m;
-        const int row = (CH == CH_PP ? 0 : (2 * ti.N - 1)) + (CH == CH_DPH ? (2 * ti.N - 2 - m) : m);
-        const float lb = P.Lmax[row] * vb * (CH == CH_DPH ? 6.f : 2.f);
-        const int eB = bound_exp(vb), eA = bound_exp(lb);
-        invB = pow2f(-eB);
-        scB = pow2f(eB);
-        invA = pow2f(-eA);
-        scA = pow2f(eA);
-      }
-      // this thread's tasks: A' (row r, 4-k group qa); B' (column pair cp, 4-k group qb)
-      const int r = lt >> 2, qa = lt & 3;
-      const int half_nt = ti.NT / 2;
-      const bool has_b = lt < 2 * ti.NT;
-      const int cp = lt % half_nt, qb = lt / half_nt;
-      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
-        if ((it & 1u) != parity) continue;
-        const int s = it % NSTAGE;
-        const uint32_t ph = (it / NSTAGE) & 1u;
-        const int k0 = kb * KSTEP;
-        float2 a[4], v0[4], v1[4];
-        fetch_left<CH>(P, S, ti, r, k0 + 4 * qa, a);
-        if (has_b) fetch_right<CH>(S, ti, U, k0 + 4 * qb, ti.c0 + 2 * cp, v0, v1);
-        if (!mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) goto prod_done;
-        {
-          uint8_t *A = stages + s * LY::STAGE;
-          float re[4], im[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            re[j] = a[j].x;
-            im[j] = a[j].y;
-          }
-          Emit<PREC> er, ei;
-          er.make(re, invA, scA);
-          ei.make(im, invA, scA);
-          er.store(A, LY::A_SLICE, r, qa);           // Re row, first half:  Re a
-          ei.store(A, LY::A_SLICE, r + 64, qa);      // Im row, first half:  Im a
-          er.store(A, LY::A_SLICE, r + 64, qa + 4);  // Im row, second half: Re a
-          ei.neg();
-          ei.store(A, LY::A_SLICE, r, qa + 4);       // Re row, second half: -Im a
-        }
-        if (has_b) {
-          uint8_t *B = stages + s * LY::STAGE + T::SLICES * LY::A_SLICE;
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            const float2 *v = side ? v1 : v0;
-            float re[4], im[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              re[j] = v[j].x;
-              im[j] = v[j].y;
-            }
-            Emit<PREC> er, ei;
-            er.make(re, invB, scB);
-            ei.make(im, invB, scB);
-            er.store(B, LY::B_SLICE, 2 * cp + side, qb);
-            ei.store(B, LY::B_SLICE, 2 * cp + side, qb + 4);
-          }
-        }
-        fence_async_smem();
-        mbar_arrive(&full[s]);
-      }
-    }
-  prod_done:;
-  } else if (warp == MMA_WARP) {
-    // ------------------------------------------------------ MMA issue ----
-    uint32_t it = 0, tcount = 0;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      const int buf = tcount & 1;
-      if (!mbar_wait(&tempty[buf], ((tcount >> 1) & 1u) ^ 1u, err, abort_flag)) break;
-      tc_after();
-      const uint32_t d0 = tmem + (uint32_t)(buf * 256);  // group 0 columns
-      const uint32_t d1 = d0 + 128;                       // group 1 columns
-      const uint32_t id = idesc<PREC>(ti.NT);
-      bool ok = true;
-      for (int kb = 0; kb < ti.nk; ++kb, ++it) {
-        const int s = it % NSTAGE;
-        const uint32_t ph = (it / NSTAGE) & 1u;
-        if (!mbar_wait(&full[s], ph, err, abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_after();
-        if (lane == 0) {
-          const uint32_t a0 = smem_u32(stages + s * LY::STAGE);
-          const uint32_t b0 = a0 + T::SLICES * LY::A_SLICE;
-          constexpr int NI = 32 / T::KINSTR;                                 // instructions per stage
-          constexpr int STEPB = T::KINSTR * (PREC == FRG_3XTF32 ? 4 : 2);  // bytes per instruction
-#pragma unroll
-          for (int kk = 0; kk < NI; ++kk) {
-            const uint32_t off = kk * STEPB;
-            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            auto A_ = [&](int i) { return sdesc<PREC>(a0 + i * LY::A_SLICE + off); };
-            auto B_ = [&](int i) { return sdesc<PREC>(b0 + i * LY::B_SLICE + off); };
-            mma<PREC>(d0, A_(0), B_(0), id, first);  // leading slices
-            mma<PREC>(d1, A_(0), B_(1), id, first);
-            mma<PREC>(d1, A_(1), B_(0), id, 1u);
-            if (PREC == FRG_BF16X3) {
-              mma<PREC>(d1, A_(0), B_(2), id, 1u);
-              mma<PREC>(d1, A_(1), B_(1), id, 1u);
-              mma<PREC>(d1, A_(2), B_(0), id, 1u);
-            }
-          }
-          mma_commit(&empty[s]);
-        }
-        __syncwarp();
-      }
-      if (!ok) break;
-      if (lane == 0) mma_commit(&tfull[buf]);
-      __syncwarp();
-      ++tcount;
-    }
-  } else {
-    // ------------------------------------------------------- epilogue ----
-    uint32_t tcount = 0;
-    const int row_t = warp * 32 + lane;  // TMEM lane = real row of A'
-    const int crow = row_t & 63, comp = row_t >> 6;
-    const int etid = tid;  // 0..127
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-      TileInfo ti;
-      if (!tile_info<CH>(pts, io, work[wi], nt_of, ti)) continue;
-      const int buf = tcount & 1;
-      if (!mbar_wait(&tfull[buf], (tcount >> 1) & 1u, err, abort_flag)) break;
-      tc_after();
-      const PointDesc &P = pts[ti.point];
-      const RhsIO &o = io[ti.point];
-      const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
-      float2 *kN = static_cast<float2 *>(o.dgam);
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 256);
-      for (int cb = 0; cb < ti.NT; cb += 32) {
-        float g0[32], g1[32];
-        tmem_ld32(tl + cb, g0);
-        tmem_ld32(tl + 128 + cb, g1);
-        tmem_wait_ld();
-        float *st = reinterpret_cast<float *>(staging);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) st[(crow * 33 + j) * 2 + comp] = (g0[j] + g1[j]) * sc;
-        named_bar(1, 32 * N_EPI_WARPS);
-        // each warp stores whole 32-column runs of output rows
-#pragma unroll 4
-        for (int i = 0; i < (MROWS * 32) / (32 * N_EPI_WARPS); ++i) {
-          const int idx = i * 32 * N_EPI_WARPS + etid;
-          const int r = idx >> 5, c = idx & 31;
-          const int rr = ti.r0 + r, cc = ti.c0 + cb + c;
-          if (rr < ti.g.D && cc < ti.N && cb + c < ti.NT) out_row<CH>(P, kN, ti, rr)[cc] = staging[r * 33 + c];
-        }
-        named_bar(1, 32 * N_EPI_WARPS);
-      }
-      tc_before();
-      mbar_arrive(&tempty[buf]);
-      ++tcount;
-    }
-  }
-  tc_before();
-  __syncthreads();
-  tc_after();
-  if (warp == MMA_WARP) tmem_dealloc(tmem, TMEM_COLS);
-}
-
 // ===================================================================
-// 3xTF32: one persistent launch over the tiles of all channels and points.
+// The persistent contraction over the tiles of all channels and points.
 //
-// The complex product uses the real form on the output side:
-//   A'' rows 2r = Re a(r,.), rows 2r+1 = Im a(r,.)     (K = 16 per k-step)
-//   B'  rows 2c = Re b(.,c), rows 2c+1 = Im b(.,c)     (N' = 2 NT rows)
-//   D[2r][2c] - D[2r+1][2c+1] = Re(a b)[r][c],  D[2r][2c+1] + D[2r+1][2c] = Im
-// one MMA shape M = 128, N = 2 NT (<= 256), K = 8 per instruction, three
-// products: hi*hi into one TMEM accumulator, hi*lo + lo*hi into a second one
-// (the FP32 accumulator does not round to nearest, so the large sum should see
-// as few additions as possible); each transfer's k-chunks are fed in increasing
-// order of their largest bubble weight.
-// Roles: warps 0-3 epilogue (TMEM -> shuffles -> staged, coalesced stores),
-// warp 4 MMA issue, warp 5 loader (tensor-map TMA of the raw operand rows,
-// NRAW k-steps ahead), warps 6-17 transform (raw -> bubble-weighted, split,
-// 64-byte-swizzled K-major operand tiles in NOP stages).  Every
-// wait is bounded: a wait that runs out sets the context error word and all
-// roles leave their loops.
+// A tile is 64 complex rows x NT <= 128 complex columns; per k-step of 16
+// complex k the left operand goes in its real form (operand rows [Re a | -Im a]
+// and [Im a | Re a], K' = 32) and the right one as rows [Re b | Im b], so that
+// one MMA shape M = 128, N = NT, K' = 32 gives Re and Im of the product in the
+// accumulator rows.  Per k-step: 3xTF32 issues 4 x 3 products of K = 8 (hi*hi
+// into one TMEM accumulator, hi*lo + lo*hi into a second: the FP32 accumulator
+// does not round to nearest, so the large sum should see as few additions as
+// possible), BF16x3 2 x 6 products of K = 16 (leading slices into the first
+// accumulator, the rest into the second).  Each transfer's k-chunks are fed in
+// increasing order of their largest bubble weight.
+// Roles: warps 0-7 epilogue (two per TMEM lane quarter: TMEM -> staged,
+// coalesced stores), warp 8 MMA issue, warp 9 loader (tensor-map TMA of the
+// raw FP32 operand rows, NRAW k-steps ahead), warps 10-21 transform (raw ->
+// bubble-weighted, sliced, swizzled K-major operand tiles in NOP stages).
+// Every wait is bounded: a wait that runs out sets the context error word and
+// all roles leave their loops.
 namespace st {
 // Warp-uniform bounded wait: every lane of the warp leaves with the same result,
 // so warp-collective code after it (shuffles, __syncwarp) never splits.
@@ -670,12 +284,8 @@ __device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t parity, unsigned *
   const bool ok = mbar_wait(bar, parity, err, abort_flag);
   return __all_sync(0xffffffffu, ok);
 }
-constexpr int KS = 16;                                  // complex k per step
-constexpr int ROWB = 128;                               // bytes per operand row: 32 tf32 (K' = 2 KS)
-constexpr int A_SLICE = 128 * ROWB;                     // 16 KB
-constexpr int B_SLICE = NT_MAX * ROWB;                  // 16 KB
-constexpr int OP_STAGE = 2 * (A_SLICE + B_SLICE);       // 64 KB
-constexpr int NOP = 2;
+constexpr int KS = 16;                                  // complex k per step (K' = 2 KS real values)
+constexpr int NOP = 2;                                  // operand stages
 constexpr int RA = 18;                                  // complex per raw left row (aligned window)
 constexpr int RAW_A = MROWS * RA * 8;                   // 9216 B
 constexpr int RAW_B = KS * NT_MAX * 8;                  // 16 KB
@@ -688,22 +298,32 @@ constexpr int EPI_PLANE = 16 * EPI_PITCH;               // floats: 16 rows of on
 constexpr int EPI_STG = 2 * EPI_PLANE * 4;              // bytes per epilogue warp: Re and Im planes
 // warps 0-7 epilogue (two per TMEM lane quarter), 8 MMA, 9 loader, 10-21 transform
 constexpr int EPI_W = 8, MMA_W = 8, LOAD_W = 9, XF_W0 = 10, N_XF = 12;
-constexpr int SMEM = 1024 + NOP * OP_STAGE + NRAW * RAW_STAGE + EPI_W * EPI_STG + 512;
 constexpr int THREADS = 32 * (XF_W0 + N_XF);
-static_assert(SMEM <= 232448, "shared memory budget");
+// One operand stage: SL slices of A' (128 rows) and of B' (NT_MAX rows), rows
+// of K' = 32 values: 128 B for TF32 (two slices, 64 KB per stage), 64 B for
+// BF16 (three slices, 48 KB per stage).
+template <int PREC>
+struct OpL {
+  static constexpr int SL = Tr<PREC>::SLICES, ROWB = Tr<PREC>::ROWB;
+  static constexpr int A_SLICE = 128 * ROWB, B_SLICE = NT_MAX * ROWB;
+  static constexpr int STAGE = SL * (A_SLICE + B_SLICE);
+  static constexpr int IM_ROWS = 16 * ROWB;  // Im row of a complex row: 16 operand rows further
+  static constexpr int SMEM = 1024 + NOP * STAGE + NRAW * RAW_STAGE + EPI_W * EPI_STG + 512;
+  static_assert(SMEM <= 232448, "shared memory budget");
+};
 
 // 128-byte swizzle: 16-byte chunk ch of row r sits at chunk ch ^ (r % 8);
 // 8-row atoms of 1024 B.
 __device__ __forceinline__ uint32_t swz128(int row, int ch) {
   return (uint32_t)(row * 128 + ((ch ^ (row & 7)) << 4));
 }
-__device__ __forceinline__ uint64_t sdesc128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= 1ull << 46;
-  d |= 2ull << 61;
-  return d;
+// Byte offset of the 4-value group q (0..7) of K' in operand row `row`: a
+// 16-byte chunk of a 128-byte TF32 row, half of a 16-byte chunk of a 64-byte
+// BF16 row (64-byte swizzle: chunk ^ (row / 2) % 4, 8-row atoms of 512 B).
+template <int PREC>
+__device__ __forceinline__ uint32_t grp_off(int row, int q) {
+  if (PREC == FRG_3XTF32) return swz128(row, q);
+  return (uint32_t)(row * 64 + (((q >> 1) ^ ((row >> 1) & 3)) << 4) + (q & 1) * 8);
 }
 __device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -846,10 +466,8 @@ __device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__rest
 }
 
 // One transform item: 4 consecutive k of one complex operand row (left) or
-// column (right), split into hi / lo of the real and the imaginary parts.
-struct XfVals {
-  float4 rh, rl, ih, il;
-};
+// column (right), cut into the slices of the precision (TF32: hi / lo; BF16:
+// three slices) of the real and the imaginary parts.
 // Real form of the complex product (one operand row = K' = 32 values: the 16
 // k of the step for the real part, then the same 16 k for the imaginary part):
 //   left row "Re" of complex row r = [Re a | -Im a], row "Im" = [Im a | Re a],
@@ -858,47 +476,118 @@ struct XfVals {
 // of complex row r: 32 (r / 16) + (r % 16) for Re and 16 more for Im, so that
 // every 32-lane TMEM quarter (one epilogue warp) holds both parts of 16 rows.
 // Where an item lives, fixed for all k-steps of a tile: its first raw element
-// and the byte offsets of its 16-byte chunks in the k-group g4 (real half) and
-// 4 + g4 (imaginary half); lanes take consecutive rows of one k-group, so each
-// store instruction of a warp covers all eight bank groups of the swizzle.
+// and the byte offsets of its value groups g4 (real half) and 4 + g4
+// (imaginary half); lanes take consecutive rows of one k-group, so each store
+// instruction of a warp spreads over all bank groups of the swizzle.
 struct XfAt {
   uint32_t lo_half, hi_half;
   int src, l;
   bool valid;
 };
-constexpr uint32_t IM_ROWS = 16 * ROWB;  // Im row of a complex row: 16 operand rows further
+template <int PREC>
 __device__ __forceinline__ XfAt xf_left_at(int t) {
   XfAt a;
   const int r = t & 63, g4 = t >> 6;
   const int row = 32 * (r >> 4) + (r & 15);
-  a.lo_half = swz128(row, g4);
-  a.hi_half = swz128(row, 4 + g4);
+  a.lo_half = grp_off<PREC>(row, g4);
+  a.hi_half = grp_off<PREC>(row, 4 + g4);
   a.src = r * RA + 4 * g4;
   a.l = 4 * g4;
   a.valid = true;
   return a;
 }
+template <int PREC>
 __device__ __forceinline__ XfAt xf_right_at(int bt, int NT) {
   XfAt a;
   a.valid = bt < 4 * NT;
   const int c = bt % NT, g4 = a.valid ? bt / NT : 0;
-  a.lo_half = swz128(c, g4);
-  a.hi_half = swz128(c, 4 + g4);
+  a.lo_half = grp_off<PREC>(c, g4);
+  a.hi_half = grp_off<PREC>(c, 4 + g4);
   a.src = 4 * g4 * NT + c;
   a.l = 0;
   return a;
 }
-__device__ __forceinline__ void split4(XfVals &o, const float re[4], const float im[4]) {
-  split_tf32(re[0], o.rh.x, o.rl.x);
-  split_tf32(re[1], o.rh.y, o.rl.y);
-  split_tf32(re[2], o.rh.z, o.rl.z);
-  split_tf32(re[3], o.rh.w, o.rl.w);
-  split_tf32(im[0], o.ih.x, o.il.x);
-  split_tf32(im[1], o.ih.y, o.il.y);
-  split_tf32(im[2], o.ih.z, o.il.z);
-  split_tf32(im[3], o.ih.w, o.il.w);
-}
 __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+
+// Slices of one item: the real and the imaginary parts of 4 values.
+template <int PREC>
+struct XfV;
+template <>
+struct XfV<FRG_3XTF32> {
+  using L = OpL<FRG_3XTF32>;
+  float4 rh, rl, ih, il;  // hi / lo of Re and Im
+  __device__ __forceinline__ void make(const float re[4], const float im[4], float, float) {
+    split_tf32(re[0], rh.x, rl.x);
+    split_tf32(re[1], rh.y, rl.y);
+    split_tf32(re[2], rh.z, rl.z);
+    split_tf32(re[3], rh.w, rl.w);
+    split_tf32(im[0], ih.x, il.x);
+    split_tf32(im[1], ih.y, il.y);
+    split_tf32(im[2], ih.z, il.z);
+    split_tf32(im[3], ih.w, il.w);
+  }
+  // hi slice at T, lo slice at T + A_SLICE
+  __device__ __forceinline__ void store_left(uint8_t *T, const XfAt &a) const {
+    *reinterpret_cast<float4 *>(T + a.lo_half) = rh;
+    *reinterpret_cast<float4 *>(T + a.hi_half) = neg4(ih);
+    *reinterpret_cast<float4 *>(T + L::IM_ROWS + a.lo_half) = ih;
+    *reinterpret_cast<float4 *>(T + L::IM_ROWS + a.hi_half) = rh;
+    *reinterpret_cast<float4 *>(T + L::A_SLICE + a.lo_half) = rl;
+    *reinterpret_cast<float4 *>(T + L::A_SLICE + a.hi_half) = neg4(il);
+    *reinterpret_cast<float4 *>(T + L::A_SLICE + L::IM_ROWS + a.lo_half) = il;
+    *reinterpret_cast<float4 *>(T + L::A_SLICE + L::IM_ROWS + a.hi_half) = rl;
+  }
+  __device__ __forceinline__ void store_right(uint8_t *T, const XfAt &a) const {
+    *reinterpret_cast<float4 *>(T + a.lo_half) = rh;
+    *reinterpret_cast<float4 *>(T + a.hi_half) = ih;
+    *reinterpret_cast<float4 *>(T + L::B_SLICE + a.lo_half) = rl;
+    *reinterpret_cast<float4 *>(T + L::B_SLICE + a.hi_half) = il;
+  }
+};
+template <>
+struct XfV<FRG_BF16X3> {
+  using L = OpL<FRG_BF16X3>;
+  uint2 r[3], i[3];  // 4 bf16 of each slice of Re and Im
+  __device__ __forceinline__ static uint2 pack(const __nv_bfloat16 v[4]) {
+    __nv_bfloat162 lo = __halves2bfloat162(v[0], v[1]), hi = __halves2bfloat162(v[2], v[3]);
+    return make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+  }
+  // slices on the grids of the operand's bound 2^e (inv = 2^-e, sc = 2^e)
+  __device__ __forceinline__ void make(const float re[4], const float im[4], float inv, float sc) {
+    __nv_bfloat16 sr[3][4], si[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      slice3(re[j], inv, sc, sr[0][j], sr[1][j], sr[2][j]);
+      slice3(im[j], inv, sc, si[0][j], si[1][j], si[2][j]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r[k] = pack(sr[k]);
+      i[k] = pack(si[k]);
+    }
+  }
+  __device__ __forceinline__ static uint2 neg(uint2 v) { return make_uint2(v.x ^ 0x80008000u, v.y ^ 0x80008000u); }
+  // slice k at T + k A_SLICE
+  __device__ __forceinline__ void store_left(uint8_t *T, const XfAt &a) const {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint8_t *t = T + k * L::A_SLICE;
+      *reinterpret_cast<uint2 *>(t + a.lo_half) = r[k];
+      *reinterpret_cast<uint2 *>(t + a.hi_half) = neg(i[k]);
+      *reinterpret_cast<uint2 *>(t + L::IM_ROWS + a.lo_half) = i[k];
+      *reinterpret_cast<uint2 *>(t + L::IM_ROWS + a.hi_half) = r[k];
+    }
+  }
+  __device__ __forceinline__ void store_right(uint8_t *T, const XfAt &a) const {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint8_t *t = T + k * L::B_SLICE;
+      *reinterpret_cast<uint2 *>(t + a.lo_half) = r[k];
+      *reinterpret_cast<uint2 *>(t + a.hi_half) = i[k];
+    }
+  }
+};
+
 // Left item: Lb-weighted, and for the direct channel 2A - C (first half of K)
 // or -A (second half).  No masks: past the valid k of a transfer the bubble
 // weight is zero (the table holds zeros outside the box and the map's fill
@@ -921,9 +610,9 @@ __device__ __forceinline__ void ld4c(const float2 *p, int base, int off, float2 
     v[3] = make_float2(t2.x, t2.y);
   }
 }
-template <int CH>
-__device__ __forceinline__ void xf_left(XfVals &o, const float2 *rA, const float2 *rC, const float2 *rL,
-                                        const XfAt &a, int off, int half) {
+template <int CH, int PREC>
+__device__ __forceinline__ void xf_left(XfV<PREC> &o, const float2 *rA, const float2 *rC, const float2 *rL,
+                                        const XfAt &a, int off, int half, float inv, float sc) {
   float2 v[4], c[4], L[4];
   ld4c(rA, a.src, off, v);
   ld4c(rL, a.l, off, L);
@@ -937,12 +626,14 @@ __device__ __forceinline__ void xf_left(XfVals &o, const float2 *rA, const float
     re[x] = w.x;
     im[x] = w.y;
   }
-  split4(o, re, im);
+  o.make(re, im, inv, sc);
 }
 // Right item: the raw rows as they are.  The FP32 operand copies hold the bare
 // U wherever the fourth frequency leaves the box; rows past the valid k meet
 // zero left weights and columns past the grid are never stored.
-__device__ __forceinline__ void xf_right(XfVals &o, const float2 *rB, const XfAt &a, int NT) {
+template <int PREC>
+__device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const XfAt &a, int NT, float inv,
+                                         float sc) {
   float re[4], im[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -950,39 +641,38 @@ __device__ __forceinline__ void xf_right(XfVals &o, const float2 *rB, const XfAt
     re[x] = b.x;
     im[x] = b.y;
   }
-  split4(o, re, im);
-}
-// hi slice at T, lo slice at T + slice
-__device__ __forceinline__ void xf_store_left(uint8_t *T, int slice, const XfVals &v, const XfAt &a) {
-  *reinterpret_cast<float4 *>(T + a.lo_half) = v.rh;
-  *reinterpret_cast<float4 *>(T + a.hi_half) = neg4(v.ih);
-  *reinterpret_cast<float4 *>(T + IM_ROWS + a.lo_half) = v.ih;
-  *reinterpret_cast<float4 *>(T + IM_ROWS + a.hi_half) = v.rh;
-  *reinterpret_cast<float4 *>(T + slice + a.lo_half) = v.rl;
-  *reinterpret_cast<float4 *>(T + slice + a.hi_half) = neg4(v.il);
-  *reinterpret_cast<float4 *>(T + slice + IM_ROWS + a.lo_half) = v.il;
-  *reinterpret_cast<float4 *>(T + slice + IM_ROWS + a.hi_half) = v.rl;
-}
-__device__ __forceinline__ void xf_store_right(uint8_t *T, int slice, const XfVals &v, const XfAt &a) {
-  *reinterpret_cast<float4 *>(T + a.lo_half) = v.rh;
-  *reinterpret_cast<float4 *>(T + a.hi_half) = v.ih;
-  *reinterpret_cast<float4 *>(T + slice + a.lo_half) = v.rl;
-  *reinterpret_cast<float4 *>(T + slice + a.hi_half) = v.il;
+  o.make(re, im, inv, sc);
 }
 
-// Transform warps: raw rows -> bubble-weighted (left), split hi/lo, swizzled
-// K-major operand tiles.
-template <int CH>
+// Transform warps: raw rows -> bubble-weighted (left), sliced, swizzled
+// K-major operand tiles.  BF16 slices sit on fixed grids below a power-of-two
+// bound of each operand, taken once per tile: the vertex bound of the stage
+// input for the right operand, that times the transfer's largest bubble
+// weight (x 3 for the direct channel's 2A - C), x 2 for a complex product's
+// parts, for the left one.
+template <int CH, int PREC>
 __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                         const RhsIO *__restrict__ io, const StWork &w,
                                         const int *__restrict__ nt_of, uint32_t &it, int xt, int lane) {
+  using L = OpL<PREC>;
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  const uint4 ord = korder_row<CH>(pts[ti.point], ti.N, w.m);
+  const PointDesc &P = pts[ti.point];
+  const uint4 ord = korder_row<CH>(P, ti.N, w.m);
+  float invA = 1.f, scA = 1.f, invB = 1.f, scB = 1.f;
+  if (PREC == FRG_BF16X3) {
+    const float vb = fmaxf(__uint_as_float(*P.vmax), fabsf((float)P.U));
+    const int row = CH == CH_PP ? w.m : (2 * ti.N - 1) + (CH == CH_XPH ? w.m : 2 * ti.N - 2 - w.m);
+    const int eB = bound_exp(vb), eA = bound_exp(P.Lmax[row] * vb * (CH == CH_DPH ? 6.f : 2.f));
+    invB = pow2f(-eB);
+    scB = pow2f(eB);
+    invA = pow2f(-eA);
+    scA = pow2f(eA);
+  }
   // warps 0-7: left item xt and right item xt; warps 8-11: right items xt and xt + 128
   const bool lr = xt < 256;
-  const XfAt a0 = lr ? xf_left_at(xt) : xf_right_at(xt, ti.NT);
-  const XfAt a1 = xf_right_at(lr ? xt : xt + 128, ti.NT);
+  const XfAt a0 = lr ? xf_left_at<PREC>(xt) : xf_right_at<PREC>(xt, ti.NT);
+  const XfAt a1 = xf_right_at<PREC>(lr ? xt : xt + 128, ti.NT);
   for (int ki = 0; ki < ti.nk; ++ki, ++it) {
     const int j = it % NRAW, s = it % NOP;
     if (!wwait(&S.raw_full[j], (it / NRAW) & 1u, S.err, S.abort_flag)) return false;
@@ -993,12 +683,12 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     const float2 *rC = reinterpret_cast<const float2 *>(raw + RAW_A);
     const float2 *rB = reinterpret_cast<const float2 *>(raw + 2 * RAW_A);
     const float2 *rL = reinterpret_cast<const float2 *>(raw + 2 * RAW_A + RAW_B);
-    uint8_t *A = S.ops + s * OP_STAGE;
-    uint8_t *B = A + 2 * A_SLICE;
-    XfVals va, vb;
-    if (lr) xf_left<CH>(va, rA, rC, rL, a0, off, q.half);
-    else xf_right(va, rB, a0, ti.NT);
-    xf_right(vb, rB, a1, ti.NT);
+    uint8_t *A = S.ops + s * L::STAGE;
+    uint8_t *B = A + L::SL * L::A_SLICE;
+    XfV<PREC> va, vb;
+    if (lr) xf_left<CH, PREC>(va, rA, rC, rL, a0, off, q.half, invA, scA);
+    else xf_right<PREC>(va, rB, a0, ti.NT, invB, scB);
+    xf_right<PREC>(vb, rB, a1, ti.NT, invB, scB);
     // the raw rows are in registers: hand the raw stage back to the loader
     // before waiting for a free operand stage.  The loader's next tensor-map
     // copy into this stage is an async-proxy write: the proxy fence orders
@@ -1008,9 +698,9 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.raw_empty[j]);
     if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
-    if (lr) xf_store_left(A, A_SLICE, va, a0);
-    else if (a0.valid) xf_store_right(B, B_SLICE, va, a0);
-    if (a1.valid) xf_store_right(B, B_SLICE, vb, a1);
+    if (lr) va.store_left(A, a0);
+    else if (a0.valid) va.store_right(B, a0);
+    if (a1.valid) vb.store_right(B, a1);
     // one arrival per warp: the generic-proxy writes are fenced for the
     // tensor cores by every writer, then the warp converges
     fence_async_smem();
@@ -1043,13 +733,17 @@ __device__ __forceinline__ TSlot tslot_next(TBuf &t) {
   return s;
 }
 
-// MMA issue (one warp, lane 0 issues): per k-step hi*hi into one TMEM
-// accumulator and hi*lo + lo*hi into a second one, so that the large sum takes
-// a third of the accumulation steps.
-template <int CH>
+// MMA issue (one warp, lane 0 issues).  3xTF32: per k-step hi*hi into one
+// TMEM accumulator and hi*lo + lo*hi into a second one, so that the large sum
+// takes a third of the accumulation steps.  BF16x3: the product of the
+// leading slices into the first accumulator (its sum is exact in FP32: the
+// slices are integers times a power of two below 2^8), the five products of
+// order up to 4 beyond it into the second.
+template <int CH, int PREC>
 __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
                                          const int *__restrict__ nt_of, uint32_t &it, TBuf &tb, int lane) {
+  using L = OpL<PREC>;
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
   const TSlot ts = tslot_next(tb);
@@ -1058,20 +752,29 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
   ++e;
   tc_after();
   const uint32_t d = S.tmem + ts.dcol, dx = S.tmem + ts.xcol;
-  const uint32_t id = idesc<FRG_3XTF32>(ti.NT);
+  const uint32_t id = idesc<PREC>(ti.NT);
   for (int kb = 0; kb < ti.nk; ++kb, ++it) {
     const int s = it % NOP;
     if (!wwait(&S.op_full[s], (it / NOP) & 1u, S.err, S.abort_flag)) return false;
     tc_after();
     if (lane == 0) {
-      const uint32_t a0 = smem_u32(S.ops + s * OP_STAGE), b0 = a0 + 2 * A_SLICE;
+      const uint32_t a0 = smem_u32(S.ops + s * L::STAGE), b0 = a0 + L::SL * L::A_SLICE;
+      auto A_ = [&](int k, uint32_t o) { return sdesc<PREC>(a0 + k * L::A_SLICE + o); };
+      auto B_ = [&](int k, uint32_t o) { return sdesc<PREC>(b0 + k * L::B_SLICE + o); };
+      // 32 bytes of K' per instruction: 8 tf32 or 16 bf16
+      constexpr int NI = PREC == FRG_3XTF32 ? 4 : 2;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t o = kk * 32;  // 8 tf32 of K' per instruction
+      for (int kk = 0; kk < NI; ++kk) {
+        const uint32_t o = kk * 32;
         const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-        mma_tf32(d, sdesc128(a0 + o), sdesc128(b0 + o), id, first);                    // hi*hi
-        mma_tf32(dx, sdesc128(a0 + o), sdesc128(b0 + B_SLICE + o), id, first);         // hi*lo
-        mma_tf32(dx, sdesc128(a0 + A_SLICE + o), sdesc128(b0 + o), id, 1u);            // lo*hi
+        mma<PREC>(d, A_(0, o), B_(0, o), id, first);   // leading slices
+        mma<PREC>(dx, A_(0, o), B_(1, o), id, first);
+        mma<PREC>(dx, A_(1, o), B_(0, o), id, 1u);
+        if (PREC == FRG_BF16X3) {
+          mma<PREC>(dx, A_(0, o), B_(2, o), id, 1u);
+          mma<PREC>(dx, A_(1, o), B_(1, o), id, 1u);
+          mma<PREC>(dx, A_(2, o), B_(0, o), id, 1u);
+        }
       }
       mma_commit(&S.op_empty[s]);
     }
@@ -1166,16 +869,17 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   return true;
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
-    k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const StWork *__restrict__ work,
-                    const int *__restrict__ cta_start, const int *__restrict__ nt_of, unsigned *__restrict__ err,
-                    const CUtensorMap *__restrict__ maps) {
+template <int PREC>
+__device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                         const StWork *__restrict__ work, const int *__restrict__ cta_start,
+                                         const int *__restrict__ nt_of, unsigned *__restrict__ err,
+                                         const CUtensorMap *__restrict__ maps) {
   extern __shared__ uint8_t smem_raw[];
   // offset the shared array itself (keeps the shared state space for ld/st.shared)
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   Pipe S;
   S.ops = smem;
-  S.raws = S.ops + NOP * OP_STAGE;
+  S.raws = S.ops + NOP * OpL<PREC>::STAGE;
   S.epi_stg = reinterpret_cast<float *>(S.raws + NRAW * RAW_STAGE);
   uint64_t *bars = reinterpret_cast<uint64_t *>(S.raws + NRAW * RAW_STAGE + EPI_W * EPI_STG);
   S.raw_full = bars;
@@ -1214,6 +918,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 #define FRG_BY_CH(f, ...) \
   (w.ch == CH_PP ? f<CH_PP>(__VA_ARGS__) : w.ch == CH_DPH ? f<CH_DPH>(__VA_ARGS__) : f<CH_XPH>(__VA_ARGS__))
+#define FRG_BY_CH_P(f, ...)                                                                     \
+  (w.ch == CH_PP ? f<CH_PP, PREC>(__VA_ARGS__) : w.ch == CH_DPH ? f<CH_DPH, PREC>(__VA_ARGS__) \
+                                                                : f<CH_XPH, PREC>(__VA_ARGS__))
   if (warp == LOAD_W) {
     uint32_t it = 0;
     for (int wi = w0; wi < w1; ++wi) {
@@ -1228,14 +935,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t it = 0;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH(xf_tile, S, pts, io, w, nt_of, it, xt, lane)) break;
+      if (!FRG_BY_CH_P(xf_tile, S, pts, io, w, nt_of, it, xt, lane)) break;
     }
   } else if (warp == MMA_W) {
     uint32_t it = 0;
     TBuf tb;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH(mma_tile, S, pts, io, w, nt_of, it, tb, lane)) break;
+      if (!FRG_BY_CH_P(mma_tile, S, pts, io, w, nt_of, it, tb, lane)) break;
     }
   } else {
     TBuf tb;
@@ -1245,10 +952,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   }
 #undef FRG_BY_CH
+#undef FRG_BY_CH_P
   tc_before();
   __syncthreads();
   tc_after();
   if (warp == MMA_W) tmem_dealloc(S.tmem, TMEM_COLS);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const StWork *__restrict__ work,
+                    const int *__restrict__ cta_start, const int *__restrict__ nt_of, unsigned *__restrict__ err,
+                    const CUtensorMap *__restrict__ maps) {
+  contract<FRG_3XTF32>(pts, io, work, cta_start, nt_of, err, maps);
+}
+__global__ void __launch_bounds__(THREADS, 1)
+    k_contract_bf16x3(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                      const StWork *__restrict__ work, const int *__restrict__ cta_start,
+                      const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps) {
+  contract<FRG_BF16X3>(pts, io, work, cta_start, nt_of, err, maps);
 }
 }  // namespace st
 
@@ -1284,10 +1005,6 @@ struct TcPlan {
   int n = 0;
   int *d_nt = nullptr;
   unsigned *d_err = nullptr;  // owned by the context
-  tc::TcWork *d_all[3] = {nullptr, nullptr, nullptr};
-  int nall[3] = {0, 0, 0};
-  tc::TcWork *d_pt[3] = {nullptr, nullptr, nullptr};
-  std::vector<int> off[3];
   bool half = false;  // reversal reduction: transfers m <= N - 1 only
   // 3xTF32: one launch for all enabled channels; schedule [0] covers every
   // point, [1 + i] point i alone
@@ -1415,19 +1132,6 @@ static bool encode_maps(TcPlan *p, const std::vector<PointDesc> &pts, std::strin
   return true;
 }
 
-template <int PREC>
-static bool set_smem_attrs() {
-  bool ok = true;
-#define FRG_SETATTR(C)                                                                                   \
-  ok = ok && cudaFuncSetAttribute(tc::k_contract_tc<C, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                  tc::Lay<PREC>::SMEM) == cudaSuccess
-  FRG_SETATTR(CH_PP);
-  FRG_SETATTR(CH_DPH);
-  FRG_SETATTR(CH_XPH);
-#undef FRG_SETATTR
-  return ok;
-}
-
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
                    int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why, TcTune tune) {
   (void)d_pts;
@@ -1464,41 +1168,13 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
   for (int i = 0; i < p->n; ++i) nt[i] = std::min(tune.nt_cap, (pts[i].N + 15) / 16 * 16);
   bool ok = cudaMalloc(&p->d_nt, sizeof(int) * p->n) == cudaSuccess &&
             cudaMemcpy(p->d_nt, nt.data(), sizeof(int) * p->n, cudaMemcpyHostToDevice) == cudaSuccess;
-  for (int ch = 0; ch < 3 && ok; ++ch) {
-    std::vector<std::pair<int, tc::TcWork>> all, one;
-    std::vector<tc::TcWork> per;
-    p->off[ch].push_back(0);
-    for (int i = 0; i < p->n; ++i) {
-      one.clear();
-      const int N = pts[i].N;
-      for (int m = 0; m < (p->half ? N : 2 * N - 1); ++m) {
-        Geom g = geom(ch, N, m);
-        const int nk = (g.K + tc::KSTEP - 1) / tc::KSTEP;
-        for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
-          for (int ct = 0; ct * nt[i] < N; ++ct) one.push_back({nk, tc::TcWork{i, m, rt, ct}});
-      }
-      std::stable_sort(one.begin(), one.end(), [](auto &a, auto &b) { return a.first > b.first; });
-      for (auto &x : one) per.push_back(x.second);
-      all.insert(all.end(), one.begin(), one.end());
-      p->off[ch].push_back((int)per.size());
-    }
-    std::stable_sort(all.begin(), all.end(), [](auto &a, auto &b) { return a.first > b.first; });
-    std::vector<tc::TcWork> allw;
-    for (auto &x : all) allw.push_back(x.second);
-    p->nall[ch] = (int)allw.size();
-    ok = cudaMalloc(&p->d_all[ch], sizeof(tc::TcWork) * allw.size()) == cudaSuccess &&
-         cudaMalloc(&p->d_pt[ch], sizeof(tc::TcWork) * per.size()) == cudaSuccess &&
-         cudaMemcpy(p->d_all[ch], allw.data(), sizeof(tc::TcWork) * allw.size(), cudaMemcpyHostToDevice) ==
-             cudaSuccess &&
-         cudaMemcpy(p->d_pt[ch], per.data(), sizeof(tc::TcWork) * per.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-  }
   p->mask = (params.empty() ? FRG_CH_ALL : params[0].channel_mask) & 7;
-  if (precision == FRG_3XTF32 && ok) {
+  if (ok) {
     p->sched.resize(1 + p->n);
     ok = build_sched(p, pts, nt, 0, p->n, p->sched[0]);
     for (int i = 0; i < p->n && ok; ++i) ok = build_sched(p, pts, nt, i, i + 1, p->sched[1 + i]);
   }
-  if (precision == FRG_3XTF32 && ok) {
+  if (ok) {
     std::string mw;
     ok = encode_maps(p, pts, mw);
     if (!ok) {
@@ -1509,9 +1185,10 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
   }
   if (precision == FRG_3XTF32) {
     ok = ok && cudaFuncSetAttribute(tc::st::k_contract_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    tc::st::SMEM) == cudaSuccess;
+                                    tc::st::OpL<FRG_3XTF32>::SMEM) == cudaSuccess;
   } else {
-    ok = ok && set_smem_attrs<FRG_BF16X3>();
+    ok = ok && cudaFuncSetAttribute(tc::st::k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::st::OpL<FRG_BF16X3>::SMEM) == cudaSuccess;
   }
   if (!ok) {
     why = std::string("tensor-core plan setup failed: ") + cudaGetErrorString(cudaGetLastError());
@@ -1530,23 +1207,7 @@ void tc_plan_destroy(TcPlan *p) {
     cudaFree(sc.d_work);
     cudaFree(sc.d_start);
   }
-  for (int ch = 0; ch < 3; ++ch) {
-    cudaFree(p->d_all[ch]);
-    cudaFree(p->d_pt[ch]);
-  }
   delete p;
-}
-
-template <int PREC>
-static void launch_one(int ch, int grid, cudaStream_t st, const PointDesc *d_pts, const RhsIO *d_io,
-                       const tc::TcWork *w, int nw, const int *d_nt, unsigned *d_err) {
-  const int smem = tc::Lay<PREC>::SMEM;
-  if (ch == CH_PP)
-    tc::k_contract_tc<CH_PP, PREC><<<grid, tc::THREADS, smem, st>>>(d_pts, d_io, w, nw, d_nt, d_err);
-  else if (ch == CH_DPH)
-    tc::k_contract_tc<CH_DPH, PREC><<<grid, tc::THREADS, smem, st>>>(d_pts, d_io, w, nw, d_nt, d_err);
-  else
-    tc::k_contract_tc<CH_XPH, PREC><<<grid, tc::THREADS, smem, st>>>(d_pts, d_io, w, nw, d_nt, d_err);
 }
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
@@ -1557,33 +1218,17 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   }
   if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
   if (wait_before && cudaStreamWaitEvent(st, wait_before, 0) != cudaSuccess) return -3;
-  if (p->precision == FRG_3XTF32) {
-    if ((chmask & 7) != p->mask || point >= p->n) return -1;
-    const TcPlan::Sched &sc = p->sched[point < 0 ? 0 : 1 + point];
-    if (sc.grid) {
-      tc::st::k_contract_tf32<<<sc.grid, tc::st::THREADS, tc::st::SMEM, st>>>(d_pts, d_io, sc.d_work, sc.d_start,
-                                                                              p->d_nt, p->d_err, p->d_maps);
-      FRG_COUNT(1);
-      if (cudaGetLastError() != cudaSuccess) return -3;
-    }
-  } else {
-    for (int ch = 0; ch < 3; ++ch) {
-      if (!(chmask & (1 << ch))) continue;
-      const tc::TcWork *w;
-      int nw;
-      if (point < 0) {
-        w = p->d_all[ch];
-        nw = p->nall[ch];
-      } else {
-        w = p->d_pt[ch] + p->off[ch][point];
-        nw = p->off[ch][point + 1] - p->off[ch][point];
-      }
-      if (!nw) continue;
-      const int grid = std::min(nw, p->sms);
-      launch_one<FRG_BF16X3>(ch, grid, st, d_pts, d_io, w, nw, p->d_nt, p->d_err);
-      FRG_COUNT(1);
-      if (cudaGetLastError() != cudaSuccess) return -3;
-    }
+  if ((chmask & 7) != p->mask || point >= p->n) return -1;
+  const TcPlan::Sched &sc = p->sched[point < 0 ? 0 : 1 + point];
+  if (sc.grid) {
+    if (p->precision == FRG_3XTF32)
+      tc::st::k_contract_tf32<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_3XTF32>::SMEM, st>>>(
+          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps);
+    else
+      tc::st::k_contract_bf16x3<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_BF16X3>::SMEM, st>>>(
+          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps);
+    FRG_COUNT(1);
+    if (cudaGetLastError() != cudaSuccess) return -3;
   }
   if (ev_contract && cudaEventRecord(ev_contract, st) != cudaSuccess) return -3;
   // channel outputs in their own layouts -> natural layout (the scatter-add,
