@@ -39,7 +39,6 @@
 #include <string>
 #include <vector>
 
-#include <cuda_bf16.h>
 
 #include "frg.h"
 #include "frg_layout.cuh"
@@ -229,18 +228,27 @@ __device__ __forceinline__ int bound_exp(float bound) {
   return max(-90, min(100, e));
 }
 
-// Three bf16 slices of x on the grids 2^(e-7), 2^(e-15), 2^(e-23).
-__device__ __forceinline__ void slice3(float x, float inv, float sc, __nv_bfloat16 &a, __nv_bfloat16 &b,
-                                       __nv_bfloat16 &c) {
-  const float xs = x * inv;
-  const float s1 = rintf(xs * 128.f) * 0.0078125f;
-  const float r1 = xs - s1;
-  const float s2 = rintf(r1 * 32768.f) * 3.0517578125e-05f;
-  const float r2 = r1 - s2;
-  const float s3 = rintf(r2 * 8388608.f) * 1.1920928955078125e-07f;
-  a = __float2bfloat16_rn(s1 * sc);
-  b = __float2bfloat16_rn(s2 * sc);
-  c = __float2bfloat16_rn(s3 * sc);
+// Three bf16 slices of x (|x| < 2^e) on the grids 2^(e-7), 2^(e-15),
+// 2^(e-23): each slice is x's residual rounded to nearest (ties to even) on its
+// grid by adding and subtracting c = 1.5 * 2^(23 + grid exponent), whose ulp
+// is the grid; the residuals are exact and every slice has at most 8
+// significant bits, so it is exactly a bf16 (the high half of its float).
+struct SliceGrid {
+  float c1, c2, c3;  // 1.5 * 2^(16+e), 1.5 * 2^(8+e), 1.5 * 2^e
+};
+__device__ __forceinline__ SliceGrid slice_grid(int e) {
+  return SliceGrid{pow2f(16 + e) * 1.5f, pow2f(8 + e) * 1.5f, pow2f(e) * 1.5f};
+}
+__device__ __forceinline__ void slice3(float x, const SliceGrid &g, float &s1, float &s2, float &s3) {
+  s1 = __fsub_rn(__fadd_rn(x, g.c1), g.c1);
+  const float r1 = __fsub_rn(x, s1);
+  s2 = __fsub_rn(__fadd_rn(r1, g.c2), g.c2);
+  const float r2 = __fsub_rn(r1, s2);
+  s3 = __fsub_rn(__fadd_rn(r2, g.c3), g.c3);
+}
+// Two floats that are exact bf16 values, packed (lo at the lower address).
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
 template <int CH>
@@ -516,7 +524,8 @@ template <>
 struct XfV<FRG_3XTF32> {
   using L = OpL<FRG_3XTF32>;
   float4 rh, rl, ih, il;  // hi / lo of Re and Im
-  __device__ __forceinline__ void make(const float re[4], const float im[4], float, float) {
+  struct Scale {};
+  __device__ __forceinline__ void make(const float re[4], const float im[4], const Scale &) {
     split_tf32(re[0], rh.x, rl.x);
     split_tf32(re[1], rh.y, rl.y);
     split_tf32(re[2], rh.z, rl.z);
@@ -548,23 +557,17 @@ template <>
 struct XfV<FRG_BF16X3> {
   using L = OpL<FRG_BF16X3>;
   uint2 r[3], i[3];  // 4 bf16 of each slice of Re and Im
-  __device__ __forceinline__ static uint2 pack(const __nv_bfloat16 v[4]) {
-    __nv_bfloat162 lo = __halves2bfloat162(v[0], v[1]), hi = __halves2bfloat162(v[2], v[3]);
-    return make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+  using Scale = SliceGrid;  // the grids below the operand's bound 2^e
+  __device__ __forceinline__ static void make4(const float x[4], const SliceGrid &g, uint2 out[3]) {
+    float s[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) slice3(x[j], g, s[0][j], s[1][j], s[2][j]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k] = make_uint2(pack_bf16x2(s[k][0], s[k][1]), pack_bf16x2(s[k][2], s[k][3]));
   }
-  // slices on the grids of the operand's bound 2^e (inv = 2^-e, sc = 2^e)
-  __device__ __forceinline__ void make(const float re[4], const float im[4], float inv, float sc) {
-    __nv_bfloat16 sr[3][4], si[3][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      slice3(re[j], inv, sc, sr[0][j], sr[1][j], sr[2][j]);
-      slice3(im[j], inv, sc, si[0][j], si[1][j], si[2][j]);
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      r[k] = pack(sr[k]);
-      i[k] = pack(si[k]);
-    }
+  __device__ __forceinline__ void make(const float re[4], const float im[4], const SliceGrid &g) {
+    make4(re, g, r);
+    make4(im, g, i);
   }
   __device__ __forceinline__ static uint2 neg(uint2 v) { return make_uint2(v.x ^ 0x80008000u, v.y ^ 0x80008000u); }
   // slice k at T + k A_SLICE
@@ -612,7 +615,7 @@ __device__ __forceinline__ void ld4c(const float2 *p, int base, int off, float2 
 }
 template <int CH, int PREC>
 __device__ __forceinline__ void xf_left(XfV<PREC> &o, const float2 *rA, const float2 *rC, const float2 *rL,
-                                        const XfAt &a, int off, int half, float inv, float sc) {
+                                        const XfAt &a, int off, int half, const typename XfV<PREC>::Scale &sc) {
   float2 v[4], c[4], L[4];
   ld4c(rA, a.src, off, v);
   ld4c(rL, a.l, off, L);
@@ -626,14 +629,14 @@ __device__ __forceinline__ void xf_left(XfV<PREC> &o, const float2 *rA, const fl
     re[x] = w.x;
     im[x] = w.y;
   }
-  o.make(re, im, inv, sc);
+  o.make(re, im, sc);
 }
 // Right item: the raw rows as they are.  The FP32 operand copies hold the bare
 // U wherever the fourth frequency leaves the box; rows past the valid k meet
 // zero left weights and columns past the grid are never stored.
 template <int PREC>
-__device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const XfAt &a, int NT, float inv,
-                                         float sc) {
+__device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const XfAt &a, int NT,
+                                         const typename XfV<PREC>::Scale &sc) {
   float re[4], im[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -641,7 +644,7 @@ __device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const X
     re[x] = b.x;
     im[x] = b.y;
   }
-  o.make(re, im, inv, sc);
+  o.make(re, im, sc);
 }
 
 // Transform warps: raw rows -> bubble-weighted (left), sliced, swizzled
@@ -659,15 +662,12 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
   const PointDesc &P = pts[ti.point];
   const uint4 ord = korder_row<CH>(P, ti.N, w.m);
-  float invA = 1.f, scA = 1.f, invB = 1.f, scB = 1.f;
-  if (PREC == FRG_BF16X3) {
+  typename XfV<PREC>::Scale scA{}, scB{};
+  if constexpr (PREC == FRG_BF16X3) {
     const float vb = fmaxf(__uint_as_float(*P.vmax), fabsf((float)P.U));
     const int row = CH == CH_PP ? w.m : (2 * ti.N - 1) + (CH == CH_XPH ? w.m : 2 * ti.N - 2 - w.m);
-    const int eB = bound_exp(vb), eA = bound_exp(P.Lmax[row] * vb * (CH == CH_DPH ? 6.f : 2.f));
-    invB = pow2f(-eB);
-    scB = pow2f(eB);
-    invA = pow2f(-eA);
-    scA = pow2f(eA);
+    scB = slice_grid(bound_exp(vb));
+    scA = slice_grid(bound_exp(P.Lmax[row] * vb * (CH == CH_DPH ? 6.f : 2.f)));
   }
   // warps 0-7: left item xt and right item xt; warps 8-11: right items xt and xt + 128
   const bool lr = xt < 256;
@@ -686,9 +686,9 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     uint8_t *A = S.ops + s * L::STAGE;
     uint8_t *B = A + L::SL * L::A_SLICE;
     XfV<PREC> va, vb;
-    if (lr) xf_left<CH, PREC>(va, rA, rC, rL, a0, off, q.half, invA, scA);
-    else xf_right<PREC>(va, rB, a0, ti.NT, invB, scB);
-    xf_right<PREC>(vb, rB, a1, ti.NT, invB, scB);
+    if (lr) xf_left<CH, PREC>(va, rA, rC, rL, a0, off, q.half, scA);
+    else xf_right<PREC>(va, rB, a0, ti.NT, scB);
+    xf_right<PREC>(vb, rB, a1, ti.NT, scB);
     // the raw rows are in registers: hand the raw stage back to the loader
     // before waiting for a free operand stage.  The loader's next tensor-map
     // copy into this stage is an async-proxy write: the proxy fence orders
