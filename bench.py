@@ -337,7 +337,7 @@ def run_ours(args):
         executed = executed_tensor_flops(N, half=args.reversal, products=nprod) / (ph[2] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                 "frac": achieved / tc_peak,
-                "traffic": profiled_traffic("tf32") if prec == "3xtf32" and not args.reversal else None,
+                "traffic": None if args.reversal else profiled_traffic("bf16x3" if bf else "tf32"),
                 "traffic_unit": "DRAM bytes per rhs (contraction launch, ncu, cold cache)",
                 "kernel": "tcgen05 channel contractions of one rhs",
                 "peak_source": ("%s bf16 burst" if bf else "%s bf16 burst x 0.5 (nominal tf32/bf16 ratio)") % pk["_source"],
