@@ -492,15 +492,10 @@ struct XfAt {
   int src, l;
   bool valid;
 };
-// TF32 values of a group fill a 16-byte chunk: lanes take consecutive rows
-// of one group.  BF16 groups are half chunks: lanes 2i and 2i + 1 take the two
-// groups of one chunk of row i, so that a warp's 8-byte stores cover whole
-// chunks of 16 rows (no bank conflicts under the 64-byte swizzle).
 template <int PREC>
 __device__ __forceinline__ XfAt xf_left_at(int t) {
   XfAt a;
-  const int r = PREC == FRG_3XTF32 ? t & 63 : (t >> 1) & 63;
-  const int g4 = PREC == FRG_3XTF32 ? t >> 6 : ((t >> 6) & 2) | (t & 1);
+  const int r = t & 63, g4 = t >> 6;
   const int row = 32 * (r >> 4) + (r & 15);
   a.lo_half = grp_off<PREC>(row, g4);
   a.hi_half = grp_off<PREC>(row, 4 + g4);
@@ -513,14 +508,7 @@ template <int PREC>
 __device__ __forceinline__ XfAt xf_right_at(int bt, int NT) {
   XfAt a;
   a.valid = bt < 4 * NT;
-  int c, g4;
-  if (PREC == FRG_3XTF32) {
-    c = bt % NT;
-    g4 = a.valid ? bt / NT : 0;
-  } else {
-    c = (bt >> 1) % NT;
-    g4 = a.valid ? 2 * (bt / (2 * NT)) + (bt & 1) : 0;
-  }
+  const int c = bt % NT, g4 = a.valid ? bt / NT : 0;
   a.lo_half = grp_off<PREC>(c, g4);
   a.hi_half = grp_off<PREC>(c, 4 + g4);
   a.src = 4 * g4 * NT + c;
