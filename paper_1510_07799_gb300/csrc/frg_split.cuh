@@ -11,24 +11,8 @@
 
 namespace frg {
 
-// x ~ hi + lo with hi = RN_f32(x), lo = RN_f32(x - hi): 48 significant bits.
-__device__ __forceinline__ float2 split_f64(double x) {
-  const float hi = __double2float_rn(x);
-  const float lo = __double2float_rn(x - (double)hi);
-  return make_float2(hi, lo);
-}
-
-__device__ __forceinline__ float4 split_c128(double2 z) {
-  const float2 a = split_f64(z.x), b = split_f64(z.y);
-  return make_float4(a.x, a.y, b.x, b.y);
-}
-
 __device__ __forceinline__ float2 round_c64(double2 z) {
   return make_float2(__double2float_rn(z.x), __double2float_rn(z.y));
-}
-
-__device__ __forceinline__ double2 join_c128(float4 v) {
-  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
 }
 
 // Exact float -> double on the integer pipe (subnormal floats flush to 0).
@@ -78,12 +62,6 @@ __device__ __forceinline__ void ff_mac(float &hi, float &lo, float ah, float al,
   float s, e;
   two_sum(hi, p, s, e);
   lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(e, pe), __fmul_rn(al, k)));
-  hi = s;
-}
-
-__device__ __forceinline__ void ff_norm(float &hi, float &lo) {
-  const float s = __fadd_rn(hi, lo);
-  lo = __fsub_rn(lo, __fsub_rn(s, hi));
   hi = s;
 }
 

@@ -136,11 +136,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 // Shared-memory matrix descriptor (K-major, swizzled): start address, stride
 // between 8-row atoms (SBO), version bits 46-48 = 0b001, swizzle mode.
