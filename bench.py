@@ -1,12 +1,14 @@
 """Benchmark: vertex right-hand-side evaluations per second of the one-loop SIAM
 fRG flow at N_f = 128 on one GB300 (and N independent replicas for --gpus N).
 
-One benchmark step = one Dormand-Prince step attempt of the real flow through
-the C ABI (six rhs evaluations -- bubble weights, channel contractions,
-self-energy -- plus the FP64 stage sums, the error norm and the step
-controller), i.e. every row of the hot path.  value = rhs evaluations actually
-performed in the timed steps / device time (CUDA events, max over ranks),
-summed over ranks.
+One benchmark step = one whole N_f = 128 flow through the C ABI, from the bare
+vertex at Lambda0 = 1e3 down to Lambda_f = 1e-3 (about 80 Dormand-Prince step
+attempts, each six rhs evaluations -- bubble weights, channel contractions,
+self-energy -- plus the stage sums, the error norm and the step controller),
+i.e. every row of the hot path.  value = rhs evaluations actually performed in
+the timed flows / device time (CUDA events, max over ranks), summed over ranks.
+The default line also carries the other workloads' figures under "configs"
+(64-point batch, N_f = 256, N_f = 64 flows), each bounded to seconds.
 
 Arms:
   default            the CUDA library (precision --precision)
@@ -182,7 +184,13 @@ def reduce_over_ranks(ms, evals, device=None):
     return float(t.item()), float(ev.item())
 
 
-def cpu_baseline(N_rows, seconds=12.0, mask=0xF):
+def oracle_rows_per_call(threads, N=128):
+    """Vertex rows i1 per oracle call: the oracle's OpenMP loop runs over the
+    rows of a call, so a call takes two rows per thread (every core busy)."""
+    return max(1, min(N, 2 * threads))
+
+
+def cpu_baseline(seconds=12.0, mask=0xF):
     """The FP64 oracle as it stands on the host cores, on whole rows i1 of the
     N=128 vertex (a bounded sample), scaled to rhs evaluations per second."""
     import numpy as np
@@ -192,6 +200,7 @@ def cpu_baseline(N_rows, seconds=12.0, mask=0xF):
     m = oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
     V = inputs.random_vertex(w.N, w.U, seed=11)
     sig = inputs.random_sigma(w.N, seed=12, amp=0.05)
+    N_rows = oracle_rows_per_call(oracle.max_threads(), w.N)
     rows, t0 = 0, time.perf_counter()
     i = 0
     while True:
@@ -204,8 +213,8 @@ def cpu_baseline(N_rows, seconds=12.0, mask=0xF):
             break
     res = {"value": (rows / w.N) / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
            "host_cpus": os.cpu_count(),
-           "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d (channel mask 0x%x), repeated "
-                     "for %.1f s; scaled by rows/N" % (rows, w.N, w.N, mask, el)}
+           "sample": "%d vertex rows i1 (of %d) of one rhs evaluation at N_f=%d (channel mask 0x%x), %d rows "
+                     "per call, repeated for %.1f s; scaled by rows/N" % (rows, w.N, w.N, mask, N_rows, el)}
     # the same sample on one thread (a quarter of the time budget)
     oracle.set_threads(1)
     try:
@@ -221,6 +230,7 @@ def cpu_baseline(N_rows, seconds=12.0, mask=0xF):
         oracle.set_threads(0)  # back to the OpenMP default
     res["value_1thread"] = (rows1 / w.N) / el1
     res["sample_1thread"] = "%d vertex rows on one thread in %.1f s" % (rows1, el1)
+    res["speedup_vs_1thread"] = res["value"] / res["value_1thread"]
     return res
 
 
@@ -238,7 +248,8 @@ def run_reference(args):
     m = orc.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N)
     V = inputs.random_vertex(w.N, w.U, seed=11)
     sig = inputs.random_sigma(w.N, seed=12, amp=0.05)
-    rows = 4  # one step = 4 of the 128 vertex rows of one rhs evaluation
+    # one step = two vertex rows per host thread of one rhs evaluation
+    rows = oracle_rows_per_call(orc.max_threads(), w.N)
     for i in range(args.warmup):
         orc.rhs_rows(m, 0.02, V, sig, 0, rows)
     t0 = time.perf_counter()
@@ -284,27 +295,35 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    # ---- flow steps (the headline value)
-    ctx.advance(args.warmup)
-    torch.cuda.synchronize()
-    st0 = ctx.stats()[0]
-    if st0.done:
-        raise RuntimeError("flow finished during warm-up; lower --warmup")
+    # ---- whole flows (the headline value): every step integrates the N = 128
+    # flow from the bare vertex at Lambda0 down to Lambda_f
+    bare = torch.full((N, N, N), w.U, dtype=torch.complex128, device=dev)
+
+    def one_flow():
+        ctx.set_state(0, bare, None, w.Lambda0)
+        st = ctx.flow()[0]
+        if st.status != 0 or not st.done:
+            raise RuntimeError("flow failed: %s" % (st,))
+        return st
+
+    for _ in range(args.warmup):
+        one_flow()
     barrier()
     torch.cuda.synchronize()
     l0 = frg.kernel_launches()
+    evals = attempts = 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         e0.record(stream)
-        ctx.advance(args.steps)
+        for _ in range(args.steps):
+            st = one_flow()
+            evals += st.rhs_evals
+            attempts += st.accepted + st.rejected
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
     launches = frg.kernel_launches() - l0
-    st1 = ctx.stats()[0]
     ms = e0.elapsed_time(e1)
-    evals = st1.rhs_evals - st0.rhs_evals
-    attempts = (st1.accepted + st1.rejected) - (st0.accepted + st0.rejected)
     ms_max, ev_all = reduce_over_ranks(ms, evals, device=dev)
     value = ev_all / (ms_max / 1e3)
 
@@ -389,21 +408,32 @@ def run_ours(args):
                     "speedup_split_vs_fp64": (1e3 / sum(ph)) / r64}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
             "config": {"workload": w.name + ("+tails" if args.tails else "") + ("+reversal" if args.reversal else ""),
                        "N_f": N, "U": w.U, "T": w.T,
                        "eps_d": w.eps_d, "channel_mask": mask,
                        "precision": prec, "rhs_evals_timed": evals, "step_attempts_timed": attempts,
-                       "step": "one Dormand-Prince step attempt of the flow (6 rhs + FP64 stage sums + "
-                               "error norm + controller)",
+                       "ms_per_step_attempt": ms_max / max(attempts, 1),
+                       "flows_per_s": world * args.steps / (ms_max / 1e3),
+                       "step": "one whole flow from the bare vertex, Lambda 1e3 -> 1e-3 (every step attempt: "
+                               "6 rhs + stage sums + error norm + controller)",
                        "l2": "working set > L2 (state, 7 stage derivatives, stage input: %.0f MB)"
                              % ((2 * 16 + 7 * (8 if prec != 'fp64' else 16) + 16) * N ** 3 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single", "autotune": tune},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "fp64_gpu": fp64_gpu}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(2 if args.tails else 8, seconds=args.cpu_seconds, mask=mask & 0x1F)
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds, mask=mask & 0x1F)
+    if rank == 0 and world == 1 and not args.headline_only:
+        # the other workloads, each bounded to seconds (not the headline)
+        t0 = time.perf_counter()
+        line["configs"] = {
+            "batch64": measure_batch(prec, warmup=1, steps=3),
+            "siam_N256": measure_n256(prec, warmup=3, steps=20),
+            "siam_N64": measure_n64(False, warmup=1, steps=3, with_oracle=not args.no_oracle),
+        }
+        line["configs"]["wall_s"] = time.perf_counter() - t0
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -420,19 +450,18 @@ def reset_flows(ctx, pts, torch):
         ctx.set_state(i, g, None, p.Lambda0)
 
 
-def run_batch(args):
+def measure_batch(prec, warmup, steps, fp64_baseline=True):
     """64 points, uneven N_f, one context: full flows per second."""
     import torch
     from paper_1510_07799_gb300 import build as cuda_build
     cuda_build.build()
     from paper_1510_07799_gb300 import frg, inputs
     pts = inputs.batch_points()
-    prec = args.precision
     ctx = frg.Context(pts, precision=prec)
     tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
     times, evals = [], []
-    for k in range(args.warmup + args.steps):
+    for k in range(warmup + steps):
         reset_flows(ctx, pts, torch)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,14 +469,14 @@ def run_batch(args):
         st = ctx.flow()
         e1.record(stream)
         torch.cuda.synchronize()
-        if k >= args.warmup:
+        if k >= warmup:
             times.append(e0.elapsed_time(e1) / 1e3)
             evals.append(sum(x.rhs_evals for x in st))
     ctx.close()
     tb = sum(times) / len(times)
     # 64 sequential plain-FP64 GPU flows, one context each
     t64, ev64 = 0.0, 0
-    if not args.no_fp64_baseline:
+    if fp64_baseline:
         for p in pts:
             with frg.Context([p], precision="fp64") as c:
                 torch.cuda.synchronize()
@@ -457,23 +486,27 @@ def run_batch(args):
                 t64 += time.perf_counter() - t0
                 ev64 += st.rhs_evals
     line = {"metric": "full flows/s, 64-point batch (N_f 32/48/64/96) in one context", "value": len(pts) / tb,
-            "unit": "flows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "unit": "flows/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[prec], "data": "synthetic",
             "config": {"workload": "batch64", "seed": inputs.BATCH_SEED, "points": len(pts),
                        "N_f": {str(n): sum(1 for p in pts if p.N == n) for n in inputs.BATCH_SIZES},
                        "precision": prec, "step": "one full flow of all 64 points (Lambda 1e3 -> 1e-3)",
                        "rhs_evals_per_step": int(sum(evals) / len(evals)), "autotune": tune},
-            "fp64_sequential": None if args.no_fp64_baseline else {
+            "fp64_sequential": None if not fp64_baseline else {
                 "value": len(pts) / t64, "unit": "flows/s", "rhs_evals": ev64,
                 "what": "64 plain-FP64 GPU flows, one context each, one after the other"}}
-    if not args.no_fp64_baseline:
+    if fp64_baseline:
         line["speedup_vs_fp64_sequential"] = line["value"] / line["fp64_sequential"]["value"]
-    print(json.dumps(line))
+    return line
+
+
+def run_batch(args):
+    print(json.dumps(measure_batch(args.precision, args.warmup, args.steps, not args.no_fp64_baseline)))
     return 0
 
 
-def run_n256(args):
+def measure_n256(prec, warmup, steps, rhs_reps=5):
     """The largest single flow: rhs evaluations per second at N_f = 256, and
     the error of the split rhs against the FP64 GPU path on the same state."""
     import numpy as np
@@ -482,17 +515,16 @@ def run_n256(args):
     cuda_build.build()
     from paper_1510_07799_gb300 import frg, inputs
     w = inputs.SIAM_N256
-    prec = args.precision
     ctx = frg.Context([w], precision=prec)
     tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
-    ctx.advance(args.warmup)
+    ctx.advance(warmup)
     torch.cuda.synchronize()
     st0 = ctx.stats()[0]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(0) as clk:
         e0.record(stream)
-        ctx.advance(args.steps)
+        ctx.advance(steps)
         e1.record(stream)
         torch.cuda.synchronize()
     st1 = ctx.stats()[0]
@@ -502,7 +534,7 @@ def run_n256(args):
     dg, ds = torch.empty_like(g), torch.empty_like(s)
     for _ in range(2):
         ctx.rhs_timed(0, lam, g, s, dg, ds)
-    ph = np.array([ctx.rhs_timed(0, lam, g, s, dg, ds) for _ in range(args.rhs_reps)]).mean(axis=0)
+    ph = np.array([ctx.rhs_timed(0, lam, g, s, dg, ds) for _ in range(rhs_reps)]).mean(axis=0)
     ctx.close()
     with frg.Context([w], precision="fp64") as c64:
         fg, fs = torch.empty_like(g), torch.empty_like(s)
@@ -522,7 +554,7 @@ def run_n256(args):
     tc_peak = pk["bf16_tflops"] * (1.0 if bf else 0.5)
     achieved = 8.0 * macs / (ph[2] * 1e-3) / 1e12
     line = {"metric": "vertex-rhs evals/s at N_f=256 (largest single flow)", "value": evals / (ms / 1e3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": ms / max(1, (st1.accepted + st1.rejected) - (st0.accepted + st0.rejected)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
             "data": "synthetic",
@@ -535,15 +567,19 @@ def run_n256(args):
                          "phases_ms": {"bubble_and_sigma": ph[0], "regather": ph[1], "contraction": ph[2],
                                        "combine": ph[3]}},
             "error_vs_fp64_gpu": {"gamma": nrel(dg, fg), "sigma": nrel(ds, fs),
-                                  "state": "flow state at Lambda=%.4g after %d warm-up steps" % (lam, args.warmup)},
+                                  "state": "flow state at Lambda=%.4g after %d warm-up steps" % (lam, warmup)},
             "fp64_gpu": {"value": 1.0 / t64, "unit": UNIT,
                          "speedup_split_vs_fp64": (1e3 / sum(ph)) * t64},
             "clocks": clk.summary()}
-    print(json.dumps(line))
+    return line
+
+
+def run_n256(args):
+    print(json.dumps(measure_n256(args.precision, args.warmup, args.steps, args.rhs_reps)))
     return 0
 
 
-def run_n64(args):
+def measure_n64(iflow, warmup, steps, with_oracle=True):
     """Full flows per second at N_f = 64: plain FP64 and 3xTF32 on the GPU,
     and the FP64 oracle on the host cores; parity of the final vertex."""
     import numpy as np
@@ -551,19 +587,19 @@ def run_n64(args):
     from paper_1510_07799_gb300 import build as cuda_build
     cuda_build.build()
     from paper_1510_07799_gb300 import frg, inputs
-    w = inputs.SIAM_N64_IFLOW if args.workload == "siam_N64_iflow" else inputs.SIAM_N64
+    w = inputs.SIAM_N64_IFLOW if iflow else inputs.SIAM_N64
     res = {}
     finals = {}
     for prec in ("fp64", "3xtf32"):
         times, evals = [], []
-        for k in range(args.warmup + args.steps):
+        for k in range(warmup + steps):
             with frg.Context([w], precision=prec) as ctx:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 st = ctx.flow()[0]
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
-                if k >= args.warmup:
+                if k >= warmup:
                     times.append(dt)
                     evals.append(st.rhs_evals)
                 g, s, _, _ = ctx.get_state(0)
@@ -573,7 +609,7 @@ def run_n64(args):
     scheme = "interaction flow, Lambda = 1/g 1e12 -> 1" if w.cutoff else "Omega scheme, Lambda 1e3 -> 1e-3"
     line = {"metric": "full flows/s at N_f=64 (off particle-hole symmetry%s)" % (", interaction flow" if w.cutoff else ""),
             "value": res["fp64"]["flows_per_s"],
-            "unit": "flows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "unit": "flows/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": 1e3 / res["fp64"]["flows_per_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "N_f": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d,
@@ -581,7 +617,7 @@ def run_n64(args):
             "fp64_gpu": res["fp64"], "tf32x3_gpu": res["3xtf32"],
             "tf32x3_vs_fp64_gamma": float(np.max(np.abs(finals["3xtf32"] - finals["fp64"]))
                                           / np.max(np.abs(finals["fp64"])))}
-    if not args.no_oracle:
+    if with_oracle:
         import oracle as orc
         from oracle import build as oracle_build
         oracle_build.build()
@@ -593,14 +629,18 @@ def run_n64(args):
                               "rhs_evals": int(st0.rhs_evals), "cores": orc.max_threads(), "kind": "oracle",
                               "sample": "one full flow"}
         line["fp64_vs_oracle_gamma"] = float(np.max(np.abs(finals["fp64"] - g0)) / np.max(np.abs(g0)))
-    print(json.dumps(line))
+    return line
+
+
+def run_n64(args):
+    print(json.dumps(measure_n64(args.workload == "siam_N64_iflow", args.warmup, args.steps, not args.no_oracle)))
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=list(DTYPES))
@@ -611,6 +651,8 @@ def main():
     ap.add_argument("--workload", default="siam_N128",
                     choices=["siam_N128", "batch64", "siam_N256", "siam_N64", "siam_N64_iflow"])
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the N_f = 128 headline (no batch64 / N_f = 256 / N_f = 64 figures under 'configs')")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--tails", action="store_true",
                     help="headline workload with the frequency-box tail option (channel_mask | FRG_TAILS)")

@@ -52,7 +52,16 @@ extern "C" {
 #define FRG_ENOTCONV (-5)    /* step size underflow or step limit reached */
 #define FRG_ETIMEOUT (-6)    /* a bounded device-side wait ran out */
 
-/* Arithmetic of the channel contractions. */
+/*
+ * Arithmetic of the channel contractions.  Every precision evaluates the three
+ * channel sums above for whatever vertex it is given: each operand is read as
+ * the entry the sum names (no crossing, reversal or particle-hole symmetry of
+ * V is assumed; only FRG_REVERSAL below is an assertion about the inputs).
+ * The split precisions differ from FP64 by rounding alone: the vertex is
+ * rounded to FP32 and the products run on the tensor cores (normwise relative
+ * error of one rhs below 1e-6 for FRG_3XTF32 and 5e-5 for FRG_BF16X3 on the
+ * test inputs; whole flows within 1e-6 of the FP64 oracle).
+ */
 #define FRG_FP64 0    /* everything in FP64 (CUDA cores) */
 #define FRG_3XTF32 1  /* split-TF32 (hi*hi + hi*lo + lo*hi) on tcgen05, FP32 accumulate */
 #define FRG_BF16X3 2  /* three BF16 slices, six products, on tcgen05, FP32 accumulate */
@@ -73,8 +82,8 @@ extern "C" {
  * outside the box is then U, so the extra terms are -Lambda T U^2 times a
  * bubble sum per transfer for pp (s = k1 + k2) and xph (Q = k2 - k3), zero for
  * the direct particle-hole channel, and Lambda T U sum S for the self-energy;
- * the library evaluates them in FP64 per rhs.  Not available in
- * frg_rhs_noalloc.
+ * the library evaluates them in FP64 per rhs.  frg_rhs_noalloc rejects the
+ * bit (FRG_EINVAL).
  */
 #define FRG_TAILS 0x10
 #define FRG_TAIL_FACTOR 16
@@ -95,6 +104,7 @@ extern "C" {
  * sums and the error norm run over those, and every other entry of the state
  * is written as the conjugate of its mirror (so a state set with
  * frg_set_state enters the flow through its entries with i1 < N/2).
+ * frg_rhs_noalloc rejects the bit (FRG_EINVAL).
  */
 #define FRG_REVERSAL 0x20
 
@@ -150,7 +160,9 @@ typedef struct {
 } frg_obs;
 
 /*
- * Create a context for n_points parameter points (params[0..n_points-1]); all
+ * Create a context for n_points parameter points (params[0..n_points-1]): the
+ * state of the paper's ODE (Sec. 2, Eq. 1) for each point, V and Sigma at the
+ * initial scale, and the workspace of its right-hand side (Sec. 4).  All
  * points must share precision and channel_mask.  Allocates the device state
  * (initialised to V = U, Sigma = 0 at Lambda0) and all workspace, on the
  * current device.  cuda_stream is a cudaStream_t (may be NULL).
@@ -167,32 +179,31 @@ void frg_destroy(frg_ctx *ctx);
 const char *frg_last_error(const frg_ctx *ctx);
 
 /*
- * One evaluation of the right-hand side, d/dl of (V, Sigma), for point
- * `point` at scale Lambda (> 0), in the context's precision and channel mask:
- * reads d_gamma (N^3 complex128) and d_sigma (N complex128), writes d_dgamma
- * and d_dsigma (same shapes).  Device pointers, caller-owned; asynchronous on
- * the context stream.  d_sigma may be NULL (Sigma = 0).  Uses the context
- * workspace, so calls on one context must not overlap.
+ * One evaluation of the right-hand side F[V; g] of the paper's ODE (Sec. 2,
+ * Eq. 1; the three one-loop diagrams of Sec. 4 and the self-energy flow), i.e.
+ * d/dl of (V, Sigma) as written at the top of this file, for point `point` at
+ * scale Lambda (> 0), in the context's precision and channel mask: reads
+ * d_gamma (N^3 complex128) and d_sigma (N complex128), writes d_dgamma and
+ * d_dsigma (same shapes).  Any vertex is accepted (no symmetry is assumed,
+ * unless the context was created with FRG_REVERSAL).  Device pointers,
+ * caller-owned; asynchronous on the context stream.  d_sigma may be NULL
+ * (Sigma = 0).  Uses the context workspace, so calls on one context must not
+ * overlap.  Errors: FRG_EINVAL (point out of range, Lambda <= 0, NULL output
+ * or d_gamma), FRG_ENOMEM (first call's scratch), FRG_ECUDA.
  */
 int frg_rhs(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
             const void *d_sigma, void *d_dgamma, void *d_dsigma);
 
 /*
- * Same as frg_rhs with host buffers: copies the inputs to the device, evaluates,
- * copies the results back and synchronises the stream before returning.
+ * Same as frg_rhs (paper Sec. 2, Eq. 1) with host buffers: copies the inputs to
+ * the device, evaluates, copies the results back and synchronises the stream
+ * before returning.
  */
 int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma,
                  const double *h_sigma, double *h_dgamma, double *h_dsigma);
 
 /*
- * Integrate every point from its current state to its Lambda_f with the
- * Dormand-Prince 5(4) stepper (device-resident FP64 stage sums, error norm and
- * step control).  stats (host, n_points entries, may be NULL) receives the
- * per-point statistics.  Returns FRG_OK if every point reached Lambda_f, else
- * the first failing point's code (FRG_ENONFINITE, FRG_ENOTCONV).
- */
-/*
- * Pipelined host-buffer evaluations.  frg_rhs_host_async enqueues the same
+ * Pipelined host-buffer evaluations (paper Sec. 2, Eq. 1, as frg_rhs).  frg_rhs_host_async enqueues the same
  * evaluation as frg_rhs_host and returns at once: the host->device copy of the
  * input runs on a copy-in stream, the evaluation on the context stream, the
  * device->host copy of the result on a copy-out stream, through two device
@@ -207,20 +218,39 @@ int frg_rhs_host(frg_ctx *ctx, int point, double Lambda, const double *h_gamma,
 int frg_rhs_host_async(frg_ctx *ctx, int point, double Lambda, const double *h_gamma,
                        const double *h_sigma, double *h_dgamma, double *h_dsigma);
 int frg_sync(frg_ctx *ctx);
+
+/*
+ * Integrate the paper's ODE (Sec. 2, Eq. 1: an explicit stepper; Sec. 4: seven
+ * rhs evaluations for the first step) for every point from its current state
+ * to its Lambda_f with the Dormand-Prince 5(4) pair: device-resident stage
+ * sums, embedded error norm and step control, one captured CUDA graph per step
+ * attempt of all points.  stats (host, n_points entries, may be NULL) receives
+ * the per-point statistics.  Returns FRG_OK if every point reached Lambda_f,
+ * else the first failing point's code (FRG_ENONFINITE, FRG_ENOTCONV), or
+ * FRG_ETIMEOUT / FRG_ECUDA.
+ */
 int frg_flow(frg_ctx *ctx, frg_flow_stats *stats);
 
 /*
  * Advance every unfinished point by at most max_attempts step attempts
- * (accepted or rejected); finished points are left alone.  Same error rules
+ * (accepted or rejected; the stepper of frg_flow, paper Sec. 2); finished
+ * points are left alone.  Same error rules
  * as frg_flow.  Used for checkpointing and for timing a fixed amount of work.
  */
 int frg_advance(frg_ctx *ctx, long max_attempts, frg_flow_stats *stats);
 
-/* Observables of point `point` at its current scale (synchronises). */
+/*
+ * Observables of point `point` at its current scale (synchronises).  The paper
+ * names none for this model; these are the model's standard read-outs:
+ * Sigma(i pi T), the quasiparticle weight Z = 1/(1 - Im Sigma(i pi T)/(pi T)),
+ * the effective interaction U_eff = V at n1 = n2 = n3 = 0 (all four external
+ * frequencies pi T) and the in-box occupation (informational).
+ */
 int frg_observables(frg_ctx *ctx, int point, frg_obs *out);
 
 /*
- * Copy the current state of point `point` out to caller device buffers
+ * Copy the current state (the ODE's V and Sigma, paper Sec. 2) of point
+ * `point` out to caller device buffers
  * (d_gamma N^3, d_sigma N complex128), and its scale and next step (host).
  * Any of the output pointers may be NULL.  Synchronises.
  */
@@ -228,11 +258,13 @@ int frg_get_state(frg_ctx *ctx, int point, void *d_gamma, void *d_sigma,
                   double *Lambda, double *h);
 
 /*
- * Replace the state of point `point` (resume from a checkpoint or start from a
- * custom state): device buffers d_gamma / d_sigma (NULL sigma = 0), scale
- * Lambda (Lambda_f < Lambda <= Lambda0 is not required, but Lambda > Lambda_f
- * for the point to flow) and next step h in l (< 0; 0 selects the h0 of
- * frg_init).  Clears the point's statistics and done flag.
+ * Replace the state (the ODE's V and Sigma, paper Sec. 2) of point `point`
+ * (resume from a checkpoint or start from a custom state): device buffers
+ * d_gamma / d_sigma (NULL sigma = 0), scale Lambda (Lambda_f < Lambda <=
+ * Lambda0 is not required, but Lambda > Lambda_f for the point to flow) and
+ * next step h in l (< 0; 0 selects the h0 of frg_init).  Any vertex is
+ * accepted; with FRG_REVERSAL the state enters through its entries with
+ * i1 < N/2 (see there).  Clears the point's statistics and done flag.
  */
 int frg_set_state(frg_ctx *ctx, int point, const void *d_gamma, const void *d_sigma,
                   double Lambda, double h);
@@ -304,11 +336,14 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out);
  * workspace is one file-scope device array of about 290 KB that every GPU
  * which loads this library holds until the process exits.
  *  - Limit: N_f <= FRG_NOALLOC_MAX_N (even, >= 2); larger sizes, T <= 0,
- *    Delta <= 0, Lambda <= 0, non-finite parameters or NULL output pointers
- *    return FRG_EINVAL without touching the device.
+ *    Delta <= 0, Lambda <= 0, non-finite parameters, NULL output pointers, or
+ *    a channel_mask with FRG_TAILS or FRG_REVERSAL (anything above
+ *    FRG_CH_ALL) return FRG_EINVAL without touching the device.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture on that device.
+ *    (cudaGetSymbolAddress) and caches it with the device's current context;
+ *    the first call after that context changed (cudaDeviceReset, or another
+ *    context made current) looks it up again.  Make such a first call before
+ *    any stream capture on that device.
  *  - Every call on a device shares the array and leaves its contents behind;
  *    each call rewrites everything it reads.  Calls that overlap on the GPU
  *    (for example on two streams) race on the array: serialise them.

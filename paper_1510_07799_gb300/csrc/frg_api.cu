@@ -13,6 +13,7 @@
 #include "../../include/frg.h"
 #include "frg_common.cuh"
 #include "frg_integrator.cuh"
+#include "frg_layout.cuh"
 #include "frg_misc.cuh"
 #include "frg_tc.cuh"
 
@@ -143,14 +144,14 @@ int validate(const frg_params &p, std::string &why) {
   return FRG_OK;
 }
 
-constexpr int TILE = 32;  // row / column tile of the FP64 contraction
 constexpr size_t OPERAND_SLACK = 32;  // float2 elements
 
+// FP64 contraction tiles (F64_TM rows x F64_TN columns) of one channel and point.
 void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &out) {
   for (int m = 0; m < 2 * N - 1; ++m) {
     Geom g = geom(ch, N, m);
-    for (int rt = 0; rt * TILE < g.D; ++rt)
-      for (int ct = 0; ct * TILE < N; ++ct) out.push_back({g.K, WorkItem{pi, m, rt, ct}});
+    for (int rt = 0; rt * F64_TM < g.D; ++rt)
+      for (int ct = 0; ct * F64_TN < N; ++ct) out.push_back({g.K, WorkItem{pi, m, rt, ct}});
   }
 }
 
@@ -424,6 +425,11 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
           !(P.Y32X = dalloc<float2>(ctx, 2 * n3 + OPERAND_SLACK)) || !(P.PX = dalloc<float2>(ctx, n3)) ||
           !(P.PW = dalloc<float2>(ctx, n3)))
         return bail(FRG_ENOMEM);
+      // skewed layout Z (N (2N-1) N elements) for the direct channel's C and D
+      // operands; its constant entries are filled once below
+      const size_t nz = (size_t)N * (2 * N - 1) * N;
+      if (!(P.Y32Z = dalloc<float2>(ctx, nz)) || cudaMemset(P.Y32Z, 0, nz * sizeof(float2)) != cudaSuccess)
+        return bail(FRG_ENOMEM);
       // reversal reduction: the pp channel's computed half in its own buffer
       if ((p.channel_mask & FRG_REVERSAL) && !(P.PN = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
       for (int b = 0; b < 2; ++b)
@@ -467,6 +473,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     return bail(FRG_ENOMEM);
   if (cudaMemcpy(ctx->d_pts, ctx->hpts.data(), sizeof(PointDesc) * n_points, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(FRG_ECUDA);
+  if (ctx->split && launch_fill_z(ctx->d_pts, n_points, ctx->stream) != 0) return bail(FRG_ECUDA);
   if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
       cudaMemset(ctx->d_io_stage, 0, sizeof(RhsIO) * n_points) != cudaSuccess)
     return bail(FRG_ECUDA);

@@ -44,6 +44,11 @@ struct PointDesc {
   float *Lmax;       // split paths: max over p of |Re|,|Im| of each table row: [pp rows | ph rows]
   float2 *yhi[2], *ylo[2];  // split paths: vertex part of ybuf[] as float pairs (hi + lo)
   float2 *Y32W, *Y32X;      // split paths: FP32 stage input in the layouts [i2][i3][i1] and [i1][i3][i2]
+  // split paths: FP32 stage input in the skewed layout Z[i1][d][i2] with
+  // d = i2 - i3 + N - 1 in [0, 2N-1): entry (i1, d, i2) holds V(i1, i2, i2 - d + N - 1),
+  // the bare U where that third index or the fourth index i1 + d - (N - 1)
+  // leaves the box (those entries are constant and written once at set-up)
+  float2 *Y32Z;
   float2 *PX, *PW;          // split paths: direct (layout X) and crossed (layout W) channel outputs
   float2 *PN;               // split paths with the reversal reduction: pp channel output (natural layout)
   unsigned char *kord;      // split paths: per table row, its 16-wide k-chunks by increasing max |Lb| (16 each)
@@ -84,6 +89,11 @@ struct RhsIO {
   int out_f32;         // vertex output as float2
   int canon;           // 1: only the entries i < n3/2 of the vertex output are wanted (dgam holds n3/2)
 };
+
+// Output tile of one CTA of the FP64 channel contraction (k_contract_fp64):
+// F64_TM rows x F64_TN columns; the hosts that build its tile lists (the
+// context and the allocation-free entry point) count tiles with these.
+constexpr int F64_TM = 32, F64_TN = 32;
 
 // One CTA of a channel contraction.
 struct WorkItem {

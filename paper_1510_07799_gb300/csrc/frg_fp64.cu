@@ -443,7 +443,7 @@ int launch_add_tails(const PointDesc *d_pts, const RhsIO *d_io, int n_points, in
 }
 
 // ------------------------------------------------- FP64 contraction ----
-constexpr int F64_TM = 32, F64_TN = 32, F64_TK = 16, F64_THREADS = 256;
+constexpr int F64_TK = 16, F64_THREADS = 256;  // tile rows / columns: F64_TM, F64_TN (frg_common.cuh)
 
 // Left[r][k] (r local row, k in [0,K)) of channel CH for transfer geometry g.
 template <int CH>

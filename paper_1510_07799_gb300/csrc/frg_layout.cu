@@ -1,18 +1,22 @@
 // frg_layout.cu -- vertex layouts for the split-precision contraction.
 //
 // Every operand row of the three channel products is a contiguous run in one
-// of three layouts of the FP32 vertex (N = natural [i1][i2][i3],
-// W = [i2][i3][i1], X = [i1][i3][i2]); the direct particle-hole operands reach
-// that form through crossing symmetry V(k1,k2,k3) = V(k2,k1,k4):
+// of four layouts of the FP32 vertex (N = natural [i1][i2][i3],
+// W = [i2][i3][i1], X = [i1][i3][i2], and the skewed Z = [i1][i2-i3][i2]),
+// each operand read as the entry the channel sum names (no symmetry of the
+// vertex is assumed):
 //   pp : Left (a, s-a, p)            N   Right (p, s-p, k3)            N
 //   dph: A (k1, p, k1+t)             X   B (p-t, k2, p)                X
-//        C (k1, p, p-t)=(p,k1,k1+t)  W   D (p-t,k2,k2-t)=(k2,p-t,p)    W
+//        C (k1, p, p-t)              Z   D (p-t, k2, k2-t)             Z
 //   xph: Left (p, k3+Q, k3)          W   Right (k1, p+Q, p)            W
-// and each channel's output tile is a run of rows in one layout as well
-// (pp: N, dph: X, xph: W).  k_relayout writes the W and X copies of the stage
-// input; k_combine adds the three channel outputs into the natural layout.
-// Both move 16^3 tiles through shared memory so that every global access is a
-// 128-byte row.
+// (in Z both direct-channel operands C and D have i2 - i3 = t: C's rows are
+// k1, D's rows p - t, both contiguous along i2), and each channel's output
+// tile is a run of rows in one layout as well (pp: N, dph: X, xph: W).
+// k_relayout writes the W, X and Z copies of the stage input; k_combine adds
+// the three channel outputs into the natural layout.  Both move 16^3 tiles
+// through shared memory; W, X and the natural layout are written and read as
+// 128-byte rows, Z as the diagonals of a tile's (i2, i3) planes (runs of
+// 16 - |i2 - i3 - offset| elements inside one 128-byte row).
 #include "frg.h"
 #include "frg_common.cuh"
 #include "frg_layout.cuh"
@@ -45,7 +49,7 @@ __device__ __forceinline__ int sidx(int i1, int i2, int i3) { return i1 * S1 + i
 }  // namespace
 
 __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
-                                                  int want_w, int want_x) {
+                                                  int want_w, int want_x, int want_z) {
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
@@ -77,6 +81,38 @@ __global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ 
       const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
       if (a < N && b < N && c < N) P.Y32X[((size_t)a * N + c) * N + b] = sm[sidx(i1, i2, i3)];
     }
+  }
+  if (want_z) {
+    // Z[a][b - c + N - 1][b]: per (local i1, dd = i2 - i3 in [-15, 15]) the
+    // tile's entries lie on one diagonal, i2 = j with i3 = j - dd, which is a
+    // run of consecutive i2 in one Z row; a half-warp takes one diagonal
+    const int zrow = 2 * N - 1;
+    for (int n = threadIdx.x; n < TB * (2 * TB - 1) * TB; n += 256) {
+      const int i1 = n / ((2 * TB - 1) * TB), r = n - i1 * ((2 * TB - 1) * TB);
+      const int dd = r / TB - (TB - 1), j = r % TB, i3 = j - dd;
+      const int a = t.g1 + i1, b = t.g2 + j, c = t.g3 + i3;
+      if ((unsigned)i3 < (unsigned)TB && a < N && b < N && c < N)
+        P.Y32Z[((size_t)a * zrow + (b - c + N - 1)) * N + b] = sm[sidx(i1, j, i3)];
+    }
+  }
+}
+
+// Constant entries of the Z layout: the bare U wherever the third index
+// i2 - d + N - 1 or the fourth index i1 + d - (N - 1) of an entry leaves the
+// box (the relayout writes every other entry each rhs).  Once per point at
+// set-up.
+__global__ void k_fill_z(const PointDesc *__restrict__ pts) {
+  const PointDesc &P = pts[blockIdx.y];
+  if (!P.Y32Z) return;
+  const int N = P.N, zrow = 2 * N - 1;
+  const size_t total = (size_t)N * zrow * N;
+  const float2 u = make_float2((float)P.U, 0.f);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i2 = (int)(e % N);
+    const int d = (int)((e / N) % zrow);
+    const int i1 = (int)(e / ((size_t)N * zrow));
+    const int i3 = i2 - d + N - 1, i4 = i1 + d - (N - 1);
+    if (!inbox(N, i3) || !inbox(N, i4)) P.Y32Z[e] = u;
   }
 }
 
@@ -225,8 +261,14 @@ static inline int ntiles(int maxN) {
 }
 
 int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int want_w, int want_x,
-                    cudaStream_t st) {
-  k_relayout<<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, want_w, want_x);
+                    int want_z, cudaStream_t st) {
+  k_relayout<<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, want_w, want_x, want_z);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_fill_z(const PointDesc *d_pts, int n_points, cudaStream_t st) {
+  k_fill_z<<<dim3(512, n_points), 256, 0, st>>>(d_pts);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -10,6 +10,8 @@
 // of the channel contractions -- lives in one file-scope device array of fixed
 // size, which every GPU that loads this library holds until the process exits.
 // The kernels are the ones of the context path (frg_fp64.cu, frg_misc.cu).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,9 +25,8 @@ namespace frg {
 namespace noalloc {
 
 constexpr int NMAX = FRG_NOALLOC_MAX_N;
-constexpr int TILE = 32;  // row / column tile of the FP64 contraction
-constexpr int NTILE = (NMAX + TILE - 1) / TILE;
-constexpr int MAXWORK = (2 * NMAX - 1) * NTILE * NTILE;  // tiles per channel, upper bound
+// tiles of the FP64 contraction (k_contract_fp64): F64_TM rows x F64_TN columns
+constexpr int MAXWORK = (2 * NMAX - 1) * ((NMAX + F64_TM - 1) / F64_TM) * ((NMAX + F64_TN - 1) / F64_TN);
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t OFF_PTS = 0;
@@ -41,17 +42,38 @@ constexpr size_t SCRATCH_BYTES = align256(OFF_WORK + sizeof(WorkItem) * 3 * MAXW
 // The scratch of every call on this device.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
-// Per-device address of g_scratch as seen by host code (set up on first use).
+// Device address of g_scratch as seen by host code, per device, with the
+// context it belongs to: set up by the first call on a device, and again by the
+// first call after that device's context changed (a cudaDeviceReset, or a
+// driver-API context made current), since the address belongs to a context.
 constexpr int MAXDEV = 64;
 static unsigned char *g_addr[MAXDEV];
+static CUcontext g_addr_ctx[MAXDEV];
 static std::mutex g_mu;
+
+// The calling thread's current context (driver entry point fetched through the
+// runtime, so the library needs no link-time dependency on the driver);
+// nullptr when it cannot be determined.
+static CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  if (!fn) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !f)
+      return nullptr;
+    fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+  }
+  CUcontext c = nullptr;
+  return fn(&c) == CUDA_SUCCESS ? c : nullptr;
+}
 
 // Tiles of one channel in transfer order (every tile's output entries are
 // disjoint; the order only affects scheduling).
 __host__ __device__ inline int tiles_before(int ch, int N, int m) {
   int n = 0;
-  const int ct = (N + TILE - 1) / TILE;
-  for (int mm = 0; mm < m; ++mm) n += ((geom(ch, N, mm).D + TILE - 1) / TILE) * ct;
+  const int ct = (N + F64_TN - 1) / F64_TN;
+  for (int mm = 0; mm < m; ++mm) n += ((geom(ch, N, mm).D + F64_TM - 1) / F64_TM) * ct;
   return n;
 }
 
@@ -71,10 +93,10 @@ __global__ void k_setup(PointDesc pd, RhsIO io, double lam, int N) {
     *reinterpret_cast<RhsIO *>(base + OFF_IO) = io;
   }
   WorkItem *work = reinterpret_cast<WorkItem *>(base + OFF_WORK);
-  const int ct = (N + TILE - 1) / TILE;
+  const int ct = (N + F64_TN - 1) / F64_TN;
   for (int idx = threadIdx.x; idx < 3 * (2 * N - 1); idx += blockDim.x) {
     const int ch = idx / (2 * N - 1), m = idx % (2 * N - 1);
-    const int rt = (geom(ch, N, m).D + TILE - 1) / TILE;
+    const int rt = (geom(ch, N, m).D + F64_TM - 1) / F64_TM;
     int at = tiles_before(ch, N, m);
     for (int r = 0; r < rt; ++r)
       for (int c = 0; c < ct; ++c) work[ch * MAXWORK + at++] = WorkItem{0, m, r, c};
@@ -103,10 +125,13 @@ extern "C" int frg_rhs_noalloc(const frg_params *p, double Lambda, const void *d
   unsigned char *base;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    CUcontext cur = current_context();
+    if (!g_addr[dev] || !cur || cur != g_addr_ctx[dev]) {
+      // set-up on this device (and context): the array's device address
       void *a = nullptr;
       if (cudaGetSymbolAddress(&a, g_scratch) != cudaSuccess || !a) return FRG_ECUDA;
       g_addr[dev] = static_cast<unsigned char *>(a);
+      g_addr_ctx[dev] = current_context();
     }
     base = g_addr[dev];
   }

@@ -351,11 +351,14 @@ __device__ __forceinline__ void tma2(void *dst, const CUtensorMap *m, int x, int
 // Tensor maps per point (all FP32 elements, x = float index within a row):
 //   the rows of one operand family for one transfer lie on a line through a
 //   vertex layout, row index R = y*(N-1) + z (pp, layout N), y*(N+1) + z
-//   ("D1") or y*(N+1) + z*N ("D2") (layouts W and X), y counted along the line.
+//   ("D1") or y*(N+1) + z*N ("D2") (layouts W and X), y counted along the line;
+//   in the skewed layout Z the rows of the direct channel's C and D operands
+//   are rows y = i1 of the plane z = d = t + N - 1.
 enum MapId {
   M_PA = 0, M_PB,            // natural layout, left / right boxes
   M_W1A, M_W1B, M_W2A, M_W2B,  // layout W, forms D1 / D2
   M_X1A, M_X1B, M_X2A, M_X2B,  // layout X
+  M_ZA, M_ZB,                // layout Z
   M_LPP, M_LPH,              // bubble-weight tables, one row
   M_COUNT
 };
@@ -456,10 +459,15 @@ __device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__rest
       } else {
         const bool d1 = x >= 0;
         const int z = x >= 0 ? x : -x;
+        // A (k1, p, k1+t) from X; C (k1, p, p-t) = Z[k1][t+N-1][p]; B (p-t, k2, p)
+        // from X; D (p-t, k2, k2-t) = Z[p-t][t+N-1][k2], rows p - t = row_lo + kl + j
+        const int zd = x + ti.N - 1;
         tma3(raw, mp + (d1 ? M_X1A : M_X2A), xa, ti.r0, z, bar);
-        if (two) tma3(raw + RAW_A, mp + (d1 ? M_W1A : M_W2A), xa, ti.r0, z, bar);
-        const CUtensorMap *mb = q.half ? mp + (d1 ? M_W1B : M_W2B) : mp + (d1 ? M_X1B : M_X2B);
-        tma3(raw + 2 * RAW_A, mb, xb, q.kl, z, bar);
+        if (two) tma3(raw + RAW_A, mp + M_ZA, xa, ti.g.row_lo + ti.r0, zd, bar);
+        if (q.half)
+          tma3(raw + 2 * RAW_A, mp + M_ZB, xb, ti.g.row_lo + q.kl, zd, bar);
+        else
+          tma3(raw + 2 * RAW_A, mp + (d1 ? M_X1B : M_X2B), xb, q.kl, z, bar);
         tma2(raw + 2 * RAW_A + RAW_B, mp + M_LPH, xa, -x + ti.N - 1, bar);
       }
     }
@@ -1112,6 +1120,9 @@ static bool encode_maps(TcPlan *p, const std::vector<PointDesc> &pts, std::strin
       ok = ok && enc3(&m[o + 2], base, N, N, (N + 1) * row, N * row, BA, tc::MROWS);
       ok = ok && enc3(&m[o + 3], base, N, N, (N + 1) * row, N * row, BB, tc::st::KS);
     }
+    // layout Z: rows i1 (stride (2N-1) N elements) of the plane d (stride N)
+    ok = ok && enc3(&m[tc::st::M_ZA], P.Y32Z, N, 2 * N - 1, (2 * N - 1) * row, row, BA, tc::MROWS);
+    ok = ok && enc3(&m[tc::st::M_ZB], P.Y32Z, N, 2 * N - 1, (2 * N - 1) * row, row, BB, tc::st::KS);
     ok = ok && enc2(&m[tc::st::M_LPP], P.Lpp32, 2 * N - 1);
     ok = ok && enc2(&m[tc::st::M_LPH], P.Lph32, 2 * N - 1);
     if (!ok) {
@@ -1208,8 +1219,11 @@ void tc_plan_destroy(TcPlan *p) {
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
            int tails, cudaEvent_t wait_tails) {
+  // layouts of the stage input: W for the crossed channel, X and Z for the
+  // direct one
   if (chmask & 6) {
-    if (launch_relayout(d_pts, d_io, n_points, maxN, 1, (chmask & 2) != 0, st) != 0) return -3;
+    if (launch_relayout(d_pts, d_io, n_points, maxN, (chmask & 4) != 0, (chmask & 2) != 0, (chmask & 2) != 0, st) != 0)
+      return -3;
   }
   if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
   if (wait_before && cudaStreamWaitEvent(st, wait_before, 0) != cudaSuccess) return -3;

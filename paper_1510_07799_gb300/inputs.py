@@ -96,10 +96,15 @@ def all_in_box_mask(N):
     return (i4 >= 0) & (i4 < N)
 
 
-def random_vertex(N: int, U: float, seed: int, amp: float = 0.3, smooth: bool = True):
+def random_vertex(N: int, U: float, seed: int, amp: float = 0.3, smooth: bool = True,
+                  crossing: bool = True):
     """Seeded complex vertex: U plus a smooth part in the three transfer
-    frequencies plus noise, symmetric under crossing (i1,i2,i3)->(i2,i1,i4) on
-    entries whose fourth index is in the box."""
+    frequencies plus noise.  With crossing=True (the default) it is symmetric
+    under crossing (i1,i2,i3)->(i2,i1,i4) on entries whose fourth index is in
+    the box, as every SU(2) vertex is; with crossing=False the noise is left as
+    drawn, so the vertex breaks crossing (and frequency-reversal) symmetry
+    everywhere -- the channel sums are defined for any vertex and the parity
+    tests also feed such inputs."""
     rng = np.random.default_rng(seed)
     i1, i2, i3 = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
     s = (i1 + i2 - (N - 1)).astype(np.float64)  # bosonic index, centred
@@ -113,6 +118,8 @@ def random_vertex(N: int, U: float, seed: int, amp: float = 0.3, smooth: bool = 
                         + 0.5 * c / (1 + (t / w) ** 2))
     v += amp * U * 0.2 * (rng.standard_normal((N, N, N))
                           + 1j * rng.standard_normal((N, N, N)))
+    if not crossing:
+        return v
     flat = v.reshape(-1)
     part, ok = _crossing_partner(N)
     sym = flat.copy()

@@ -2,9 +2,9 @@
 
 Runs only the FP64 CPU oracle (oracle/) on a named workload from the input
 module, flowing from Lambda0 to Lambda_f, and stores a seeded sample of the final
-vertex, the whole self-energy, the observables, the norms needed for normwise
-relative errors, and the integrator statistics.  Nothing here touches the CUDA
-path.
+vertex (and, for grids up to FULL_MAX_N, the whole final vertex), the whole
+self-energy, the observables, the norms needed for normwise relative errors,
+and the integrator statistics.  Nothing here touches the CUDA path.
 
 usage: python tests/golden/make_oracle_reference.py <workload-name> [samples] [mask]
 (mask: the channel mask in hex, default 0xF; a mask other than 0xF is part of
@@ -24,6 +24,7 @@ import oracle  # noqa: E402
 from paper_1510_07799_gb300 import inputs  # noqa: E402
 
 SAMPLE_SEED = 20151025
+FULL_MAX_N = 16  # whole final vertex stored up to this grid (N^3 entries)
 
 
 def sample_indices(N, count, seed=SAMPLE_SEED):
@@ -55,7 +56,8 @@ def main():
     out = {
         "workload": name,
         "mask": mask,
-        "what": "oracle FP64 flow from Lambda0 to Lambda_f; sampled final vertex",
+        "what": "oracle FP64 flow from Lambda0 to Lambda_f; sampled final vertex (whole vertex "
+                "in full_re/full_im, flat index ((i1*N)+i2)*N+i3, when N <= %d)" % FULL_MAX_N,
         "params": {"N": w.N, "U": w.U, "T": w.T, "eps_d": w.eps_d, "Delta": w.Delta,
                    "Lambda0": w.Lambda0, "Lambda_f": w.Lambda_f, "rtol": w.rtol,
                    "atol": w.atol, "cutoff": w.cutoff},
@@ -68,6 +70,8 @@ def main():
         "sample_idx": idx.tolist(),
         "sample_re": [float(x) for x in vals.real],
         "sample_im": [float(x) for x in vals.imag],
+        "full_re": [float(x) for x in g.real.reshape(-1)] if w.N <= FULL_MAX_N else None,
+        "full_im": [float(x) for x in g.imag.reshape(-1)] if w.N <= FULL_MAX_N else None,
         "sigma_re": [float(x) for x in s.real],
         "sigma_im": [float(x) for x in s.imag],
         "observables": {"sigma_lowest": [obs["sigma_lowest"].real, obs["sigma_lowest"].imag],

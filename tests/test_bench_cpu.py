@@ -63,3 +63,14 @@ def test_profiled_traffic_follows_the_source_hash(kind, tmp_path, monkeypatch):
     with open(root / src_rel, "a") as f:
         f.write("\n// changed\n")
     assert bench.profiled_traffic(kind) is None
+
+
+def test_oracle_baseline_keeps_every_host_core_busy():
+    """The oracle's OpenMP loop runs over the vertex rows of one call: the CPU
+    baseline and the reference arm hand it two rows per thread (capped at N)."""
+    import bench
+    assert bench.oracle_rows_per_call(16) == 32
+    assert bench.oracle_rows_per_call(1) == 2
+    assert bench.oracle_rows_per_call(256, N=128) == 128
+    for t in (1, 3, 8, 16, 72):
+        assert bench.oracle_rows_per_call(t) >= min(128, 2 * t)

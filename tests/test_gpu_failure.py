@@ -37,7 +37,7 @@ def test_bounded_wait_reports_timeout_and_context_stays_usable():
         torch.cuda.synchronize()
         rg, rs = oracle.rhs(oracle.Model(U=w.U, T=w.T, eps_d=w.eps_d, Delta=w.Delta, N=w.N), 0.1, V, sig)
         dg = dg.cpu().numpy()
-        assert np.max(np.abs(dg - rg)) / np.max(np.abs(rg)) < 2e-6
+        assert np.max(np.abs(dg - rg)) / np.max(np.abs(rg)) < 1e-6
         # and a flow runs to the end
         st = ctx.flow()[0]
         assert st.status == 0 and st.done == 1

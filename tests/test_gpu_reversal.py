@@ -11,6 +11,7 @@ import os
 import numpy as np
 import pytest
 
+import flow_ref
 import oracle
 from paper_1510_07799_gb300 import frg, inputs
 
@@ -18,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-RHS_TOL = {frg.FP64: 1e-12, frg.TF32X3: 2e-6, frg.BF16X3: 5e-5}
+RHS_TOL = {frg.FP64: 1e-12, frg.TF32X3: 1e-6, frg.BF16X3: 5e-5}
 FLOW_TOL = 1e-6
 REV = frg.REVERSAL
 
@@ -53,9 +54,8 @@ def gpu_rhs(ctx, Lam, V, sig):
 @pytest.mark.parametrize("N", [2, 4, 16, 34, 100])
 @pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4, 0xF | frg.TAILS])
 def test_reversal_rhs_matches_oracle(prec, N, mask):
-    """The reduction adds no error beyond the path's own: within the path's rhs
-    bound of the oracle, or within 1.5x the error of the same path computing
-    every transfer (a channel alone can be a small difference of large terms)."""
+    """The reduced rhs is within the path's own rhs bar of the oracle, like the
+    same path computing every transfer."""
     if N == 100 and prec == frg.FP64:
         pytest.skip("the FP64 path computes every transfer; covered at smaller N")
     w = inputs.Workload("t", N=N, U=1.7, T=0.03, eps_d=-0.85 + 0.3)
@@ -67,7 +67,9 @@ def test_reversal_rhs_matches_oracle(prec, N, mask):
             fg, fs = gpu_rhs(full, Lam, V, sig)
             rg, rs = oracle.rhs(model(w), Lam, V, sig, mask=mask)
             e, ef = nrel(dg, rg), nrel(fg, rg)
-            assert e < max(RHS_TOL[prec], 1.5 * ef), (Lam, e, ef)
+            print("reversal prec=%d N=%d mask=%x Lam=%g rel=%.3e (every transfer: %.3e)" % (
+                prec, N, mask, Lam, e, ef))
+            assert e < RHS_TOL[prec] and ef < RHS_TOL[prec], (Lam, e, ef)
             assert nrel(ds, rs) < RHS_TOL[prec]
 
 
@@ -97,9 +99,7 @@ def test_reversal_flow_matches_oracle_reference(name):
     g = g.cpu().numpy()
     # the state stays exactly reversal-symmetric along the flow
     assert np.array_equal(g, np.conj(g[::-1, ::-1, ::-1]))
-    idx = np.array(ref["sample_idx"])
-    rv = np.array(ref["sample_re"]) + 1j * np.array(ref["sample_im"])
-    eg = np.max(np.abs(g[idx[:, 0], idx[:, 1], idx[:, 2]] - rv)) / ref["gamma_norm_inf"]
+    eg = flow_ref.gamma_error(g, ref)
     rsig = np.array(ref["sigma_re"]) + 1j * np.array(ref["sigma_im"])
     es = nrel(s.cpu().numpy(), rsig)
     ru = complex(*ref["observables"]["U_eff"])

@@ -61,6 +61,22 @@ def test_random_vertex_is_seeded_and_crossing_symmetric(N):
     assert np.max(np.abs(V.imag)) > 0
 
 
+@pytest.mark.parametrize("N", [4, 16])
+def test_random_vertex_without_crossing_breaks_both_symmetries(N):
+    """crossing=False leaves the seeded noise as drawn: crossing and frequency
+    reversal with conjugation fail on almost every in-box entry, so a path
+    that read an operand through either symmetry would see other values."""
+    U = 1.5
+    V = inputs.random_vertex(N, U, seed=3, crossing=False)
+    assert np.array_equal(V, inputs.random_vertex(N, U, seed=3, crossing=False))
+    i1, i2, i3 = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    i4 = i1 + i2 - i3
+    ok = (i4 >= 0) & (i4 < N) & ((i1 != i2) | (i3 != i4))
+    crossed = V[i2[ok], i1[ok], i4[ok]]
+    assert np.mean(V[ok] != crossed) > 0.99
+    assert np.mean(V != np.conj(V[::-1, ::-1, ::-1])) > 0.99
+
+
 def test_bare_state_and_random_sigma():
     g, s = inputs.bare_state(6, 2.0)
     assert np.array_equal(g, np.full((6, 6, 6), 2.0 + 0j)) and np.array_equal(s, np.zeros(6, complex))
