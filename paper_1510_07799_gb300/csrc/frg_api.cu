@@ -14,6 +14,7 @@
 #include "frg_common.cuh"
 #include "frg_integrator.cuh"
 #include "frg_layout.cuh"
+#include "frg_lblock.cuh"
 #include "frg_misc.cuh"
 #include "frg_tc.cuh"
 
@@ -43,6 +44,9 @@ struct frg_ctx {
   std::vector<int> work_off[3];  // per point offsets into d_work_pt
   int *d_seg_point = nullptr, *d_seg_base = nullptr;
   int nseg = 0;
+  // split stage kernels: layout blocks per point (the largest point's vertex
+  // blocks plus one self-energy block) and the layouts its channels read
+  int lb_grid = 0, lb_want = 0;
   std::vector<void *> allocs;
   // host-buffer entry point staging (per point, lazily)
   std::vector<double2 *> user_in, user_out;
@@ -207,8 +211,10 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
     if (ev) CK(cudaEventRecord(ev[3], st), "event");
   } else {
     if (chmask) {
+      // flow evaluations: the split stage kernels have written the layouts
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
-                ctx->maxN, fork ? ctx->ev_join : nullptr, tails, fork ? ctx->ev_tails : nullptr),
+                ctx->maxN, fork ? ctx->ev_join : nullptr, tails, fork ? ctx->ev_tails : nullptr,
+                d_io == ctx->d_io_stage),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
@@ -277,7 +283,9 @@ static SegTable seg(frg_ctx *ctx) { return SegTable{ctx->d_seg_point, ctx->d_seg
 static int issue_k1(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   if (ctx->split)
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st), "stage 0");
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, ctx->lb_grid, ctx->n,
+                    ctx->lb_want),
+       "stage 0");
   else
     LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
   int rc = run_rhs(ctx, ctx->d_io_stage, -1);
@@ -290,7 +298,9 @@ static int issue_step(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   LK(launch_prepare(ctx->d_pts, ctx->d_ctl, ctx->n, st), "prepare");
   for (int s = 1; s < 7; ++s) {
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, ctx->d_io_stage, st), "stage sum");
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, ctx->d_io_stage, st, ctx->lb_grid,
+                    ctx->n, ctx->lb_want),
+       "stage sum");
     int rc = run_rhs(ctx, ctx->d_io_stage, -1);
     if (rc) return rc;
   }
@@ -473,7 +483,14 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     return bail(FRG_ENOMEM);
   if (cudaMemcpy(ctx->d_pts, ctx->hpts.data(), sizeof(PointDesc) * n_points, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(FRG_ECUDA);
-  if (ctx->split && launch_fill_z(ctx->d_pts, n_points, ctx->stream) != 0) return bail(FRG_ECUDA);
+  if (ctx->split && (layout_init() != 0 || stage_split_init() != 0 ||
+                     launch_fill_z(ctx->d_pts, n_points, ctx->stream) != 0))
+    return bail(FRG_ECUDA);
+  if (ctx->split) {
+    for (const PointDesc &P : ctx->hpts)
+      ctx->lb_grid = std::max(ctx->lb_grid, lblocks(P.N, P.rev_half ? P.N / 2 : P.N) + 1);
+    ctx->lb_want = ((ctx->mask & FRG_CH_XPH) ? LAY_W : 0) | ((ctx->mask & FRG_CH_DPH) ? LAY_X | LAY_Z : 0);
+  }
   if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
       cudaMemset(ctx->d_io_stage, 0, sizeof(RhsIO) * n_points) != cudaSuccess)
     return bail(FRG_ECUDA);
@@ -804,7 +821,9 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out) {
     if (!fs.ok) return fail(ctx, FRG_ECUDA, "flow stream ordering");
     cudaStream_t st = ctx->stream;
     // stage input of the current state of every point
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st), "stage 0");
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, ctx->lb_grid, ctx->n,
+                    ctx->lb_want),
+       "stage 0");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "events");
     CK(cudaEventCreate(&e1), "events");

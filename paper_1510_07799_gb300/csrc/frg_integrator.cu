@@ -13,6 +13,7 @@
 #include "frg_common.cuh"
 #include "frg_integrator.cuh"
 #include "frg_split.cuh"
+#include "frg_lblock.cuh"
 
 namespace frg {
 
@@ -235,14 +236,11 @@ __global__ void __launch_bounds__(256) k_stage(const PointDesc *__restrict__ pts
 // widened to FP64.  Stage 0 only prepares the float pairs of y.  The
 // self-energy part stays in FP64 throughout.  The vertex part moves two
 // complex elements (one 16-byte access per array) per thread and pass: N is
-// even, so a segment's vertex range holds whole pairs.  With half storage
-// (reversal reduction) the kernel forms the entries i < n3/2 and writes their
-// conjugates to the mirrored entries n3-1-i of the FP32 stage input (and of the
-// FP64 state at the seventh stage); the two entries of a pair mirror to the
-// pair starting at n3-2-i, in swapped order.  Eight blocks of 256
-// threads per SM (32 registers; a few bytes of spills at stages 0, 5 and 6)
-// keep every segment of an N = 128 state in one wave: measured faster than the
-// unbounded 40-48 registers (two waves) and than 8-byte accesses.
+// even, so every row holds whole pairs.  With half storage (reversal
+// reduction) the kernel forms the entries i < n3/2 (rows i1 < N/2) and writes
+// their conjugates to the mirrored entries n3-1-i of the FP32 stage input, of
+// its W, X and Z copies (and of the FP64 state at the seventh stage); the two
+// entries of a pair mirror to the pair starting at n3-2-i, in swapped order.
 
 // y + h S rounded once to FP32, y = yh + yl, h = h_hi + h_lo, S = Sh + Sl.
 __device__ __forceinline__ float stage_round(float yh, float yl, float Sh, float Sl, float h_hi, float h_lo) {
@@ -273,26 +271,57 @@ __device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, f
   }
 }
 
+// One layout block (frg_lblock.cuh: 8 x 8 x 128 vertex entries) per CTA, plus
+// one CTA per point (the last x index) for the self-energy part.  The stage
+// values go to the natural FP32 stage input and to the shared block, from
+// which the W, X and Z copies the contraction reads are written (`want`), so
+// the stage input reaches every layout in this one pass.  Two complex elements
+// per 16-byte access; a thread's loads of one pass are issued together.
 template <int S>
-__global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
-                                                     SegTable seg, RhsIO *__restrict__ io) {
-  const int b = blockIdx.x;
-  const int pi = seg.point[b];
+__global__ void __launch_bounds__(LB_THREADS) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+                                                            RhsIO *__restrict__ io, int want) {
+  extern __shared__ float4 lsm4[];
+  float2 *sm = reinterpret_cast<float2 *>(lsm4);
+  const int pi = blockIdx.y;
+  const PointDesc &P = pts[pi];
   // the first block of the point also writes the stage's rhs IO record
-  if (io && seg.base[b] == 0 && threadIdx.x == 0) write_stage_io(pts[pi], ctl[pi], io + pi, S, 1);
+  if (io && blockIdx.x == 0 && threadIdx.x == 0) write_stage_io(P, ctl[pi], io + pi, S, 1);
   const Ctl &c = ctl[pi];
   if (c.done) return;
-  const PointDesc &P = pts[pi];
-  const int n3 = P.n3, n = n3 + P.N;
-  const int base = seg.base[b];
+  const int N = P.N, n3 = P.n3;
+  const bool half = P.rev_half != 0;
+  const int nvb = lblocks(N, half ? N / 2 : N);
   const int ys = c.yslot;
   const double h = c.h;
+  if ((int)blockIdx.x == nvb) {
+    // self-energy part
+    for (int i = n3 + (int)threadIdx.x; i < n3 + N; i += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < (S < 6 ? S : 6); ++j) {
+        const double2 k = P.kS[c.kslot[j]][i - n3];
+        acc.x += dA[S][j] * k.x;
+        acc.y += dA[S][j] * k.y;
+      }
+      const double2 yi = P.ybuf[ys][i];
+      const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
+      P.Y64[i - n3] = Y;
+      if (S == 6) P.ybuf[ys ^ 1][i] = Y;
+    }
+    return;
+  }
+  const LBlock k = lblock(N, half ? N / 2 : N, blockIdx.x);
+  if (!k.ok) return;
   const float h_hi = d2f(h), h_lo = d2f(h - f2d(h_hi));
   const float U = (float)P.U;
-  const bool half = P.rev_half != 0;
   float vm = 0.f;
-  const int vend = min(base + SEG_ELEMS, half ? n3 / 2 : n3);
-  for (int i = base + 2 * (int)threadIdx.x; i < vend; i += 2 * (int)blockDim.x) {
+  constexpr int PAIRS = LB * LB * (LC / 2), PER = PAIRS / LB_THREADS;
+#pragma unroll 2
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + u * LB_THREADS;
+    const int c2 = e % (LC / 2), r = e / (LC / 2), b = r % LB, a = r / LB;
+    if (!(a < k.n1 && b < k.n2 && 2 * c2 < k.n3)) continue;
+    const int i = ((k.g1 + a) * N + (k.g2 + b)) * N + k.g3 + 2 * c2;
     float4 out;
     if (S == 0) {
       float4 lo;
@@ -304,9 +333,9 @@ __global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restr
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         if (S == 6 && j == 1) continue;  // the fifth-order weight of k2 is zero: no read
-        const float4 k = *reinterpret_cast<const float4 *>(static_cast<const float2 *>(P.kG[c.kslot[j]]) + i);
+        const float4 kv = *reinterpret_cast<const float4 *>(static_cast<const float2 *>(P.kG[c.kslot[j]]) + i);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ff_mac(sh[q], sl[q], fAh[S][j], fAl[S][j], f4_get(k, q));
+        for (int q = 0; q < 4; ++q) ff_mac(sh[q], sl[q], fAh[S][j], fAl[S][j], f4_get(kv, q));
       }
       if (S < 6) {
         const float4 yh = *reinterpret_cast<const float4 *>(P.yhi[ys] + i);
@@ -330,28 +359,19 @@ __global__ void __launch_bounds__(256, 8) k_stage_split(const PointDesc *__restr
       }
     }
     vm = fmaxf(vm, fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))));
-    const bool in0 = fourth_in_box(i, P.N), in1 = fourth_in_box(i + 1, P.N);
-    *reinterpret_cast<float4 *>(P.Y32 + i) =
-        make_float4(in0 ? out.x : U, in0 ? out.y : 0.f, in1 ? out.z : U, in1 ? out.w : 0.f);
+    const bool in0 = fourth_in_box(i, N), in1 = fourth_in_box(i + 1, N);
+    const float4 v = make_float4(in0 ? out.x : U, in0 ? out.y : 0.f, in1 ? out.z : U, in1 ? out.w : 0.f);
+    *reinterpret_cast<float4 *>(P.Y32 + i) = v;
+    *reinterpret_cast<float4 *>(sm + lsidx(a, b, 2 * c2)) = v;
     // the box rule is reversal-symmetric: a mirrored entry is in the box iff its image is
     if (half)
-      *reinterpret_cast<float4 *>(P.Y32 + (n3 - 2 - i)) =
-          make_float4(in1 ? out.z : U, in1 ? -out.w : 0.f, in0 ? out.x : U, in0 ? -out.y : 0.f);
+      *reinterpret_cast<float4 *>(P.Y32 + (n3 - 2 - i)) = make_float4(v.z, -v.w, v.x, -v.y);
   }
-  // self-energy part
-  for (int i = max(base, n3) + (int)threadIdx.x; i < min(base + SEG_ELEMS, n); i += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int j = 0; j < (S < 6 ? S : 6); ++j) {
-      const double2 k = P.kS[c.kslot[j]][i - n3];
-      acc.x += dA[S][j] * k.x;
-      acc.y += dA[S][j] * k.y;
-    }
-    const double2 yi = P.ybuf[ys][i];
-    const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
-    P.Y64[i - n3] = Y;
-    if (S == 6) P.ybuf[ys ^ 1][i] = Y;
-  }
+  __syncthreads();
+  if (half)
+    lblock_write<true>(P, sm, k, want);
+  else
+    lblock_write<false>(P, sm, k, want);
   block_max_to(vm, P.vmax);
 }
 
@@ -587,17 +607,30 @@ int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+int stage_split_init() {
+  bool ok = true;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_stage_split<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  return ok ? 0 : -3;
+}
+
 int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int s, int split, RhsIO *d_io,
-                 cudaStream_t st) {
+                 cudaStream_t st, int lb_grid, int n_points, int want) {
   if (split) {
+    const dim3 g(lb_grid, n_points);
     switch (s) {
-      case 0: k_stage_split<0><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
-      case 1: k_stage_split<1><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
-      case 2: k_stage_split<2><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
-      case 3: k_stage_split<3><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
-      case 4: k_stage_split<4><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
-      case 5: k_stage_split<5><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
-      default: k_stage_split<6><<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, d_io); break;
+      case 0: k_stage_split<0><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 1: k_stage_split<1><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 2: k_stage_split<2><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 3: k_stage_split<3><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 4: k_stage_split<4><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 5: k_stage_split<5><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      default: k_stage_split<6><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
     }
   } else {
     k_stage<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);

@@ -12,14 +12,15 @@
 // (in Z both direct-channel operands C and D have i2 - i3 = t: C's rows are
 // k1, D's rows p - t, both contiguous along i2), and each channel's output
 // tile is a run of rows in one layout as well (pp: N, dph: X, xph: W).
-// k_relayout writes the W, X and Z copies of the stage input; k_combine adds
-// the three channel outputs into the natural layout.  Both move 16^3 tiles
-// through shared memory; W, X and the natural layout are written and read as
-// 128-byte rows, Z as the diagonals of a tile's (i2, i3) planes (runs of
-// 16 - |i2 - i3 - offset| elements inside one 128-byte row).
+// k_relayout writes the W, X and Z copies of the stage input from layout
+// blocks of 8 x 8 x 128 entries (frg_lblock.cuh; the split stage kernels write
+// the same copies themselves in a flow); k_combine adds the three channel
+// outputs into the natural layout through 16^3 tiles in shared memory, every
+// global access a 128-byte row.
 #include "frg.h"
 #include "frg_common.cuh"
 #include "frg_layout.cuh"
+#include "frg_lblock.cuh"
 
 namespace frg {
 
@@ -48,53 +49,40 @@ __device__ __forceinline__ Tile tile_of(const PointDesc &P) {
 __device__ __forceinline__ int sidx(int i1, int i2, int i3) { return i1 * S1 + i2 * S2 + i3; }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_relayout(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
-                                                  int want_w, int want_x, int want_z) {
+// W, X and Z copies of each active point's FP32 stage input (io.gam), one
+// layout block (frg_lblock.cuh) per CTA: whole natural rows in (16-byte
+// loads, all issued before the first shared-memory store), 64-byte row
+// segments of each layout out.
+__global__ void __launch_bounds__(LB_THREADS) k_relayout(const PointDesc *__restrict__ pts,
+                                                         const RhsIO *__restrict__ io, int want) {
+  extern __shared__ float4 lsm4[];
+  float2 *sm = reinterpret_cast<float2 *>(lsm4);
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
   const PointDesc &P = pts[pi];
-  const Tile t = tile_of(P);
-  if (!t.ok) return;
-  __shared__ float2 sm[TILE_SMEM];
-  const float2 *__restrict__ Y = static_cast<const float2 *>(o.gam);
-  const int N = t.N;
+  const int N = P.N;
+  const LBlock k = lblock(N, N, blockIdx.x);
+  if (!k.ok) return;
+  const float4 *__restrict__ Y = static_cast<const float4 *>(o.gam);
+  // rows (a, b) of n3 elements from g3: pairs of complex values (N is even)
+  constexpr int PAIRS = LB * LB * (LC / 2), PER = PAIRS / LB_THREADS;
+  float4 v[PER];
 #pragma unroll
-  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
-    const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
-    const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-    if (a < N && b < N && c < N) sm[sidx(i1, i2, i3)] = Y[((size_t)a * N + b) * N + c];
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + u * LB_THREADS;
+    const int c2 = e % (LC / 2), r = e / (LC / 2), b = r % LB, a = r / LB;
+    if (a < k.n1 && b < k.n2 && 2 * c2 < k.n3)
+      v[u] = Y[(((size_t)(k.g1 + a) * N + (k.g2 + b)) * N + k.g3) / 2 + c2];
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + u * LB_THREADS;
+    const int c2 = e % (LC / 2), r = e / (LC / 2), b = r % LB, a = r / LB;
+    if (a < k.n1 && b < k.n2 && 2 * c2 < k.n3) *reinterpret_cast<float4 *>(sm + lsidx(a, b, 2 * c2)) = v[u];
   }
   __syncthreads();
-  if (want_w) {
-  #pragma unroll
-  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
-      const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
-      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      if (a < N && b < N && c < N) P.Y32W[((size_t)b * N + c) * N + a] = sm[sidx(i1, i2, i3)];
-    }
-  }
-  if (want_x) {
-  #pragma unroll
-  for (int n = threadIdx.x; n < TB * TB * TB; n += 256) {
-      const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
-      const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      if (a < N && b < N && c < N) P.Y32X[((size_t)a * N + c) * N + b] = sm[sidx(i1, i2, i3)];
-    }
-  }
-  if (want_z) {
-    // Z[a][b - c + N - 1][b]: per (local i1, dd = i2 - i3 in [-15, 15]) the
-    // tile's entries lie on one diagonal, i2 = j with i3 = j - dd, which is a
-    // run of consecutive i2 in one Z row; a half-warp takes one diagonal
-    const int zrow = 2 * N - 1;
-    for (int n = threadIdx.x; n < TB * (2 * TB - 1) * TB; n += 256) {
-      const int i1 = n / ((2 * TB - 1) * TB), r = n - i1 * ((2 * TB - 1) * TB);
-      const int dd = r / TB - (TB - 1), j = r % TB, i3 = j - dd;
-      const int a = t.g1 + i1, b = t.g2 + j, c = t.g3 + i3;
-      if ((unsigned)i3 < (unsigned)TB && a < N && b < N && c < N)
-        P.Y32Z[((size_t)a * zrow + (b - c + N - 1)) * N + b] = sm[sidx(i1, j, i3)];
-    }
-  }
+  lblock_write<false>(P, sm, k, want);
 }
 
 // Constant entries of the Z layout: the bare U wherever the third index
@@ -260,9 +248,16 @@ static inline int ntiles(int maxN) {
   return nt * nt * nt;
 }
 
+int layout_init() {
+  return cudaFuncSetAttribute(k_relayout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess
+             ? 0
+             : -3;
+}
+
 int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int want_w, int want_x,
                     int want_z, cudaStream_t st) {
-  k_relayout<<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, want_w, want_x, want_z);
+  const int want = (want_w ? LAY_W : 0) | (want_x ? LAY_X : 0) | (want_z ? LAY_Z : 0);
+  k_relayout<<<dim3(lblocks(maxN, maxN), n_points), LB_THREADS, LB_SMEM, st>>>(d_pts, d_io, want);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

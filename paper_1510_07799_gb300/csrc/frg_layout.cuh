@@ -3,6 +3,8 @@
 #include "frg_common.cuh"
 
 namespace frg {
+// Dynamic shared-memory limits of the layout kernels (once per context set-up).
+int layout_init();
 // W, X and Z copies of each active point's FP32 stage input (io.gam).
 int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int want_w, int want_x,
                     int want_z, cudaStream_t st);

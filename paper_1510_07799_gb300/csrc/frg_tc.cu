@@ -1218,10 +1218,10 @@ void tc_plan_destroy(TcPlan *p) {
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
-           int tails, cudaEvent_t wait_tails) {
+           int tails, cudaEvent_t wait_tails, bool layouts_ready) {
   // layouts of the stage input: W for the crossed channel, X and Z for the
   // direct one
-  if (chmask & 6) {
+  if ((chmask & 6) && !layouts_ready) {
     if (launch_relayout(d_pts, d_io, n_points, maxN, (chmask & 4) != 0, (chmask & 2) != 0, (chmask & 2) != 0, st) != 0)
       return -3;
   }

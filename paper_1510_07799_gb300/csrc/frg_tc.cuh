@@ -27,11 +27,14 @@ void tc_plan_destroy(TcPlan *plan);
 int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // Evaluate the enabled vertex channels of every active point (point = -1) or of
 // one point, writing the float2 vertex output of each active RhsIO.
-// Relayout of the stage input, the channel products, and the combine into the
-// natural layout.  ev_gather / ev_contract (optional) are recorded after the
-// relayout and after the products; the products wait for wait_before
-// (optional: the bubble weights computed on another stream).
+// Relayout of the stage input (skipped with layouts_ready: the split stage
+// kernels of a flow write the W, X and Z copies themselves), the channel
+// products, and the combine into the natural layout.  ev_gather / ev_contract
+// (optional) are recorded after the relayout and after the products; the
+// products wait for wait_before (optional: the bubble weights computed on
+// another stream).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
-           cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_tails = nullptr);
+           cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_tails = nullptr,
+           bool layouts_ready = false);
 }  // namespace frg
