@@ -278,7 +278,7 @@ __device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, f
 // the stage input reaches every layout in this one pass.  Two complex elements
 // per 16-byte access; a thread's loads of one pass are issued together.
 template <int S>
-__global__ void __launch_bounds__(LB_THREADS) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+__global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
                                                             RhsIO *__restrict__ io, int want) {
   extern __shared__ float4 lsm4[];
   float2 *sm = reinterpret_cast<float2 *>(lsm4);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_stage_split(const PointDesc *__r
   const float U = (float)P.U;
   float vm = 0.f;
   constexpr int PAIRS = LB * LB * (LC / 2), PER = PAIRS / LB_THREADS;
-#pragma unroll 2
+#pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int e = threadIdx.x + u * LB_THREADS;
     const int c2 = e % (LC / 2), r = e / (LC / 2), b = r % LB, a = r / LB;

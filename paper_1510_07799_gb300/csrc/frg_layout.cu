@@ -53,7 +53,7 @@ __device__ __forceinline__ int sidx(int i1, int i2, int i3) { return i1 * S1 + i
 // layout block (frg_lblock.cuh) per CTA: whole natural rows in (16-byte
 // loads, all issued before the first shared-memory store), 64-byte row
 // segments of each layout out.
-__global__ void __launch_bounds__(LB_THREADS) k_relayout(const PointDesc *__restrict__ pts,
+__global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_relayout(const PointDesc *__restrict__ pts,
                                                          const RhsIO *__restrict__ io, int want) {
   extern __shared__ float4 lsm4[];
   float2 *sm = reinterpret_cast<float2 *>(lsm4);

@@ -3,12 +3,12 @@
 // The split contraction reads its operand rows from four layouts of the FP32
 // vertex: natural [i1][i2][i3], W = [i2][i3][i1], X = [i1][i3][i2] and the
 // skewed Z = [i1][i2 - i3 + N - 1][i2] (frg_layout.cu lists which operand comes
-// from which).  A layout block holds 8 (i1) x 8 (i2) x 128 (i3) entries of the
-// natural layout in shared memory -- whole 1 KB rows of the natural layout at
-// N = 128 -- from which every W, X and Z row segment it covers is written as 8
-// consecutive elements (64 bytes): W rows run along i1, X rows along i2, and Z
-// rows along i2 at fixed i1 and i2 - i3, which in natural tiles would be
-// diagonals.  The stand-alone relayout (frg_layout.cu) fills a block from the
+// from which).  A layout block holds 8 (i1) x 8 (i2) x 32 (i3) entries of the
+// natural layout in shared memory (256-byte runs of its rows), from which every
+// W, X and Z row segment it covers is written as up to 8 consecutive elements
+// (64 bytes): W rows run along i1, X rows along i2, and Z rows along i2 at
+// fixed i1 and i2 - i3, which in natural tiles would be diagonals (the Z
+// segments that cross a block's i3 edge are written in two parts).  The stand-alone relayout (frg_layout.cu) fills a block from the
 // natural layout; the split stage kernels (frg_integrator.cu) fill it with the
 // stage values they compute, so that the stage input reaches every layout in
 // one pass.
@@ -18,10 +18,16 @@
 namespace frg {
 
 constexpr int LB = 8;                 // i1 and i2 extent of a block
-constexpr int LC = 128;               // i3 extent (one chunk of a row)
-constexpr int LCP = LC + 4;           // shared-memory pitch of a row (float2; 16-byte aligned rows)
+constexpr int LC = 32;                // i3 extent (one chunk of a row)
+// Shared-memory pitches (float2) of a row (i2) and of a plane (i1): rows stay
+// 16-byte aligned, and the 8 lanes that write one layout segment (8
+// consecutive i2, or 8 consecutive i1) hit distinct bank pairs: 2 x 34 = 4
+// and 2 x 274 = 4 (mod 32) banks apart.
+constexpr int LCP = LC + 2;
+constexpr int LAP = LB * LCP + 2;
 constexpr int LB_THREADS = 256;
-constexpr size_t LB_SMEM = (size_t)LB * LB * LCP * sizeof(float2);  // 67,584 bytes
+constexpr int LB_MINBLOCKS = 8;       // resident blocks per SM the kernels are compiled for
+constexpr size_t LB_SMEM = (size_t)LB * LAP * sizeof(float2);  // 17,536 bytes
 
 // Layout bits.
 constexpr int LAY_W = 1, LAY_X = 2, LAY_Z = 4;
@@ -53,55 +59,86 @@ __device__ inline LBlock lblock(int N, int n1lim, int b) {
   return k;
 }
 
-__device__ __forceinline__ int lsidx(int a, int b, int c) { return (a * LB + b) * LCP + c; }
+__device__ __forceinline__ int lsidx(int a, int b, int c) { return a * LAP + b * LCP + c; }
 
 // Writes the W, X and Z entries of the block (the layouts in `want`) from the
 // shared block s (values with the box rule applied).  MIRROR: the block holds
 // canonical entries of a reversal-symmetric vertex; every entry's mirror
-// (N-1-i1, N-1-i2, N-1-i3) is written too, as the complex conjugate.  A warp
-// writes 4 rows of 8 consecutive elements per pass.
+// (N-1-i1, N-1-i2, N-1-i3) is written too, as the complex conjugate.  Each
+// lane moves two consecutive elements of a segment (one 16-byte store; N is
+// even and every segment starts at an even index), four lanes a segment, eight
+// segments per warp instruction.  Flat indices fit in 32 bits (N <= 256).
+__device__ __forceinline__ float4 conj2(float4 v) { return make_float4(v.z, -v.w, v.x, -v.y); }
+
 template <bool MIRROR>
 __device__ __forceinline__ void lblock_write(const PointDesc &P, const float2 *__restrict__ s, const LBlock &k,
                                              int want) {
   const int N = P.N, M = N - 1, zrow = 2 * N - 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int lo = lane & 7, hi = lane >> 3;
+  const int q = lane & 3, r = lane >> 2;  // element pair 2q, 2q + 1 of segment r of the pass
+  const int e0 = 2 * q;
   if (want & LAY_X) {
-    // X[a][c][b]: 8 consecutive b per (a, c)
-    for (int it = warp; it < LB * (LC / 4); it += nw) {
-      const int a = it / (LC / 4), c = (it % (LC / 4)) * 4 + hi, b = lo;
-      if (a < k.n1 && b < k.n2 && c < k.n3) {
-        const float2 v = s[lsidx(a, b, c)];
-        const size_t ga = k.g1 + a, gb = k.g2 + b, gc = k.g3 + c;
-        P.Y32X[(ga * N + gc) * N + gb] = v;
-        if (MIRROR) P.Y32X[((M - ga) * N + (M - gc)) * N + (M - gb)] = make_float2(v.x, -v.y);
+    // X[a][c][b]: segments (a, c), b = e0, e0 + 1
+    float4 *X = reinterpret_cast<float4 *>(P.Y32X);
+    for (int it = warp; it < LB * LC / 8; it += nw) {
+      const int seg = it * 8 + r, a = seg / LC, c = seg % LC;
+      if (a < k.n1 && c < k.n3 && e0 < k.n2) {
+        const float2 u = s[lsidx(a, e0, c)], w = s[lsidx(a, e0 + 1, c)];
+        const float4 v = make_float4(u.x, u.y, w.x, w.y);
+        const int ga = k.g1 + a, gc = k.g3 + c, gb = k.g2 + e0;
+        X[((ga * N + gc) * N + gb) >> 1] = v;
+        if (MIRROR) X[(((M - ga) * N + (M - gc)) * N + (M - gb - 1)) >> 1] = conj2(v);
       }
     }
   }
   if (want & LAY_W) {
-    // W[b][c][a]: 8 consecutive a per (b, c)
-    for (int it = warp; it < LB * (LC / 4); it += nw) {
-      const int b = it / (LC / 4), c = (it % (LC / 4)) * 4 + hi, a = lo;
-      if (a < k.n1 && b < k.n2 && c < k.n3) {
-        const float2 v = s[lsidx(a, b, c)];
-        const size_t ga = k.g1 + a, gb = k.g2 + b, gc = k.g3 + c;
-        P.Y32W[(gb * N + gc) * N + ga] = v;
-        if (MIRROR) P.Y32W[((M - gb) * N + (M - gc)) * N + (M - ga)] = make_float2(v.x, -v.y);
+    // W[b][c][a]: segments (b, c), a = e0, e0 + 1 (the block's rows a are owned)
+    float4 *W = reinterpret_cast<float4 *>(P.Y32W);
+    for (int it = warp; it < LB * LC / 8; it += nw) {
+      const int seg = it * 8 + r, b = seg / LC, c = seg % LC;
+      if (b < k.n2 && c < k.n3 && e0 < k.n1) {
+        const float2 u = s[lsidx(e0, b, c)];
+        const float2 w = e0 + 1 < k.n1 ? s[lsidx(e0 + 1, b, c)] : make_float2(0.f, 0.f);
+        const int ga = k.g1 + e0, gb = k.g2 + b, gc = k.g3 + c;
+        if (e0 + 1 < k.n1) {
+          const float4 v = make_float4(u.x, u.y, w.x, w.y);
+          W[((gb * N + gc) * N + ga) >> 1] = v;
+          if (MIRROR) W[(((M - gb) * N + (M - gc)) * N + (M - ga - 1)) >> 1] = conj2(v);
+        } else {
+          // an odd count of owned rows (reversal half of N = 2 mod 4): one element
+          P.Y32W[(gb * N + gc) * N + ga] = u;
+          if (MIRROR) P.Y32W[((M - gb) * N + (M - gc)) * N + (M - ga)] = make_float2(u.x, -u.y);
+        }
       }
     }
   }
   if (want & LAY_Z) {
-    // Z[a][b - c + N - 1][b]: 8 consecutive b per (a, dd = b - c); local
-    // dd = b - c runs over [-(LC - 1), LB - 1]
-    constexpr int NDD = LC + LB - 1, NG = (NDD + 3) / 4;
-    for (int it = warp; it < LB * NG; it += nw) {
-      const int a = it / NG, dd = (it % NG) * 4 + hi - (LC - 1), b = lo, c = b - dd;
-      if (a < k.n1 && b < k.n2 && (unsigned)c < (unsigned)k.n3) {
-        const float2 v = s[lsidx(a, b, c)];
-        const int ga = k.g1 + a, gb = k.g2 + b, gc = k.g3 + c;
-        P.Y32Z[((size_t)ga * zrow + (gb - gc + N - 1)) * N + gb] = v;
-        if (MIRROR)
-          P.Y32Z[((size_t)(M - ga) * zrow + (gc - gb + N - 1)) * N + (M - gb)] = make_float2(v.x, -v.y);
+    // Z[a][b - c + N - 1][b]: segments (a, dd = b - c), b = e0, e0 + 1 with
+    // c = b - dd; local dd runs over [-(LC - 1), LB - 1].  A pair whose second
+    // element leaves the block's i3 range (or whose first one does) is written
+    // element by element.
+    constexpr int NDD = LC + LB - 1;
+    for (int it = warp; it < (LB * NDD + 7) / 8; it += nw) {
+      const int seg = it * 8 + r, a = seg / NDD, dd = seg % NDD - (LC - 1);
+      if (a >= k.n1 || e0 >= k.n2) continue;
+      const int c0 = e0 - dd;  // i3 of element e0; element e0 + 1 has c0 + 1
+      const bool v0 = (unsigned)c0 < (unsigned)k.n3, v1 = e0 + 1 < k.n2 && (unsigned)(c0 + 1) < (unsigned)k.n3;
+      if (!v0 && !v1) continue;
+      const int ga = k.g1 + a, gb = k.g2 + e0, dz = k.g2 - k.g3 + dd + N - 1;  // b - c + N - 1
+      const float2 u = v0 ? s[lsidx(a, e0, c0)] : make_float2(0.f, 0.f);
+      const float2 w = v1 ? s[lsidx(a, e0 + 1, c0 + 1)] : make_float2(0.f, 0.f);
+      const int at = (ga * zrow + dz) * N + gb;
+      const int atm = ((M - ga) * zrow + (2 * N - 2 - dz)) * N + (M - gb - 1);  // mirror of element e0 + 1
+      if (v0 && v1) {
+        const float4 v = make_float4(u.x, u.y, w.x, w.y);
+        reinterpret_cast<float4 *>(P.Y32Z)[at >> 1] = v;
+        if (MIRROR) reinterpret_cast<float4 *>(P.Y32Z)[atm >> 1] = conj2(v);
+      } else if (v0) {
+        P.Y32Z[at] = u;
+        if (MIRROR) P.Y32Z[atm + 1] = make_float2(u.x, -u.y);
+      } else {
+        P.Y32Z[at + 1] = w;
+        if (MIRROR) P.Y32Z[atm] = make_float2(w.x, -w.y);
       }
     }
   }
