@@ -24,30 +24,6 @@
 
 namespace frg {
 
-namespace {
-constexpr int TB = 16;
-constexpr int S2 = TB + 1;           // smem stride of i2
-constexpr int S1 = TB * S2 + 1;      // smem stride of i1
-constexpr int TILE_SMEM = TB * S1;   // float2 elements
-
-struct Tile {
-  int N, g1, g2, g3;
-  bool ok;
-};
-
-__device__ __forceinline__ Tile tile_of(const PointDesc &P) {
-  Tile t;
-  t.N = P.N;
-  const int nt = (P.N + TB - 1) / TB;
-  const int tile = blockIdx.x;
-  t.ok = tile < nt * nt * nt;
-  t.g1 = (tile / (nt * nt)) * TB;
-  t.g2 = ((tile / nt) % nt) * TB;
-  t.g3 = (tile % nt) * TB;
-  return t;
-}
-__device__ __forceinline__ int sidx(int i1, int i2, int i3) { return i1 * S1 + i2 * S2 + i3; }
-}  // namespace
 
 // W, X and Z copies of each active point's FP32 stage input (io.gam), one
 // layout block (frg_lblock.cuh) per CTA: whole natural rows in (16-byte
@@ -104,6 +80,12 @@ __global__ void k_fill_z(const PointDesc *__restrict__ pts) {
   }
 }
 
+// FP32 copy of the FP64 frequency-box tail constant j of a point.
+__device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) {
+  const double2 t = P.tail[j];
+  return make_float2((float)t.x, (float)t.y);
+}
+
 // k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
 // (launched for every split-path rhs, also when only pp is enabled), plus the
 // frequency-box tail constants when mask has FRG_TAILS (block 0 of a point also
@@ -113,140 +95,144 @@ __global__ void k_fill_z(const PointDesc *__restrict__ pts) {
 // N-1-i3); on the self-mirrored transfer m = N - 1 the entry of each mirror pair
 // with the smaller leading index keeps its own value and the other takes its
 // conjugate, so that the result is exactly reversal-symmetric.  With half
-// storage (RhsIO.canon) only the entries with i1 < N/2 are formed and written:
-// tiles that start at i1 >= N/2 leave after block 0's self-energy tail.  Every thread
-// issues all 48 of its loads before the first shared-memory pass, so that a
-// block keeps 96 KB of reads in flight.
+// storage (RhsIO.canon) only the entries with i1 < N/2 are formed and written.
+// One layout block (8 x 8 x 32 entries, frg_lblock.cuh) per CTA: the direct
+// channel's output is read as 64-byte segments of X rows, the crossed
+// channel's as segments of W rows, the pp output and the result as 256-byte
+// runs of natural rows, every access 16 bytes (two complex values); whether a
+// value comes from its mirror depends only on the segment (the transfer of an
+// X segment is t = i3 - i1, of a W segment Q = i2 - i3, of a natural row
+// s = i1 + i2), so a mirrored segment is one 16-byte load in reverse order.
+// Per element the sum is ((X + W) + tails) + pp, in that order.
 template <bool REV>
-__global__ void __launch_bounds__(256, 2) k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
-                                                    int mask) {
+__global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
+    k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask) {
+  __shared__ __align__(16) float2 sm[LB * LAP];
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
   const PointDesc &P = pts[pi];
-  const Tile t = tile_of(P);
-  if (!t.ok) return;
-  __shared__ float2 sm[TILE_SMEM];
-  __shared__ float2 ttab[2 * (2 * FRG_MAX_N - 1)];
-  const int N = t.N, nrow = 2 * N - 1;
+  const int N = P.N, M = N - 1, nrow = 2 * N - 1;
   const bool tails = (mask & FRG_TAILS) && P.tail;
-  if (tails) {
-    for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x)
-      ttab[j] = make_float2((float)P.tail[j].x, (float)P.tail[j].y);
-    if (blockIdx.x == 0 && threadIdx.x < N && o.dsig) {
-      const double2 a = o.dsig[threadIdx.x], b = P.tail[2 * nrow];
-      o.dsig[threadIdx.x] = make_double2(a.x + b.x, a.y + b.y);
-    }
+  if (tails && blockIdx.x == 0 && threadIdx.x < N && o.dsig) {
+    const double2 a = o.dsig[threadIdx.x], b = P.tail[2 * nrow];
+    o.dsig[threadIdx.x] = make_double2(a.x + b.x, a.y + b.y);
   }
-  // half storage: entries with i1 >= hN are not wanted (and have no room in K)
-  const int hN = (REV && o.canon) ? N / 2 : N;
-  if (t.g1 >= hN) return;
-  float2 *__restrict__ K = static_cast<float2 *>(o.dgam);
-  const float2 z = make_float2(0.f, 0.f);
-  const float2 *__restrict__ src_pp = REV ? P.PN : K;
-  const int M = N - 1;  // mirror: i -> M - i
-  float2 vx[16], vw[16], vk[16];
-  // REV: bit u of flip{x,w,k} marks a value taken from the mirrored entry
-  unsigned flipx = 0u, flipw = 0u, flipk = 0u;
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int n = threadIdx.x + 256 * u;
-    {
-      // dph, layout X [a][c][b]; REV: transfer t = c - a computed for t <= 0
-      const int i1 = n >> 8, i3 = (n >> 4) & 15, i2 = n & 15;
-      int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool ok = (mask & 2) && a < hN && b < N && c < N;
-      if (REV && !(c < a || (c == a && 2 * a < M))) {
-        a = M - a, b = M - b, c = M - c;
-        flipx |= 1u << u;
-      }
-      vx[u] = ok ? P.PX[((size_t)a * N + c) * N + b] : z;
-    }
-    {
-      // xph, layout W [b][c][a]; REV: transfer Q = b - c computed for Q <= 0
-      const int i2 = n >> 8, i3 = (n >> 4) & 15, i1 = n & 15;
-      int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool ok = (mask & 4) && a < hN && b < N && c < N;
-      if (REV && !(b < c || (b == c && 2 * b < M))) {
-        a = M - a, b = M - b, c = M - c;
-        flipw |= 1u << u;
-      }
-      vw[u] = ok ? P.PW[((size_t)b * N + c) * N + a] : z;
-    }
-    {
-      // pp, natural layout; REV: transfer s = a + b computed for s <= N - 1
-      const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
-      int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-      const bool ok = (mask & 1) && a < hN && b < N && c < N;
-      if (REV && !(a + b < M || (a + b == M && 2 * a < M))) {
-        a = M - a, b = M - b, c = M - c;
-        flipk |= 1u << u;
-      }
-      vk[u] = ok ? src_pp[((size_t)a * N + b) * N + c] : z;
-    }
-  }
-  if (REV) {
-    // mirrored values enter as complex conjugates
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      if (flipx >> u & 1u) vx[u].y = -vx[u].y;
-      if (flipw >> u & 1u) vw[u].y = -vw[u].y;
-      if (flipk >> u & 1u) vk[u].y = -vk[u].y;
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int n = threadIdx.x + 256 * u;
-    sm[sidx(n >> 8, n & 15, (n >> 4) & 15)] = vx[u];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int n = threadIdx.x + 256 * u;
-    float2 &v = sm[sidx(n & 15, n >> 8, (n >> 4) & 15)];
-    v.x += vw[u].x;
-    v.y += vw[u].y;
-  }
-  __syncthreads();
   // the channel products of this rhs have consumed the vertex bound of the
   // stage input (BF16 slicing): reset it for the next stage
   if (blockIdx.x == 0 && threadIdx.x == 0 && P.vmax) *P.vmax = 0u;
+  // half storage: entries with i1 >= hN are not wanted (and have no room in K)
+  const int hN = (REV && o.canon) ? N / 2 : N;
+  const LBlock k = lblock(N, hN, blockIdx.x);
+  if (!k.ok) return;
+  float4 *__restrict__ K4 = static_cast<float4 *>(o.dgam);
+  const float4 *__restrict__ X4 = reinterpret_cast<const float4 *>(P.PX);
+  const float4 *__restrict__ W4 = reinterpret_cast<const float4 *>(P.PW);
+  const float4 *__restrict__ src_pp = REV ? reinterpret_cast<const float4 *>(P.PN) : K4;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr int PER = LB * LB * LC / 2 / LB_THREADS;  // pairs per thread and source
+  float4 vx[PER], vw[PER];
+  // direct channel (X layout [a][c][b]), segments (a, c), pairs b = 2q, 2q + 1
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int n = threadIdx.x + 256 * u;
-    const int i1 = n >> 8, i2 = (n >> 4) & 15, i3 = n & 15;
-    const int a = t.g1 + i1, b = t.g2 + i2, c = t.g3 + i3;
-    if (a < hN && b < N && c < N) {
-      float2 v = sm[sidx(i1, i2, i3)];
-      if (tails) {
-        float2 ta = ttab[a + b], tb = ttab[nrow + b - c + N - 1];
-        if (REV) {
-          // the constants of mirrored transfers as exact conjugates, so that
-          // the sum stays exactly reversal-symmetric
-          if (a + b > M) {
-            ta = ttab[2 * M - (a + b)];
-            ta.y = -ta.y;
-          } else if (a + b == M) {
-            ta.y = 0.f;
-          }
-          if (b > c) {
-            tb = ttab[nrow + c - b + N - 1];
-            tb.y = -tb.y;
-          } else if (b == c) {
-            tb.y = 0.f;
-          }
-        }
-        v = make_float2(v.x + (ta.x + tb.x), v.y + (ta.y + tb.y));
-      }
-      K[((size_t)a * N + b) * N + c] = make_float2(v.x + vk[u].x, v.y + vk[u].y);
+  for (int u = 0; u < PER; ++u) {
+    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int a = seg / LC, c = seg % LC;
+    vx[u] = z4;
+    if ((mask & 2) && a < k.n1 && c < k.n3 && e0 < k.n2) {
+      const int ga = k.g1 + a, gb = k.g2 + e0, gc = k.g3 + c;
+      if (!REV || gc < ga || (gc == ga && 2 * ga < M))
+        vx[u] = X4[((ga * N + gc) * N + gb) >> 1];
+      else
+        vx[u] = conj2(X4[(((M - ga) * N + (M - gc)) * N + (M - gb - 1)) >> 1]);
     }
+  }
+  // crossed channel (W layout [b][c][a]), segments (b, c), pairs a = 2q, 2q + 1
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int b = seg / LC, c = seg % LC;
+    vw[u] = z4;
+    if ((mask & 4) && b < k.n2 && c < k.n3 && e0 < k.n1) {
+      const int ga = k.g1 + e0, gb = k.g2 + b, gc = k.g3 + c;
+      if (!REV || gb < gc || (gb == gc && 2 * gb < M))
+        vw[u] = W4[((gb * N + gc) * N + ga) >> 1];
+      else
+        vw[u] = conj2(W4[(((M - gb) * N + (M - gc)) * N + (M - ga - 1)) >> 1]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int a = seg / LC, c = seg % LC;
+    if (a < k.n1 && c < k.n3 && e0 < k.n2) {
+      sm[lsidx(a, e0, c)] = make_float2(vx[u].x, vx[u].y);
+      sm[lsidx(a, e0 + 1, c)] = make_float2(vx[u].z, vx[u].w);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int b = seg / LC, c = seg % LC;
+    if (b < k.n2 && c < k.n3 && e0 < k.n1) {
+      float2 &p = sm[lsidx(e0, b, c)];
+      p.x += vw[u].x;
+      p.y += vw[u].y;
+      if (e0 + 1 < k.n1) {
+        float2 &q = sm[lsidx(e0 + 1, b, c)];
+        q.x += vw[u].z;
+        q.y += vw[u].w;
+      }
+    }
+  }
+  __syncthreads();
+  // pp (natural rows (a, b)), pairs c = 2j, 2j + 1; the sum in natural rows
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int t = threadIdx.x + u * LB_THREADS, row = t / (LC / 2), c = 2 * (t % (LC / 2));
+    const int a = row / LB, b = row % LB;
+    if (!(a < k.n1 && b < k.n2 && c < k.n3)) continue;
+    const int ga = k.g1 + a, gb = k.g2 + b, gc = k.g3 + c;
+    float4 vk = z4;
+    if (mask & 1) {
+      if (!REV || ga + gb < M || (ga + gb == M && 2 * ga < M))
+        vk = src_pp[((ga * N + gb) * N + gc) >> 1];
+      else
+        vk = conj2(src_pp[(((M - ga) * N + (M - gb)) * N + (M - gc - 1)) >> 1]);
+    }
+    float4 v = *reinterpret_cast<const float4 *>(&sm[lsidx(a, b, c)]);
+    if (tails) {
+      // pp transfer s = a + b (one per row), xph transfer Q = b - c per element
+      float2 ta = tail_c(P, ga + gb), tb0 = tail_c(P, nrow + gb - gc + N - 1),
+             tb1 = tail_c(P, nrow + gb - gc - 1 + N - 1);
+      if (REV) {
+        // the constants of mirrored transfers as exact conjugates, so that
+        // the sum stays exactly reversal-symmetric
+        if (ga + gb > M) {
+          ta = tail_c(P, 2 * M - (ga + gb));
+          ta.y = -ta.y;
+        } else if (ga + gb == M) {
+          ta.y = 0.f;
+        }
+        if (gb > gc) {
+          tb0 = tail_c(P, nrow + gc - gb + N - 1);
+          tb0.y = -tb0.y;
+        } else if (gb == gc) {
+          tb0.y = 0.f;
+        }
+        if (gb > gc + 1) {
+          tb1 = tail_c(P, nrow + gc + 1 - gb + N - 1);
+          tb1.y = -tb1.y;
+        } else if (gb == gc + 1) {
+          tb1.y = 0.f;
+        }
+      }
+      v = make_float4(v.x + (ta.x + tb0.x), v.y + (ta.y + tb0.y), v.z + (ta.x + tb1.x), v.w + (ta.y + tb1.y));
+    }
+    K4[((ga * N + gb) * N + gc) >> 1] = make_float4(v.x + vk.x, v.y + vk.y, v.z + vk.z, v.w + vk.w);
   }
 }
 
-static inline int ntiles(int maxN) {
-  const int nt = (maxN + TB - 1) / TB;
-  return nt * nt * nt;
-}
 
 int layout_init() {
   return cudaFuncSetAttribute(k_relayout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess
@@ -269,10 +255,11 @@ int launch_fill_z(const PointDesc *d_pts, int n_points, cudaStream_t st) {
 }
 
 int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
+  const dim3 g(lblocks(maxN, maxN), n_points);
   if (mask & FRG_REVERSAL)
-    k_combine<true><<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, mask);
+    k_combine<true><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask);
   else
-    k_combine<false><<<dim3(ntiles(maxN), n_points), 256, 0, st>>>(d_pts, d_io, mask);
+    k_combine<false><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
