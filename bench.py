@@ -29,7 +29,11 @@ headline):
   siam_N64_iflow  the same with the interaction-flow cutoff (Lambda = 1/g from
              1e12 down to the full model at 1)
 Options of the headline workload: --tails (frequency-box tails), --reversal
-(frequency-reversal reduction).
+(the frequency-reversal reduction asserted for every input, half storage),
+--no-reversal (flows compute every transfer).  By default a split-precision
+flow uses the reversal reduction automatically (every flow from the bare vertex
+is exactly reversal-symmetric); the line then also reports the same flows
+computing every transfer under "every_transfer".
 """
 import argparse
 import json
@@ -285,7 +289,10 @@ def run_ours(args):
     w = inputs.SIAM_N128
     N = w.N
     prec = args.precision
-    mask = frg.CH_ALL | (frg.TAILS if args.tails else 0) | (frg.REVERSAL if args.reversal else 0)
+    mask = frg.CH_ALL | (frg.TAILS if args.tails else 0) | (frg.REVERSAL if args.reversal else 0) | \
+        (frg.NO_REVERSAL if args.no_reversal else 0)
+    # the reversal reduction is in effect for split-precision flows unless turned off
+    reduced = prec != "fp64" and not args.no_reversal
     ctx = frg.Context([w], precision=prec, channel_mask=mask)
     tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
@@ -336,6 +343,8 @@ def run_ours(args):
     phases = np.array([ctx.rhs_timed(0, lam, g, s, dg, ds) for _ in range(args.rhs_reps)])
     ph = phases.mean(axis=0)
     pk = peaks()
+    # the per-phase split above is of stand-alone rhs evaluations (every
+    # transfer unless --reversal asserts the symmetry)
     macs = contraction_macs(N, half=args.reversal)
     if prec == "fp64":
         flops = 8.0 * macs
@@ -407,10 +416,33 @@ def run_ours(args):
         fp64_gpu = {"value": r64, "unit": UNIT, "what": "plain FP64 GPU rhs on the same state",
                     "speedup_split_vs_fp64": (1e3 / sum(ph)) / r64}
 
+    # the same flows computing every transfer (no reversal reduction)
+    every = None
+    if reduced and rank == 0 and world == 1 and not args.headline_only:
+        with frg.Context([w], precision=prec, channel_mask=(mask & ~frg.REVERSAL) | frg.NO_REVERSAL) as cf:
+            if prec != "fp64":
+                cf.autotune()
+            ev_f = 0
+            cf.set_state(0, bare, None, w.Lambda0)
+            cf.flow()
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(3):
+                cf.set_state(0, bare, None, w.Lambda0)
+                st = cf.flow()[0]
+                ev_f += st.rhs_evals
+            f1.record(stream)
+            torch.cuda.synchronize()
+            every = {"value": ev_f / (f0.elapsed_time(f1) / 1e3), "unit": UNIT, "flows": 3,
+                     "what": "the same whole flows with FRG_NO_REVERSAL (every transfer of every channel)"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
             "config": {"workload": w.name + ("+tails" if args.tails else "") + ("+reversal" if args.reversal else ""),
+                       "reversal_reduction": ("asserted (FRG_REVERSAL)" if args.reversal else
+                                              "automatic (states reversal-symmetric)" if reduced else "off"),
                        "N_f": N, "U": w.U, "T": w.T,
                        "eps_d": w.eps_d, "channel_mask": mask,
                        "precision": prec, "rhs_evals_timed": evals, "step_attempts_timed": attempts,
@@ -421,7 +453,7 @@ def run_ours(args):
                        "l2": "working set > L2 (state, 7 stage derivatives, stage input: %.0f MB)"
                              % ((2 * 16 + 7 * (8 if prec != 'fp64' else 16) + 16) * N ** 3 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single", "autotune": tune},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "every_transfer": every,
             "clocks": clk.summary(), "fp64_gpu": fp64_gpu}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds, mask=mask & 0x1F)
@@ -656,6 +688,8 @@ def main():
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--tails", action="store_true",
                     help="headline workload with the frequency-box tail option (channel_mask | FRG_TAILS)")
+    ap.add_argument("--no-reversal", action="store_true",
+                    help="flows compute every transfer (channel_mask | FRG_NO_REVERSAL)")
     ap.add_argument("--reversal", action="store_true",
                     help="headline workload with the frequency-reversal reduction (channel_mask | FRG_REVERSAL): "
                          "the contraction computes half of the transfers of each channel")

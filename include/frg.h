@@ -88,8 +88,22 @@ extern "C" {
 #define FRG_TAILS 0x10
 #define FRG_TAIL_FACTOR 16
 /*
- * Frequency-reversal reduction (split precisions; FRG_FP64 accepts the bit
- * and computes everything).  The caller asserts that every vertex and
+ * Frequency-reversal reduction (split precisions; FRG_FP64 computes every
+ * transfer whatever the bits).  A reversal-symmetric state,
+ *   V(N-1-i1, N-1-i2, N-1-i3) = conj V(i1, i2, i3),  Sigma(N-1-i) = conj Sigma(i)
+ * (index i = n + N/2, i.e. n -> -n-1 with complex conjugation), has a
+ * reversal-symmetric rhs, channel by channel, and every flow from the bare
+ * vertex keeps that symmetry exactly; the paper reduces its ODE system to the
+ * independent couplings the same way (Sec. 4).  By default a split-precision
+ * context uses the reduction for its flows (frg_flow, frg_advance) while the
+ * state of every point is reversal-symmetric: always from frg_init, and
+ * frg_set_state checks a new state exactly (entry by entry) and switches the
+ * context's flows to computing every transfer while any point's state is
+ * not.  frg_rhs then computes every transfer (its inputs are arbitrary).
+ * FRG_NO_REVERSAL turns the reduction off; FRG_REVERSAL asserts instead that
+ * every vertex and self-energy handed to the context, frg_rhs's included, is
+ * reversal-symmetric, and halves the flow's storage (below).
+ * With FRG_REVERSAL the caller asserts that every vertex and
  * self-energy handed to the context is reversal-symmetric,
  *   V(N-1-i1, N-1-i2, N-1-i3) = conj V(i1, i2, i3),  Sigma(N-1-i) = conj Sigma(i)
  * (index i = n + N/2, i.e. n -> -n-1 with complex conjugation), which every
@@ -107,6 +121,7 @@ extern "C" {
  * frg_rhs_noalloc rejects the bit (FRG_EINVAL).
  */
 #define FRG_REVERSAL 0x20
+#define FRG_NO_REVERSAL 0x40
 
 /*
  * Cutoff schemes (frg_params.cutoff).  Both regularise the bare propagator as
@@ -136,7 +151,7 @@ typedef struct {
     double h0;        /* first step in l = ln Lambda (< 0); 0 selects -0.01 */
     long max_steps;   /* step attempts before FRG_ENOTCONV; 0 selects 100000 */
     int precision;    /* FRG_FP64, FRG_3XTF32 or FRG_BF16X3 */
-    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS | FRG_REVERSAL; 0 selects FRG_CH_ALL */
+    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS | FRG_REVERSAL or FRG_NO_REVERSAL; 0 selects FRG_CH_ALL */
     int cutoff;       /* FRG_CUTOFF_OMEGA (default) or FRG_CUTOFF_INTERACTION */
 } frg_params;
 
@@ -263,8 +278,10 @@ int frg_get_state(frg_ctx *ctx, int point, void *d_gamma, void *d_sigma,
  * d_gamma / d_sigma (NULL sigma = 0), scale Lambda (Lambda_f < Lambda <=
  * Lambda0 is not required, but Lambda > Lambda_f for the point to flow) and
  * next step h in l (< 0; 0 selects the h0 of frg_init).  Any vertex is
- * accepted; with FRG_REVERSAL the state enters through its entries with
- * i1 < N/2 (see there).  Clears the point's statistics and done flag.
+ * accepted: by default a split-precision context checks the state's
+ * reversal symmetry exactly and its flows use the reduction only while every
+ * point's state has it; with FRG_REVERSAL the state enters through its entries
+ * with i1 < N/2 (see there).  Clears the point's statistics and done flag.
  */
 int frg_set_state(frg_ctx *ctx, int point, const void *d_gamma, const void *d_sigma,
                   double Lambda, double h);

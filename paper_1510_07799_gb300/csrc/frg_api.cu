@@ -47,6 +47,15 @@ struct frg_ctx {
   // split stage kernels: layout blocks per point (the largest point's vertex
   // blocks plus one self-energy block) and the layouts its channels read
   int lb_grid = 0, lb_want = 0;
+  // frequency-reversal reduction of the split paths: rev_mode 0 off (FP64,
+  // FRG_NO_REVERSAL), 1 automatic (flows use it while every point's state is
+  // reversal-symmetric, checked exactly by frg_set_state), 2 asserted by the
+  // caller (FRG_REVERSAL: every evaluation, half storage); rev_on: the flows
+  // use it now; sym: per point, whether its state is symmetric
+  int rev_mode = 0;
+  bool rev_on = false;
+  std::vector<char> sym;
+  int *d_asym = nullptr, *h_asym = nullptr;
   std::vector<void *> allocs;
   // host-buffer entry point staging (per point, lazily)
   std::vector<double2 *> user_in, user_out;
@@ -141,8 +150,12 @@ int validate(const frg_params &p, std::string &why) {
   if (p.h0 > 0.0) { why = "h0 must be <= 0 (the flow runs towards small Lambda)"; return FRG_EINVAL; }
   if (p.precision < FRG_FP64 || p.precision > FRG_BF16X3) { why = "unknown precision"; return FRG_EINVAL; }
   if (p.cutoff != FRG_CUTOFF_OMEGA && p.cutoff != FRG_CUTOFF_INTERACTION) { why = "unknown cutoff"; return FRG_EINVAL; }
-  if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL)) {
-    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL";
+  if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL | FRG_NO_REVERSAL)) {
+    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL | FRG_NO_REVERSAL";
+    return FRG_EINVAL;
+  }
+  if ((p.channel_mask & FRG_REVERSAL) && (p.channel_mask & FRG_NO_REVERSAL)) {
+    why = "FRG_REVERSAL and FRG_NO_REVERSAL exclude each other";
     return FRG_EINVAL;
   }
   return FRG_OK;
@@ -214,7 +227,7 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
       // flow evaluations: the split stage kernels have written the layouts
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
                 ctx->maxN, fork ? ctx->ev_join : nullptr, tails, fork ? ctx->ev_tails : nullptr,
-                d_io == ctx->d_io_stage),
+                d_io == ctx->d_io_stage, d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
@@ -279,6 +292,32 @@ static int flow_status(frg_ctx *ctx) {
 }
 
 static SegTable seg(frg_ctx *ctx) { return SegTable{ctx->d_seg_point, ctx->d_seg_base}; }
+
+// Contraction schedules the context needs: the reversal reduction's alone when
+// the caller asserts the symmetry, both when the flows switch automatically.
+static int tc_schedules(const frg_ctx *ctx) {
+  return ctx->rev_mode == 2 ? TC_HALF : ctx->rev_mode == 1 ? (TC_FULL | TC_HALF) : TC_FULL;
+}
+
+// Automatic reversal reduction: the flows use it iff every point's state is
+// reversal-symmetric.  A change updates the points' half-storage flag on the
+// device and drops the captured step graph (whose contraction schedule and
+// combine follow the flag).
+static int update_reversal(frg_ctx *ctx) {
+  if (ctx->rev_mode != 1) return FRG_OK;
+  bool on = true;
+  for (char c : ctx->sym) on = on && c;
+  if (on == ctx->rev_on) return FRG_OK;
+  ctx->rev_on = on;
+  for (PointDesc &P : ctx->hpts) P.rev_half = on ? 1 : 0;
+  CK(cudaMemcpyAsync(ctx->d_pts, ctx->hpts.data(), sizeof(PointDesc) * ctx->n, cudaMemcpyHostToDevice, ctx->stream),
+     "point table");
+  if (ctx->step_exec) {
+    cudaGraphExecDestroy(ctx->step_exec);
+    ctx->step_exec = nullptr;
+  }
+  return FRG_OK;
+}
 
 static int issue_k1(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
@@ -385,6 +424,9 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
   ctx->precision = ctx->params[0].precision;
   ctx->mask = ctx->params[0].channel_mask;
   ctx->split = ctx->precision != FRG_FP64;
+  ctx->rev_mode = !ctx->split ? 0 : (ctx->mask & FRG_REVERSAL) ? 2 : (ctx->mask & FRG_NO_REVERSAL) ? 0 : 1;
+  ctx->rev_on = ctx->rev_mode != 0;
+  ctx->sym.assign(n_points, 1);
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaStreamCreateWithFlags(&ctx->fstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -408,9 +450,11 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     P.N = N;
     P.n3 = (int)n3;
     P.cutoff = p.cutoff;
-    P.rev_half = ctx->split && (p.channel_mask & FRG_REVERSAL) ? 1 : 0;
-    // vertex elements of the flow's stage derivatives and float-pair state
-    const size_t nv = P.rev_half ? n3 / 2 : n3;
+    P.rev_half = ctx->rev_on ? 1 : 0;
+    // vertex elements of the flow's stage derivatives and float-pair state:
+    // half storage when the caller asserts the symmetry, whole storage when
+    // the flows may switch to computing every transfer
+    const size_t nv = ctx->rev_mode == 2 ? n3 / 2 : n3;
     P.U = p.U;
     P.T = p.T;
     P.et = p.eps_d + 0.5 * p.U;
@@ -441,7 +485,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       if (!(P.Y32Z = dalloc<float2>(ctx, nz)) || cudaMemset(P.Y32Z, 0, nz * sizeof(float2)) != cudaSuccess)
         return bail(FRG_ENOMEM);
       // reversal reduction: the pp channel's computed half in its own buffer
-      if ((p.channel_mask & FRG_REVERSAL) && !(P.PN = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
+      if (ctx->rev_mode && !(P.PN = dalloc<float2>(ctx, n3))) return bail(FRG_ENOMEM);
       for (int b = 0; b < 2; ++b)
         if (!(P.yhi[b] = dalloc<float2>(ctx, nv)) || !(P.ylo[b] = dalloc<float2>(ctx, nv))) return bail(FRG_ENOMEM);
       if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
@@ -478,6 +522,8 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     return bail(FRG_ENOMEM);
   if (cudaMallocHost(&ctx->h_ctl, sizeof(Ctl) * n_points) != cudaSuccess) return bail(FRG_ENOMEM);
   if (cudaMallocHost(&ctx->h_err, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ENOMEM);
+  if (cudaMallocHost(&ctx->h_asym, sizeof(int)) != cudaSuccess || !(ctx->d_asym = dalloc<int>(ctx, 1)))
+    return bail(FRG_ENOMEM);
   *ctx->h_err = 0;
   if (!(ctx->d_err = dalloc<unsigned>(ctx, 1)) || cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess)
     return bail(FRG_ENOMEM);
@@ -488,7 +534,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     return bail(FRG_ECUDA);
   if (ctx->split) {
     for (const PointDesc &P : ctx->hpts)
-      ctx->lb_grid = std::max(ctx->lb_grid, lblocks(P.N, P.rev_half ? P.N / 2 : P.N) + 1);
+      ctx->lb_grid = std::max(ctx->lb_grid, lblocks(P.N, P.N) + 1);
     ctx->lb_want = ((ctx->mask & FRG_CH_XPH) ? LAY_W : 0) | ((ctx->mask & FRG_CH_DPH) ? LAY_X | LAY_Z : 0);
   }
   if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
@@ -521,7 +567,8 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       cudaMemcpy(ctx->d_work_pt[ch], per.data(), sizeof(WorkItem) * per.size(), cudaMemcpyHostToDevice);
     }
   } else {
-    int rc = tc_plan_create(&ctx->tc, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, ctx->d_err, why);
+    int rc = tc_plan_create(&ctx->tc, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, ctx->d_err, why,
+                            TcTune(), tc_schedules(ctx));
     if (rc) {
       ctx->err = why;
       return bail(rc);
@@ -533,7 +580,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     std::vector<int> sp, sb;
     for (int i = 0; i < n_points; ++i) {
       const PointDesc &P = ctx->hpts[i];
-      if (P.rev_half) {
+      if (ctx->rev_mode == 2) {
         // the vertex entries i < n3/2, then the self-energy
         for (int b = 0; b < P.n3 / 2; b += SEG_ELEMS) {
           sp.push_back(i);
@@ -602,6 +649,7 @@ void frg_destroy(frg_ctx *ctx) {
   for (auto p : ctx->user_out) if (p) cudaFree(p);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  if (ctx->h_asym) cudaFreeHost(ctx->h_asym);
   delete ctx;
 }
 
@@ -841,7 +889,8 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out) {
         const TcTune t{caps[ci], costs[cj]};
         TcPlan *p = nullptr;
         std::string why;
-        if ((rc = tc_plan_create(&p, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, ctx->d_err, why, t))) {
+        if ((rc = tc_plan_create(&p, ctx->hpts, ctx->params, ctx->precision, ctx->d_pts, ctx->d_err, why, t,
+                                 tc_schedules(ctx)))) {
           fail(ctx, rc, why);
           break;
         }
@@ -930,7 +979,20 @@ int frg_set_state(frg_ctx *ctx, int point, const void *d_gamma, const void *d_si
     CK(cudaMemsetAsync(P.ybuf[0] + P.n3, 0, (size_t)P.N * sizeof(double2), ctx->stream), "set state");
   LK(launch_set_ctl(ctx->d_pts, ctx->d_ctl, point, std::log(Lambda), h, ctx->stream), "set state");
   ctx->need_k1 = true;
+  if (ctx->rev_mode == 1) {
+    // is the new state exactly reversal-symmetric (every entry the conjugate
+    // of its mirror)?  The flows use the reduction only while all are.
+    CK(cudaMemsetAsync(ctx->d_asym, 0, sizeof(int), ctx->stream), "set state");
+    LK(launch_check_reversal(P.ybuf[0], P.N, ctx->d_asym, ctx->stream), "set state");
+    CK(cudaMemcpyAsync(ctx->h_asym, ctx->d_asym, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "set state");
+  }
   CK(cudaStreamSynchronize(ctx->stream), "set state");
+  if (ctx->rev_mode == 1) {
+    ctx->sym[point] = *ctx->h_asym == 0;
+    int rc = update_reversal(ctx);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream), "set state");
+  }
   return FRG_OK;
 }
 

@@ -294,8 +294,10 @@ __global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const 
   const int ys = c.yslot;
   const double h = c.h;
   if ((int)blockIdx.x == nvb) {
-    // self-energy part
-    for (int i = n3 + (int)threadIdx.x; i < n3 + N; i += blockDim.x) {
+    // self-energy part; with the reversal reduction the entries i < N/2 are
+    // formed and their mirrors N-1-i written as conjugates, so that the state
+    // stays exactly reversal-symmetric in its self-energy too
+    for (int i = n3 + (int)threadIdx.x; i < n3 + (half ? N / 2 : N); i += blockDim.x) {
       double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
       for (int j = 0; j < (S < 6 ? S : 6); ++j) {
@@ -307,6 +309,12 @@ __global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const 
       const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
       P.Y64[i - n3] = Y;
       if (S == 6) P.ybuf[ys ^ 1][i] = Y;
+      if (half) {
+        const int m = N - 1 - (i - n3);
+        const double2 Yc = make_double2(Y.x, -Y.y);
+        P.Y64[m] = Yc;
+        if (S == 6) P.ybuf[ys ^ 1][n3 + m] = Yc;
+      }
     }
     return;
   }

@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
   float4 *__restrict__ K4 = static_cast<float4 *>(o.dgam);
   const float4 *__restrict__ X4 = reinterpret_cast<const float4 *>(P.PX);
   const float4 *__restrict__ W4 = reinterpret_cast<const float4 *>(P.PW);
-  const float4 *__restrict__ src_pp = REV ? reinterpret_cast<const float4 *>(P.PN) : K4;
+  // the contraction writes the pp output to PN whenever the point has that
+  // buffer (contexts that may use the reversal reduction), else into K itself
+  const float4 *__restrict__ src_pp = P.PN ? reinterpret_cast<const float4 *>(P.PN) : K4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   constexpr int PER = LB * LB * LC / 2 / LB_THREADS;  // pairs per thread and source
   float4 vx[PER], vw[PER];

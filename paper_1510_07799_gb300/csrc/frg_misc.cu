@@ -89,4 +89,24 @@ int launch_widen(double2 *out, const float2 *in, int n3, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// *asym = 1 unless the state (vertex N^3 then self-energy N, FP64) is exactly
+// reversal-symmetric: every entry equal to the complex conjugate of its mirror
+// (flat index n3 - 1 - i for the vertex, N - 1 - i for the self-energy).
+__global__ void k_check_reversal(const double2 *__restrict__ y, int N, int *asym) {
+  const int n3 = N * N * N;
+  bool bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3 / 2 + N / 2; i += gridDim.x * blockDim.x) {
+    const int j = i < n3 / 2 ? n3 - 1 - i : n3 + (N - 1 - (i - n3 / 2));
+    const double2 a = y[i < n3 / 2 ? i : n3 + (i - n3 / 2)], b = y[j];
+    if (a.x != b.x || a.y != -b.y) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *asym = 1;
+}
+
+int launch_check_reversal(const double2 *y, int N, int *d_asym, cudaStream_t st) {
+  k_check_reversal<<<256, 256, 0, st>>>(y, N, d_asym);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 }  // namespace frg

@@ -1008,15 +1008,15 @@ struct TcPlan {
   int n = 0;
   int *d_nt = nullptr;
   unsigned *d_err = nullptr;  // owned by the context
-  bool half = false;  // reversal reduction: transfers m <= N - 1 only
-  // 3xTF32: one launch for all enabled channels; schedule [0] covers every
-  // point, [1 + i] point i alone
+  // one launch for all enabled channels; schedule [0] covers every point,
+  // [1 + i] point i alone; sched: every transfer, sched_half: the reversal
+  // reduction's transfers m <= N - 1 (either may be absent)
   struct Sched {
     tc::st::StWork *d_work = nullptr;
     int *d_start = nullptr;
     int grid = 0;
   };
-  std::vector<Sched> sched;
+  std::vector<Sched> sched, sched_half;
   int mask = 7;
   TcTune tune;
 };
@@ -1026,14 +1026,14 @@ struct TcPlan {
 // allowance), each given to the CTA with the least work so far; stored CTA by
 // CTA with start offsets.
 static bool build_sched(TcPlan *p, const std::vector<PointDesc> &pts, const std::vector<int> &nt, int first,
-                        int last, TcPlan::Sched &out) {
+                        int last, TcPlan::Sched &out, bool half) {
   const int EPI_COST = p->tune.epi_cost;  // epilogue of one tile, in k-step units
   std::vector<std::pair<int, tc::st::StWork>> tiles;
   for (int i = first; i < last; ++i) {
     const int N = pts[i].N;
     for (int ch = 0; ch < 3; ++ch) {
       if (!(p->mask & (1 << ch))) continue;
-      for (int m = 0; m < (p->half ? N : 2 * N - 1); ++m) {
+      for (int m = 0; m < (half ? N : 2 * N - 1); ++m) {
         const Geom g = geom(ch, N, m);
         const int nk = (ch == CH_DPH ? 2 : 1) * ((g.D + tc::KSTEP - 1) / tc::KSTEP);
         for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
@@ -1139,7 +1139,8 @@ static bool encode_maps(TcPlan *p, const std::vector<PointDesc> &pts, std::strin
 }
 
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
-                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why, TcTune tune) {
+                   int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why, TcTune tune,
+                   int schedules) {
   (void)d_pts;
   *out = nullptr;
   if (precision != FRG_3XTF32 && precision != FRG_BF16X3) {
@@ -1168,17 +1169,17 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
     return FRG_EINVAL;
   }
   p->tune = tune;
-  // reversal reduction: transfers m <= N - 1 only (the others by symmetry)
-  p->half = !params.empty() && (params[0].channel_mask & FRG_REVERSAL) != 0;
   std::vector<int> nt(p->n);
   for (int i = 0; i < p->n; ++i) nt[i] = std::min(tune.nt_cap, (pts[i].N + 15) / 16 * 16);
   bool ok = cudaMalloc(&p->d_nt, sizeof(int) * p->n) == cudaSuccess &&
             cudaMemcpy(p->d_nt, nt.data(), sizeof(int) * p->n, cudaMemcpyHostToDevice) == cudaSuccess;
   p->mask = (params.empty() ? FRG_CH_ALL : params[0].channel_mask) & 7;
-  if (ok) {
-    p->sched.resize(1 + p->n);
-    ok = build_sched(p, pts, nt, 0, p->n, p->sched[0]);
-    for (int i = 0; i < p->n && ok; ++i) ok = build_sched(p, pts, nt, i, i + 1, p->sched[1 + i]);
+  for (int h = 0; h < 2 && ok; ++h) {
+    if (!(schedules & (h ? TC_HALF : TC_FULL))) continue;
+    std::vector<TcPlan::Sched> &v = h ? p->sched_half : p->sched;
+    v.resize(1 + p->n);
+    ok = build_sched(p, pts, nt, 0, p->n, v[0], h != 0);
+    for (int i = 0; i < p->n && ok; ++i) ok = build_sched(p, pts, nt, i, i + 1, v[1 + i], h != 0);
   }
   if (ok) {
     std::string mw;
@@ -1209,16 +1210,17 @@ void tc_plan_destroy(TcPlan *p) {
   if (!p) return;
   cudaFree(p->d_maps);
   cudaFree(p->d_nt);
-  for (auto &sc : p->sched) {
-    cudaFree(sc.d_work);
-    cudaFree(sc.d_start);
-  }
+  for (auto *v : {&p->sched, &p->sched_half})
+    for (auto &sc : *v) {
+      cudaFree(sc.d_work);
+      cudaFree(sc.d_start);
+    }
   delete p;
 }
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
-           int tails, cudaEvent_t wait_tails, bool layouts_ready) {
+           int tails, cudaEvent_t wait_tails, bool layouts_ready, bool half) {
   // layouts of the stage input: W for the crossed channel, X and Z for the
   // direct one
   if ((chmask & 6) && !layouts_ready) {
@@ -1227,8 +1229,9 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   }
   if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
   if (wait_before && cudaStreamWaitEvent(st, wait_before, 0) != cudaSuccess) return -3;
-  if ((chmask & 7) != p->mask || point >= p->n) return -1;
-  const TcPlan::Sched &sc = p->sched[point < 0 ? 0 : 1 + point];
+  const std::vector<TcPlan::Sched> &scv = half ? p->sched_half : p->sched;
+  if ((chmask & 7) != p->mask || point >= p->n || scv.empty()) return -1;
+  const TcPlan::Sched &sc = scv[point < 0 ? 0 : 1 + point];
   if (sc.grid) {
     if (p->precision == FRG_3XTF32)
       tc::st::k_contract_tf32<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_3XTF32>::SMEM, st>>>(
@@ -1244,7 +1247,7 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   // with the frequency-box tail constants when enabled); also resets the
   // vertex bound that the BF16 slicing read
   if (tails && wait_tails && cudaStreamWaitEvent(st, wait_tails, 0) != cudaSuccess) return -3;
-  const int cmask = chmask | (tails ? FRG_TAILS : 0) | (p->half ? FRG_REVERSAL : 0);
+  const int cmask = chmask | (tails ? FRG_TAILS : 0) | (half ? FRG_REVERSAL : 0);
   if (launch_combine(d_pts, d_io, n_points, maxN, cmask, st) != 0) return -3;
   return 0;
 }

@@ -17,10 +17,13 @@ struct TcTune {
   int nt_cap = 128;
   int epi_cost = 3;
 };
+// Tile schedules a plan holds: every transfer of each channel, and/or (the
+// frequency-reversal reduction) the transfers m <= N - 1 only.
+constexpr int TC_FULL = 1, TC_HALF = 2;
 // d_err: device word that a kernel whose bounded wait ran out sets non-zero.
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
                    int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why,
-                   TcTune tune = TcTune());
+                   TcTune tune = TcTune(), int schedules = TC_FULL);
 void tc_plan_destroy(TcPlan *plan);
 // One bounded pipeline wait on a barrier nothing completes (limit in ms,
 // clamped to [1, 2000]): the kernel sets *d_err and returns.
@@ -29,12 +32,14 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // one point, writing the float2 vertex output of each active RhsIO.
 // Relayout of the stage input (skipped with layouts_ready: the split stage
 // kernels of a flow write the W, X and Z copies themselves), the channel
-// products, and the combine into the natural layout.  ev_gather / ev_contract
+// products (with half: the reversal reduction's schedule, transfers m <= N - 1,
+// the combine taking the others from the mirrored entries), and the combine
+// into the natural layout.  ev_gather / ev_contract
 // (optional) are recorded after the relayout and after the products; the
 // products wait for wait_before (optional: the bubble weights computed on
 // another stream).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
            cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_tails = nullptr,
-           bool layouts_ready = false);
+           bool layouts_ready = false, bool half = false);
 }  // namespace frg

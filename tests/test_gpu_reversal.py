@@ -189,3 +189,54 @@ def test_half_storage_symmetrises_a_state_from_its_canonical_half():
             assert st.status == 0 and st.accepted >= 1
             out.append(c.get_state(0)[0].cpu().numpy())
     assert np.array_equal(out[0], out[1])
+
+
+def _flow_state(prec, mask, w, state=None):
+    with frg.Context([w], precision=prec, channel_mask=mask) as ctx:
+        if state is not None:
+            g, s = state
+            ctx.set_state(0, torch.from_numpy(g).cuda(), torch.from_numpy(s).cuda(), w.Lambda0)
+        st = ctx.flow()[0]
+        g, s, _, _ = ctx.get_state(0)
+    assert st.status == 0 and st.done == 1
+    return g.cpu().numpy(), s.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("prec", [frg.TF32X3, frg.BF16X3])
+def test_default_flows_use_the_reduction(prec):
+    """A split-precision context uses the reversal reduction by default while
+    its states are reversal-symmetric: a flow from the bare vertex is bitwise
+    the flow of a context that asserts the symmetry (FRG_REVERSAL, half
+    storage), stays exactly symmetric, and is within the flow bar of the same
+    flow computing every transfer (FRG_NO_REVERSAL)."""
+    w = inputs.Workload("t", N=34, U=2.2, T=0.02, eps_d=-1.1 + 0.3)
+    g, s, st = _flow_state(prec, frg.CH_ALL, w)
+    gf, sf, stf = _flow_state(prec, frg.CH_ALL | REV, w)
+    gn, sn, _ = _flow_state(prec, frg.CH_ALL | frg.NO_REVERSAL, w)
+    assert np.array_equal(g, gf) and np.array_equal(s, sf) and st.rhs_evals == stf.rhs_evals
+    assert np.array_equal(g, np.conj(g[::-1, ::-1, ::-1])) and np.array_equal(s, np.conj(s[::-1]))
+    assert nrel(g, gn) < FLOW_TOL and nrel(s, sn) < FLOW_TOL
+
+
+def test_a_state_without_the_symmetry_switches_the_flows_to_every_transfer():
+    """frg_set_state checks the symmetry exactly: an asymmetric state makes the
+    context's flows compute every transfer (bitwise the FRG_NO_REVERSAL flow);
+    a symmetric state brings the reduction back (bitwise the FRG_REVERSAL
+    flow); frg_rhs computes every transfer on any input."""
+    w = inputs.Workload("t", N=24, U=1.4, T=0.03, eps_d=-0.7 + 0.2, Lambda0=2.0)
+    Va = inputs.random_vertex(w.N, w.U, seed=5, amp=0.1, crossing=False)
+    sa = inputs.random_sigma(w.N, seed=6, amp=0.01)
+    Vs, ss = symmetric_state(w.N, w.U, seed=7)
+    with frg.Context([w], precision=frg.TF32X3) as ctx:
+        for state, ref_mask in (((Va, sa), frg.NO_REVERSAL), ((Vs, ss), REV), ((Va, sa), frg.NO_REVERSAL)):
+            ctx.set_state(0, torch.from_numpy(state[0]).cuda(), torch.from_numpy(state[1]).cuda(), w.Lambda0)
+            st = ctx.flow()[0]
+            g, s, _, _ = ctx.get_state(0)
+            gr, sr, str_ = _flow_state(frg.TF32X3, frg.CH_ALL | ref_mask, w, state)
+            assert st.status == 0 and st.rhs_evals == str_.rhs_evals
+            assert np.array_equal(g.cpu().numpy(), gr) and np.array_equal(s.cpu().numpy(), sr)
+        # a stand-alone rhs on an asymmetric input: every transfer
+        with frg.Context([w], precision=frg.TF32X3, channel_mask=frg.CH_ALL | frg.NO_REVERSAL) as full:
+            dg, ds = gpu_rhs(ctx, 0.3, Va, sa)
+            fg, fs = gpu_rhs(full, 0.3, Va, sa)
+        assert np.array_equal(dg, fg) and np.array_equal(ds, fs)
