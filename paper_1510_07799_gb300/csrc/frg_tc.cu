@@ -549,11 +549,13 @@ struct XfV<FRG_3XTF32> {
     *reinterpret_cast<float4 *>(T + L::A_SLICE + L::IM_ROWS + a.lo_half) = il;
     *reinterpret_cast<float4 *>(T + L::A_SLICE + L::IM_ROWS + a.hi_half) = rl;
   }
-  __device__ __forceinline__ void store_right(uint8_t *T, const XfAt &a) const {
+  // hi slice at T, lo slice at T + bsl (bsl = NT operand rows: the two
+  // slices are adjacent, so one product of N = 2 NT covers both)
+  __device__ __forceinline__ void store_right(uint8_t *T, const XfAt &a, int bsl) const {
     *reinterpret_cast<float4 *>(T + a.lo_half) = rh;
     *reinterpret_cast<float4 *>(T + a.hi_half) = ih;
-    *reinterpret_cast<float4 *>(T + L::B_SLICE + a.lo_half) = rl;
-    *reinterpret_cast<float4 *>(T + L::B_SLICE + a.hi_half) = il;
+    *reinterpret_cast<float4 *>(T + bsl + a.lo_half) = rl;
+    *reinterpret_cast<float4 *>(T + bsl + a.hi_half) = il;
   }
 };
 template <>
@@ -584,10 +586,10 @@ struct XfV<FRG_BF16X3> {
       *reinterpret_cast<uint2 *>(t + L::IM_ROWS + a.hi_half) = r[k];
     }
   }
-  __device__ __forceinline__ void store_right(uint8_t *T, const XfAt &a) const {
+  __device__ __forceinline__ void store_right(uint8_t *T, const XfAt &a, int bsl) const {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      uint8_t *t = T + k * L::B_SLICE;
+      uint8_t *t = T + k * bsl;
       *reinterpret_cast<uint2 *>(t + a.lo_half) = r[k];
       *reinterpret_cast<uint2 *>(t + a.hi_half) = i[k];
     }
@@ -701,9 +703,10 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.raw_empty[j]);
     if (!wwait(&S.op_empty[s], ((it / NOP) & 1u) ^ 1u, S.err, S.abort_flag)) return false;
+    const int bsl = ti.NT * L::ROWB;
     if (lr) va.store_left(A, a0);
-    else if (a0.valid) va.store_right(B, a0);
-    if (a1.valid) vb.store_right(B, a1);
+    else if (a0.valid) va.store_right(B, a0, bsl);
+    if (a1.valid) vb.store_right(B, a1, bsl);
     // one arrival per warp: the generic-proxy writes are fenced for the
     // tensor cores by every writer, then the warp converges
     fence_async_smem();
@@ -725,14 +728,16 @@ struct TBuf {
 };
 struct TSlot {
   int b;               // half of TMEM
-  uint32_t dcol, xcol; // columns of the hi*hi and the cross accumulator
+  uint32_t dcol, xcol; // columns of the leading and the cross accumulator
 };
-__device__ __forceinline__ TSlot tslot_next(TBuf &t) {
+// The cross accumulator follows the leading one directly (NT columns on), so
+// that one product with N = 2 NT feeds both from the two adjacent B slices.
+__device__ __forceinline__ TSlot tslot_next(TBuf &t, int NT) {
   TSlot s;
   s.b = t.flip;
   t.flip ^= 1;
   s.dcol = 256u * s.b;
-  s.xcol = s.dcol + 128u;
+  s.xcol = s.dcol + (uint32_t)NT;
   return s;
 }
 
@@ -749,13 +754,14 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
   using L = OpL<PREC>;
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  const TSlot ts = tslot_next(tb);
+  const TSlot ts = tslot_next(tb, ti.NT);
   uint32_t &e = ts.b ? tb.e1 : tb.e0;
   if (!wwait(&S.tempty[ts.b], (e & 1u) ^ 1u, S.err, S.abort_flag)) return false;
   ++e;
   tc_after();
   const uint32_t d = S.tmem + ts.dcol, dx = S.tmem + ts.xcol;
-  const uint32_t id = idesc<PREC>(ti.NT);
+  const uint32_t id = idesc<PREC>(ti.NT), id2 = idesc<PREC>(2 * ti.NT);
+  const uint32_t bsl = (uint32_t)(ti.NT * L::ROWB);
   for (int kb = 0; kb < ti.nk; ++kb, ++it) {
     const int s = it % NOP;
     if (!wwait(&S.op_full[s], (it / NOP) & 1u, S.err, S.abort_flag)) return false;
@@ -763,15 +769,17 @@ __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restr
     if (lane == 0) {
       const uint32_t a0 = smem_u32(S.ops + s * L::STAGE), b0 = a0 + L::SL * L::A_SLICE;
       auto A_ = [&](int k, uint32_t o) { return sdesc<PREC>(a0 + k * L::A_SLICE + o); };
-      auto B_ = [&](int k, uint32_t o) { return sdesc<PREC>(b0 + k * L::B_SLICE + o); };
+      auto B_ = [&](int k, uint32_t o) { return sdesc<PREC>(b0 + k * bsl + o); };
       // 32 bytes of K' per instruction: 8 tf32 or 16 bf16
       constexpr int NI = PREC == FRG_3XTF32 ? 4 : 2;
 #pragma unroll
       for (int kk = 0; kk < NI; ++kk) {
         const uint32_t o = kk * 32;
         const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-        mma<PREC>(d, A_(0, o), B_(0, o), id, first);   // leading slices
-        mma<PREC>(dx, A_(0, o), B_(1, o), id, first);
+        // leading A slice times the adjacent first and second B slices, N = 2 NT:
+        // the product of the leading slices into the first accumulator, the
+        // leading-A x second-B product into the cross accumulator next to it
+        mma<PREC>(d, A_(0, o), B_(0, o), id2, first);
         mma<PREC>(dx, A_(1, o), B_(0, o), id, 1u);
         if (PREC == FRG_BF16X3) {
           mma<PREC>(dx, A_(0, o), B_(2, o), id, 1u);
@@ -813,7 +821,7 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
                                          const int *__restrict__ nt_of, TBuf &tb, int warp, int lane) {
   TileInfo ti;
   if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
-  const TSlot ts = tslot_next(tb);
+  const TSlot ts = tslot_next(tb, ti.NT);
   uint32_t &f = ts.b ? tb.f1 : tb.f0;
   if (!wwait(&S.tfull[ts.b], f & 1u, S.err, S.abort_flag)) return false;
   ++f;
