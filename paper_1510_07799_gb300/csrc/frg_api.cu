@@ -699,6 +699,10 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
   LK(launch_set_user_io(ctx->d_io_user, ctx->d_ctl, ctx->n, point, s, Lambda, ctx->stream), "user io");
   int rc = run_rhs(ctx, ctx->d_io_user, point, ev);
   if (rc) return rc;
+  // the relayout above rewrote every entry of the point's layouts: the flow's
+  // next step attempt writes every entry again (not only the half the
+  // reversal reduction reads)
+  CK(cudaMemsetAsync(&ctx->d_ctl[point].lay_both, 1, sizeof(int), ctx->stream), "layout flag");
   LK(launch_widen(static_cast<double2 *>(d_dgamma), u.kout, P.n3, ctx->stream), "widen output");
   return FRG_OK;
 }

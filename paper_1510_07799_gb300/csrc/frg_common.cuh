@@ -76,6 +76,11 @@ struct Ctl {
   // their accumulators for the current one (bits of non-negative doubles)
   double yfloor, sfloor;
   unsigned long long ymax_acc, smax_acc;
+  // split paths: non-zero after a stand-alone rhs wrote this point's stage
+  // input layouts; the stage kernels then write every layout entry until the
+  // controller ends the step attempt (under the reversal reduction they write
+  // only the half the contraction reads)
+  int lay_both;
 };
 
 // Inputs/outputs of one rhs evaluation for one point.

@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const 
   }
   __syncthreads();
   if (half)
-    lblock_write<true>(P, sm, k, want);
+    lblock_write<true>(P, sm, k, want, S == 0 || c.lay_both != 0);
   else
     lblock_write<false>(P, sm, k, want);
   block_max_to(vm, P.vmax);
@@ -547,6 +547,7 @@ __global__ void k_controller(const PointDesc *__restrict__ pts, Ctl *__restrict_
   const int pi = blockIdx.x * blockDim.x + threadIdx.x;
   if (pi >= n) return;
   Ctl &c = ctl[pi];
+  c.lay_both = 0;  // every stage of this attempt wrote every layout entry
   if (c.done) return;
   const PointDesc &P = pts[pi];
   c.rhs_evals += 6;

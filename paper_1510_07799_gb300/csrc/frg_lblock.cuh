@@ -63,8 +63,17 @@ __device__ __forceinline__ int lsidx(int a, int b, int c) { return a * LAP + b *
 
 // Writes the W, X and Z entries of the block (the layouts in `want`) from the
 // shared block s (values with the box rule applied).  MIRROR: the block holds
-// canonical entries of a reversal-symmetric vertex; every entry's mirror
-// (N-1-i1, N-1-i2, N-1-i3) is written too, as the complex conjugate.  Each
+// canonical entries of a reversal-symmetric vertex for a contraction under the
+// reversal reduction, which reads only the transfers m <= N - 1 of each channel:
+// X entries with i3 <= i1 (direct channel, t = i3 - i1 <= 0), W entries with
+// i2 <= i3 (crossed channel, Q = i2 - i3 <= 0) and Z entries with i2 <= i3
+// (t = i2 - i3 <= 0); of an entry and its mirror (N-1-i1, N-1-i2, N-1-i3),
+// whose transfer is the negative, the one in that half is written (the mirror
+// as the complex conjugate), both on the self-mirrored transfer.  With `both`
+// every entry and its mirror are written: the first stage of a flow does so,
+// so that the entries outside the half that the contraction's boxes touch past
+// the end of a line (products with zero bubble weights) hold this flow's
+// finite values, not those of an earlier evaluation.  Each
 // lane moves two consecutive elements of a segment (one 16-byte store; N is
 // even and every segment starts at an even index), four lanes a segment, eight
 // segments per warp instruction.  Flat indices fit in 32 bits (N <= 256).
@@ -72,7 +81,7 @@ __device__ __forceinline__ float4 conj2(float4 v) { return make_float4(v.z, -v.w
 
 template <bool MIRROR>
 __device__ __forceinline__ void lblock_write(const PointDesc &P, const float2 *__restrict__ s, const LBlock &k,
-                                             int want) {
+                                             int want, bool both = false) {
   const int N = P.N, M = N - 1, zrow = 2 * N - 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int q = lane & 3, r = lane >> 2;  // element pair 2q, 2q + 1 of segment r of the pass
@@ -86,8 +95,8 @@ __device__ __forceinline__ void lblock_write(const PointDesc &P, const float2 *_
         const float2 u = s[lsidx(a, e0, c)], w = s[lsidx(a, e0 + 1, c)];
         const float4 v = make_float4(u.x, u.y, w.x, w.y);
         const int ga = k.g1 + a, gc = k.g3 + c, gb = k.g2 + e0;
-        X[((ga * N + gc) * N + gb) >> 1] = v;
-        if (MIRROR) X[(((M - ga) * N + (M - gc)) * N + (M - gb - 1)) >> 1] = conj2(v);
+        if (!MIRROR || both || gc <= ga) X[((ga * N + gc) * N + gb) >> 1] = v;
+        if (MIRROR && (both || gc >= ga)) X[(((M - ga) * N + (M - gc)) * N + (M - gb - 1)) >> 1] = conj2(v);
       }
     }
   }
@@ -100,14 +109,15 @@ __device__ __forceinline__ void lblock_write(const PointDesc &P, const float2 *_
         const float2 u = s[lsidx(e0, b, c)];
         const float2 w = e0 + 1 < k.n1 ? s[lsidx(e0 + 1, b, c)] : make_float2(0.f, 0.f);
         const int ga = k.g1 + e0, gb = k.g2 + b, gc = k.g3 + c;
+        const bool own = !MIRROR || both || gb <= gc, mir = MIRROR && (both || gb >= gc);
         if (e0 + 1 < k.n1) {
           const float4 v = make_float4(u.x, u.y, w.x, w.y);
-          W[((gb * N + gc) * N + ga) >> 1] = v;
-          if (MIRROR) W[(((M - gb) * N + (M - gc)) * N + (M - ga - 1)) >> 1] = conj2(v);
+          if (own) W[((gb * N + gc) * N + ga) >> 1] = v;
+          if (mir) W[(((M - gb) * N + (M - gc)) * N + (M - ga - 1)) >> 1] = conj2(v);
         } else {
           // an odd count of owned rows (reversal half of N = 2 mod 4): one element
-          P.Y32W[(gb * N + gc) * N + ga] = u;
-          if (MIRROR) P.Y32W[((M - gb) * N + (M - gc)) * N + (M - ga)] = make_float2(u.x, -u.y);
+          if (own) P.Y32W[(gb * N + gc) * N + ga] = u;
+          if (mir) P.Y32W[((M - gb) * N + (M - gc)) * N + (M - ga)] = make_float2(u.x, -u.y);
         }
       }
     }
@@ -129,16 +139,18 @@ __device__ __forceinline__ void lblock_write(const PointDesc &P, const float2 *_
       const float2 w = v1 ? s[lsidx(a, e0 + 1, c0 + 1)] : make_float2(0.f, 0.f);
       const int at = (ga * zrow + dz) * N + gb;
       const int atm = ((M - ga) * zrow + (2 * N - 2 - dz)) * N + (M - gb - 1);  // mirror of element e0 + 1
+      // i2 - i3 = dz - (N - 1), the same for the whole segment
+      const bool own = !MIRROR || both || dz <= N - 1, mir = MIRROR && (both || dz >= N - 1);
       if (v0 && v1) {
         const float4 v = make_float4(u.x, u.y, w.x, w.y);
-        reinterpret_cast<float4 *>(P.Y32Z)[at >> 1] = v;
-        if (MIRROR) reinterpret_cast<float4 *>(P.Y32Z)[atm >> 1] = conj2(v);
+        if (own) reinterpret_cast<float4 *>(P.Y32Z)[at >> 1] = v;
+        if (mir) reinterpret_cast<float4 *>(P.Y32Z)[atm >> 1] = conj2(v);
       } else if (v0) {
-        P.Y32Z[at] = u;
-        if (MIRROR) P.Y32Z[atm + 1] = make_float2(u.x, -u.y);
+        if (own) P.Y32Z[at] = u;
+        if (mir) P.Y32Z[atm + 1] = make_float2(u.x, -u.y);
       } else {
-        P.Y32Z[at + 1] = w;
-        if (MIRROR) P.Y32Z[atm] = make_float2(w.x, -w.y);
+        if (own) P.Y32Z[at + 1] = w;
+        if (mir) P.Y32Z[atm] = make_float2(w.x, -w.y);
       }
     }
   }
