@@ -105,7 +105,7 @@ __device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) {
 // s = i1 + i2), so a mirrored segment is one 16-byte load in reverse order.
 // Per element the sum is ((X + W) + tails) + pp, in that order.
 template <bool REV>
-__global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
+__global__ void __launch_bounds__(LB_THREADS, REV ? 6 : LB_MINBLOCKS)
     k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask) {
   __shared__ __align__(16) float2 sm[LB * LAP];
   const int pi = blockIdx.y;
@@ -128,12 +128,16 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
   float4 *__restrict__ K4 = static_cast<float4 *>(o.dgam);
   const float4 *__restrict__ X4 = reinterpret_cast<const float4 *>(P.PX);
   const float4 *__restrict__ W4 = reinterpret_cast<const float4 *>(P.PW);
-  // the contraction writes the pp output to PN whenever the point has that
-  // buffer (contexts that may use the reversal reduction), else into K itself
-  const float4 *__restrict__ src_pp = P.PN ? reinterpret_cast<const float4 *>(P.PN) : K4;
+  // the contraction writes the pp output to PN under the reversal reduction,
+  // else into K itself
+  const float4 *__restrict__ src_pp = REV ? reinterpret_cast<const float4 *>(P.PN) : K4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   constexpr int PER = LB * LB * LC / 2 / LB_THREADS;  // pairs per thread and source
+  // the mirror of the pair at flat index i (even) is the pair at n3 - 2 - i, in
+  // reverse order: in 16-byte units, h3 - 1 - i/2
+  const int h3 = P.n3 >> 1;
   float4 vx[PER], vw[PER];
+  unsigned flx = 0u, flw = 0u;  // REV: bit u marks a pair read from its mirror
   // direct channel (X layout [a][c][b]), segments (a, c), pairs b = 2q, 2q + 1
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
@@ -141,11 +145,14 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
     const int a = seg / LC, c = seg % LC;
     vx[u] = z4;
     if ((mask & 2) && a < k.n1 && c < k.n3 && e0 < k.n2) {
-      const int ga = k.g1 + a, gb = k.g2 + e0, gc = k.g3 + c;
-      if (!REV || gc < ga || (gc == ga && 2 * ga < M))
-        vx[u] = X4[((ga * N + gc) * N + gb) >> 1];
-      else
-        vx[u] = conj2(X4[(((M - ga) * N + (M - gc)) * N + (M - gb - 1)) >> 1]);
+      const int ga = k.g1 + a, gc = k.g3 + c, i2 = ((ga * N + gc) * N + k.g2 + e0) >> 1;
+      if constexpr (REV) {
+        const bool fl = !(gc < ga || (gc == ga && 2 * ga < M));
+        vx[u] = X4[fl ? h3 - 1 - i2 : i2];
+        flx |= (unsigned)fl << u;
+      } else {
+        vx[u] = X4[i2];
+      }
     }
   }
   // crossed channel (W layout [b][c][a]), segments (b, c), pairs a = 2q, 2q + 1
@@ -155,11 +162,14 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
     const int b = seg / LC, c = seg % LC;
     vw[u] = z4;
     if ((mask & 4) && b < k.n2 && c < k.n3 && e0 < k.n1) {
-      const int ga = k.g1 + e0, gb = k.g2 + b, gc = k.g3 + c;
-      if (!REV || gb < gc || (gb == gc && 2 * gb < M))
-        vw[u] = W4[((gb * N + gc) * N + ga) >> 1];
-      else
-        vw[u] = conj2(W4[(((M - gb) * N + (M - gc)) * N + (M - ga - 1)) >> 1]);
+      const int gb = k.g2 + b, gc = k.g3 + c, i2 = ((gb * N + gc) * N + k.g1 + e0) >> 1;
+      if constexpr (REV) {
+        const bool fl = !(gb < gc || (gb == gc && 2 * gb < M));
+        vw[u] = W4[fl ? h3 - 1 - i2 : i2];
+        flw |= (unsigned)fl << u;
+      } else {
+        vw[u] = W4[i2];
+      }
     }
   }
 #pragma unroll
@@ -167,8 +177,9 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
     const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
     const int a = seg / LC, c = seg % LC;
     if (a < k.n1 && c < k.n3 && e0 < k.n2) {
-      sm[lsidx(a, e0, c)] = make_float2(vx[u].x, vx[u].y);
-      sm[lsidx(a, e0 + 1, c)] = make_float2(vx[u].z, vx[u].w);
+      const float4 v = (REV && (flx >> u & 1u)) ? conj2(vx[u]) : vx[u];
+      sm[lsidx(a, e0, c)] = make_float2(v.x, v.y);
+      sm[lsidx(a, e0 + 1, c)] = make_float2(v.z, v.w);
     }
   }
   __syncthreads();
@@ -177,13 +188,14 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
     const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
     const int b = seg / LC, c = seg % LC;
     if (b < k.n2 && c < k.n3 && e0 < k.n1) {
+      const float4 w = (REV && (flw >> u & 1u)) ? conj2(vw[u]) : vw[u];
       float2 &p = sm[lsidx(e0, b, c)];
-      p.x += vw[u].x;
-      p.y += vw[u].y;
+      p.x += w.x;
+      p.y += w.y;
       if (e0 + 1 < k.n1) {
         float2 &q = sm[lsidx(e0 + 1, b, c)];
-        q.x += vw[u].z;
-        q.y += vw[u].w;
+        q.x += w.z;
+        q.y += w.w;
       }
     }
   }
@@ -197,10 +209,11 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 4 : LB_MINBLOCKS)
     const int ga = k.g1 + a, gb = k.g2 + b, gc = k.g3 + c;
     float4 vk = z4;
     if (mask & 1) {
+      const int i2 = ((ga * N + gb) * N + gc) >> 1;
       if (!REV || ga + gb < M || (ga + gb == M && 2 * ga < M))
-        vk = src_pp[((ga * N + gb) * N + gc) >> 1];
+        vk = src_pp[i2];
       else
-        vk = conj2(src_pp[(((M - ga) * N + (M - gb)) * N + (M - gc - 1)) >> 1]);
+        vk = conj2(src_pp[h3 - 1 - i2]);
     }
     float4 v = *reinterpret_cast<const float4 *>(&sm[lsidx(a, b, c)]);
     if (tails) {

@@ -187,7 +187,7 @@ __device__ __forceinline__ float2 *out_row(const PointDesc &P, float2 *kN, const
   const Geom &g = ti.g;
   if (CH == CH_PP) {
     const int a = g.row_lo + rr;
-    return (P.PN ? P.PN : kN) + ((size_t)a * N + (g.x - a)) * N;
+    return kN + ((size_t)a * N + (g.x - a)) * N;
   } else if (CH == CH_DPH) {
     const int k1 = g.row_lo + rr;
     return P.PX + ((size_t)k1 * N + (k1 + g.x)) * N;
@@ -416,6 +416,7 @@ struct Pipe {
   volatile int *abort_flag;
   unsigned *err;
   uint32_t tmem;
+  int pp_pn;  // reversal reduction: the pp output goes to PN (the combine mirrors it)
 };
 
 template <int CH>
@@ -832,7 +833,8 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   const PointDesc &P = pts[ti.point];
   const RhsIO &o = io[ti.point];
   const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
-  float2 *kN = static_cast<float2 *>(o.dgam);
+  // pp output: the vertex output itself, or PN under the reversal reduction
+  float2 *kN = (CH == CH_PP && S.pp_pn) ? P.PN : static_cast<float2 *>(o.dgam);
   const int rr = ti.r0 + 16 * quarter + row16;
   float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
   const uint32_t tl = S.tmem + ((uint32_t)(quarter * 32) << 16);
@@ -884,7 +886,7 @@ template <int PREC>
 __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                          const StWork *__restrict__ work, const int *__restrict__ cta_start,
                                          const int *__restrict__ nt_of, unsigned *__restrict__ err,
-                                         const CUtensorMap *__restrict__ maps) {
+                                         const CUtensorMap *__restrict__ maps, int half) {
   extern __shared__ uint8_t smem_raw[];
   // offset the shared array itself (keeps the shared state space for ld/st.shared)
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -902,6 +904,7 @@ __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, cons
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(S.tempty + 2);
   S.abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   S.err = err;
+  S.pp_pn = half;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -973,14 +976,15 @@ __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, cons
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const StWork *__restrict__ work,
                     const int *__restrict__ cta_start, const int *__restrict__ nt_of, unsigned *__restrict__ err,
-                    const CUtensorMap *__restrict__ maps) {
-  contract<FRG_3XTF32>(pts, io, work, cta_start, nt_of, err, maps);
+                    const CUtensorMap *__restrict__ maps, int half) {
+  contract<FRG_3XTF32>(pts, io, work, cta_start, nt_of, err, maps, half);
 }
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_bf16x3(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                       const StWork *__restrict__ work, const int *__restrict__ cta_start,
-                      const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps) {
-  contract<FRG_BF16X3>(pts, io, work, cta_start, nt_of, err, maps);
+                      const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps,
+                      int half) {
+  contract<FRG_BF16X3>(pts, io, work, cta_start, nt_of, err, maps, half);
 }
 }  // namespace st
 
@@ -1243,10 +1247,10 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   if (sc.grid) {
     if (p->precision == FRG_3XTF32)
       tc::st::k_contract_tf32<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_3XTF32>::SMEM, st>>>(
-          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps);
+          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps, half ? 1 : 0);
     else
       tc::st::k_contract_bf16x3<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_BF16X3>::SMEM, st>>>(
-          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps);
+          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps, half ? 1 : 0);
     FRG_COUNT(1);
     if (cudaGetLastError() != cudaSuccess) return -3;
   }
