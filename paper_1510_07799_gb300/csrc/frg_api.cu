@@ -178,7 +178,8 @@ void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &ou
 // ev (optional, 6 events): start, after the bubble weights and the self-energy
 // (one fused kernel), after the operand regather, after the channel products,
 // after the combine; the last event follows the combine directly.
-static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr) {
+static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr,
+                   bool err = false) {
   cudaStream_t st = ctx->stream;
   if (ev) CK(cudaEventRecord(ev[0], st), "event");
   // untimed split evaluations overlap the bubble weights with the relayout
@@ -227,7 +228,7 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
       // flow evaluations: the split stage kernels have written the layouts
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
                 ctx->maxN, fork ? ctx->ev_join : nullptr, tails, fork ? ctx->ev_tails : nullptr,
-                d_io == ctx->d_io_stage, d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2),
+                d_io == ctx->d_io_stage, d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2, err),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
@@ -340,10 +341,12 @@ static int issue_step(frg_ctx *ctx) {
     LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, ctx->d_io_stage, st, ctx->lb_grid,
                     ctx->n, ctx->lb_want),
        "stage sum");
-    int rc = run_rhs(ctx, ctx->d_io_stage, -1);
+    // the split paths' scatter-add of the seventh rhs (k7) also completes the
+    // step's error norm
+    int rc = run_rhs(ctx, ctx->d_io_stage, -1, nullptr, s == 6);
     if (rc) return rc;
   }
-  LK(launch_error(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, ctx->split, st), "error norm");
+  if (!ctx->split) LK(launch_error(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, st), "error norm");
   LK(launch_controller(ctx->d_pts, ctx->d_ctl, ctx->n, st), "controller");
   return FRG_OK;
 }
@@ -503,6 +506,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
         return bail(FRG_ECUDA);
       for (int j = 0; j < 7; ++j)
         if (!(P.kG[j] = dalloc<float2>(ctx, nv))) return bail(FRG_ENOMEM);
+      if (!(P.eacc = dalloc<float4>(ctx, nv))) return bail(FRG_ENOMEM);
     }
     for (int j = 0; j < 7; ++j)
       if (!(P.kS[j] = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
@@ -674,6 +678,7 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
   o.active = 1;
   o.out_f32 = 0;
   o.canon = 0;
+  o.ctl = nullptr;
   if (!ctx->split) {
     LK(launch_set_user_io(ctx->d_io_user, ctx->d_ctl, ctx->n, point, o, Lambda, ctx->stream), "user io");
     return run_rhs(ctx, ctx->d_io_user, point, ev);

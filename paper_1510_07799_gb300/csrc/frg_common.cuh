@@ -51,6 +51,11 @@ struct PointDesc {
   float2 *Y32Z;
   float2 *PX, *PW;          // split paths: direct (layout X) and crossed (layout W) channel outputs
   float2 *PN;               // split paths with the reversal reduction: pp channel output (natural layout)
+  // split paths: the step's partial error sum h^-1 e' = sum_{j != 7} E_j k_j in
+  // float-float, written by the seventh stage kernel (which reads those k_j
+  // anyway): per pair of complex entries two float4, hi then lo of the four
+  // real components; the scatter-add of k7 adds E_7 k7 and takes the norm
+  float4 *eacc;
   unsigned char *kord;      // split paths: per table row, its 16-wide k-chunks by increasing max |Lb| (16 each)
   unsigned *vmax;    // split paths: bits of max |Re|,|Im| over the FP32 vertex input of the current rhs
   // frequency-box tails (null when off): propagators on the window of
@@ -93,6 +98,10 @@ struct RhsIO {
   int active;          // 0: skip this point
   int out_f32;         // vertex output as float2
   int canon;           // 1: only the entries i < n3/2 of the vertex output are wanted (dgam holds n3/2)
+  // split paths, the seventh rhs of a step (k7): the scatter-add that forms it
+  // also completes the embedded error estimate of the step (ctl: the point's
+  // controller state); null otherwise
+  Ctl *ctl;
 };
 
 // Output tile of one CTA of the FP64 channel contraction (k_contract_fp64):

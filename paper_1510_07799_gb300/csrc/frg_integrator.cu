@@ -57,6 +57,14 @@ int upload_tableau() {
   return 0;
 }
 
+ErrWeights host_error_weights() {
+  ErrWeights w;
+  for (int j = 0; j < 7; ++j) w.E[j] = (j < 6 ? hA[6][j] : 0.0) - hBstar[j];
+  w.e7h = (float)w.E[6];
+  w.e7l = (float)(w.E[6] - (double)w.e7h);
+  return w;
+}
+
 void host_tableau(double *c, double *a, double *bstar) {
   for (int i = 0; i < 7; ++i) {
     c[i] = hC[i];
@@ -126,6 +134,8 @@ __device__ __forceinline__ void write_stage_io(const PointDesc &P, Ctl &c, RhsIO
   o.dsig = P.kS[c.kslot[stage]];
   o.out_f32 = split;
   o.canon = split ? P.rev_half : 0;
+  // the scatter-add of k7 completes the split paths' error estimate
+  o.ctl = (split && stage == 6) ? &c : nullptr;
   *io = o;
 }
 
@@ -338,12 +348,23 @@ __global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const 
       *reinterpret_cast<float4 *>(P.ylo[ys] + i) = lo;
     } else {
       float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+      // seventh stage: also the partial error sum over the same k_j (E_2 = 0
+      // like a_62; E_7 k7 is added by the scatter-add that forms k7)
+      float eh[4] = {0.f, 0.f, 0.f, 0.f}, el[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         if (S == 6 && j == 1) continue;  // the fifth-order weight of k2 is zero: no read
         const float4 kv = *reinterpret_cast<const float4 *>(static_cast<const float2 *>(P.kG[c.kslot[j]]) + i);
 #pragma unroll
         for (int q = 0; q < 4; ++q) ff_mac(sh[q], sl[q], fAh[S][j], fAl[S][j], f4_get(kv, q));
+        if (S == 6) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ff_mac(eh[q], el[q], fEh[j], fEl[j], f4_get(kv, q));
+        }
+      }
+      if (S == 6) {
+        P.eacc[i] = make_float4(eh[0], eh[1], eh[2], eh[3]);
+        P.eacc[i + 1] = make_float4(el[0], el[1], el[2], el[3]);
       }
       if (S < 6) {
         const float4 yh = *reinterpret_cast<const float4 *>(P.yhi[ys] + i);
@@ -383,111 +404,13 @@ __global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const 
   block_max_to(vm, P.vmax);
 }
 
-// Error estimate of the split paths: e = h sum_j (b_j - bstar_j) k_j with the
-// FP32 k_j summed in float-float; the scaled ratio |e| / (atol + rtol max(|y|,
-// |ynew|)) of every vertex component in FP32, of the self-energy in FP64.
-// Bounded to eight blocks per SM like the stage kernels.
-__global__ void __launch_bounds__(256, 8) k_error_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
-                                                     SegTable seg) {
-  const int b = blockIdx.x;
-  const int pi = seg.point[b];
-  Ctl &c = ctl[pi];
-  if (c.done) return;
-  const PointDesc &P = pts[pi];
-  const int n3 = P.n3, n = n3 + P.N;
-  const int base = seg.base[b];
-  const int ys = c.yslot;
-  const double h = c.h;
-  const float hf = d2f(h), atolf = d2f(P.atol), rtolf = d2f(P.rtol);
-  // the split rhs carries a normwise relative error of order 1e-7 (3xTF32),
-  // so no component's tolerance is taken below rtol x the largest component
-  const float yfl = d2f(c.yfloor);
-  const double sfl = c.sfloor;
-  float fmax_ = 0.f, ym = 0.f;
-  double dmax = 0.0, sm = 0.0;
-  int bad = 0;
-  // vertex part: two complex elements per thread and pass (16-byte accesses);
-  // with half storage the entries i < n3/2 (their mirrors have the same moduli)
-  const int vend = min(base + SEG_ELEMS, P.rev_half ? n3 / 2 : n3);
-  for (int i = base + 2 * (int)threadIdx.x; i < vend; i += 2 * (int)blockDim.x) {
-    float eh[4] = {0.f, 0.f, 0.f, 0.f}, el[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      if (j == 1) continue;  // b2 = bstar2 = 0: no read
-      const float4 k = *reinterpret_cast<const float4 *>(static_cast<const float2 *>(P.kG[c.kslot[j]]) + i);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ff_mac(eh[q], el[q], fEh[j], fEl[j], f4_get(k, q));
-    }
-    const float4 y = *reinterpret_cast<const float4 *>(P.yhi[ys] + i);
-    const float4 yn = *reinterpret_cast<const float4 *>(P.yhi[ys ^ 1] + i);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float m = fmaxf(fabsf(f4_get(y, q)), fabsf(f4_get(yn, q)));
-      ym = fmaxf(ym, m);
-      // the ratio only decides accept / reject and the step factor: a fast
-      // division (a few ulp) is enough
-      const float r = __fdividef(fabsf(hf * __fadd_rn(eh[q], el[q])), atolf + rtolf * fmaxf(m, yfl));
-      if (!isfinite(r) || !isfinite(f4_get(yn, q))) bad = 1;
-      else fmax_ = fmaxf(fmax_, r);
-    }
-  }
-  // self-energy part
-  for (int i = max(base, n3) + (int)threadIdx.x; i < min(base + SEG_ELEMS, n); i += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      const double2 k = P.kS[c.kslot[j]][i - n3];
-      acc.x += dE[j] * k.x;
-      acc.y += dE[j] * k.y;
-    }
-    const double2 yi = P.ybuf[ys][i], yni = P.ybuf[ys ^ 1][i];
-    const double mx = fmax(fabs(yi.x), fabs(yni.x)), my = fmax(fabs(yi.y), fabs(yni.y));
-    sm = fmax(sm, fmax(mx, my));
-    const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(mx, sfl));
-    const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(my, sfl));
-    if (!isfinite(rx) || !isfinite(ry) || !isfinite(yni.x) || !isfinite(yni.y)) bad = 1;
-    else dmax = fmax(dmax, fmax(rx, ry));
-  }
-  double emax = fmax(dmax, f2d(fmax_));
-  double ymd = f2d(ym);
-  for (int off = 16; off > 0; off >>= 1) {
-    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
-    ymd = fmax(ymd, __shfl_xor_sync(0xffffffffu, ymd, off));
-    sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, off));
-    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
-  }
-  __shared__ double wmax[8], wy[8], ws[8];
-  __shared__ int wbad[8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    wmax[wid] = emax;
-    wy[wid] = ymd;
-    ws[wid] = sm;
-    wbad[wid] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0, a = 0.0, b2 = 0.0;
-    int bb = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      m = fmax(m, wmax[w]);
-      a = fmax(a, wy[w]);
-      b2 = fmax(b2, ws[w]);
-      bb |= wbad[w];
-    }
-    atomicMax(&c.errbits, (unsigned long long)__double_as_longlong(m));
-    if (a > 0.0) atomicMax(&c.ymax_acc, (unsigned long long)__double_as_longlong(a));
-    if (b2 > 0.0) atomicMax(&c.smax_acc, (unsigned long long)__double_as_longlong(b2));
-    if (bb) atomicOr(&c.nonfinite, 1);
-  }
-}
-
 // ----------------------------------------------------------- error norm ----
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// Error norm of the FP64 path (the split paths use k_error_split).
+// Error norm of the FP64 path (the split paths complete theirs in the scatter-add
+// of the seventh rhs, k_combine in frg_layout.cu).
 __global__ void __launch_bounds__(256) k_error(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
                                                SegTable seg) {
   const int b = blockIdx.x;
@@ -649,10 +572,8 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
 }
 
 int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int split, cudaStream_t st) {
-  if (split)
-    k_error_split<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
-  else
-    k_error<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
+  (void)split;  // the split paths' error norm is part of their scatter-add (frg_layout.cu)
+  k_error<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -13,6 +13,14 @@ struct SegTable {
 };
 
 int upload_tableau();
+// Embedded error weights E_j = b_j - bstar_j of the Dormand-Prince pair (FP64)
+// and E_7 as a float pair, for the split paths' scatter-add of k7, which
+// completes the step's error estimate.
+struct ErrWeights {
+  double E[7];
+  float e7h, e7l;
+};
+ErrWeights host_error_weights();
 void host_tableau(double *c, double *a, double *bstar);
 int launch_init(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int n, cudaStream_t st);
 int launch_set_ctl(const PointDesc *d_pts, Ctl *d_ctl, int pi, double t, double h, cudaStream_t st);

@@ -21,6 +21,8 @@
 #include "frg_common.cuh"
 #include "frg_layout.cuh"
 #include "frg_lblock.cuh"
+#include "frg_integrator.cuh"
+#include "frg_split.cuh"
 
 namespace frg {
 
@@ -86,6 +88,68 @@ __device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) {
   return make_float2((float)t.x, (float)t.y);
 }
 
+// Block-wide fold of the error estimate of one layout block into the point's
+// controller state (seventh rhs of a flow step): the vertex part's maxima from
+// every thread; block 0 adds the self-energy part in FP64 (its derivatives,
+// the tails included, are final by now: this block's threads added the
+// self-energy tail constant to the very entries they read here).
+__device__ void err_fold(const PointDesc &P, const RhsIO &o, const ErrWeights &ew, float fmax_, float ym, int bad) {
+  Ctl &c = *o.ctl;
+  double dmax = 0.0, sm = 0.0;
+  if (blockIdx.x == 0) {
+    const int n3 = P.n3, ys = c.yslot;
+    const double sfl = c.sfloor, h = c.h;
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const double2 k = P.kS[c.kslot[j]][i];
+        acc.x += ew.E[j] * k.x;
+        acc.y += ew.E[j] * k.y;
+      }
+      const double2 yi = P.ybuf[ys][n3 + i], yni = P.ybuf[ys ^ 1][n3 + i];
+      const double mx = fmax(fabs(yi.x), fabs(yni.x)), my = fmax(fabs(yi.y), fabs(yni.y));
+      sm = fmax(sm, fmax(mx, my));
+      const double rx = fabs(h * acc.x) / (P.atol + P.rtol * fmax(mx, sfl));
+      const double ry = fabs(h * acc.y) / (P.atol + P.rtol * fmax(my, sfl));
+      if (!isfinite(rx) || !isfinite(ry) || !isfinite(yni.x) || !isfinite(yni.y)) bad = 1;
+      else dmax = fmax(dmax, fmax(rx, ry));
+    }
+  }
+  double emax = fmax(dmax, f2d(fmax_));
+  double ymd = f2d(ym);
+  for (int off = 16; off > 0; off >>= 1) {
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    ymd = fmax(ymd, __shfl_xor_sync(0xffffffffu, ymd, off));
+    sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, off));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  __shared__ double wmax[LB_THREADS / 32], wy[LB_THREADS / 32], ws[LB_THREADS / 32];
+  __shared__ int wbad[LB_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    wmax[wid] = emax;
+    wy[wid] = ymd;
+    ws[wid] = sm;
+    wbad[wid] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0, a = 0.0, b2 = 0.0;
+    int bb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, wmax[w]);
+      a = fmax(a, wy[w]);
+      b2 = fmax(b2, ws[w]);
+      bb |= wbad[w];
+    }
+    atomicMax(&c.errbits, (unsigned long long)__double_as_longlong(m));
+    if (a > 0.0) atomicMax(&c.ymax_acc, (unsigned long long)__double_as_longlong(a));
+    if (b2 > 0.0) atomicMax(&c.smax_acc, (unsigned long long)__double_as_longlong(b2));
+    if (bb) atomicOr(&c.nonfinite, 1);
+  }
+}
+
 // k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
 // (launched for every split-path rhs, also when only pp is enabled), plus the
 // frequency-box tail constants when mask has FRG_TAILS (block 0 of a point also
@@ -104,9 +168,16 @@ __device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) {
 // X segment is t = i3 - i1, of a W segment Q = i2 - i3, of a natural row
 // s = i1 + i2), so a mirrored segment is one 16-byte load in reverse order.
 // Per element the sum is ((X + W) + tails) + pp, in that order.
-template <bool REV>
-__global__ void __launch_bounds__(LB_THREADS, REV ? 6 : LB_MINBLOCKS)
-    k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask) {
+// For the seventh rhs of a flow step (io.ctl set) the kernel also completes the
+// step's embedded error estimate: e = h (e' + E_7 k7) with the partial
+// float-float sum e' the seventh stage kernel left in P.eacc and k7 the value
+// just formed, the ratio |e| / (atol + rtol max(|y|, |ynew|, floor)) per real
+// component in FP32 (the self-energy's in FP64, block 0), block maxima folded
+// into the controller state with atomics -- the same arithmetic, in the same
+// order, as a separate pass over the stage derivatives would do.
+template <bool REV, bool ERR>
+__global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
+    k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask, ErrWeights ew) {
   __shared__ __align__(16) float2 sm[LB * LAP];
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
@@ -246,6 +317,42 @@ __global__ void __launch_bounds__(LB_THREADS, REV ? 6 : LB_MINBLOCKS)
     }
     K4[((ga * N + gb) * N + gc) >> 1] = make_float4(v.x + vk.x, v.y + vk.y, v.z + vk.z, v.w + vk.w);
   }
+  if constexpr (!ERR) return;
+  if (!o.ctl) return;
+  // seventh rhs: the error estimate over the pairs this thread just wrote
+  float e_max = 0.f, e_ym = 0.f;  // max ratio, max |y|
+  int e_bad = 0;
+  {
+    const Ctl &c = *o.ctl;
+    const float hf = d2f(c.h), atolf = d2f(P.atol), rtolf = d2f(P.rtol), yfl = d2f(c.yfloor);
+    const float2 *__restrict__ yh = P.yhi[c.yslot], *__restrict__ yhn = P.yhi[c.yslot ^ 1];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int t = threadIdx.x + u * LB_THREADS, row = t / (LC / 2), cc = 2 * (t % (LC / 2));
+      const int a = row / LB, b = row % LB;
+      if (!(a < k.n1 && b < k.n2 && cc < k.n3)) continue;
+      const int i = ((k.g1 + a) * N + (k.g2 + b)) * N + k.g3 + cc;  // even: the pair (i, i + 1)
+      const float4 kout = K4[i >> 1];
+      const float4 e0 = P.eacc[i], e1 = P.eacc[i + 1];
+      float eh[4] = {e0.x, e0.y, e0.z, e0.w}, el[4] = {e1.x, e1.y, e1.z, e1.w};
+      const float kq[4] = {kout.x, kout.y, kout.z, kout.w};
+      const float4 y4 = *reinterpret_cast<const float4 *>(yh + i);
+      const float4 yn4 = *reinterpret_cast<const float4 *>(yhn + i);
+      const float yq[4] = {y4.x, y4.y, y4.z, y4.w}, ynq[4] = {yn4.x, yn4.y, yn4.z, yn4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ff_mac(eh[q], el[q], ew.e7h, ew.e7l, kq[q]);
+        const float m = fmaxf(fabsf(yq[q]), fabsf(ynq[q]));
+        e_ym = fmaxf(e_ym, m);
+        // the ratio only decides accept / reject and the step factor: a fast
+        // division (a few ulp) is enough
+        const float r = __fdividef(fabsf(hf * __fadd_rn(eh[q], el[q])), atolf + rtolf * fmaxf(m, yfl));
+        if (!isfinite(r) || !isfinite(ynq[q])) e_bad = 1;
+        else e_max = fmaxf(e_max, r);
+      }
+    }
+  }
+  err_fold(P, o, ew, e_max, e_ym, e_bad);
 }
 
 
@@ -269,12 +376,19 @@ int launch_fill_z(const PointDesc *d_pts, int n_points, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
+int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
+                   bool err) {
   const dim3 g(lblocks(maxN, maxN), n_points);
-  if (mask & FRG_REVERSAL)
-    k_combine<true><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask);
+  const ErrWeights ew = host_error_weights();
+  const bool rev = (mask & FRG_REVERSAL) != 0;
+  if (rev && err)
+    k_combine<true, true><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
+  else if (rev)
+    k_combine<true, false><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
+  else if (err)
+    k_combine<false, true><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
   else
-    k_combine<false><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask);
+    k_combine<false, false><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -10,6 +10,8 @@ int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int
                     int want_z, cudaStream_t st);
 // The constant (bare U) entries of every point's Z layout, once at set-up.
 int launch_fill_z(const PointDesc *d_pts, int n_points, cudaStream_t st);
-// io.dgam (natural, holding the pp output when mask bit 0) += PX, PW.
-int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st);
+// io.dgam (natural, holding the pp output when mask bit 0) += PX, PW; with err
+// (the seventh rhs of a flow step) also the step's error estimate (io.ctl).
+int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
+                   bool err = false);
 }  // namespace frg

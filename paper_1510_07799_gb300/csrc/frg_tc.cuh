@@ -34,12 +34,13 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // kernels of a flow write the W, X and Z copies themselves), the channel
 // products (with half: the reversal reduction's schedule, transfers m <= N - 1,
 // the combine taking the others from the mirrored entries), and the combine
-// into the natural layout.  ev_gather / ev_contract
+// into the natural layout (with err also the step's error estimate: the
+// seventh rhs of a flow step).  ev_gather / ev_contract
 // (optional) are recorded after the relayout and after the products; the
 // products wait for wait_before (optional: the bubble weights computed on
 // another stream).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
            cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_tails = nullptr,
-           bool layouts_ready = false, bool half = false);
+           bool layouts_ready = false, bool half = false, bool err = false);
 }  // namespace frg
