@@ -287,9 +287,16 @@ __device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, f
 // which the W, X and Z copies the contraction reads are written (`want`), so
 // the stage input reaches every layout in this one pass.  Two complex elements
 // per 16-byte access; a thread's loads of one pass are issued together.
+// Threads of a stage block: wide blocks (the canonical half of the reversal
+// reduction has half as many blocks with work); the seventh stage, with the
+// FP64 state update and the partial error sum, at three blocks per SM for its
+// registers.
 template <int S>
-__global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
-                                                            RhsIO *__restrict__ io, int want) {
+__host__ __device__ constexpr int stage_threads() { return LB_THREADS_WIDE; }
+
+template <int S>
+__global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_WIDE)
+    k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl, RhsIO *__restrict__ io, int want) {
   extern __shared__ float4 lsm4[];
   float2 *sm = reinterpret_cast<float2 *>(lsm4);
   const int pi = blockIdx.y;
@@ -333,10 +340,11 @@ __global__ void __launch_bounds__(LB_THREADS, LB_MINBLOCKS) k_stage_split(const 
   const float h_hi = d2f(h), h_lo = d2f(h - f2d(h_hi));
   const float U = (float)P.U;
   float vm = 0.f;
-  constexpr int PAIRS = LB * LB * (LC / 2), PER = PAIRS / LB_THREADS;
+  constexpr int TPB = stage_threads<S>();
+  constexpr int PAIRS = LB * LB * (LC / 2), PER = PAIRS / TPB;
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int e = threadIdx.x + u * LB_THREADS;
+    const int e = threadIdx.x + u * TPB;
     const int c2 = e % (LC / 2), r = e / (LC / 2), b = r % LB, a = r / LB;
     if (!(a < k.n1 && b < k.n2 && 2 * c2 < k.n3)) continue;
     const int i = ((k.g1 + a) * N + (k.g2 + b)) * N + k.g3 + 2 * c2;
@@ -556,13 +564,13 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
   if (split) {
     const dim3 g(lb_grid, n_points);
     switch (s) {
-      case 0: k_stage_split<0><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 1: k_stage_split<1><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 2: k_stage_split<2><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 3: k_stage_split<3><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 4: k_stage_split<4><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 5: k_stage_split<5><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      default: k_stage_split<6><<<g, LB_THREADS, LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 0: k_stage_split<0><<<g, stage_threads<0>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 1: k_stage_split<1><<<g, stage_threads<1>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 2: k_stage_split<2><<<g, stage_threads<2>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 3: k_stage_split<3><<<g, stage_threads<3>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 4: k_stage_split<4><<<g, stage_threads<4>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 5: k_stage_split<5><<<g, stage_threads<5>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      default: k_stage_split<6><<<g, stage_threads<6>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
     }
   } else {
     k_stage<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);

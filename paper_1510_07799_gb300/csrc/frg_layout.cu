@@ -124,8 +124,8 @@ __device__ void err_fold(const PointDesc &P, const RhsIO &o, const ErrWeights &e
     sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, off));
     bad |= __shfl_xor_sync(0xffffffffu, bad, off);
   }
-  __shared__ double wmax[LB_THREADS / 32], wy[LB_THREADS / 32], ws[LB_THREADS / 32];
-  __shared__ int wbad[LB_THREADS / 32];
+  __shared__ double wmax[LB_THREADS_WIDE / 32], wy[LB_THREADS_WIDE / 32], ws[LB_THREADS_WIDE / 32];
+  __shared__ int wbad[LB_THREADS_WIDE / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     wmax[wid] = emax;
@@ -175,9 +175,16 @@ __device__ void err_fold(const PointDesc &P, const RhsIO &o, const ErrWeights &e
 // component in FP32 (the self-energy's in FP64, block 0), block maxima folded
 // into the controller state with atomics -- the same arithmetic, in the same
 // order, as a separate pass over the stage derivatives would do.
+// Threads of a combine block: wide blocks when only the canonical half has work
+// (the error-carrying variant, register-bound, keeps narrow blocks: measured
+// faster).
 template <bool REV, bool ERR>
-__global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
+__host__ __device__ constexpr int comb_threads() { return (REV && !ERR) ? LB_THREADS_WIDE : LB_THREADS; }
+
+template <bool REV, bool ERR>
+__global__ void __launch_bounds__(comb_threads<REV, ERR>(), ERR ? 4 : REV ? LB_MINBLOCKS_WIDE : LB_MINBLOCKS)
     k_combine(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask, ErrWeights ew) {
+  constexpr int TPB = comb_threads<REV, ERR>();
   __shared__ __align__(16) float2 sm[LB * LAP];
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
   // else into K itself
   const float4 *__restrict__ src_pp = REV ? reinterpret_cast<const float4 *>(P.PN) : K4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  constexpr int PER = LB * LB * LC / 2 / LB_THREADS;  // pairs per thread and source
+  constexpr int PER = LB * LB * LC / 2 / TPB;  // pairs per thread and source
   // the mirror of the pair at flat index i (even) is the pair at n3 - 2 - i, in
   // reverse order: in 16-byte units, h3 - 1 - i/2
   const int h3 = P.n3 >> 1;
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
   // direct channel (X layout [a][c][b]), segments (a, c), pairs b = 2q, 2q + 1
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int t = threadIdx.x + u * TPB, seg = t >> 2, e0 = 2 * (t & 3);
     const int a = seg / LC, c = seg % LC;
     vx[u] = z4;
     if ((mask & 2) && a < k.n1 && c < k.n3 && e0 < k.n2) {
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
   // crossed channel (W layout [b][c][a]), segments (b, c), pairs a = 2q, 2q + 1
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int t = threadIdx.x + u * TPB, seg = t >> 2, e0 = 2 * (t & 3);
     const int b = seg / LC, c = seg % LC;
     vw[u] = z4;
     if ((mask & 4) && b < k.n2 && c < k.n3 && e0 < k.n1) {
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
   }
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int t = threadIdx.x + u * TPB, seg = t >> 2, e0 = 2 * (t & 3);
     const int a = seg / LC, c = seg % LC;
     if (a < k.n1 && c < k.n3 && e0 < k.n2) {
       const float4 v = (REV && (flx >> u & 1u)) ? conj2(vx[u]) : vx[u];
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int t = threadIdx.x + u * LB_THREADS, seg = t >> 2, e0 = 2 * (t & 3);
+    const int t = threadIdx.x + u * TPB, seg = t >> 2, e0 = 2 * (t & 3);
     const int b = seg / LC, c = seg % LC;
     if (b < k.n2 && c < k.n3 && e0 < k.n1) {
       const float4 w = (REV && (flw >> u & 1u)) ? conj2(vw[u]) : vw[u];
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
   // pp (natural rows (a, b)), pairs c = 2j, 2j + 1; the sum in natural rows
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int t = threadIdx.x + u * LB_THREADS, row = t / (LC / 2), c = 2 * (t % (LC / 2));
+    const int t = threadIdx.x + u * TPB, row = t / (LC / 2), c = 2 * (t % (LC / 2));
     const int a = row / LB, b = row % LB;
     if (!(a < k.n1 && b < k.n2 && c < k.n3)) continue;
     const int ga = k.g1 + a, gb = k.g2 + b, gc = k.g3 + c;
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(LB_THREADS, ERR ? 4 : REV ? 6 : LB_MINBLOCKS)
     const float2 *__restrict__ yh = P.yhi[c.yslot], *__restrict__ yhn = P.yhi[c.yslot ^ 1];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const int t = threadIdx.x + u * LB_THREADS, row = t / (LC / 2), cc = 2 * (t % (LC / 2));
+      const int t = threadIdx.x + u * TPB, row = t / (LC / 2), cc = 2 * (t % (LC / 2));
       const int a = row / LB, b = row % LB;
       if (!(a < k.n1 && b < k.n2 && cc < k.n3)) continue;
       const int i = ((k.g1 + a) * N + (k.g2 + b)) * N + k.g3 + cc;  // even: the pair (i, i + 1)
@@ -382,13 +389,13 @@ int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int 
   const ErrWeights ew = host_error_weights();
   const bool rev = (mask & FRG_REVERSAL) != 0;
   if (rev && err)
-    k_combine<true, true><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
+    k_combine<true, true><<<g, comb_threads<true, true>(), 0, st>>>(d_pts, d_io, mask, ew);
   else if (rev)
-    k_combine<true, false><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
+    k_combine<true, false><<<g, comb_threads<true, false>(), 0, st>>>(d_pts, d_io, mask, ew);
   else if (err)
-    k_combine<false, true><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
+    k_combine<false, true><<<g, comb_threads<false, true>(), 0, st>>>(d_pts, d_io, mask, ew);
   else
-    k_combine<false, false><<<g, LB_THREADS, 0, st>>>(d_pts, d_io, mask, ew);
+    k_combine<false, false><<<g, comb_threads<false, false>(), 0, st>>>(d_pts, d_io, mask, ew);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

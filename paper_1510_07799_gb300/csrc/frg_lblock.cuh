@@ -27,6 +27,11 @@ constexpr int LCP = LC + 2;
 constexpr int LAP = LB * LCP + 2;
 constexpr int LB_THREADS = 256;
 constexpr int LB_MINBLOCKS = 8;       // resident blocks per SM the kernels are compiled for
+// Kernels that also run on the canonical half only (reversal reduction: half
+// as many blocks with work) use blocks of 512 threads, four per SM, so that the
+// SMs stay as full of warps as with the whole vertex.
+constexpr int LB_THREADS_WIDE = 512;
+constexpr int LB_MINBLOCKS_WIDE = 4;
 constexpr size_t LB_SMEM = (size_t)LB * LAP * sizeof(float2);  // 17,536 bytes
 
 // Layout bits.
