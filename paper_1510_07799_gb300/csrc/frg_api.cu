@@ -72,9 +72,9 @@ struct frg_ctx {
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // split paths: the bubble weights and the self-energy run on a side stream
-  // while the stage input is relaid (fork / join by events)
+  // while the stage input is formed or relaid (fork / join by events)
   cudaStream_t sstream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tails = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tails = nullptr, ev_stage = nullptr, ev_sig = nullptr;
   // pipelined host-buffer evaluations: copy-in and copy-out streams, two device
   // slots per point, per-slot events (input copied, compute done, output read)
   cudaStream_t cin = nullptr, cout = nullptr;
@@ -178,8 +178,7 @@ void build_work(int ch, int pi, int N, std::vector<std::pair<int, WorkItem>> &ou
 // ev (optional, 6 events): start, after the bubble weights and the self-energy
 // (one fused kernel), after the operand regather, after the channel products,
 // after the combine; the last event follows the combine directly.
-static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr,
-                   bool err = false) {
+static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent_t *ev = nullptr) {
   cudaStream_t st = ctx->stream;
   if (ev) CK(cudaEventRecord(ev[0], st), "event");
   // untimed split evaluations overlap the bubble weights with the relayout
@@ -227,8 +226,8 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
     if (chmask) {
       // flow evaluations: the split stage kernels have written the layouts
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
-                ctx->maxN, fork ? ctx->ev_join : nullptr, tails, fork ? ctx->ev_tails : nullptr,
-                d_io == ctx->d_io_stage, d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2, err),
+                ctx->maxN, fork ? ctx->ev_join : nullptr, tails, (fork && tails) ? ctx->ev_tails : nullptr,
+                d_io == ctx->d_io_stage, d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2, false),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
@@ -320,16 +319,55 @@ static int update_reversal(frg_ctx *ctx) {
   return FRG_OK;
 }
 
+// One rhs evaluation of a split-precision flow at stage s (the vertex part of
+// the stage input is formed by this function's stage kernel).  Side stream:
+// the self-energy part of the stage input, the propagators, the bubble-weight
+// tables (and the tail constants), beside the stage kernel's vertex part on
+// the main stream; then the self-energy rhs, which reads the vertex stage
+// input, beside the contraction.  The scatter-add waits for both (it adds the
+// self-energy tail and, for k7, takes the self-energy error), and so does
+// everything after it: the next stage kernel overwrites the vertex input that
+// the self-energy rhs reads.
+static int run_split_stage(frg_ctx *ctx, int s, bool err) {
+  cudaStream_t st = ctx->stream, ss = ctx->sstream;
+  RhsIO *io = ctx->d_io_stage;
+  const bool tails = (ctx->mask & FRG_TAILS) != 0;
+  const int chmask = ctx->mask & 7;
+  CK(cudaEventRecord(ctx->ev_fork, st), "fork");
+  CK(cudaStreamWaitEvent(ss, ctx->ev_fork, 0), "fork");
+  LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, io, s, ctx->n, ss), "self-energy stage");
+  LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_TABLES), "bubble weights");
+  CK(cudaEventRecord(ctx->ev_join, ss), "join");
+  if (tails) LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ss), "tail sums");
+  LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, ctx->lb_grid, ctx->n, ctx->lb_want),
+     "stage sum");
+  CK(cudaEventRecord(ctx->ev_stage, st), "stage");
+  CK(cudaStreamWaitEvent(ss, ctx->ev_stage, 0), "stage");
+  LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_SIGMA), "self-energy rhs");
+  CK(cudaEventRecord(ctx->ev_sig, ss), "self-energy");
+  if (chmask) {
+    LK(tc_run(ctx->tc, ctx->d_pts, io, -1, chmask, st, nullptr, nullptr, ctx->n, ctx->maxN, ctx->ev_join, tails,
+              ctx->ev_sig, true, ctx->rev_on, err),
+       "split contraction");
+  } else {
+    // no vertex channel: the scatter-add writes the zero (or tail-only)
+    // vertex derivative and, for k7, completes the error estimate
+    CK(cudaStreamWaitEvent(st, ctx->ev_sig, 0), "self-energy");
+    const int cmask = (tails ? FRG_TAILS : 0) | (ctx->rev_on ? FRG_REVERSAL : 0);
+    LK(launch_combine(ctx->d_pts, io, ctx->n, ctx->maxN, cmask, st, err), "scatter-add");
+  }
+  return FRG_OK;
+}
+
 static int issue_k1(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
-  if (ctx->split)
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, ctx->lb_grid, ctx->n,
-                    ctx->lb_want),
-       "stage 0");
-  else
+  int rc;
+  if (ctx->split) {
+    if ((rc = run_split_stage(ctx, 0, false))) return rc;
+  } else {
     LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
-  int rc = run_rhs(ctx, ctx->d_io_stage, -1);
-  if (rc) return rc;
+    if ((rc = run_rhs(ctx, ctx->d_io_stage, -1))) return rc;
+  }
   LK(launch_finish_k1(ctx->d_ctl, ctx->d_io_stage, ctx->n, st), "finish k1");
   return FRG_OK;
 }
@@ -338,13 +376,15 @@ static int issue_step(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   LK(launch_prepare(ctx->d_pts, ctx->d_ctl, ctx->n, st), "prepare");
   for (int s = 1; s < 7; ++s) {
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, ctx->split, ctx->d_io_stage, st, ctx->lb_grid,
-                    ctx->n, ctx->lb_want),
-       "stage sum");
-    // the split paths' scatter-add of the seventh rhs (k7) also completes the
-    // step's error norm
-    int rc = run_rhs(ctx, ctx->d_io_stage, -1, nullptr, s == 6);
-    if (rc) return rc;
+    int rc;
+    if (ctx->split) {
+      // the split paths' scatter-add of the seventh rhs (k7) also completes
+      // the step's error norm
+      if ((rc = run_split_stage(ctx, s, s == 6))) return rc;
+    } else {
+      LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 0, ctx->d_io_stage, st), "stage sum");
+      if ((rc = run_rhs(ctx, ctx->d_io_stage, -1))) return rc;
+    }
   }
   if (!ctx->split) LK(launch_error(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, st), "error norm");
   LK(launch_controller(ctx->d_pts, ctx->d_ctl, ctx->n, st), "controller");
@@ -436,6 +476,8 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_tails, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_sig, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return bail(FRG_ECUDA);
@@ -538,7 +580,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
     return bail(FRG_ECUDA);
   if (ctx->split) {
     for (const PointDesc &P : ctx->hpts)
-      ctx->lb_grid = std::max(ctx->lb_grid, lblocks(P.N, P.N) + 1);
+      ctx->lb_grid = std::max(ctx->lb_grid, lblocks(P.N, P.N));
     ctx->lb_want = ((ctx->mask & FRG_CH_XPH) ? LAY_W : 0) | ((ctx->mask & FRG_CH_DPH) ? LAY_X | LAY_Z : 0);
   }
   if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
@@ -645,6 +687,8 @@ void frg_destroy(frg_ctx *ctx) {
   }
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_tails) cudaEventDestroy(ctx->ev_tails);
+  if (ctx->ev_stage) cudaEventDestroy(ctx->ev_stage);
+  if (ctx->ev_sig) cudaEventDestroy(ctx->ev_sig);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->tc) tc_plan_destroy(ctx->tc);
@@ -881,6 +925,7 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out) {
     LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, ctx->lb_grid, ctx->n,
                     ctx->lb_want),
        "stage 0");
+    LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->n, st), "self-energy stage 0");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "events");
     CK(cudaEventCreate(&e1), "events");

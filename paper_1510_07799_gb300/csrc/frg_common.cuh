@@ -223,9 +223,13 @@ int launch_bubble(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int m
 int launch_contract_fp64(const PointDesc *d_pts, const RhsIO *d_io, const WorkItem *const d_work[3],
                          const int nwork[3], int mask, cudaStream_t st);
 // Propagators (16 frequencies per block), then both bubble-weight tables and
-// the self-energy rhs in one launch.
+// the self-energy rhs in one launch.  `parts` selects the propagators and the
+// tables (BUBBLE_TABLES: they need the self-energy input alone) and the
+// self-energy rhs (BUBBLE_SIGMA: it also reads the vertex input), so that a
+// flow can compute the tables before the vertex stage input exists.
+constexpr int BUBBLE_TABLES = 1, BUBBLE_SIGMA = 2;
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
-                        cudaStream_t st);
+                        cudaStream_t st, int parts = BUBBLE_TABLES | BUBBLE_SIGMA);
 // Frequency-box tails: window propagators, then the per-transfer constants
 // (before launch_bubble_sigma, which adds the self-energy constant) ...
 int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st);

@@ -182,14 +182,14 @@ int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int ma
 // loop index p and a fixed-order block reduction.
 template <bool SPLIT>
 __global__ void __launch_bounds__(128)
-    k_bubble_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int maxN, int sigma_on) {
+    k_bubble_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int maxN, int sigma_on, int b0) {
   const int pi = blockIdx.y;
   const RhsIO &o = io[pi];
   if (!o.active) return;
   const PointDesc &P = pts[pi];
   const int N = P.N;
   const int nrow_max = 2 * maxN - 1;
-  const int b = blockIdx.x;
+  const int b = b0 + (int)blockIdx.x;
   const bool table = b < 2 * nrow_max;
   const int which = table ? b / nrow_max : 0;
   const int row = table ? b % nrow_max : 0;
@@ -289,15 +289,23 @@ __global__ void __launch_bounds__(128)
 }
 
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
-                        cudaStream_t st) {
-  k_bubble_gs<<<dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0, st>>>(d_pts, d_io);
-  FRG_COUNT(1);
-  dim3 g(2 * (2 * maxN - 1) + maxN, n_points);
-  if (split)
-    k_bubble_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0);
-  else
-    k_bubble_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0);
-  FRG_COUNT(1);
+                        cudaStream_t st, int parts) {
+  const int nrow_max = 2 * maxN - 1;
+  if (parts & BUBBLE_TABLES) {
+    k_bubble_gs<<<dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0, st>>>(d_pts, d_io);
+    FRG_COUNT(1);
+  }
+  // blocks [0, 2 nrow_max): table rows; [2 nrow_max, 2 nrow_max + maxN): self-energy entries
+  const int b0 = (parts & BUBBLE_TABLES) ? 0 : 2 * nrow_max;
+  const int b1 = (parts & BUBBLE_SIGMA) ? 2 * nrow_max + maxN : 2 * nrow_max;
+  if (b1 > b0) {
+    const dim3 g(b1 - b0, n_points);
+    if (split)
+      k_bubble_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0, b0);
+    else
+      k_bubble_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0, b0);
+    FRG_COUNT(1);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -281,12 +281,14 @@ __device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, f
   }
 }
 
-// One layout block (frg_lblock.cuh: 8 x 8 x 128 vertex entries) per CTA, plus
-// one CTA per point (the last x index) for the self-energy part.  The stage
-// values go to the natural FP32 stage input and to the shared block, from
+// One layout block (frg_lblock.cuh: 8 x 8 x 32 vertex entries) per CTA.  The
+// stage values go to the natural FP32 stage input and to the shared block, from
 // which the W, X and Z copies the contraction reads are written (`want`), so
 // the stage input reaches every layout in this one pass.  Two complex elements
-// per 16-byte access; a thread's loads of one pass are issued together.
+// per 16-byte access; a thread's loads of one pass are issued together.  The
+// self-energy part of the stage and the stage's rhs IO record are written by
+// k_sigma_stage, which runs beside this kernel (with the propagators and the
+// bubble weights that depend on it alone).
 // Threads of a stage block: wide blocks (the canonical half of the reversal
 // reduction has half as many blocks with work); the seventh stage, with the
 // FP64 state update and the partial error sum, at three blocks per SM for its
@@ -296,45 +298,17 @@ __host__ __device__ constexpr int stage_threads() { return LB_THREADS_WIDE; }
 
 template <int S>
 __global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_WIDE)
-    k_stage_split(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl, RhsIO *__restrict__ io, int want) {
+    k_stage_split(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int want) {
   extern __shared__ float4 lsm4[];
   float2 *sm = reinterpret_cast<float2 *>(lsm4);
   const int pi = blockIdx.y;
   const PointDesc &P = pts[pi];
-  // the first block of the point also writes the stage's rhs IO record
-  if (io && blockIdx.x == 0 && threadIdx.x == 0) write_stage_io(P, ctl[pi], io + pi, S, 1);
   const Ctl &c = ctl[pi];
   if (c.done) return;
   const int N = P.N, n3 = P.n3;
   const bool half = P.rev_half != 0;
-  const int nvb = lblocks(N, half ? N / 2 : N);
   const int ys = c.yslot;
   const double h = c.h;
-  if ((int)blockIdx.x == nvb) {
-    // self-energy part; with the reversal reduction the entries i < N/2 are
-    // formed and their mirrors N-1-i written as conjugates, so that the state
-    // stays exactly reversal-symmetric in its self-energy too
-    for (int i = n3 + (int)threadIdx.x; i < n3 + (half ? N / 2 : N); i += blockDim.x) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int j = 0; j < (S < 6 ? S : 6); ++j) {
-        const double2 k = P.kS[c.kslot[j]][i - n3];
-        acc.x += dA[S][j] * k.x;
-        acc.y += dA[S][j] * k.y;
-      }
-      const double2 yi = P.ybuf[ys][i];
-      const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
-      P.Y64[i - n3] = Y;
-      if (S == 6) P.ybuf[ys ^ 1][i] = Y;
-      if (half) {
-        const int m = N - 1 - (i - n3);
-        const double2 Yc = make_double2(Y.x, -Y.y);
-        P.Y64[m] = Yc;
-        if (S == 6) P.ybuf[ys ^ 1][n3 + m] = Yc;
-      }
-    }
-    return;
-  }
   const LBlock k = lblock(N, half ? N / 2 : N, blockIdx.x);
   if (!k.ok) return;
   const float h_hi = d2f(h), h_lo = d2f(h - f2d(h_hi));
@@ -410,6 +384,46 @@ __global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_
   else
     lblock_write<false>(P, sm, k, want);
   block_max_to(vm, P.vmax);
+}
+
+// Self-energy part of split stage s (one block per point), and the stage's rhs
+// IO record: Sigma_s = y_Sigma + h sum_j a_sj kS_j in FP64; the seventh stage
+// also writes the candidate state's self-energy.  With the reversal reduction
+// the entries i < N/2 are formed and their mirrors N-1-i written as
+// conjugates, so that the state stays exactly reversal-symmetric in its
+// self-energy too.  It reads only the self-energy parts, so it runs beside the
+// stage's vertex part (k_stage_split).
+constexpr int SIG_THREADS = 128;
+template <int S>
+__global__ void __launch_bounds__(SIG_THREADS) k_sigma_stage(const PointDesc *__restrict__ pts, Ctl *__restrict__ ctl,
+                                                             RhsIO *__restrict__ io) {
+  const int pi = blockIdx.x;
+  const PointDesc &P = pts[pi];
+  if (threadIdx.x == 0) write_stage_io(P, ctl[pi], io + pi, S, 1);
+  const Ctl &c = ctl[pi];
+  if (c.done) return;
+  const int N = P.N, n3 = P.n3, ys = c.yslot;
+  const bool half = P.rev_half != 0;
+  const double h = c.h;
+  for (int i = threadIdx.x; i < (half ? N / 2 : N); i += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < (S < 6 ? S : 6); ++j) {
+      const double2 k = P.kS[c.kslot[j]][i];
+      acc.x += dA[S][j] * k.x;
+      acc.y += dA[S][j] * k.y;
+    }
+    const double2 yi = P.ybuf[ys][n3 + i];
+    const double2 Y = make_double2(yi.x + h * acc.x, yi.y + h * acc.y);
+    P.Y64[i] = Y;
+    if (S == 6) P.ybuf[ys ^ 1][n3 + i] = Y;
+    if (half) {
+      const int m = N - 1 - i;
+      const double2 Yc = make_double2(Y.x, -Y.y);
+      P.Y64[m] = Yc;
+      if (S == 6) P.ybuf[ys ^ 1][n3 + m] = Yc;
+    }
+  }
 }
 
 // ----------------------------------------------------------- error norm ----
@@ -564,16 +578,30 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
   if (split) {
     const dim3 g(lb_grid, n_points);
     switch (s) {
-      case 0: k_stage_split<0><<<g, stage_threads<0>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 1: k_stage_split<1><<<g, stage_threads<1>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 2: k_stage_split<2><<<g, stage_threads<2>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 3: k_stage_split<3><<<g, stage_threads<3>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 4: k_stage_split<4><<<g, stage_threads<4>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      case 5: k_stage_split<5><<<g, stage_threads<5>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
-      default: k_stage_split<6><<<g, stage_threads<6>(), LB_SMEM, st>>>(d_pts, d_ctl, d_io, want); break;
+      case 0: k_stage_split<0><<<g, stage_threads<0>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      case 1: k_stage_split<1><<<g, stage_threads<1>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      case 2: k_stage_split<2><<<g, stage_threads<2>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      case 3: k_stage_split<3><<<g, stage_threads<3>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      case 4: k_stage_split<4><<<g, stage_threads<4>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      case 5: k_stage_split<5><<<g, stage_threads<5>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      default: k_stage_split<6><<<g, stage_threads<6>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
     }
   } else {
     k_stage<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);
+  }
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st) {
+  switch (s) {
+    case 0: k_sigma_stage<0><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    case 1: k_sigma_stage<1><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    case 2: k_sigma_stage<2><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    case 3: k_sigma_stage<3><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    case 4: k_sigma_stage<4><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    case 5: k_sigma_stage<5><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    default: k_sigma_stage<6><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
   }
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;

@@ -28,13 +28,18 @@ int launch_set_stage_io(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int sta
                         cudaStream_t st);
 int launch_finish_k1(Ctl *d_ctl, const RhsIO *d_io, int n, cudaStream_t st);
 int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st);
-// Stage sum s of every point; with d_io non-null the first block of each point
-// also writes the stage's rhs IO record (as launch_set_stage_io).  FP64 path:
-// nblk segments of the table seg.  Split paths: a grid of lb_grid x n_points
-// layout blocks (frg_lblock.cuh; lb_grid = the largest point's vertex blocks
-// plus one for the self-energy), also writing the W / X / Z copies in `want`.
+// Stage sum s of every point.  FP64 path: nblk segments of the table seg; with
+// d_io non-null the first block of each point also writes the stage's rhs IO
+// record (as launch_set_stage_io).  Split paths: the vertex part only, on a
+// grid of lb_grid x n_points layout blocks (frg_lblock.cuh; lb_grid = the
+// largest point's vertex blocks), also writing the W / X / Z copies in `want`;
+// launch_sigma_stage does the self-energy part and the IO record.
 int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int s, int split, RhsIO *d_io,
                  cudaStream_t st, int lb_grid = 0, int n_points = 0, int want = 0);
+// Split paths: the self-energy part of stage s and the stage's rhs IO record
+// (one block per point).  Independent of the vertex part, so it may run on
+// another stream beside launch_stage's kernel.
+int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st);
 // Dynamic shared-memory limits of the split stage kernels (once per set-up).
 int stage_split_init();
 int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int split, cudaStream_t st);

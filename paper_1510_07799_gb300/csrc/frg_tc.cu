@@ -1232,7 +1232,7 @@ void tc_plan_destroy(TcPlan *p) {
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
-           int tails, cudaEvent_t wait_tails, bool layouts_ready, bool half, bool err) {
+           int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err) {
   // layouts of the stage input: W for the crossed channel, X and Z for the
   // direct one
   if ((chmask & 6) && !layouts_ready) {
@@ -1258,7 +1258,7 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   // channel outputs in their own layouts -> natural layout (the scatter-add,
   // with the frequency-box tail constants when enabled); also resets the
   // vertex bound that the BF16 slicing read
-  if (tails && wait_tails && cudaStreamWaitEvent(st, wait_tails, 0) != cudaSuccess) return -3;
+  if (wait_combine && cudaStreamWaitEvent(st, wait_combine, 0) != cudaSuccess) return -3;
   const int cmask = chmask | (tails ? FRG_TAILS : 0) | (half ? FRG_REVERSAL : 0);
   if (launch_combine(d_pts, d_io, n_points, maxN, cmask, st, err) != 0) return -3;
   return 0;

@@ -38,9 +38,10 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // seventh rhs of a flow step).  ev_gather / ev_contract
 // (optional) are recorded after the relayout and after the products; the
 // products wait for wait_before (optional: the bubble weights computed on
-// another stream).
+// another stream), the combine for wait_combine (optional: the tail constants
+// and the self-energy rhs computed on another stream).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
-           cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_tails = nullptr,
+           cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_combine = nullptr,
            bool layouts_ready = false, bool half = false, bool err = false);
 }  // namespace frg

@@ -142,6 +142,28 @@ def test_split_flow_matches_oracle_reference(name, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mask", [0x8, 0x8 | frg.TAILS])
+@pytest.mark.parametrize("rev", [0, frg.NO_REVERSAL])
+def test_split_flow_without_vertex_channels_matches_oracle(prec, mask, rev):
+    """No vertex channel: the self-energy flows alone (with the tails the
+    vertex also takes the tail constants).  The step control of the split
+    paths still takes the embedded error estimate (the scatter-add that writes
+    the vertex derivative of k7 completes it), so the flow matches the
+    oracle's within the flow bar with about the oracle's number of steps."""
+    w = inputs.Workload("t", N=16, U=1.3, T=0.04, eps_d=-0.65 + 0.25)
+    rg, rs, rst = oracle.flow(model(w), Lambda0=w.Lambda0, Lambda_f=w.Lambda_f, rtol=w.rtol, atol=w.atol,
+                              mask=mask)
+    with frg.Context([w], precision=prec, channel_mask=mask | rev) as ctx:
+        st = ctx.flow()[0]
+        g, s, _, _ = ctx.get_state(0)
+    print("prec=%d mask=%#x steps %d+%d vs oracle %d+%d" % (prec, mask, st.accepted, st.rejected, rst.accepted,
+                                                             rst.rejected))
+    assert st.status == 0 and st.done == 1
+    assert nrel(g.cpu().numpy(), rg) < FLOW_TOL[prec] and nrel(s.cpu().numpy(), rs) < FLOW_TOL[prec]
+    assert abs(st.accepted - rst.accepted) <= max(2, rst.accepted // 10)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_split_batched_points_equal_single_point_runs(prec):
     """Uneven grid sizes in one context: every tile's sum runs in a fixed order
     whichever CTA the schedule gives it to, so each point's flow is bitwise the
