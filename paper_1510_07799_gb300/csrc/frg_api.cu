@@ -46,7 +46,7 @@ struct frg_ctx {
   int nseg = 0;
   // split stage kernels: layout blocks per point (the largest point's vertex
   // blocks plus one self-energy block) and the layouts its channels read
-  int lb_grid = 0, lb_want = 0;
+  int lb_grid = 0, lb_grid_half = 0, lb_want = 0;
   // frequency-reversal reduction of the split paths: rev_mode 0 off (FP64,
   // FRG_NO_REVERSAL), 1 automatic (flows use it while every point's state is
   // reversal-symmetric, checked exactly by frg_set_state), 2 asserted by the
@@ -319,6 +319,10 @@ static int update_reversal(frg_ctx *ctx) {
   return FRG_OK;
 }
 
+// Layout blocks of the split stage kernels: the canonical half's (rows i1 <
+// N/2) under the reversal reduction, else the whole vertex's.
+static int stage_grid(const frg_ctx *ctx) { return ctx->rev_on ? ctx->lb_grid_half : ctx->lb_grid; }
+
 // One rhs evaluation of a split-precision flow at stage s (the vertex part of
 // the stage input is formed by this function's stage kernel).  Side stream:
 // the self-energy part of the stage input, the propagators, the bubble-weight
@@ -339,7 +343,7 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err) {
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_TABLES), "bubble weights");
   CK(cudaEventRecord(ctx->ev_join, ss), "join");
   if (tails) LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ss), "tail sums");
-  LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, ctx->lb_grid, ctx->n, ctx->lb_want),
+  LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, stage_grid(ctx), ctx->n, ctx->lb_want),
      "stage sum");
   CK(cudaEventRecord(ctx->ev_stage, st), "stage");
   CK(cudaStreamWaitEvent(ss, ctx->ev_stage, 0), "stage");
@@ -354,7 +358,7 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err) {
     // vertex derivative and, for k7, completes the error estimate
     CK(cudaStreamWaitEvent(st, ctx->ev_sig, 0), "self-energy");
     const int cmask = (tails ? FRG_TAILS : 0) | (ctx->rev_on ? FRG_REVERSAL : 0);
-    LK(launch_combine(ctx->d_pts, io, ctx->n, ctx->maxN, cmask, st, err), "scatter-add");
+    LK(launch_combine(ctx->d_pts, io, ctx->n, ctx->maxN, cmask, st, err, ctx->rev_on), "scatter-add");
   }
   return FRG_OK;
 }
@@ -579,8 +583,10 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
                      launch_fill_z(ctx->d_pts, n_points, ctx->stream) != 0))
     return bail(FRG_ECUDA);
   if (ctx->split) {
-    for (const PointDesc &P : ctx->hpts)
+    for (const PointDesc &P : ctx->hpts) {
       ctx->lb_grid = std::max(ctx->lb_grid, lblocks(P.N, P.N));
+      ctx->lb_grid_half = std::max(ctx->lb_grid_half, lblocks(P.N, P.N / 2));
+    }
     ctx->lb_want = ((ctx->mask & FRG_CH_XPH) ? LAY_W : 0) | ((ctx->mask & FRG_CH_DPH) ? LAY_X | LAY_Z : 0);
   }
   if (cudaMemset(ctx->d_io_user, 0, sizeof(RhsIO) * n_points) != cudaSuccess ||
@@ -922,7 +928,7 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out) {
     if (!fs.ok) return fail(ctx, FRG_ECUDA, "flow stream ordering");
     cudaStream_t st = ctx->stream;
     // stage input of the current state of every point
-    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, ctx->lb_grid, ctx->n,
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, stage_grid(ctx), ctx->n,
                     ctx->lb_want),
        "stage 0");
     LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->n, st), "self-energy stage 0");

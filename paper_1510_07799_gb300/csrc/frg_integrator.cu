@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_
       }
     }
     vm = fmaxf(vm, fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))));
-    const bool in0 = fourth_in_box(i, N), in1 = fourth_in_box(i + 1, N);
+    // fourth frequencies of the pair: i4 = i1 + i2 - i3 and i4 - 1
+    const int i4 = (k.g1 + a) + (k.g2 + b) - (k.g3 + 2 * c2);
+    const bool in0 = inbox(N, i4), in1 = inbox(N, i4 - 1);
     const float4 v = make_float4(in0 ? out.x : U, in0 ? out.y : 0.f, in1 ? out.z : U, in1 ? out.w : 0.f);
     *reinterpret_cast<float4 *>(P.Y32 + i) = v;
     *reinterpret_cast<float4 *>(sm + lsidx(a, b, 2 * c2)) = v;

@@ -177,7 +177,7 @@ __device__ void err_fold(const PointDesc &P, const RhsIO &o, const ErrWeights &e
 // order, as a separate pass over the stage derivatives would do.
 // Threads of a combine block: wide blocks when only the canonical half has work
 // (the error-carrying variant, register-bound, keeps narrow blocks: measured
-// faster).
+// faster, also against wide blocks at two per SM, which spill nothing).
 template <bool REV, bool ERR>
 __host__ __device__ constexpr int comb_threads() { return (REV && !ERR) ? LB_THREADS_WIDE : LB_THREADS; }
 
@@ -384,8 +384,8 @@ int launch_fill_z(const PointDesc *d_pts, int n_points, cudaStream_t st) {
 }
 
 int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
-                   bool err) {
-  const dim3 g(lblocks(maxN, maxN), n_points);
+                   bool err, bool canon_half) {
+  const dim3 g(lblocks(maxN, canon_half ? maxN / 2 : maxN), n_points);
   const ErrWeights ew = host_error_weights();
   const bool rev = (mask & FRG_REVERSAL) != 0;
   if (rev && err)

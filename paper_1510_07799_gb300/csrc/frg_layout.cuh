@@ -10,8 +10,11 @@ int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int
                     int want_z, cudaStream_t st);
 // The constant (bare U) entries of every point's Z layout, once at set-up.
 int launch_fill_z(const PointDesc *d_pts, int n_points, cudaStream_t st);
-// io.dgam (natural, holding the pp output when mask bit 0) += PX, PW; with err
-// (the seventh rhs of a flow step) also the step's error estimate (io.ctl).
+// io.dgam (natural; it holds the pp output when mask bit 0, unless FRG_REVERSAL
+// in mask: then PN holds it) += PX, PW; with err (the seventh rhs of a flow
+// step) also the step's error estimate (io.ctl).  canon_half: every active
+// point's io.canon is set (only the rows i1 < N/2 are formed), so the grid
+// covers those alone.
 int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
-                   bool err = false);
+                   bool err = false, bool canon_half = false);
 }  // namespace frg

@@ -1260,7 +1260,8 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   // vertex bound that the BF16 slicing read
   if (wait_combine && cudaStreamWaitEvent(st, wait_combine, 0) != cudaSuccess) return -3;
   const int cmask = chmask | (tails ? FRG_TAILS : 0) | (half ? FRG_REVERSAL : 0);
-  if (launch_combine(d_pts, d_io, n_points, maxN, cmask, st, err) != 0) return -3;
+  // a flow's stage input under the reversal reduction: canonical half only
+  if (launch_combine(d_pts, d_io, n_points, maxN, cmask, st, err, layouts_ready && half) != 0) return -3;
   return 0;
 }
 
