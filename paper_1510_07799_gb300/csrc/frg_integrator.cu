@@ -563,15 +563,21 @@ int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// Dynamic shared memory of the split stage kernels, and the largest shared
+// memory carveout: the flow alternates them with the contraction, which needs
+// nearly all of an SM's shared memory, so that an SM need not be reconfigured
+// between the two.
+template <typename K>
+static bool stage_attrs(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+}
+
 int stage_split_init() {
-  bool ok = true;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_stage_split<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
+  const bool ok = stage_attrs(k_stage_split<0>) && stage_attrs(k_stage_split<1>) && stage_attrs(k_stage_split<2>) &&
+                  stage_attrs(k_stage_split<3>) && stage_attrs(k_stage_split<4>) && stage_attrs(k_stage_split<5>) &&
+                  stage_attrs(k_stage_split<6>);
   return ok ? 0 : -3;
 }
 

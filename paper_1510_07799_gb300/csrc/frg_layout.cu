@@ -363,10 +363,21 @@ __global__ void __launch_bounds__(comb_threads<REV, ERR>(), ERR ? 4 : REV ? LB_M
 }
 
 
+// The combine kernels alternate with the contraction in every rhs, which needs
+// nearly all of an SM's shared memory: they take the largest shared memory
+// carveout too, so that an SM need not be reconfigured between them.
+template <typename K>
+static bool max_carveout(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+}
+
 int layout_init() {
-  return cudaFuncSetAttribute(k_relayout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess
-             ? 0
-             : -3;
+  const bool ok =
+      cudaFuncSetAttribute(k_relayout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess &&
+      max_carveout(k_relayout) && max_carveout(k_combine<false, false>) && max_carveout(k_combine<false, true>) &&
+      max_carveout(k_combine<true, false>) && max_carveout(k_combine<true, true>);
+  return ok ? 0 : -3;
 }
 
 int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int want_w, int want_x,
