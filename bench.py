@@ -30,7 +30,9 @@ headline):
              1e12 down to the full model at 1)
 Options of the headline workload: --tails (frequency-box tails), --reversal
 (the frequency-reversal reduction asserted for every input, half storage),
---no-reversal (flows compute every transfer).  By default a split-precision
+--no-reversal (flows compute every transfer), --no-crossing (no crossing
+reduction of the channel products; by default the headline flows assert
+FRG_CROSSING, as every flow from the bare vertex may).  By default a split-precision
 flow uses the reversal reduction automatically (every flow from the bare vertex
 is exactly reversal-symmetric); the line then also reports the same flows
 computing every transfer under "every_transfer".
@@ -290,7 +292,7 @@ def run_ours(args):
     N = w.N
     prec = args.precision
     mask = frg.CH_ALL | (frg.TAILS if args.tails else 0) | (frg.REVERSAL if args.reversal else 0) | \
-        (frg.NO_REVERSAL if args.no_reversal else 0)
+        (frg.NO_REVERSAL if args.no_reversal else 0) | (frg.CROSSING if args.crossing else 0)
     # the reversal reduction is in effect for split-precision flows unless turned off
     reduced = prec != "fp64" and not args.no_reversal
     ctx = frg.Context([w], precision=prec, channel_mask=mask)
@@ -441,6 +443,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
             "config": {"workload": w.name + ("+tails" if args.tails else "") + ("+reversal" if args.reversal else ""),
+                       "crossing_reduction": "asserted (FRG_CROSSING; flows from the bare vertex)"
+                       if args.crossing and prec != "fp64" else "off",
                        "reversal_reduction": ("asserted (FRG_REVERSAL)" if args.reversal else
                                               "automatic (states reversal-symmetric)" if reduced else "off"),
                        "N_f": N, "U": w.U, "T": w.T,
@@ -461,7 +465,7 @@ def run_ours(args):
         # the other workloads, each bounded to seconds (not the headline)
         t0 = time.perf_counter()
         line["configs"] = {
-            "batch64": measure_batch(prec, warmup=1, steps=3),
+            "batch64": measure_batch(prec, warmup=1, steps=3, crossing=args.crossing),
             "siam_N256": measure_n256(prec, warmup=3, steps=20),
             "siam_N64": measure_n64(False, warmup=1, steps=3, with_oracle=not args.no_oracle),
         }
@@ -482,14 +486,15 @@ def reset_flows(ctx, pts, torch):
         ctx.set_state(i, g, None, p.Lambda0)
 
 
-def measure_batch(prec, warmup, steps, fp64_baseline=True):
-    """64 points, uneven N_f, one context: full flows per second."""
+def measure_batch(prec, warmup, steps, fp64_baseline=True, crossing=True):
+    """64 points, uneven N_f, one context: full flows per second (from the bare
+    vertex, so the split precisions may assert the crossing reduction)."""
     import torch
     from paper_1510_07799_gb300 import build as cuda_build
     cuda_build.build()
     from paper_1510_07799_gb300 import frg, inputs
     pts = inputs.batch_points()
-    ctx = frg.Context(pts, precision=prec)
+    ctx = frg.Context(pts, precision=prec, channel_mask=frg.CH_ALL | (frg.CROSSING if crossing else 0))
     tune = ctx.autotune() if prec != "fp64" else None
     stream = torch.cuda.current_stream()
     times, evals = [], []
@@ -534,7 +539,8 @@ def measure_batch(prec, warmup, steps, fp64_baseline=True):
 
 
 def run_batch(args):
-    print(json.dumps(measure_batch(args.precision, args.warmup, args.steps, not args.no_fp64_baseline)))
+    print(json.dumps(measure_batch(args.precision, args.warmup, args.steps, not args.no_fp64_baseline,
+                                   args.crossing)))
     return 0
 
 
@@ -690,6 +696,10 @@ def main():
                     help="headline workload with the frequency-box tail option (channel_mask | FRG_TAILS)")
     ap.add_argument("--no-reversal", action="store_true",
                     help="flows compute every transfer (channel_mask | FRG_NO_REVERSAL)")
+    ap.add_argument("--no-crossing", dest="crossing", action="store_false",
+                    help="headline workload without the crossing reduction of the products (by default the "
+                         "split-precision flows assert it, channel_mask | FRG_CROSSING: they start from the "
+                         "crossing-symmetric bare vertex)")
     ap.add_argument("--reversal", action="store_true",
                     help="headline workload with the frequency-reversal reduction (channel_mask | FRG_REVERSAL): "
                          "the contraction computes half of the transfers of each channel")

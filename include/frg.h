@@ -122,6 +122,26 @@ extern "C" {
  */
 #define FRG_REVERSAL 0x20
 #define FRG_NO_REVERSAL 0x40
+/* Crossing reduction of the split-precision channel products (channel_mask
+ * bit, paper Sec. 4: the reduction of the ODE system to independent couplings
+ * by the model's symmetries).  With FRG_CROSSING the caller asserts that every
+ * vertex handed to the context, frg_rhs's included, is crossing-symmetric,
+ *   V(i1, i2, i3) = V(i2, i1, i4),  i4 = i1 + i2 - i3
+ * (exchange of the two incoming and of the two outgoing particles), which the
+ * flow from the bare vertex has in exact arithmetic.  Each channel's product
+ * at a transfer m then holds pairs of equal entries: pp (s = m) the entries
+ * (k1, k3) and (s - k1, s - k3); composed with the frequency reversal above,
+ * which maps m to itself, the direct and the crossed channel the entries
+ * (k1, k2) and (N-1-k2, N-1-k1), resp. (k3, k1) and (N-1-Q-k1, N-1-Q-k3), with
+ * conjugate values.  Wherever the reversal reduction computes the transfers
+ * m <= N - 1 (split precisions), the tiles of a transfer with more than 64
+ * valid rows then skip one rectangle of such partners and write it from the
+ * entries they computed (N <= 128 with one column tile of N columns; larger
+ * grids compute every entry).  The flow's states are crossing-symmetric up to
+ * the rounding of the split products, which is also the size of the change.
+ * For inputs without the symmetry the result is not the input's rhs.  The FP64
+ * path computes every entry; frg_rhs_noalloc rejects the bit (FRG_EINVAL). */
+#define FRG_CROSSING 0x80
 
 /*
  * Cutoff schemes (frg_params.cutoff).  Both regularise the bare propagator as
@@ -151,7 +171,7 @@ typedef struct {
     double h0;        /* first step in l = ln Lambda (< 0); 0 selects -0.01 */
     long max_steps;   /* step attempts before FRG_ENOTCONV; 0 selects 100000 */
     int precision;    /* FRG_FP64, FRG_3XTF32 or FRG_BF16X3 */
-    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS | FRG_REVERSAL or FRG_NO_REVERSAL; 0 selects FRG_CH_ALL */
+    int channel_mask; /* FRG_CH_* bits, optionally | FRG_TAILS | FRG_REVERSAL or FRG_NO_REVERSAL | FRG_CROSSING; 0 selects FRG_CH_ALL */
     int cutoff;       /* FRG_CUTOFF_OMEGA (default) or FRG_CUTOFF_INTERACTION */
 } frg_params;
 
@@ -354,8 +374,9 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out);
  * which loads this library holds until the process exits.
  *  - Limit: N_f <= FRG_NOALLOC_MAX_N (even, >= 2); larger sizes, T <= 0,
  *    Delta <= 0, Lambda <= 0, non-finite parameters, NULL output pointers, or
- *    a channel_mask with FRG_TAILS or FRG_REVERSAL (anything above
- *    FRG_CH_ALL) return FRG_EINVAL without touching the device.
+ *    a channel_mask with FRG_TAILS, FRG_REVERSAL, FRG_NO_REVERSAL or
+ *    FRG_CROSSING (anything above FRG_CH_ALL) return FRG_EINVAL without
+ *    touching the device.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it with the device's current context;
  *    the first call after that context changed (cudaDeviceReset, or another

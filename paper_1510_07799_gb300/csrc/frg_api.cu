@@ -54,6 +54,9 @@ struct frg_ctx {
   // use it now; sym: per point, whether its state is symmetric
   int rev_mode = 0;
   bool rev_on = false;
+  // crossing reduction of the products (FRG_CROSSING, split paths): used
+  // wherever the reversal reduction's schedule is
+  bool cross = false;
   std::vector<char> sym;
   int *d_asym = nullptr, *h_asym = nullptr;
   std::vector<void *> allocs;
@@ -150,8 +153,9 @@ int validate(const frg_params &p, std::string &why) {
   if (p.h0 > 0.0) { why = "h0 must be <= 0 (the flow runs towards small Lambda)"; return FRG_EINVAL; }
   if (p.precision < FRG_FP64 || p.precision > FRG_BF16X3) { why = "unknown precision"; return FRG_EINVAL; }
   if (p.cutoff != FRG_CUTOFF_OMEGA && p.cutoff != FRG_CUTOFF_INTERACTION) { why = "unknown cutoff"; return FRG_EINVAL; }
-  if (p.channel_mask < 0 || p.channel_mask > (FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL | FRG_NO_REVERSAL)) {
-    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL | FRG_NO_REVERSAL";
+  if (p.channel_mask < 0 ||
+      p.channel_mask > (FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL | FRG_NO_REVERSAL | FRG_CROSSING)) {
+    why = "channel_mask must be within FRG_CH_ALL | FRG_TAILS | FRG_REVERSAL | FRG_NO_REVERSAL | FRG_CROSSING";
     return FRG_EINVAL;
   }
   if ((p.channel_mask & FRG_REVERSAL) && (p.channel_mask & FRG_NO_REVERSAL)) {
@@ -224,10 +228,13 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
     if (ev) CK(cudaEventRecord(ev[3], st), "event");
   } else {
     if (chmask) {
+      // the reversal reduction's transfers: flows while it is on, every call
+      // when the caller asserts the symmetry
+      const bool half = d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2;
       // flow evaluations: the split stage kernels have written the layouts
       LK(tc_run(ctx->tc, ctx->d_pts, d_io, point, chmask, st, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr, ctx->n,
                 ctx->maxN, fork ? ctx->ev_join : nullptr, tails, (fork && tails) ? ctx->ev_tails : nullptr,
-                d_io == ctx->d_io_stage, d_io == ctx->d_io_stage ? ctx->rev_on : ctx->rev_mode == 2, false),
+                d_io == ctx->d_io_stage, half, false, ctx->cross),
          "split contraction");
     } else {
       if (ev) CK(cudaEventRecord(ev[2], st), "event");
@@ -296,7 +303,8 @@ static SegTable seg(frg_ctx *ctx) { return SegTable{ctx->d_seg_point, ctx->d_seg
 // Contraction schedules the context needs: the reversal reduction's alone when
 // the caller asserts the symmetry, both when the flows switch automatically.
 static int tc_schedules(const frg_ctx *ctx) {
-  return ctx->rev_mode == 2 ? TC_HALF : ctx->rev_mode == 1 ? (TC_FULL | TC_HALF) : TC_FULL;
+  const int half = ctx->cross ? TC_CROSS : TC_HALF;
+  return ctx->rev_mode == 2 ? half : ctx->rev_mode == 1 ? (TC_FULL | half) : TC_FULL;
 }
 
 // Automatic reversal reduction: the flows use it iff every point's state is
@@ -351,7 +359,7 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err) {
   CK(cudaEventRecord(ctx->ev_sig, ss), "self-energy");
   if (chmask) {
     LK(tc_run(ctx->tc, ctx->d_pts, io, -1, chmask, st, nullptr, nullptr, ctx->n, ctx->maxN, ctx->ev_join, tails,
-              ctx->ev_sig, true, ctx->rev_on, err),
+              ctx->ev_sig, true, ctx->rev_on, err, ctx->cross),
        "split contraction");
   } else {
     // no vertex channel: the scatter-add writes the zero (or tail-only)
@@ -473,6 +481,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
   ctx->split = ctx->precision != FRG_FP64;
   ctx->rev_mode = !ctx->split ? 0 : (ctx->mask & FRG_REVERSAL) ? 2 : (ctx->mask & FRG_NO_REVERSAL) ? 0 : 1;
   ctx->rev_on = ctx->rev_mode != 0;
+  ctx->cross = ctx->split && (ctx->mask & FRG_CROSSING) != 0;
   ctx->sym.assign(n_points, 1);
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaStreamCreateWithFlags(&ctx->fstream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -69,7 +69,7 @@ struct Tr<FRG_BF16X3> {
 };
 
 struct TcWork {
-  int point, m, rt, ct;
+  int point, m, rt, ct, cx;
 };
 
 // ---------------------------------------------------------------- PTX ----
@@ -177,8 +177,65 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 
 struct TileInfo {
   int point, N, NT, nk, r0, c0, D16;
+  int NTb;             // column width of the raw right-operand box (the point's column-tile width)
+  int own_lo, own_hi;  // columns whose entries the tile writes itself
+  int m_lo, m_hi, m_row;  // crossing reduction: entries (row <= m_row, column in [m_lo, m_hi)) whose partners it writes
   Geom g;
 };
+
+// Crossing reduction of a transfer's product (tiles marked in the schedule).
+// Crossing symmetry V(k1,k2,k3) = V(k2,k1,k4) maps every entry of a channel's
+// product at a transfer m <= N - 1 to a partner in the same product: pp (rows
+// a = k1 in [0, D), D = s + 1 with s = m; columns k3) (a, c) <-> (s - a, s - c)
+// with the same value; the direct and the crossed channel (D = m + 1 rows r;
+// columns k2, resp. k1, of local index c' = c - coff with coff = 0, resp.
+// N - D, in [0, D) for the paired ones) (r, c') <-> (D - 1 - c', D - 1 - r)
+// with the conjugate value (crossing composed with frequency reversal, which
+// maps m to itself).  For a transfer with two row tiles (64 < D <= N <= the
+// tile width) one rectangle of the product is not computed: pp and xph drop
+// the second row tile's paired columns (pp: columns <= s; xph: columns >= N -
+// 64), dph the first row tile's columns < D - 64; the other row tile writes
+// those entries as the partners of its own.  nt = 0: nothing to compute.
+struct CrossTile {
+  int c0, nt, own_lo, own_hi, m_lo, m_hi, m_row;
+};
+__host__ __device__ inline CrossTile cross_tile(int ch, int N, int NT, int m, int rt) {
+  CrossTile x{0, NT, 0, N, 0, 0, -1};
+  const int D = m + 1;
+  const int all_rows = 1 << 20;
+  if (ch == CH_PP) {
+    const int s = m;
+    if (rt == 0) {
+      x.m_lo = 0;
+      x.m_hi = s + 1;
+      x.m_row = s - MROWS;
+    } else {
+      x.c0 = (s + 1) & ~1;
+      x.nt = (N - x.c0 + 15) / 16 * 16;
+      x.own_lo = s + 1;
+    }
+  } else if (ch == CH_DPH) {
+    if (rt == 0) {
+      x.c0 = (D - MROWS) & ~1;
+      x.nt = (N - x.c0 + 15) / 16 * 16;
+      x.own_lo = D - MROWS;
+    } else {
+      x.m_lo = D - MROWS;
+      x.m_hi = D;
+      x.m_row = all_rows;
+    }
+  } else {
+    if (rt == 0) {
+      x.m_lo = N - D;
+      x.m_hi = N - MROWS;
+      x.m_row = all_rows;
+    } else {
+      x.nt = (N - MROWS + 15) / 16 * 16;
+      x.own_hi = N - MROWS;
+    }
+  }
+  return x;
+}
 
 // Output row pointer (channel layout) of local row rr.
 template <int CH>
@@ -252,12 +309,28 @@ __device__ __forceinline__ bool tile_info(const PointDesc *__restrict__ pts, con
   ti.point = w.point;
   const PointDesc &P = pts[w.point];
   ti.N = P.N;
-  ti.NT = nt_of[w.point];
+  ti.NTb = nt_of[w.point];
   ti.g = geom(CH, P.N, w.m);
   ti.D16 = (ti.g.D + KSTEP - 1) / KSTEP * KSTEP;
   ti.nk = (CH == CH_DPH ? 2 : 1) * ti.D16 / KSTEP;
   ti.r0 = w.rt * MROWS;
-  ti.c0 = w.ct * ti.NT;
+  if (w.cx) {
+    const CrossTile x = cross_tile(CH, P.N, ti.NTb, w.m, w.rt);
+    ti.c0 = x.c0;
+    ti.NT = x.nt;
+    ti.own_lo = x.own_lo;
+    ti.own_hi = x.own_hi;
+    ti.m_lo = x.m_lo;
+    ti.m_hi = x.m_hi;
+    ti.m_row = x.m_row;
+  } else {
+    ti.NT = ti.NTb;
+    ti.c0 = w.ct * ti.NT;
+    ti.own_lo = 0;
+    ti.own_hi = P.N;
+    ti.m_lo = ti.m_hi = 0;
+    ti.m_row = -1;
+  }
   return io[w.point].active != 0;
 }
 
@@ -405,7 +478,7 @@ __device__ __forceinline__ int kstep_at(const uint4 &ord, const TileInfo &ti, in
 // least loaded CTA) and stores them CTA by CTA.
 struct StWork {
   int point;
-  short m, ch, rt, ct;
+  short m, ch, rt, ct, cx, pad_;  // cx: a crossing-reduced tile (cross_tile)
 };
 
 // Shared pipeline state of one CTA.
@@ -422,7 +495,7 @@ struct Pipe {
 template <int CH>
 __device__ __forceinline__ bool st_tile_info(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                              const StWork &w, const int *__restrict__ nt_of, TileInfo &ti) {
-  return tile_info<CH>(pts, io, TcWork{w.point, w.m, w.rt, w.ct}, nt_of, ti);
+  return tile_info<CH>(pts, io, TcWork{w.point, w.m, w.rt, w.ct, w.cx}, nt_of, ti);
 }
 
 // Loader (one warp, lane 0 issues): the raw rows of every k-step of a tile by
@@ -442,7 +515,7 @@ __device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__rest
     const Step q = step_of<CH>(ti, kstep_at<CH>(ord, ti, ki));
     const bool two = CH == CH_DPH && !q.half;
     uint8_t *raw = S.raws + j * RAW_STAGE;
-    const uint32_t bytes = (uint32_t)(RAW_A * (two ? 2 : 1) + KS * ti.NT * 8 + RA * 8);
+    const uint32_t bytes = (uint32_t)(RAW_A * (two ? 2 : 1) + KS * ti.NTb * 8 + RA * 8);
     if (lane == 0) {
       uint64_t *bar = &S.raw_full[j];
       arrive_expect_tx(bar, bytes);
@@ -508,14 +581,15 @@ __device__ __forceinline__ XfAt xf_left_at(int t) {
   a.valid = true;
   return a;
 }
+// Right item bt of a tile of NT columns whose raw rows are NTb wide.
 template <int PREC>
-__device__ __forceinline__ XfAt xf_right_at(int bt, int NT) {
+__device__ __forceinline__ XfAt xf_right_at(int bt, int NT, int NTb) {
   XfAt a;
   a.valid = bt < 4 * NT;
   const int c = bt % NT, g4 = a.valid ? bt / NT : 0;
   a.lo_half = grp_off<PREC>(c, g4);
   a.hi_half = grp_off<PREC>(c, 4 + g4);
-  a.src = 4 * g4 * NT + c;
+  a.src = 4 * g4 * NTb + c;
   a.l = 0;
   return a;
 }
@@ -641,12 +715,12 @@ __device__ __forceinline__ void xf_left(XfV<PREC> &o, const float2 *rA, const fl
 // U wherever the fourth frequency leaves the box; rows past the valid k meet
 // zero left weights and columns past the grid are never stored.
 template <int PREC>
-__device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const XfAt &a, int NT,
+__device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const XfAt &a, int NTb,
                                          const typename XfV<PREC>::Scale &sc) {
   float re[4], im[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
-    const float2 b = rB[a.src + x * NT];
+    const float2 b = rB[a.src + x * NTb];
     re[x] = b.x;
     im[x] = b.y;
   }
@@ -677,8 +751,8 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
   }
   // warps 0-7: left item xt and right item xt; warps 8-11: right items xt and xt + 128
   const bool lr = xt < 256;
-  const XfAt a0 = lr ? xf_left_at<PREC>(xt) : xf_right_at<PREC>(xt, ti.NT);
-  const XfAt a1 = xf_right_at<PREC>(lr ? xt : xt + 128, ti.NT);
+  const XfAt a0 = lr ? xf_left_at<PREC>(xt) : xf_right_at<PREC>(xt, ti.NT, ti.NTb);
+  const XfAt a1 = xf_right_at<PREC>(lr ? xt : xt + 128, ti.NT, ti.NTb);
   for (int ki = 0; ki < ti.nk; ++ki, ++it) {
     const int j = it % NRAW, s = it % NOP;
     if (!wwait(&S.raw_full[j], (it / NRAW) & 1u, S.err, S.abort_flag)) return false;
@@ -693,8 +767,8 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
     uint8_t *B = A + L::SL * L::A_SLICE;
     XfV<PREC> va, vb;
     if (lr) xf_left<CH, PREC>(va, rA, rC, rL, a0, off, q.half, scA);
-    else xf_right<PREC>(va, rB, a0, ti.NT, scB);
-    xf_right<PREC>(vb, rB, a1, ti.NT, scB);
+    else xf_right<PREC>(va, rB, a0, ti.NTb, scB);
+    xf_right<PREC>(vb, rB, a1, ti.NTb, scB);
     // the raw rows are in registers: hand the raw stage back to the loader
     // before waiting for a free operand stage.  The loader's next tensor-map
     // copy into this stage is an async-proxy write: the proxy fence orders
@@ -815,7 +889,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // 0-15 the real, lanes 16-31 the imaginary part of complex rows 16w..16w+15,
 // both accumulators added) and take alternate 16-column chunks of the tile;
 // a warp stages the two parts of a chunk in shared memory and stores them
-// interleaved as whole row segments.
+// interleaved as whole row segments (the entries of columns [own_lo, own_hi)).
+// A crossing-reduced tile also writes the partners of its entries in
+// [m_lo, m_hi) x rows <= m_row (cross_tile): pp the entry (s - a, s - c), a row
+// segment in reverse order; the direct and the crossed channel the conjugate
+// at (D - 1 - c', P0 - r) with P0 = D - 1, resp. N - 1, read column by column
+// from the staged chunk, so that the stores of a row stay consecutive.
+// Two complex values a (column x) and b (column x + 1), or the one of them
+// whose column is written, one 16-byte store when both go and x is even.
+__device__ __forceinline__ void st_pair(float2 *row, int x, float2 a, float2 b, bool wa, bool wb) {
+  if (wa && wb && !(x & 1)) {
+    *reinterpret_cast<float4 *>(row + x) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    if (wa) row[x] = a;
+    if (wb) row[x + 1] = b;
+  }
+}
 template <int CH>
 __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
@@ -835,8 +924,13 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   const float sc = (float)((CH == CH_DPH ? 1.0 : -1.0) * P.T * (*o.lam));
   // pp output: the vertex output itself, or PN under the reversal reduction
   float2 *kN = (CH == CH_PP && S.pp_pn) ? P.PN : static_cast<float2 *>(o.dgam);
-  const int rr = ti.r0 + 16 * quarter + row16;
+  const int rq = ti.r0 + 16 * quarter;  // first row of this warp's quarter
+  const int rr = rq + row16;
   float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
+  // pp partner rows (crossing reduction): row s - a of the same transfer
+  const bool mir = ti.m_hi > ti.m_lo;
+  float2 *prow = nullptr;
+  if (CH == CH_PP && mir && rr < ti.g.D && rr <= ti.m_row) prow = out_row<CH>(P, kN, ti, ti.g.x - rr);
   const uint32_t tl = S.tmem + ((uint32_t)(quarter * 32) << 16);
   float *mine = plane + comp * EPI_PLANE + row16 * EPI_PITCH;
   const int q = lane & 7;
@@ -868,6 +962,8 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
     __syncwarp();
     const int cl = cb + 2 * q;  // column (pair) within the tile
     const int cg = ti.c0 + cl;
+    const bool in0 = cl < ti.NT && cg >= ti.own_lo && cg < ti.own_hi;
+    const bool in1 = cl + 1 < ti.NT && cg + 1 >= ti.own_lo && cg + 1 < ti.own_hi;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int rho = (lane >> 3) + 4 * i;  // staged row 0..15
@@ -875,7 +971,39 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
           __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(orow), rho));
       const float2 re = *reinterpret_cast<const float2 *>(plane + rho * EPI_PITCH + 2 * q);
       const float2 im = *reinterpret_cast<const float2 *>(plane + EPI_PLANE + rho * EPI_PITCH + 2 * q);
-      if (dst && cg < ti.N && cl < ti.NT) *reinterpret_cast<float4 *>(dst + cg) = make_float4(re.x, im.x, re.y, im.y);
+      const float2 a = make_float2(re.x, im.x), b = make_float2(re.y, im.y);
+      if (dst) st_pair(dst, cg, a, b, in0, in1);
+      if (CH == CH_PP && mir) {
+        // partner (s - a, s - c): columns s - cg - 1, s - cg hold b, a
+        float2 *pd = reinterpret_cast<float2 *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(prow), rho));
+        const bool m0 = cl < ti.NT && cg >= ti.m_lo && cg < ti.m_hi;
+        const bool m1 = cl + 1 < ti.NT && cg + 1 >= ti.m_lo && cg + 1 < ti.m_hi;
+        if (pd) st_pair(pd, ti.g.x - cg - 1, b, a, m1, m0);
+      }
+    }
+    if (CH != CH_PP && mir) {
+      // partners of this chunk's entries (rows rq + rho, columns c0 + cb + cc):
+      // row D - 1 - (column - coff), columns P0 - row; lane (cc, q) takes the
+      // rows 2q, 2q + 1 of column cc, whose partners are adjacent columns
+      const int D = ti.g.D;
+      const int coff = CH == CH_DPH ? 0 : ti.N - D, P0 = CH == CH_DPH ? D - 1 : ti.N - 1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int cc = (lane >> 3) + 4 * i;
+        const int c = ti.c0 + cb + cc;
+        const int r0e = rq + 2 * q;  // own rows r0e, r0e + 1
+        const bool colok = cb + cc < ti.NT && c >= ti.m_lo && c < ti.m_hi;
+        const bool w0 = colok && r0e < D && r0e <= ti.m_row, w1 = colok && r0e + 1 < D && r0e + 1 <= ti.m_row;
+        if (w0 || w1) {
+          const float re0 = plane[(2 * q) * EPI_PITCH + cc], im0 = plane[EPI_PLANE + (2 * q) * EPI_PITCH + cc];
+          const float re1 = plane[(2 * q + 1) * EPI_PITCH + cc],
+                      im1 = plane[EPI_PLANE + (2 * q + 1) * EPI_PITCH + cc];
+          float2 *pd = out_row<CH>(P, kN, ti, D - 1 - (c - coff));
+          // row r0e -> column P0 - r0e, row r0e + 1 -> the column before it
+          st_pair(pd, P0 - r0e - 1, make_float2(re1, -im1), make_float2(re0, -im0), w1, w0);
+        }
+      }
     }
   }
   ++(ts.b ? tb.e1 : tb.e0);
@@ -1022,13 +1150,14 @@ struct TcPlan {
   unsigned *d_err = nullptr;  // owned by the context
   // one launch for all enabled channels; schedule [0] covers every point,
   // [1 + i] point i alone; sched: every transfer, sched_half: the reversal
-  // reduction's transfers m <= N - 1 (either may be absent)
+  // reduction's transfers m <= N - 1, sched_cross: those with the crossing
+  // reduction (each may be absent)
   struct Sched {
     tc::st::StWork *d_work = nullptr;
     int *d_start = nullptr;
     int grid = 0;
   };
-  std::vector<Sched> sched, sched_half;
+  std::vector<Sched> sched, sched_half, sched_cross;
   int mask = 7;
   TcTune tune;
 };
@@ -1037,10 +1166,14 @@ struct TcPlan {
 // most `sms` persistent CTAs: tiles sorted by cost (k-steps plus an epilogue
 // allowance), each given to the CTA with the least work so far; stored CTA by
 // CTA with start offsets.
+// cross (with half): the transfers with two row tiles of points whose one
+// column tile spans all N columns take the crossing-reduced tiles (cross_tile);
+// a tile's cost then scales with its width (the left operand's share and the
+// products' floor keep half of it).
 static bool build_sched(TcPlan *p, const std::vector<PointDesc> &pts, const std::vector<int> &nt, int first,
-                        int last, TcPlan::Sched &out, bool half) {
+                        int last, TcPlan::Sched &out, bool half, bool cross) {
   const int EPI_COST = p->tune.epi_cost;  // epilogue of one tile, in k-step units
-  std::vector<std::pair<int, tc::st::StWork>> tiles;
+  std::vector<std::pair<int, tc::st::StWork>> tiles;  // cost in 1/256 k-step
   for (int i = first; i < last; ++i) {
     const int N = pts[i].N;
     for (int ch = 0; ch < 3; ++ch) {
@@ -1048,9 +1181,18 @@ static bool build_sched(TcPlan *p, const std::vector<PointDesc> &pts, const std:
       for (int m = 0; m < (half ? N : 2 * N - 1); ++m) {
         const Geom g = geom(ch, N, m);
         const int nk = (ch == CH_DPH ? 2 : 1) * ((g.D + tc::KSTEP - 1) / tc::KSTEP);
+        const bool cx = half && cross && nt[i] >= N && g.D > tc::MROWS;
         for (int rt = 0; rt * tc::MROWS < g.D; ++rt)
-          for (int ct = 0; ct * nt[i] < N; ++ct)
-            tiles.push_back({nk + EPI_COST, tc::st::StWork{i, (short)m, (short)ch, (short)rt, (short)ct}});
+          for (int ct = 0; ct * nt[i] < N; ++ct) {
+            int w = 256;
+            if (cx) {
+              const tc::CrossTile x = tc::cross_tile(ch, N, nt[i], m, rt);
+              if (x.nt == 0) continue;
+              w = 128 + 128 * x.nt / nt[i];
+            }
+            tiles.push_back({(nk + EPI_COST) * w,
+                             tc::st::StWork{i, (short)m, (short)ch, (short)rt, (short)ct, (short)(cx ? 1 : 0), 0}});
+          }
       }
     }
   }
@@ -1186,12 +1328,12 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
   bool ok = cudaMalloc(&p->d_nt, sizeof(int) * p->n) == cudaSuccess &&
             cudaMemcpy(p->d_nt, nt.data(), sizeof(int) * p->n, cudaMemcpyHostToDevice) == cudaSuccess;
   p->mask = (params.empty() ? FRG_CH_ALL : params[0].channel_mask) & 7;
-  for (int h = 0; h < 2 && ok; ++h) {
-    if (!(schedules & (h ? TC_HALF : TC_FULL))) continue;
-    std::vector<TcPlan::Sched> &v = h ? p->sched_half : p->sched;
+  for (int h = 0; h < 3 && ok; ++h) {
+    if (!(schedules & (h == 0 ? TC_FULL : h == 1 ? TC_HALF : TC_CROSS))) continue;
+    std::vector<TcPlan::Sched> &v = h == 0 ? p->sched : h == 1 ? p->sched_half : p->sched_cross;
     v.resize(1 + p->n);
-    ok = build_sched(p, pts, nt, 0, p->n, v[0], h != 0);
-    for (int i = 0; i < p->n && ok; ++i) ok = build_sched(p, pts, nt, i, i + 1, v[1 + i], h != 0);
+    ok = build_sched(p, pts, nt, 0, p->n, v[0], h != 0, h == 2);
+    for (int i = 0; i < p->n && ok; ++i) ok = build_sched(p, pts, nt, i, i + 1, v[1 + i], h != 0, h == 2);
   }
   if (ok) {
     std::string mw;
@@ -1222,7 +1364,7 @@ void tc_plan_destroy(TcPlan *p) {
   if (!p) return;
   cudaFree(p->d_maps);
   cudaFree(p->d_nt);
-  for (auto *v : {&p->sched, &p->sched_half})
+  for (auto *v : {&p->sched, &p->sched_half, &p->sched_cross})
     for (auto &sc : *v) {
       cudaFree(sc.d_work);
       cudaFree(sc.d_start);
@@ -1232,7 +1374,7 @@ void tc_plan_destroy(TcPlan *p) {
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
-           int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err) {
+           int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err, bool cross) {
   // layouts of the stage input: W for the crossed channel, X and Z for the
   // direct one
   if ((chmask & 6) && !layouts_ready) {
@@ -1241,7 +1383,7 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   }
   if (ev_gather && cudaEventRecord(ev_gather, st) != cudaSuccess) return -3;
   if (wait_before && cudaStreamWaitEvent(st, wait_before, 0) != cudaSuccess) return -3;
-  const std::vector<TcPlan::Sched> &scv = half ? p->sched_half : p->sched;
+  const std::vector<TcPlan::Sched> &scv = half ? (cross ? p->sched_cross : p->sched_half) : p->sched;
   if ((chmask & 7) != p->mask || point >= p->n || scv.empty()) return -1;
   const TcPlan::Sched &sc = scv[point < 0 ? 0 : 1 + point];
   if (sc.grid) {

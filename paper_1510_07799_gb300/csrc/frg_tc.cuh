@@ -18,8 +18,9 @@ struct TcTune {
   int epi_cost = 3;
 };
 // Tile schedules a plan holds: every transfer of each channel, and/or (the
-// frequency-reversal reduction) the transfers m <= N - 1 only.
-constexpr int TC_FULL = 1, TC_HALF = 2;
+// frequency-reversal reduction) the transfers m <= N - 1 only, and/or those
+// with the crossing reduction of their products (FRG_CROSSING).
+constexpr int TC_FULL = 1, TC_HALF = 2, TC_CROSS = 4;
 // d_err: device word that a kernel whose bounded wait ran out sets non-zero.
 int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::vector<frg_params> &params,
                    int precision, const PointDesc *d_pts, unsigned *d_err, std::string &why,
@@ -35,7 +36,8 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // products (with half: the reversal reduction's schedule, transfers m <= N - 1,
 // the combine taking the others from the mirrored entries), and the combine
 // into the natural layout (with err also the step's error estimate: the
-// seventh rhs of a flow step).  ev_gather / ev_contract
+// seventh rhs of a flow step; with half and cross the crossing-reduced
+// tiles).  ev_gather / ev_contract
 // (optional) are recorded after the relayout and after the products; the
 // products wait for wait_before (optional: the bubble weights computed on
 // another stream), the combine for wait_combine (optional: the tail constants
@@ -43,5 +45,5 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
            cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_combine = nullptr,
-           bool layouts_ready = false, bool half = false, bool err = false);
+           bool layouts_ready = false, bool half = false, bool err = false, bool cross = false);
 }  // namespace frg

@@ -20,6 +20,7 @@ CH_PP, CH_DPH, CH_XPH, CH_SIGMA, CH_ALL = 0x1, 0x2, 0x4, 0x8, 0xF
 TAILS, TAIL_FACTOR = 0x10, 16  # frequency-box tails option of channel_mask (FRG_TAILS)
 REVERSAL = 0x20  # frequency-reversal reduction asserted for every input (FRG_REVERSAL)
 NO_REVERSAL = 0x40  # no reversal reduction in flows (FRG_NO_REVERSAL; default: while the states are symmetric)
+CROSSING = 0x80  # crossing symmetry asserted for every input: crossing-reduced products (FRG_CROSSING)
 CUTOFF_OMEGA, CUTOFF_INTERACTION = 0, 1  # frg_params.cutoff
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOTCONV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6

@@ -5,7 +5,9 @@ Runs `repeats` rhs evaluations (default 2) of a seeded vertex at N (default
 128, the U=3, T=0.005 workload parameters) and prints the phase timings of the
 last one; with a fourth argument `steps` > 0 it then advances a flow of the
 same workload by that many Dormand-Prince step attempts (one captured graph
-per step), so that a launch list shows the kernels of the flow step.
+per step), so that a launch list shows the kernels of the flow step.  The
+context asserts the crossing symmetry (FRG_CROSSING), as the benchmark's flows
+from the bare vertex do.
 With N = batch64 it advances the 64-point batch context by `steps` attempts
 (no single-point evaluations) and prints the time of the last 10.
 """
@@ -18,7 +20,7 @@ from . import build, frg, inputs
 
 def batch(prec, steps):
     build.build()
-    ctx = frg.Context(inputs.batch_points(), precision=prec)
+    ctx = frg.Context(inputs.batch_points(), precision=prec, channel_mask=frg.CH_ALL | frg.CROSSING)
     ctx.advance(max(steps - 10, 0))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -40,7 +42,8 @@ def main():
     steps = int(sys.argv[4]) if len(sys.argv) > 4 else 0
     build.build()
     w = inputs.Workload("profile", N=N, U=3.0, T=0.005, eps_d=-1.5)
-    ctx = frg.Context([w], precision=prec)
+    # the benchmark's flows from the bare vertex assert the crossing symmetry
+    ctx = frg.Context([w], precision=prec, channel_mask=frg.CH_ALL | frg.CROSSING)
     V = torch.from_numpy(inputs.random_vertex(N, w.U, 1)).cuda()
     s = torch.from_numpy(inputs.random_sigma(N, 2)).cuda()
     dg = torch.empty_like(V)

@@ -57,7 +57,7 @@ def _params(**kw):
 @pytest.mark.parametrize("bad", [dict(N_f=15), dict(N_f=0), dict(N_f=258), dict(T=0.0),
                                  dict(T=-1.0), dict(Delta=0.0), dict(rtol=0.0),
                                  dict(Lambda_f=2e3), dict(Lambda_f=0.0), dict(h0=0.5),
-                                 dict(precision=7), dict(channel_mask=0x80), dict(channel_mask=0xF | 0x20 | 0x40),
+                                 dict(precision=7), dict(channel_mask=0x100), dict(channel_mask=0xF | 0x20 | 0x40),
                                  dict(channel_mask=-1), dict(cutoff=2),
                                  dict(U=float("nan"))])
 def test_init_rejects_invalid_parameters_without_device(lib, bad):

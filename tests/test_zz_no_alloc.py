@@ -92,7 +92,7 @@ def test_noalloc_matches_oracle_at_its_largest_grid():
 
 def test_noalloc_rejects_sizes_beyond_its_array():
     for N, mask in ((frg.NOALLOC_MAX_N + 2, frg.CH_ALL), (7, frg.CH_ALL), (16, frg.CH_ALL | frg.TAILS),
-                    (16, frg.CH_ALL | frg.REVERSAL)):
+                    (16, frg.CH_ALL | frg.REVERSAL), (16, frg.CH_ALL | frg.CROSSING)):
         w, V, S = case(N, 7)
         dg, ds = torch.full_like(V, 1.0), torch.full_like(S, 1.0)
         with pytest.raises(frg.FrgError) as e:
