@@ -30,9 +30,9 @@ headline):
              1e12 down to the full model at 1)
 Options of the headline workload: --tails (frequency-box tails), --reversal
 (the frequency-reversal reduction asserted for every input, half storage),
---no-reversal (flows compute every transfer), --no-crossing (no crossing
-reduction of the channel products; by default the headline flows assert
-FRG_CROSSING, as every flow from the bare vertex may).  By default a split-precision
+--no-reversal (flows compute every transfer), --crossing (the crossing
+reduction of the channel products, FRG_CROSSING, which every flow from the
+bare vertex may assert).  By default a split-precision
 flow uses the reversal reduction automatically (every flow from the bare vertex
 is exactly reversal-symmetric); the line then also reports the same flows
 computing every transfer under "every_transfer".
@@ -486,7 +486,7 @@ def reset_flows(ctx, pts, torch):
         ctx.set_state(i, g, None, p.Lambda0)
 
 
-def measure_batch(prec, warmup, steps, fp64_baseline=True, crossing=True):
+def measure_batch(prec, warmup, steps, fp64_baseline=True, crossing=False):
     """64 points, uneven N_f, one context: full flows per second (from the bare
     vertex, so the split precisions may assert the crossing reduction)."""
     import torch
@@ -696,10 +696,9 @@ def main():
                     help="headline workload with the frequency-box tail option (channel_mask | FRG_TAILS)")
     ap.add_argument("--no-reversal", action="store_true",
                     help="flows compute every transfer (channel_mask | FRG_NO_REVERSAL)")
-    ap.add_argument("--no-crossing", dest="crossing", action="store_false",
-                    help="headline workload without the crossing reduction of the products (by default the "
-                         "split-precision flows assert it, channel_mask | FRG_CROSSING: they start from the "
-                         "crossing-symmetric bare vertex)")
+    ap.add_argument("--crossing", action="store_true",
+                    help="headline workload with the crossing reduction of the products (channel_mask | "
+                         "FRG_CROSSING; the flows start from the crossing-symmetric bare vertex)")
     ap.add_argument("--reversal", action="store_true",
                     help="headline workload with the frequency-reversal reduction (channel_mask | FRG_REVERSAL): "
                          "the contraction computes half of the transfers of each channel")

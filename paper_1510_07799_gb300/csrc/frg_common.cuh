@@ -209,6 +209,31 @@ __device__ __forceinline__ void propagator_at(const PointDesc &P, int i, double 
   s = cscale(cmul(cmul(g, g), gi), -dthinv);
 }
 
+// Launch of a kernel with a shared-memory carveout preference for this launch
+// (carveout in percent of the unified L1/shared storage, or -1: the default).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_with_carveout(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                        cudaStream_t st, int carveout, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+  a[0].val.sharedMemCarveout = carveout < 0 ? 0u : (unsigned)carveout;
+  cfg.attrs = a;
+  cfg.numAttrs = carveout < 0 ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+// Carveout of the split paths' stage and combine kernels, which alternate with
+// the contraction (nearly all of an SM's shared memory): the largest shared
+// memory share spares the SM a reconfiguration between them (measured: a single
+// N = 128 point's flow step -1.3 %), but leaves an L1 too small for the
+// per-point descriptors that the blocks of a large batch read (64 points: +4.5
+// %), so contexts of more than a few points keep the default.
+inline int step_carveout(int n_points) { return n_points <= 4 ? (int)cudaSharedmemCarveoutMaxShared : -1; }
+
 // Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).
 struct StageArgs {
   int stage;  // 0..6

@@ -563,15 +563,10 @@ int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// Dynamic shared memory of the split stage kernels, and the largest shared
-// memory carveout: the flow alternates them with the contraction, which needs
-// nearly all of an SM's shared memory, so that an SM need not be reconfigured
-// between the two.
+// Dynamic shared memory of the split stage kernels.
 template <typename K>
 static bool stage_attrs(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess &&
-         cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
 }
 
 int stage_split_init() {
@@ -585,15 +580,19 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
                  cudaStream_t st, int lb_grid, int n_points, int want) {
   if (split) {
     const dim3 g(lb_grid, n_points);
+    const int cv = step_carveout(n_points);
+    const Ctl *c = d_ctl;
+    cudaError_t e;
     switch (s) {
-      case 0: k_stage_split<0><<<g, stage_threads<0>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
-      case 1: k_stage_split<1><<<g, stage_threads<1>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
-      case 2: k_stage_split<2><<<g, stage_threads<2>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
-      case 3: k_stage_split<3><<<g, stage_threads<3>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
-      case 4: k_stage_split<4><<<g, stage_threads<4>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
-      case 5: k_stage_split<5><<<g, stage_threads<5>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
-      default: k_stage_split<6><<<g, stage_threads<6>(), LB_SMEM, st>>>(d_pts, d_ctl, want); break;
+      case 0: e = launch_with_carveout(k_stage_split<0>, g, stage_threads<0>(), LB_SMEM, st, cv, d_pts, c, want); break;
+      case 1: e = launch_with_carveout(k_stage_split<1>, g, stage_threads<1>(), LB_SMEM, st, cv, d_pts, c, want); break;
+      case 2: e = launch_with_carveout(k_stage_split<2>, g, stage_threads<2>(), LB_SMEM, st, cv, d_pts, c, want); break;
+      case 3: e = launch_with_carveout(k_stage_split<3>, g, stage_threads<3>(), LB_SMEM, st, cv, d_pts, c, want); break;
+      case 4: e = launch_with_carveout(k_stage_split<4>, g, stage_threads<4>(), LB_SMEM, st, cv, d_pts, c, want); break;
+      case 5: e = launch_with_carveout(k_stage_split<5>, g, stage_threads<5>(), LB_SMEM, st, cv, d_pts, c, want); break;
+      default: e = launch_with_carveout(k_stage_split<6>, g, stage_threads<6>(), LB_SMEM, st, cv, d_pts, c, want); break;
     }
+    if (e != cudaSuccess) return -3;
   } else {
     k_stage<<<nblk, 256, 0, st>>>(d_pts, d_ctl, seg, s, d_io);
   }

@@ -363,21 +363,10 @@ __global__ void __launch_bounds__(comb_threads<REV, ERR>(), ERR ? 4 : REV ? LB_M
 }
 
 
-// The combine kernels alternate with the contraction in every rhs, which needs
-// nearly all of an SM's shared memory: they take the largest shared memory
-// carveout too, so that an SM need not be reconfigured between them.
-template <typename K>
-static bool max_carveout(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
-}
-
 int layout_init() {
-  const bool ok =
-      cudaFuncSetAttribute(k_relayout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess &&
-      max_carveout(k_relayout) && max_carveout(k_combine<false, false>) && max_carveout(k_combine<false, true>) &&
-      max_carveout(k_combine<true, false>) && max_carveout(k_combine<true, true>);
-  return ok ? 0 : -3;
+  return cudaFuncSetAttribute(k_relayout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess
+             ? 0
+             : -3;
 }
 
 int launch_relayout(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int want_w, int want_x,
@@ -399,16 +388,19 @@ int launch_combine(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int 
   const dim3 g(lblocks(maxN, canon_half ? maxN / 2 : maxN), n_points);
   const ErrWeights ew = host_error_weights();
   const bool rev = (mask & FRG_REVERSAL) != 0;
+  const int cv = step_carveout(n_points);
+  cudaError_t e;
   if (rev && err)
-    k_combine<true, true><<<g, comb_threads<true, true>(), 0, st>>>(d_pts, d_io, mask, ew);
+    e = launch_with_carveout(k_combine<true, true>, g, comb_threads<true, true>(), 0, st, cv, d_pts, d_io, mask, ew);
   else if (rev)
-    k_combine<true, false><<<g, comb_threads<true, false>(), 0, st>>>(d_pts, d_io, mask, ew);
+    e = launch_with_carveout(k_combine<true, false>, g, comb_threads<true, false>(), 0, st, cv, d_pts, d_io, mask, ew);
   else if (err)
-    k_combine<false, true><<<g, comb_threads<false, true>(), 0, st>>>(d_pts, d_io, mask, ew);
+    e = launch_with_carveout(k_combine<false, true>, g, comb_threads<false, true>(), 0, st, cv, d_pts, d_io, mask, ew);
   else
-    k_combine<false, false><<<g, comb_threads<false, false>(), 0, st>>>(d_pts, d_io, mask, ew);
+    e = launch_with_carveout(k_combine<false, false>, g, comb_threads<false, false>(), 0, st, cv, d_pts, d_io, mask,
+                             ew);
   FRG_COUNT(1);
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 }  // namespace frg

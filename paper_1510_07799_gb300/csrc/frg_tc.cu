@@ -492,10 +492,13 @@ struct Pipe {
   int pp_pn;  // reversal reduction: the pp output goes to PN (the combine mirrors it)
 };
 
+// X: the kernel instance that runs crossing-reduced schedules (the other one
+// ignores the tile mark, so its tiles keep the plain geometry at no cost).
 template <int CH>
 __device__ __forceinline__ bool st_tile_info(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
-                                             const StWork &w, const int *__restrict__ nt_of, TileInfo &ti) {
-  return tile_info<CH>(pts, io, TcWork{w.point, w.m, w.rt, w.ct, w.cx}, nt_of, ti);
+                                             const StWork &w, const int *__restrict__ nt_of, TileInfo &ti,
+                                             bool X) {
+  return tile_info<CH>(pts, io, TcWork{w.point, w.m, w.rt, w.ct, X ? (int)w.cx : 0}, nt_of, ti);
 }
 
 // Loader (one warp, lane 0 issues): the raw rows of every k-step of a tile by
@@ -504,9 +507,9 @@ template <int CH>
 __device__ __forceinline__ bool load_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                           const RhsIO *__restrict__ io, const StWork &w,
                                           const int *__restrict__ nt_of, const CUtensorMap *__restrict__ maps,
-                                          uint32_t &it, int lane) {
+                                          uint32_t &it, int lane, bool X) {
   TileInfo ti;
-  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti, X)) return true;
   const uint4 ord = korder_row<CH>(pts[ti.point], ti.N, w.m);
   const CUtensorMap *mp = maps + (size_t)ti.point * M_COUNT;
   for (int ki = 0; ki < ti.nk; ++ki, ++it) {
@@ -736,10 +739,10 @@ __device__ __forceinline__ void xf_right(XfV<PREC> &o, const float2 *rB, const X
 template <int CH, int PREC>
 __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                         const RhsIO *__restrict__ io, const StWork &w,
-                                        const int *__restrict__ nt_of, uint32_t &it, int xt, int lane) {
+                                        const int *__restrict__ nt_of, uint32_t &it, int xt, int lane, bool X) {
   using L = OpL<PREC>;
   TileInfo ti;
-  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti, X)) return true;
   const PointDesc &P = pts[ti.point];
   const uint4 ord = korder_row<CH>(P, ti.N, w.m);
   typename XfV<PREC>::Scale scA{}, scB{};
@@ -825,10 +828,10 @@ __device__ __forceinline__ TSlot tslot_next(TBuf &t, int NT) {
 template <int CH, int PREC>
 __device__ __forceinline__ bool mma_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
-                                         const int *__restrict__ nt_of, uint32_t &it, TBuf &tb, int lane) {
+                                         const int *__restrict__ nt_of, uint32_t &it, TBuf &tb, int lane, bool X) {
   using L = OpL<PREC>;
   TileInfo ti;
-  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti, X)) return true;
   const TSlot ts = tslot_next(tb, ti.NT);
   uint32_t &e = ts.b ? tb.e1 : tb.e0;
   if (!wwait(&S.tempty[ts.b], (e & 1u) ^ 1u, S.err, S.abort_flag)) return false;
@@ -908,9 +911,9 @@ __device__ __forceinline__ void st_pair(float2 *row, int x, float2 a, float2 b, 
 template <int CH>
 __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restrict__ pts,
                                          const RhsIO *__restrict__ io, const StWork &w,
-                                         const int *__restrict__ nt_of, TBuf &tb, int warp, int lane) {
+                                         const int *__restrict__ nt_of, TBuf &tb, int warp, int lane, bool X) {
   TileInfo ti;
-  if (!st_tile_info<CH>(pts, io, w, nt_of, ti)) return true;
+  if (!st_tile_info<CH>(pts, io, w, nt_of, ti, X)) return true;
   const TSlot ts = tslot_next(tb, ti.NT);
   uint32_t &f = ts.b ? tb.f1 : tb.f0;
   if (!wwait(&S.tfull[ts.b], f & 1u, S.err, S.abort_flag)) return false;
@@ -928,7 +931,7 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   const int rr = rq + row16;
   float2 *orow = rr < ti.g.D ? out_row<CH>(P, kN, ti, rr) : nullptr;
   // pp partner rows (crossing reduction): row s - a of the same transfer
-  const bool mir = ti.m_hi > ti.m_lo;
+  const bool mir = X && ti.m_hi > ti.m_lo;
   float2 *prow = nullptr;
   if (CH == CH_PP && mir && rr < ti.g.D && rr <= ti.m_row) prow = out_row<CH>(P, kN, ti, ti.g.x - rr);
   const uint32_t tl = S.tmem + ((uint32_t)(quarter * 32) << 16);
@@ -972,7 +975,11 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
       const float2 re = *reinterpret_cast<const float2 *>(plane + rho * EPI_PITCH + 2 * q);
       const float2 im = *reinterpret_cast<const float2 *>(plane + EPI_PLANE + rho * EPI_PITCH + 2 * q);
       const float2 a = make_float2(re.x, im.x), b = make_float2(re.y, im.y);
-      if (dst) st_pair(dst, cg, a, b, in0, in1);
+      if (!X) {
+        if (dst && cg < ti.N && cl < ti.NT) *reinterpret_cast<float4 *>(dst + cg) = make_float4(a.x, a.y, b.x, b.y);
+      } else if (dst) {
+        st_pair(dst, cg, a, b, in0, in1);
+      }
       if (CH == CH_PP && mir) {
         // partner (s - a, s - c): columns s - cg - 1, s - cg hold b, a
         float2 *pd = reinterpret_cast<float2 *>(
@@ -1010,7 +1017,7 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   return true;
 }
 
-template <int PREC>
+template <int PREC, bool X>
 __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                          const StWork *__restrict__ work, const int *__restrict__ cta_start,
                                          const int *__restrict__ nt_of, unsigned *__restrict__ err,
@@ -1067,7 +1074,7 @@ __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, cons
     uint32_t it = 0;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH(load_tile, S, pts, io, w, nt_of, maps, it, lane)) break;
+      if (!FRG_BY_CH(load_tile, S, pts, io, w, nt_of, maps, it, lane, X)) break;
     }
     // copies still in flight must land before the CTA leaves
     for (uint32_t k = it > (uint32_t)NRAW ? it - NRAW : 0u; k < it; ++k)
@@ -1077,20 +1084,20 @@ __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, cons
     uint32_t it = 0;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH_P(xf_tile, S, pts, io, w, nt_of, it, xt, lane)) break;
+      if (!FRG_BY_CH_P(xf_tile, S, pts, io, w, nt_of, it, xt, lane, X)) break;
     }
   } else if (warp == MMA_W) {
     uint32_t it = 0;
     TBuf tb;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH_P(mma_tile, S, pts, io, w, nt_of, it, tb, lane)) break;
+      if (!FRG_BY_CH_P(mma_tile, S, pts, io, w, nt_of, it, tb, lane, X)) break;
     }
   } else {
     TBuf tb;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
-      if (!FRG_BY_CH(epi_tile, S, pts, io, w, nt_of, tb, warp, lane)) break;
+      if (!FRG_BY_CH(epi_tile, S, pts, io, w, nt_of, tb, warp, lane, X)) break;
     }
   }
 #undef FRG_BY_CH
@@ -1105,14 +1112,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const StWork *__restrict__ work,
                     const int *__restrict__ cta_start, const int *__restrict__ nt_of, unsigned *__restrict__ err,
                     const CUtensorMap *__restrict__ maps, int half) {
-  contract<FRG_3XTF32>(pts, io, work, cta_start, nt_of, err, maps, half);
+  contract<FRG_3XTF32, false>(pts, io, work, cta_start, nt_of, err, maps, half);
 }
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_bf16x3(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                       const StWork *__restrict__ work, const int *__restrict__ cta_start,
                       const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps,
                       int half) {
-  contract<FRG_BF16X3>(pts, io, work, cta_start, nt_of, err, maps, half);
+  contract<FRG_BF16X3, false>(pts, io, work, cta_start, nt_of, err, maps, half);
+}
+// The same for crossing-reduced schedules (cross_tile).
+__global__ void __launch_bounds__(THREADS, 1)
+    k_contract_tf32_x(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                      const StWork *__restrict__ work, const int *__restrict__ cta_start,
+                      const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps,
+                      int half) {
+  contract<FRG_3XTF32, true>(pts, io, work, cta_start, nt_of, err, maps, half);
+}
+__global__ void __launch_bounds__(THREADS, 1)
+    k_contract_bf16x3_x(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                        const StWork *__restrict__ work, const int *__restrict__ cta_start,
+                        const int *__restrict__ nt_of, unsigned *__restrict__ err,
+                        const CUtensorMap *__restrict__ maps, int half) {
+  contract<FRG_BF16X3, true>(pts, io, work, cta_start, nt_of, err, maps, half);
 }
 }  // namespace st
 
@@ -1347,8 +1369,12 @@ int tc_plan_create(TcPlan **out, const std::vector<PointDesc> &pts, const std::v
   if (precision == FRG_3XTF32) {
     ok = ok && cudaFuncSetAttribute(tc::st::k_contract_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     tc::st::OpL<FRG_3XTF32>::SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(tc::st::k_contract_tf32_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::st::OpL<FRG_3XTF32>::SMEM) == cudaSuccess;
   } else {
     ok = ok && cudaFuncSetAttribute(tc::st::k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::st::OpL<FRG_BF16X3>::SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(tc::st::k_contract_bf16x3_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     tc::st::OpL<FRG_BF16X3>::SMEM) == cudaSuccess;
   }
   if (!ok) {
@@ -1387,12 +1413,12 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   if ((chmask & 7) != p->mask || point >= p->n || scv.empty()) return -1;
   const TcPlan::Sched &sc = scv[point < 0 ? 0 : 1 + point];
   if (sc.grid) {
-    if (p->precision == FRG_3XTF32)
-      tc::st::k_contract_tf32<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_3XTF32>::SMEM, st>>>(
-          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps, half ? 1 : 0);
-    else
-      tc::st::k_contract_bf16x3<<<sc.grid, tc::st::THREADS, tc::st::OpL<FRG_BF16X3>::SMEM, st>>>(
-          d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps, half ? 1 : 0);
+    const bool x = half && cross;
+    auto kern = p->precision == FRG_3XTF32 ? (x ? tc::st::k_contract_tf32_x : tc::st::k_contract_tf32)
+                                           : (x ? tc::st::k_contract_bf16x3_x : tc::st::k_contract_bf16x3);
+    const int smem = p->precision == FRG_3XTF32 ? tc::st::OpL<FRG_3XTF32>::SMEM : tc::st::OpL<FRG_BF16X3>::SMEM;
+    kern<<<sc.grid, tc::st::THREADS, smem, st>>>(d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps,
+                                                 half ? 1 : 0);
     FRG_COUNT(1);
     if (cudaGetLastError() != cudaSuccess) return -3;
   }

@@ -1,13 +1,13 @@
 """Small, self-terminating workloads of the library for ncu captures.
 
-usage: python -m paper_1510_07799_gb300.profile_rhs [precision] [N] [repeats] [steps]
+usage: python -m paper_1510_07799_gb300.profile_rhs [precision] [N] [repeats] [steps] [crossing]
 Runs `repeats` rhs evaluations (default 2) of a seeded vertex at N (default
 128, the U=3, T=0.005 workload parameters) and prints the phase timings of the
 last one; with a fourth argument `steps` > 0 it then advances a flow of the
 same workload by that many Dormand-Prince step attempts (one captured graph
-per step), so that a launch list shows the kernels of the flow step.  The
-context asserts the crossing symmetry (FRG_CROSSING), as the benchmark's flows
-from the bare vertex do.
+per step), so that a launch list shows the kernels of the flow step.  A fifth
+argument `crossing` makes the context assert the crossing symmetry
+(FRG_CROSSING), as `bench.py --crossing` does.
 With N = batch64 it advances the 64-point batch context by `steps` attempts
 (no single-point evaluations) and prints the time of the last 10.
 """
@@ -20,7 +20,7 @@ from . import build, frg, inputs
 
 def batch(prec, steps):
     build.build()
-    ctx = frg.Context(inputs.batch_points(), precision=prec, channel_mask=frg.CH_ALL | frg.CROSSING)
+    ctx = frg.Context(inputs.batch_points(), precision=prec)
     ctx.advance(max(steps - 10, 0))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -40,10 +40,11 @@ def main():
     N = int(sys.argv[2]) if len(sys.argv) > 2 else 128
     reps = int(sys.argv[3]) if len(sys.argv) > 3 else 2
     steps = int(sys.argv[4]) if len(sys.argv) > 4 else 0
+    cross = len(sys.argv) > 5 and sys.argv[5] == "crossing"
     build.build()
     w = inputs.Workload("profile", N=N, U=3.0, T=0.005, eps_d=-1.5)
-    # the benchmark's flows from the bare vertex assert the crossing symmetry
-    ctx = frg.Context([w], precision=prec, channel_mask=frg.CH_ALL | frg.CROSSING)
+    mask = frg.CH_ALL | (frg.CROSSING if cross else 0)
+    ctx = frg.Context([w], precision=prec, channel_mask=mask)
     V = torch.from_numpy(inputs.random_vertex(N, w.U, 1)).cuda()
     s = torch.from_numpy(inputs.random_sigma(N, 2)).cuda()
     dg = torch.empty_like(V)
