@@ -78,6 +78,10 @@ struct frg_ctx {
   // while the stage input is formed or relaid (fork / join by events)
   cudaStream_t sstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tails = nullptr, ev_stage = nullptr, ev_sig = nullptr;
+  // split flows with the frequency-box tails: the tail constants on a third
+  // stream, from the self-energy stage input on (ev_sst)
+  cudaStream_t tstream = nullptr;
+  cudaEvent_t ev_sst = nullptr;
   // pipelined host-buffer evaluations: copy-in and copy-out streams, two device
   // slots per point, per-slot events (input copied, compute done, output read)
   cudaStream_t cin = nullptr, cout = nullptr;
@@ -333,29 +337,37 @@ static int stage_grid(const frg_ctx *ctx) { return ctx->rev_on ? ctx->lb_grid_ha
 
 // One rhs evaluation of a split-precision flow at stage s (the vertex part of
 // the stage input is formed by this function's stage kernel).  Side stream:
-// the self-energy part of the stage input, the propagators, the bubble-weight
-// tables (and the tail constants), beside the stage kernel's vertex part on
-// the main stream; then the self-energy rhs, which reads the vertex stage
-// input, beside the contraction.  The scatter-add waits for both (it adds the
+// the self-energy part of the stage input, the propagators and the
+// bubble-weight tables, beside the stage kernel's vertex part on the main
+// stream; then the self-energy rhs, which reads the vertex stage input,
+// beside the contraction.  The frequency-box tail constants (a window of
+// propagators of their own) run on a third stream from the self-energy stage
+// input on.  The scatter-add waits for all of them (it adds the tails and the
 // self-energy tail and, for k7, takes the self-energy error), and so does
 // everything after it: the next stage kernel overwrites the vertex input that
 // the self-energy rhs reads.
 static int run_split_stage(frg_ctx *ctx, int s, bool err) {
-  cudaStream_t st = ctx->stream, ss = ctx->sstream;
+  cudaStream_t st = ctx->stream, ss = ctx->sstream, ts = ctx->tstream;
   RhsIO *io = ctx->d_io_stage;
   const bool tails = (ctx->mask & FRG_TAILS) != 0;
   const int chmask = ctx->mask & 7;
   CK(cudaEventRecord(ctx->ev_fork, st), "fork");
   CK(cudaStreamWaitEvent(ss, ctx->ev_fork, 0), "fork");
   LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, io, s, ctx->n, ss), "self-energy stage");
+  if (tails) {
+    CK(cudaEventRecord(ctx->ev_sst, ss), "self-energy stage");
+    CK(cudaStreamWaitEvent(ts, ctx->ev_sst, 0), "self-energy stage");
+    LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ts), "tail sums");
+    CK(cudaEventRecord(ctx->ev_tails, ts), "tails");
+  }
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_TABLES), "bubble weights");
   CK(cudaEventRecord(ctx->ev_join, ss), "join");
-  if (tails) LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ss), "tail sums");
   LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, stage_grid(ctx), ctx->n, ctx->lb_want),
      "stage sum");
   CK(cudaEventRecord(ctx->ev_stage, st), "stage");
   CK(cudaStreamWaitEvent(ss, ctx->ev_stage, 0), "stage");
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_SIGMA), "self-energy rhs");
+  if (tails) CK(cudaStreamWaitEvent(ss, ctx->ev_tails, 0), "tails");
   CK(cudaEventRecord(ctx->ev_sig, ss), "self-energy");
   if (chmask) {
     LK(tc_run(ctx->tc, ctx->d_pts, io, -1, chmask, st, nullptr, nullptr, ctx->n, ctx->maxN, ctx->ev_join, tails,
@@ -486,6 +498,8 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaStreamCreateWithFlags(&ctx->fstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->tstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_sst, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_tails, cudaEventDisableTiming) != cudaSuccess ||
@@ -567,9 +581,11 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       if (!(P.kS[j] = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
     if (p.channel_mask & FRG_TAILS) {
       const size_t W = (size_t)FRG_TAIL_FACTOR * N;
+      const size_t nt = 2 * (2 * (size_t)N - 1) + 1;
       if (!(P.Gw = dalloc<double2>(ctx, W)) || !(P.Sw = dalloc<double2>(ctx, W)) ||
-          !(P.tail = dalloc<double2>(ctx, 2 * (2 * (size_t)N - 1) + 1)))
+          !(P.tail = dalloc<double2>(ctx, nt)) || !(P.tailB = dalloc<double2>(ctx, 2 * (size_t)N - 1)))
         return bail(FRG_ENOMEM);
+      if (ctx->split && !(P.tail32 = dalloc<float2>(ctx, nt))) return bail(FRG_ENOMEM);
     }
     if (!(P.G = dalloc<double2>(ctx, N)) || !(P.S = dalloc<double2>(ctx, N)) ||
         !(P.Lpp = dalloc<double2>(ctx, (size_t)(2 * N - 1) * N)) ||
@@ -686,6 +702,11 @@ void frg_destroy(frg_ctx *ctx) {
     cudaStreamSynchronize(ctx->sstream);
     cudaStreamDestroy(ctx->sstream);
   }
+  if (ctx->tstream) {
+    cudaStreamSynchronize(ctx->tstream);
+    cudaStreamDestroy(ctx->tstream);
+  }
+  if (ctx->ev_sst) cudaEventDestroy(ctx->ev_sst);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->cin) {
     cudaStreamSynchronize(ctx->cin);

@@ -61,8 +61,10 @@ struct PointDesc {
   // frequency-box tails (null when off): propagators on the window of
   // FRG_TAIL_FACTOR * N indices starting at -(W - N)/2 (Sigma = 0 outside the
   // box), and per rhs the additive constants: pp transfer s at [s], xph
-  // transfer Q at [2N-1 + Q+N-1], the self-energy at [4N-2]
-  double2 *Gw, *Sw, *tail;
+  // transfer Q at [2N-1 + Q+N-1], the self-energy at [4N-2]; tailB: the xph
+  // half sums (below); tail32 (split paths): the constants rounded to FP32
+  double2 *Gw, *Sw, *tail, *tailB;
+  float2 *tail32;
 };
 
 // Device-side step controller state, one per point.

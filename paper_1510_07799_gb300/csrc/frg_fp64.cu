@@ -334,6 +334,11 @@ __global__ void k_tail_gs(const PointDesc *__restrict__ pts, const RhsIO *__rest
 
 // blocks [0, 2 maxN - 1): pp transfers; the next 2 maxN - 1: xph transfers;
 // the last one: the self-energy constant.  128 threads, fixed-order reduction.
+// The two halves of a bubble weight give equal sums: for pp the window set of
+// transfer s is symmetric under p <-> s - p, so sum Lb(p, s-p) = 2 sum S(p)
+// G(s-p); for xph the second half at Q is the first half at -Q,
+// sum_p G(p) S(p+Q) = sum_p' S(p') G(p'-Q), so the blocks form
+// B(Q) = sum S(p) G(p+Q) (in tailB) and k_tail_finish adds B(Q) + B(-Q).
 __global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                                    int maxN, int mask) {
   const int pi = blockIdx.y;
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__
     const int q = which == 0 ? row - p : p + (row - (N - 1));
     const int y = q - lo;
     if ((unsigned)y >= (unsigned)W || (inbox(N, p) && inbox(N, q))) continue;
-    acc = cadd(acc, cadd(cmul(P.Sw[x], P.Gw[y]), cmul(P.Gw[x], P.Sw[y])));
+    cfma(acc, P.Sw[x], P.Gw[y]);
   }
   for (int off = 16; off > 0; off >>= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -370,9 +375,29 @@ __global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__
     double2 t = part[0];
     for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
     const double L = *o.lam;
-    if (which == 0) P.tail[row] = (mask & 1) ? cscale(t, -L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
-    else if (which == 1) P.tail[nrow + row] = (mask & 4) ? cscale(t, -L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
+    if (which == 0) P.tail[row] = (mask & 1) ? cscale(t, -2.0 * L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
+    else if (which == 1) P.tailB[row] = t;
     else P.tail[2 * nrow] = (mask & 8) ? cscale(t, L * P.T * P.U) : make_double2(0.0, 0.0);
+  }
+}
+
+// xph constants from the half sums, B(Q) + B(-Q), and the FP32 copies of all
+// constants (split paths); one block per point.
+__global__ void k_tail_finish(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask) {
+  const int pi = blockIdx.x;
+  const RhsIO &o = io[pi];
+  if (!o.active) return;
+  const PointDesc &P = pts[pi];
+  if (!P.tail) return;
+  const int N = P.N, nrow = 2 * N - 1;
+  const double f = -(*o.lam) * P.T * P.U * P.U;
+  for (int r = threadIdx.x; r < nrow; r += blockDim.x)
+    P.tail[nrow + r] = (mask & 4) ? cscale(cadd(P.tailB[r], P.tailB[nrow - 1 - r]), f) : make_double2(0.0, 0.0);
+  if (!P.tail32) return;
+  __syncthreads();
+  for (int j = threadIdx.x; j < 2 * nrow + 1; j += blockDim.x) {
+    const double2 t = P.tail[j];
+    P.tail32[j] = make_float2((float)t.x, (float)t.y);
   }
 }
 
@@ -438,6 +463,8 @@ int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, in
   k_tail_gs<<<dim3((W + 127) / 128, n_points), 128, 0, st>>>(d_pts, d_io);
   FRG_COUNT(1);
   k_tail_sums<<<dim3(2 * (2 * maxN - 1) + 1, n_points), 128, 0, st>>>(d_pts, d_io, maxN, mask);
+  FRG_COUNT(1);
+  k_tail_finish<<<n_points, 256, 0, st>>>(d_pts, d_io, mask);
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -82,11 +82,9 @@ __global__ void k_fill_z(const PointDesc *__restrict__ pts) {
   }
 }
 
-// FP32 copy of the FP64 frequency-box tail constant j of a point.
-__device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) {
-  const double2 t = P.tail[j];
-  return make_float2((float)t.x, (float)t.y);
-}
+// FP32 copy of the FP64 frequency-box tail constant j of a point (rounded once
+// per rhs by the tail kernels).
+__device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) { return P.tail32[j]; }
 
 // Block-wide fold of the error estimate of one layout block into the point's
 // controller state (seventh rhs of a flow step): the vertex part's maxima from
