@@ -401,6 +401,10 @@ def run_ours(args):
     e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
            "what": "frg_rhs_host_async with pinned host buffers (%d calls in flight, then frg_sync), copies "
                    "inside the timed region" % reps}
+    e2e["link"] = host_link(torch, nb)
+    bound = min(e2e["link"]["h2d_concurrent_gbs"], e2e["link"]["d2h_concurrent_gbs"]) * 1e9 / nb
+    e2e["link"]["bound_rhs_per_s"] = bound
+    e2e["link"]["frac"] = e2e["value"] / world / bound
 
     # the plain FP64 GPU path on the same state (the metric's comparison arm)
     fp64_gpu = None
@@ -484,6 +488,42 @@ def reset_flows(ctx, pts, torch):
     for i, p in enumerate(pts):
         g = torch.full((p.N,) * 3, p.U, dtype=torch.complex128, device="cuda")
         ctx.set_state(i, g, None, p.Lambda0)
+
+
+def host_link(torch, nbytes, reps=6):
+    """Copy-engine bandwidth of the host link for one call's bytes (pinned host
+    buffers, CUDA events): each direction alone, and both at once on two
+    streams, as the pipelined host-buffer calls overlap them."""
+    hin = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    din = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dout = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn, stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            fn()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        return e0, e1
+
+    def gbs(ev):
+        return reps * nbytes / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e9
+
+    h2d = timed(lambda: din.copy_(hin, non_blocking=True), s1)
+    torch.cuda.synchronize()
+    d2h = timed(lambda: hout.copy_(dout, non_blocking=True), s2)
+    torch.cuda.synchronize()
+    out = {"h2d_gbs": gbs(h2d), "d2h_gbs": gbs(d2h)}
+    a = timed(lambda: din.copy_(hin, non_blocking=True), s1)
+    b = timed(lambda: hout.copy_(dout, non_blocking=True), s2)
+    torch.cuda.synchronize()
+    out.update({"h2d_concurrent_gbs": gbs(a), "d2h_concurrent_gbs": gbs(b), "bytes": nbytes,
+                "what": "pinned copies of one call's bytes, each direction alone and both at once on two streams"})
+    return out
 
 
 def measure_batch(prec, warmup, steps, fp64_baseline=True, crossing=False):
