@@ -323,6 +323,19 @@ int frg_rhs_timed(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
                   const void *d_sigma, void *d_dgamma, void *d_dsigma, float *ms);
 long frg_kernel_launches(void);
 /*
+ * Tile geometry of the crossing reduction (diagnostic; FRG_CROSSING, paper
+ * Sec. 4 symmetry reduction): for channel ch (0 pp, 1 direct, 2 crossed
+ * particle-hole) at a transfer m <= N - 1 with more than 64 valid rows, on a
+ * grid of N frequencies with tiles of nt columns (N <= nt <= 128, nt a multiple
+ * of 16), row tile rt (0 or 1) computes the columns [out[0], out[0] + out[1])
+ * (out[1] = 0: the tile is dropped), writes its own entries of the columns
+ * [out[2], out[3]), and writes the crossing partners of its entries whose
+ * column lies in [out[4], out[5]) and whose row (counted from the transfer's
+ * first valid row) is at most out[6].  No device work.  Returns FRG_OK, or
+ * FRG_EINVAL (arguments outside those ranges, out NULL).
+ */
+int frg_cross_tile(int ch, int N, int nt, int m, int rt, int out[7]);
+/*
  * Failure-path self-test (no counterpart in the paper).  Every wait of the
  * tensor-core pipeline is bounded: a wait that runs out records the failure in
  * the context's device error word and the kernel returns, so the host sees

@@ -1398,6 +1398,20 @@ void tc_plan_destroy(TcPlan *p) {
   delete p;
 }
 
+}  // namespace frg
+
+extern "C" int frg_cross_tile(int ch, int N, int nt, int m, int rt, int out[7]) {
+  if (!out || ch < 0 || ch > 2 || rt < 0 || rt > 1 || nt < 16 || nt > frg::tc::NT_MAX || nt % 16 || N < 2 ||
+      (N & 1) || N > nt || m + 1 <= frg::tc::MROWS || m > N - 1)
+    return FRG_EINVAL;
+  const frg::tc::CrossTile x = frg::tc::cross_tile(ch, N, nt, m, rt);
+  const int v[7] = {x.c0, x.nt, x.own_lo, x.own_hi, x.m_lo, x.m_hi, x.m_row};
+  for (int j = 0; j < 7; ++j) out[j] = v[j];
+  return FRG_OK;
+}
+
+namespace frg {
+
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
            int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err, bool cross) {

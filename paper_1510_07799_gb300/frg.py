@@ -29,7 +29,8 @@ ERRNAMES = {EINVAL: "FRG_EINVAL", ENOMEM: "FRG_ENOMEM", ECUDA: "FRG_ECUDA",
 
 EXPORTED = ("frg_init", "frg_destroy", "frg_last_error", "frg_rhs", "frg_rhs_host", "frg_flow",
             "frg_advance", "frg_observables", "frg_get_state", "frg_set_state", "frg_stats",
-            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune", "frg_selftest_wait", "frg_rhs_host_async", "frg_sync")
+            "frg_rhs_timed", "frg_kernel_launches", "frg_rhs_noalloc", "frg_autotune", "frg_selftest_wait", "frg_rhs_host_async", "frg_sync",
+            "frg_cross_tile")
 NOALLOC_MAX_N = 64
 
 
@@ -128,10 +129,21 @@ def load():
     lib.frg_selftest_wait.argtypes = [vp, C.c_double]
     lib.frg_rhs_host_async.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp]
     lib.frg_sync.argtypes = [vp]
+    lib.frg_cross_tile.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
     lib.frg_kernel_launches.argtypes = []
     lib.frg_kernel_launches.restype = C.c_long
     _lib = lib
     return lib
+
+
+def cross_tile(ch, N, nt, m, rt):
+    """Crossing-reduced tile geometry (frg_cross_tile): (c0, width, own_lo,
+    own_hi, partner_lo, partner_hi, partner_row_max)."""
+    out = (C.c_int * 7)()
+    rc = load().frg_cross_tile(ch, N, nt, m, rt, out)
+    if rc != OK:
+        raise FrgError(rc, "frg_cross_tile: invalid arguments")
+    return tuple(out)
 
 
 def kernel_launches():
