@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(comb_threads<REV, ERR>(), ERR ? 4 : REV ? LB_M
     const Ctl &c = *o.ctl;
     const float hf = d2f(c.h), atolf = d2f(P.atol), rtolf = d2f(P.rtol), yfl = d2f(c.yfloor);
     const float2 *__restrict__ yh = P.yhi[c.yslot], *__restrict__ yhn = P.yhi[c.yslot ^ 1];
-#pragma unroll
+#pragma unroll 1
     for (int u = 0; u < PER; ++u) {
       const int t = threadIdx.x + u * TPB, row = t / (LC / 2), cc = 2 * (t % (LC / 2));
       const int a = row / LB, b = row % LB;

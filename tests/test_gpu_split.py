@@ -163,6 +163,20 @@ def test_split_flow_without_vertex_channels_matches_oracle(prec, mask, rev):
     assert abs(st.accepted - rst.accepted) <= max(2, rst.accepted // 10)
 
 
+@pytest.mark.parametrize("prec", [frg.FP64] + PRECS)
+@pytest.mark.parametrize("N", [2, 16, 100])
+def test_zero_interaction_flows_nothing(prec, N):
+    """U = 0 (a degenerate case): every diagram and the self-energy rhs vanish,
+    so the whole flow keeps the vertex and the self-energy exactly zero in
+    every precision (the split slicing of an all-zero operand included)."""
+    w = inputs.Workload("u0", N=N, U=0.0, T=0.05, eps_d=0.2)
+    with frg.Context([w], precision=prec) as ctx:
+        st = ctx.flow()[0]
+        g, s, lam, _ = ctx.get_state(0)
+    assert st.status == 0 and st.done == 1 and abs(lam / w.Lambda_f - 1.0) < 1e-12
+    assert torch.count_nonzero(g).item() == 0 and torch.count_nonzero(s).item() == 0
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_split_batched_points_equal_single_point_runs(prec):
     """Uneven grid sizes in one context: every tile's sum runs in a fixed order
