@@ -346,11 +346,16 @@ static int stage_grid(const frg_ctx *ctx) { return ctx->rev_on ? ctx->lb_grid_ha
 // self-energy tail and, for k7, takes the self-energy error), and so does
 // everything after it: the next stage kernel overwrites the vertex input that
 // the self-energy rhs reads.
-static int run_split_stage(frg_ctx *ctx, int s, bool err) {
+// fused (3xTF32 flows without tails, stages 2-6): the scatter-add of the
+// previous rhs was left out of that rhs (`deferred`) and runs in this stage's
+// kernel, after the previous rhs's side-stream work (the self-energy rhs reads
+// the vertex stage input this kernel overwrites).
+static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool deferred) {
   cudaStream_t st = ctx->stream, ss = ctx->sstream, ts = ctx->tstream;
   RhsIO *io = ctx->d_io_stage;
   const bool tails = (ctx->mask & FRG_TAILS) != 0;
   const int chmask = ctx->mask & 7;
+  if (fused) CK(cudaStreamWaitEvent(st, ctx->ev_sig, 0), "self-energy");
   CK(cudaEventRecord(ctx->ev_fork, st), "fork");
   CK(cudaStreamWaitEvent(ss, ctx->ev_fork, 0), "fork");
   LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, io, s, ctx->n, ss), "self-energy stage");
@@ -362,8 +367,14 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err) {
   }
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_TABLES), "bubble weights");
   CK(cudaEventRecord(ctx->ev_join, ss), "join");
-  LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, stage_grid(ctx), ctx->n, ctx->lb_want),
-     "stage sum");
+  if (fused)
+    LK(launch_combine_stage(ctx->d_pts, ctx->d_ctl, s, ctx->rev_on, chmask, st, stage_grid(ctx), ctx->n,
+                            ctx->lb_want),
+       "scatter-add and stage sum");
+  else
+    LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, stage_grid(ctx), ctx->n,
+                    ctx->lb_want),
+       "stage sum");
   CK(cudaEventRecord(ctx->ev_stage, st), "stage");
   CK(cudaStreamWaitEvent(ss, ctx->ev_stage, 0), "stage");
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_SIGMA), "self-energy rhs");
@@ -371,9 +382,9 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err) {
   CK(cudaEventRecord(ctx->ev_sig, ss), "self-energy");
   if (chmask) {
     LK(tc_run(ctx->tc, ctx->d_pts, io, -1, chmask, st, nullptr, nullptr, ctx->n, ctx->maxN, ctx->ev_join, tails,
-              ctx->ev_sig, true, ctx->rev_on, err, ctx->cross),
+              ctx->ev_sig, true, ctx->rev_on, err, ctx->cross, !deferred),
        "split contraction");
-  } else {
+  } else if (!deferred) {
     // no vertex channel: the scatter-add writes the zero (or tail-only)
     // vertex derivative and, for k7, completes the error estimate
     CK(cudaStreamWaitEvent(st, ctx->ev_sig, 0), "self-energy");
@@ -387,7 +398,7 @@ static int issue_k1(frg_ctx *ctx) {
   cudaStream_t st = ctx->stream;
   int rc;
   if (ctx->split) {
-    if ((rc = run_split_stage(ctx, 0, false))) return rc;
+    if ((rc = run_split_stage(ctx, 0, false, false, false))) return rc;
   } else {
     LK(launch_set_stage_io(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->split, ctx->n, st), "stage io");
     if ((rc = run_rhs(ctx, ctx->d_io_stage, -1))) return rc;
@@ -403,8 +414,10 @@ static int issue_step(frg_ctx *ctx) {
     int rc;
     if (ctx->split) {
       // the split paths' scatter-add of the seventh rhs (k7) also completes
-      // the step's error norm
-      if ((rc = run_split_stage(ctx, s, s == 6))) return rc;
+      // the step's error norm; 3xTF32 flows without tails run the scatter-adds
+      // of k2..k6 fused with the stage sums 2..6 that read them
+      const bool fuse = ctx->precision == FRG_3XTF32 && !(ctx->mask & FRG_TAILS);
+      if ((rc = run_split_stage(ctx, s, s == 6, fuse && s >= 2, fuse && s <= 5))) return rc;
     } else {
       LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 0, ctx->d_io_stage, st), "stage sum");
       if ((rc = run_rhs(ctx, ctx->d_io_stage, -1))) return rc;

@@ -13,6 +13,7 @@
 #include "frg_common.cuh"
 #include "frg_integrator.cuh"
 #include "frg_split.cuh"
+#include "frg_combine.cuh"
 #include "frg_lblock.cuh"
 
 namespace frg {
@@ -296,15 +297,11 @@ __device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, f
 template <int S>
 __host__ __device__ constexpr int stage_threads() { return LB_THREADS_WIDE; }
 
-template <int S>
-__global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_WIDE)
-    k_stage_split(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int want) {
-  extern __shared__ float4 lsm4[];
-  float2 *sm = reinterpret_cast<float2 *>(lsm4);
-  const int pi = blockIdx.y;
-  const PointDesc &P = pts[pi];
-  const Ctl &c = ctl[pi];
-  if (c.done) return;
+// One layout block of split stage S for a point whose flow is not done; sm:
+// the block in shared memory (LB x LAP float2).  VMAX: fold the block's bound of
+// the FP32 stage input into P.vmax (BF16 slicing).
+template <int S, bool VMAX>
+__device__ __forceinline__ void stage_block(const PointDesc &P, const Ctl &c, int want, float2 *__restrict__ sm) {
   const int N = P.N, n3 = P.n3;
   const bool half = P.rev_half != 0;
   const int ys = c.yslot;
@@ -385,7 +382,41 @@ __global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_
     lblock_write<true>(P, sm, k, want, S == 0 || c.lay_both != 0);
   else
     lblock_write<false>(P, sm, k, want);
-  block_max_to(vm, P.vmax);
+  if (VMAX) block_max_to(vm, P.vmax);
+}
+
+template <int S>
+__global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_WIDE)
+    k_stage_split(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int want) {
+  extern __shared__ float4 lsm4[];
+  const Ctl &c = ctl[blockIdx.y];
+  if (c.done) return;
+  stage_block<S, true>(pts[blockIdx.y], c, want, reinterpret_cast<float2 *>(lsm4));
+}
+
+// A 3xTF32 flow's scatter-add of the rhs of stage S - 1 (it forms k_S) fused
+// with the stage sum S that reads it, block by block: both run over the same
+// layout blocks (the canonical half under the reversal reduction) with the
+// same thread per pair, so a thread's stage sum reads k_S from its own writes
+// (no frequency-box tails; the BF16 vertex bound is not kept, 3xTF32 does not
+// read it).  The scatter-add's IO record is formed from the controller state:
+// output k_S = kG[kslot[S-1]].
+template <int S, bool REV>
+__global__ void __launch_bounds__(LB_THREADS_WIDE, S == 6 ? 3 : LB_MINBLOCKS_WIDE)
+    k_combine_stage(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int mask, int want) {
+  extern __shared__ float4 lsm4[];
+  float2 *sm = reinterpret_cast<float2 *>(lsm4);
+  const PointDesc &P = pts[blockIdx.y];
+  const Ctl &c = ctl[blockIdx.y];
+  if (c.done) return;
+  RhsIO o = {};
+  o.active = 1;
+  o.dgam = P.kG[c.kslot[S - 1]];
+  o.out_f32 = 1;
+  o.canon = P.rev_half;
+  combine_block<REV, false, LB_THREADS_WIDE, false>(P, o, mask, ErrWeights{}, sm);
+  __syncthreads();  // the scatter-add's reads of the shared block are done
+  stage_block<S, false>(P, c, want, sm);
 }
 
 // Self-energy part of split stage s (one block per point), and the stage's rhs
@@ -572,7 +603,12 @@ static bool stage_attrs(K kernel) {
 int stage_split_init() {
   const bool ok = stage_attrs(k_stage_split<0>) && stage_attrs(k_stage_split<1>) && stage_attrs(k_stage_split<2>) &&
                   stage_attrs(k_stage_split<3>) && stage_attrs(k_stage_split<4>) && stage_attrs(k_stage_split<5>) &&
-                  stage_attrs(k_stage_split<6>);
+                  stage_attrs(k_stage_split<6>) && stage_attrs(k_combine_stage<2, true>) &&
+                  stage_attrs(k_combine_stage<3, true>) && stage_attrs(k_combine_stage<4, true>) &&
+                  stage_attrs(k_combine_stage<5, true>) && stage_attrs(k_combine_stage<6, true>) &&
+                  stage_attrs(k_combine_stage<2, false>) && stage_attrs(k_combine_stage<3, false>) &&
+                  stage_attrs(k_combine_stage<4, false>) && stage_attrs(k_combine_stage<5, false>) &&
+                  stage_attrs(k_combine_stage<6, false>);
   return ok ? 0 : -3;
 }
 
@@ -598,6 +634,29 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
   }
   FRG_COUNT(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, int mask, cudaStream_t st,
+                         int lb_grid, int n_points, int want) {
+  const dim3 g(lb_grid, n_points);
+  const int cv = step_carveout(n_points);
+  const Ctl *c = d_ctl;
+  const int m = mask | (rev ? FRG_REVERSAL : 0);
+  cudaError_t e = cudaErrorInvalidValue;
+#define FRG_CS(S)                                                                                              \
+  e = rev ? launch_with_carveout(k_combine_stage<S, true>, g, LB_THREADS_WIDE, LB_SMEM, st, cv, d_pts, c, m, want) \
+          : launch_with_carveout(k_combine_stage<S, false>, g, LB_THREADS_WIDE, LB_SMEM, st, cv, d_pts, c, m, want)
+  switch (s) {
+    case 2: FRG_CS(2); break;
+    case 3: FRG_CS(3); break;
+    case 4: FRG_CS(4); break;
+    case 5: FRG_CS(5); break;
+    case 6: FRG_CS(6); break;
+    default: return -1;
+  }
+#undef FRG_CS
+  FRG_COUNT(1);
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st) {

@@ -1414,7 +1414,8 @@ namespace frg {
 
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
-           int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err, bool cross) {
+           int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err, bool cross,
+           bool combine) {
   // layouts of the stage input: W for the crossed channel, X and Z for the
   // direct one
   if ((chmask & 6) && !layouts_ready) {
@@ -1437,6 +1438,7 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
     if (cudaGetLastError() != cudaSuccess) return -3;
   }
   if (ev_contract && cudaEventRecord(ev_contract, st) != cudaSuccess) return -3;
+  if (!combine) return 0;
   // channel outputs in their own layouts -> natural layout (the scatter-add,
   // with the frequency-box tail constants when enabled); also resets the
   // vertex bound that the BF16 slicing read

@@ -37,7 +37,8 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // the combine taking the others from the mirrored entries), and the combine
 // into the natural layout (with err also the step's error estimate: the
 // seventh rhs of a flow step; with half and cross the crossing-reduced
-// tiles).  ev_gather / ev_contract
+// tiles; without combine the caller runs the scatter-add itself, e.g. fused
+// with the next stage sum).  ev_gather / ev_contract
 // (optional) are recorded after the relayout and after the products; the
 // products wait for wait_before (optional: the bubble weights computed on
 // another stream), the combine for wait_combine (optional: the tail constants
@@ -45,5 +46,6 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
            cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_combine = nullptr,
-           bool layouts_ready = false, bool half = false, bool err = false, bool cross = false);
+           bool layouts_ready = false, bool half = false, bool err = false, bool cross = false,
+           bool combine = true);
 }  // namespace frg
