@@ -79,9 +79,10 @@ struct frg_ctx {
   cudaStream_t sstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tails = nullptr, ev_stage = nullptr, ev_sig = nullptr;
   // split flows with the frequency-box tails: the tail constants on a third
-  // stream, from the self-energy stage input on (ev_sst)
+  // stream, from the self-energy stage input on (ev_sst); the last of them
+  // adds the self-energy's to the self-energy rhs (ev_srhs)
   cudaStream_t tstream = nullptr;
-  cudaEvent_t ev_sst = nullptr;
+  cudaEvent_t ev_sst = nullptr, ev_srhs = nullptr;
   // pipelined host-buffer evaluations: copy-in and copy-out streams, two device
   // slots per point, per-slot events (input copied, compute done, output read)
   cudaStream_t cin = nullptr, cout = nullptr;
@@ -199,15 +200,16 @@ static int run_rhs(frg_ctx *ctx, RhsIO *d_io, int point /* -1: all */, cudaEvent
        "bubble weights and self-energy");
     CK(cudaEventRecord(ctx->ev_join, ctx->sstream), "join");
     // the tail constants are needed only after the contraction: they run on
-    // the side stream while the main stream regathers and contracts
+    // the side stream while the main stream regathers and contracts (the
+    // self-energy's is added to the self-energy rhs, which has run)
     if (tails) {
       LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, ctx->sstream), "tail sums");
       CK(cudaEventRecord(ctx->ev_tails, ctx->sstream), "tails");
     }
   } else {
-    if (tails) LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, st), "tail sums");
     LK(launch_bubble_sigma(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->split, ctx->mask, st),
        "bubble weights and self-energy");
+    if (tails) LK(launch_tail_sums(ctx->d_pts, d_io, ctx->n, ctx->maxN, ctx->mask, st), "tail sums");
   }
   if (ev) CK(cudaEventRecord(ev[1], st), "event");
   const int chmask = ctx->mask & 7;
@@ -342,14 +344,18 @@ static int stage_grid(const frg_ctx *ctx) { return ctx->rev_on ? ctx->lb_grid_ha
 // stream; then the self-energy rhs, which reads the vertex stage input,
 // beside the contraction.  The frequency-box tail constants (a window of
 // propagators of their own) run on a third stream from the self-energy stage
-// input on.  The scatter-add waits for all of them (it adds the tails and the
-// self-energy tail and, for k7, takes the self-energy error), and so does
+// input on; their last kernel, after the self-energy rhs, adds the
+// self-energy's constant to it.  The scatter-add waits for all of them (it
+// adds the vertex tails and, for k7, takes the self-energy error), and so does
 // everything after it: the next stage kernel overwrites the vertex input that
 // the self-energy rhs reads.
-// fused (3xTF32 flows without tails, stages 2-6): the scatter-add of the
-// previous rhs was left out of that rhs (`deferred`) and runs in this stage's
-// kernel, after the previous rhs's side-stream work (the self-energy rhs reads
-// the vertex stage input this kernel overwrites).
+// The tail constants and the BF16x3 vertex bound are kept per stage parity
+// (RhsIO.par): the next rhs's side-stream work may run while this rhs's
+// scatter-add still reads them.
+// fused (stages 2-6): the scatter-add of the previous rhs was left out of
+// that rhs (`deferred`) and runs in this stage's kernel, after the previous
+// rhs's side-stream work (the self-energy rhs reads the vertex stage input
+// this kernel overwrites; the vertex tails are what the scatter-add adds).
 static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool deferred) {
   cudaStream_t st = ctx->stream, ss = ctx->sstream, ts = ctx->tstream;
   RhsIO *io = ctx->d_io_stage;
@@ -362,14 +368,13 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool defer
   if (tails) {
     CK(cudaEventRecord(ctx->ev_sst, ss), "self-energy stage");
     CK(cudaStreamWaitEvent(ts, ctx->ev_sst, 0), "self-energy stage");
-    LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ts), "tail sums");
-    CK(cudaEventRecord(ctx->ev_tails, ts), "tails");
+    LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ts, TAIL_WINDOW), "tail sums");
   }
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_TABLES), "bubble weights");
   CK(cudaEventRecord(ctx->ev_join, ss), "join");
   if (fused)
-    LK(launch_combine_stage(ctx->d_pts, ctx->d_ctl, s, ctx->rev_on, chmask, st, stage_grid(ctx), ctx->n,
-                            ctx->lb_want),
+    LK(launch_combine_stage(ctx->d_pts, ctx->d_ctl, s, ctx->rev_on, ctx->precision == FRG_BF16X3,
+                            chmask | (tails ? FRG_TAILS : 0), st, stage_grid(ctx), ctx->n, ctx->lb_want),
        "scatter-add and stage sum");
   else
     LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 1, io, st, stage_grid(ctx), ctx->n,
@@ -378,7 +383,14 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool defer
   CK(cudaEventRecord(ctx->ev_stage, st), "stage");
   CK(cudaStreamWaitEvent(ss, ctx->ev_stage, 0), "stage");
   LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_SIGMA), "self-energy rhs");
-  if (tails) CK(cudaStreamWaitEvent(ss, ctx->ev_tails, 0), "tails");
+  if (tails) {
+    // the tail constants, the self-energy's added to the self-energy rhs
+    CK(cudaEventRecord(ctx->ev_srhs, ss), "self-energy rhs");
+    CK(cudaStreamWaitEvent(ts, ctx->ev_srhs, 0), "self-energy rhs");
+    LK(launch_tail_sums(ctx->d_pts, io, ctx->n, ctx->maxN, ctx->mask, ts, TAIL_FINISH), "tail constants");
+    CK(cudaEventRecord(ctx->ev_tails, ts), "tails");
+    CK(cudaStreamWaitEvent(ss, ctx->ev_tails, 0), "tails");
+  }
   CK(cudaEventRecord(ctx->ev_sig, ss), "self-energy");
   if (chmask) {
     LK(tc_run(ctx->tc, ctx->d_pts, io, -1, chmask, st, nullptr, nullptr, ctx->n, ctx->maxN, ctx->ev_join, tails,
@@ -414,10 +426,9 @@ static int issue_step(frg_ctx *ctx) {
     int rc;
     if (ctx->split) {
       // the split paths' scatter-add of the seventh rhs (k7) also completes
-      // the step's error norm; 3xTF32 flows without tails run the scatter-adds
-      // of k2..k6 fused with the stage sums 2..6 that read them
-      const bool fuse = ctx->precision == FRG_3XTF32 && !(ctx->mask & FRG_TAILS);
-      if ((rc = run_split_stage(ctx, s, s == 6, fuse && s >= 2, fuse && s <= 5))) return rc;
+      // the step's error norm; the scatter-adds of k2..k6 run fused with the
+      // stage sums 2..6 that read them
+      if ((rc = run_split_stage(ctx, s, s == 6, s >= 2, s <= 5))) return rc;
     } else {
       LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, s, 0, ctx->d_io_stage, st), "stage sum");
       if ((rc = run_rhs(ctx, ctx->d_io_stage, -1))) return rc;
@@ -513,6 +524,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->tstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_sst, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_srhs, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_tails, cudaEventDisableTiming) != cudaSuccess ||
@@ -575,10 +587,10 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
         if (!(P.yhi[b] = dalloc<float2>(ctx, nv)) || !(P.ylo[b] = dalloc<float2>(ctx, nv))) return bail(FRG_ENOMEM);
       if (!(P.Lpp32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
           !(P.Lph32 = dalloc<float2>(ctx, (size_t)(2 * N - 1) * N + OPERAND_SLACK)) ||
-          !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 1)) ||
+          !(P.Lmax = dalloc<float>(ctx, (size_t)2 * (2 * N - 1))) || !(P.vmax = dalloc<unsigned>(ctx, 2)) ||
           !(P.kord = dalloc<unsigned char>(ctx, (size_t)2 * (2 * N - 1) * 16)))
         return bail(FRG_ENOMEM);
-      if (cudaMemset(P.vmax, 0, sizeof(unsigned)) != cudaSuccess) return bail(FRG_ECUDA);
+      if (cudaMemset(P.vmax, 0, 2 * sizeof(unsigned)) != cudaSuccess) return bail(FRG_ECUDA);
       // the operand maps also read rows past the valid part of each line (their
       // products are zero through the bubble weights): keep every such element
       // finite, the slack included
@@ -594,7 +606,7 @@ int frg_init(const frg_params *params, int n_points, void *cuda_stream, frg_ctx 
       if (!(P.kS[j] = dalloc<double2>(ctx, N))) return bail(FRG_ENOMEM);
     if (p.channel_mask & FRG_TAILS) {
       const size_t W = (size_t)FRG_TAIL_FACTOR * N;
-      const size_t nt = 2 * (2 * (size_t)N - 1) + 1;
+      const size_t nt = 2 * (size_t)tail_set(N);
       if (!(P.Gw = dalloc<double2>(ctx, W)) || !(P.Sw = dalloc<double2>(ctx, W)) ||
           !(P.tail = dalloc<double2>(ctx, nt)) || !(P.tailB = dalloc<double2>(ctx, 2 * (size_t)N - 1)))
         return bail(FRG_ENOMEM);
@@ -720,6 +732,7 @@ void frg_destroy(frg_ctx *ctx) {
     cudaStreamDestroy(ctx->tstream);
   }
   if (ctx->ev_sst) cudaEventDestroy(ctx->ev_sst);
+  if (ctx->ev_srhs) cudaEventDestroy(ctx->ev_srhs);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->cin) {
     cudaStreamSynchronize(ctx->cin);
@@ -772,6 +785,7 @@ static int rhs_impl(frg_ctx *ctx, int point, double Lambda, const void *d_gamma,
   o.out_f32 = 0;
   o.canon = 0;
   o.ctl = nullptr;
+  o.par = 0;
   if (!ctx->split) {
     LK(launch_set_user_io(ctx->d_io_user, ctx->d_ctl, ctx->n, point, o, Lambda, ctx->stream), "user io");
     return run_rhs(ctx, ctx->d_io_user, point, ev);

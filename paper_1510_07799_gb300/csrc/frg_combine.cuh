@@ -12,13 +12,15 @@ namespace frg {
 
 // FP32 copy of the FP64 frequency-box tail constant j of a point (rounded once
 // per rhs by the tail kernels).
-__device__ __forceinline__ float2 tail_c(const PointDesc &P, int j) { return P.tail32[j]; }
+__device__ __forceinline__ float2 tail_c(const PointDesc &P, const RhsIO &o, int j) {
+  return P.tail32[o.par * tail_set(P.N) + j];
+}
 
 // Block-wide fold of the error estimate of one layout block into the point's
 // controller state (seventh rhs of a flow step): the vertex part's maxima from
 // every thread; block 0 adds the self-energy part in FP64 (its derivatives,
-// the tails included, are final by now: this block's threads added the
-// self-energy tail constant to the very entries they read here).
+// the tail constants included, are final: the scatter-add runs after the
+// self-energy rhs).
 static __device__ void err_fold(const PointDesc &P, const RhsIO &o, const ErrWeights &ew, float fmax_, float ym, int bad) {
   Ctl &c = *o.ctl;
   double dmax = 0.0, sm = 0.0;
@@ -78,8 +80,8 @@ static __device__ void err_fold(const PointDesc &P, const RhsIO &o, const ErrWei
 
 // k (natural) = [pp part already in k] + X^T(PX) + W^T(PW), for enabled channels
 // (launched for every split-path rhs, also when only pp is enabled), plus the
-// frequency-box tail constants when mask has FRG_TAILS (block 0 of a point also
-// adds the self-energy's).  With FRG_REVERSAL each channel holds only its
+// frequency-box tail constants when mask has FRG_TAILS (the self-energy rhs
+// takes its own).  With FRG_REVERSAL each channel holds only its
 // transfers m <= N - 1 (pp in PN): an entry whose transfer lies beyond takes the
 // conjugate of the channel's value at the mirrored entry (N-1-i1, N-1-i2,
 // N-1-i3); on the self-mirrored transfer m = N - 1 the entry of each mirror pair
@@ -115,13 +117,9 @@ __device__ __forceinline__ void combine_block(const PointDesc &P, const RhsIO &o
                                               float2 *__restrict__ sm) {
   const int N = P.N, M = N - 1, nrow = 2 * N - 1;
   const bool tails = (mask & FRG_TAILS) && P.tail;
-  if (tails && blockIdx.x == 0 && threadIdx.x < N && o.dsig) {
-    const double2 a = o.dsig[threadIdx.x], b = P.tail[2 * nrow];
-    o.dsig[threadIdx.x] = make_double2(a.x + b.x, a.y + b.y);
-  }
   // the channel products of this rhs have consumed the vertex bound of the
   // stage input (BF16 slicing): reset it for the next stage
-  if (VMAX && blockIdx.x == 0 && threadIdx.x == 0 && P.vmax) *P.vmax = 0u;
+  if (VMAX && blockIdx.x == 0 && threadIdx.x == 0 && P.vmax) P.vmax[o.par] = 0u;
   // half storage: entries with i1 >= hN are not wanted (and have no room in K)
   const int hN = (REV && o.canon) ? N / 2 : N;
   const LBlock k = lblock(N, hN, blockIdx.x);
@@ -219,25 +217,25 @@ __device__ __forceinline__ void combine_block(const PointDesc &P, const RhsIO &o
     float4 v = *reinterpret_cast<const float4 *>(&sm[lsidx(a, b, c)]);
     if (tails) {
       // pp transfer s = a + b (one per row), xph transfer Q = b - c per element
-      float2 ta = tail_c(P, ga + gb), tb0 = tail_c(P, nrow + gb - gc + N - 1),
-             tb1 = tail_c(P, nrow + gb - gc - 1 + N - 1);
+      float2 ta = tail_c(P, o, ga + gb), tb0 = tail_c(P, o, nrow + gb - gc + N - 1),
+             tb1 = tail_c(P, o, nrow + gb - gc - 1 + N - 1);
       if (REV) {
         // the constants of mirrored transfers as exact conjugates, so that
         // the sum stays exactly reversal-symmetric
         if (ga + gb > M) {
-          ta = tail_c(P, 2 * M - (ga + gb));
+          ta = tail_c(P, o, 2 * M - (ga + gb));
           ta.y = -ta.y;
         } else if (ga + gb == M) {
           ta.y = 0.f;
         }
         if (gb > gc) {
-          tb0 = tail_c(P, nrow + gc - gb + N - 1);
+          tb0 = tail_c(P, o, nrow + gc - gb + N - 1);
           tb0.y = -tb0.y;
         } else if (gb == gc) {
           tb0.y = 0.f;
         }
         if (gb > gc + 1) {
-          tb1 = tail_c(P, nrow + gc + 1 - gb + N - 1);
+          tb1 = tail_c(P, o, nrow + gc + 1 - gb + N - 1);
           tb1.y = -tb1.y;
         } else if (gb == gc + 1) {
           tb1.y = 0.f;

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "frg.h"
+
 #define FRG_MAX_N 256
 
 namespace frg {
@@ -57,12 +59,16 @@ struct PointDesc {
   // real components; the scatter-add of k7 adds E_7 k7 and takes the norm
   float4 *eacc;
   unsigned char *kord;      // split paths: per table row, its 16-wide k-chunks by increasing max |Lb| (16 each)
-  unsigned *vmax;    // split paths: bits of max |Re|,|Im| over the FP32 vertex input of the current rhs
+  // split paths: bits of max |Re|,|Im| over the FP32 vertex input of an rhs,
+  // two of them (RhsIO.par): a flow's stage input and the previous one's
+  unsigned *vmax;
   // frequency-box tails (null when off): propagators on the window of
   // FRG_TAIL_FACTOR * N indices starting at -(W - N)/2 (Sigma = 0 outside the
-  // box), and per rhs the additive constants: pp transfer s at [s], xph
-  // transfer Q at [2N-1 + Q+N-1], the self-energy at [4N-2]; tailB: the xph
-  // half sums (below); tail32 (split paths): the constants rounded to FP32
+  // box), and per rhs the vertex's additive constants: pp transfer s at [s],
+  // xph transfer Q at [2N-1 + Q+N-1], twice (RhsIO.par: an rhs's and its
+  // predecessor's), then the partial sums of the self-energy's constant, one
+  // per TAIL_GS_THREADS window indices; tailB: the xph half sums (below);
+  // tail32 (split paths): the vertex's constants rounded to FP32
   double2 *Gw, *Sw, *tail, *tailB;
   float2 *tail32;
 };
@@ -104,7 +110,18 @@ struct RhsIO {
   // also completes the embedded error estimate of the step (ctl: the point's
   // controller state); null otherwise
   Ctl *ctl;
+  // which of the two per-rhs buffers (vertex bound, tail constants) this rhs
+  // uses: a flow's stage parity, so that the scatter-add of one rhs and the
+  // next stage's kernels, which run together, never share one
+  int par;
 };
+// Size of one set of tail constants of a point: the vertex's, then the
+// self-energy's partial sums.
+constexpr int TAIL_GS_THREADS = 128;
+__host__ __device__ inline int tail_parts(int N) {
+  return (FRG_TAIL_FACTOR * N + TAIL_GS_THREADS - 1) / TAIL_GS_THREADS;
+}
+__host__ __device__ inline int tail_set(int N) { return 2 * (2 * N - 1) + tail_parts(N); }
 
 // Output tile of one CTA of the FP64 channel contraction (k_contract_fp64):
 // F64_TM rows x F64_TN columns; the hosts that build its tile lists (the
@@ -257,9 +274,13 @@ int launch_contract_fp64(const PointDesc *d_pts, const RhsIO *d_io, const WorkIt
 constexpr int BUBBLE_TABLES = 1, BUBBLE_SIGMA = 2;
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
                         cudaStream_t st, int parts = BUBBLE_TABLES | BUBBLE_SIGMA);
-// Frequency-box tails: window propagators, then the per-transfer constants
-// (before launch_bubble_sigma, which adds the self-energy constant) ...
-int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st);
+// Frequency-box tails: the window propagators and the sums over the window
+// (TAIL_WINDOW), then the constants, the self-energy's added to the
+// self-energy rhs (TAIL_FINISH: after launch_bubble_sigma's self-energy
+// part) ...
+constexpr int TAIL_WINDOW = 1, TAIL_FINISH = 2;
+int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
+                     int parts = TAIL_WINDOW | TAIL_FINISH);
 // ... and their addition to the vertex derivative (after the contraction).
 int launch_add_tails(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, cudaStream_t st);
 // Self-energy rhs from FP64 input alone (after launch_bubble).

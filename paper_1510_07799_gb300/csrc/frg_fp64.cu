@@ -179,7 +179,8 @@ int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int ma
 // slow on this part, so they are done once per frequency), then computes either
 // one row of a bubble-weight table (blocks [0, 2(2 maxN - 1))) or one
 // self-energy entry dSigma(w)/dl (blocks beyond), with 128 threads over the
-// loop index p and a fixed-order block reduction.
+// loop index p and a fixed-order block reduction.  (With the frequency-box
+// tails, k_tail_finish adds the self-energy's tail constant afterwards.)
 template <bool SPLIT>
 __global__ void __launch_bounds__(128)
     k_bubble_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int maxN, int sigma_on, int b0) {
@@ -323,17 +324,34 @@ __global__ void k_tail_gs(const PointDesc *__restrict__ pts, const RhsIO *__rest
   if (!o.active) return;
   const PointDesc &P = pts[pi];
   const int N = P.N, W = FRG_TAIL_FACTOR * N, lo = -(W - N) / 2;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!P.Gw || x >= W) return;
+  if (!P.Gw || (int)blockIdx.x >= tail_parts(N)) return;
+  const int x = blockIdx.x * TAIL_GS_THREADS + threadIdx.x;
   const int i = lo + x;
-  double2 g, s;
-  propagator_at(P, i, *o.lam, (o.sig && inbox(N, i)) ? o.sig[i] : make_double2(0.0, 0.0), g, s);
-  P.Gw[x] = g;
-  P.Sw[x] = s;
+  double2 s = make_double2(0.0, 0.0);
+  if (x < W) {
+    double2 g;
+    propagator_at(P, i, *o.lam, (o.sig && inbox(N, i)) ? o.sig[i] : make_double2(0.0, 0.0), g, s);
+    P.Gw[x] = g;
+    P.Sw[x] = s;
+  }
+  // this block's part of the self-energy's sum over the indices outside the box
+  double2 t = (x < W && !inbox(N, i)) ? s : make_double2(0.0, 0.0);
+  for (int off = 16; off > 0; off >>= 1) {
+    t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+    t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+  }
+  __shared__ double2 part[TAIL_GS_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 r = part[0];
+    for (int j = 1; j < TAIL_GS_THREADS / 32; ++j) r = cadd(r, part[j]);
+    P.tail[o.par * tail_set(N) + 2 * (2 * N - 1) + blockIdx.x] = r;
+  }
 }
 
-// blocks [0, 2 maxN - 1): pp transfers; the next 2 maxN - 1: xph transfers;
-// the last one: the self-energy constant.  128 threads, fixed-order reduction.
+// blocks [0, 2 maxN - 1): pp transfers; the next 2 maxN - 1: xph transfers.
+// 128 threads, fixed-order reduction.
 // The two halves of a bubble weight give equal sums: for pp the window set of
 // transfer s is symmetric under p <-> s - p, so sum Lb(p, s-p) = 2 sum S(p)
 // G(s-p); for xph the second half at Q is the first half at -Q,
@@ -348,17 +366,13 @@ __global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__
   if (!P.tail) return;
   const int N = P.N, nrow = 2 * N - 1, nrow_max = 2 * maxN - 1;
   const int b = blockIdx.x;
-  const int which = b < nrow_max ? 0 : (b < 2 * nrow_max ? 1 : 2);
-  const int row = which == 2 ? 0 : b - which * nrow_max;
-  if (which < 2 && row >= nrow) return;
+  const int which = b < nrow_max ? 0 : 1;
+  const int row = b - which * nrow_max;
+  if (row >= nrow) return;
   const int W = FRG_TAIL_FACTOR * N, lo = -(W - N) / 2;
   double2 acc = make_double2(0.0, 0.0);
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
     const int p = lo + x;
-    if (which == 2) {
-      if (!inbox(N, p)) acc = cadd(acc, P.Sw[x]);
-      continue;
-    }
     const int q = which == 0 ? row - p : p + (row - (N - 1));
     const int y = q - lo;
     if ((unsigned)y >= (unsigned)W || (inbox(N, p) && inbox(N, q))) continue;
@@ -375,14 +389,16 @@ __global__ void __launch_bounds__(128) k_tail_sums(const PointDesc *__restrict__
     double2 t = part[0];
     for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
     const double L = *o.lam;
-    if (which == 0) P.tail[row] = (mask & 1) ? cscale(t, -2.0 * L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
-    else if (which == 1) P.tailB[row] = t;
-    else P.tail[2 * nrow] = (mask & 8) ? cscale(t, L * P.T * P.U) : make_double2(0.0, 0.0);
+    double2 *tl = P.tail + o.par * tail_set(N);
+    if (which == 0) tl[row] = (mask & 1) ? cscale(t, -2.0 * L * P.T * P.U * P.U) : make_double2(0.0, 0.0);
+    else P.tailB[row] = t;
   }
 }
 
-// xph constants from the half sums, B(Q) + B(-Q), and the FP32 copies of all
-// constants (split paths); one block per point.
+// xph constants from the half sums, B(Q) + B(-Q), and the FP32 copies of the
+// vertex's constants (split paths); the self-energy's constant, L T U times
+// the sum of k_tail_gs's partial sums (warp 0, a fixed-order fold), added to
+// the self-energy rhs, which has run before.  One block per point.
 __global__ void k_tail_finish(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int mask) {
   const int pi = blockIdx.x;
   const RhsIO &o = io[pi];
@@ -391,19 +407,32 @@ __global__ void k_tail_finish(const PointDesc *__restrict__ pts, const RhsIO *__
   if (!P.tail) return;
   const int N = P.N, nrow = 2 * N - 1;
   const double f = -(*o.lam) * P.T * P.U * P.U;
+  const int off = o.par * tail_set(N);
+  if ((mask & 8) && o.dsig && threadIdx.x < 32) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int j = threadIdx.x; j < tail_parts(N); j += 32) t = cadd(t, P.tail[off + 2 * nrow + j]);
+    for (int d = 16; d > 0; d >>= 1) {
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, d);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, d);
+    }
+    const double2 c = cscale(t, (*o.lam) * P.T * P.U);
+    for (int i = threadIdx.x; i < N; i += 32) o.dsig[i] = cadd(o.dsig[i], c);
+  }
   for (int r = threadIdx.x; r < nrow; r += blockDim.x)
-    P.tail[nrow + r] = (mask & 4) ? cscale(cadd(P.tailB[r], P.tailB[nrow - 1 - r]), f) : make_double2(0.0, 0.0);
+    P.tail[off + nrow + r] =
+        (mask & 4) ? cscale(cadd(P.tailB[r], P.tailB[nrow - 1 - r]), f) : make_double2(0.0, 0.0);
   if (!P.tail32) return;
   __syncthreads();
-  for (int j = threadIdx.x; j < 2 * nrow + 1; j += blockDim.x) {
-    const double2 t = P.tail[j];
-    P.tail32[j] = make_float2((float)t.x, (float)t.y);
+  for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x) {
+    const double2 t = P.tail[off + j];
+    P.tail32[off + j] = make_float2((float)t.x, (float)t.y);
   }
 }
 
 // dGamma(k1,k2,k3) += tail_pp[k1 + k2] + tail_xph[k2 - k3] (FP32 or FP64
-// output, the constants rounded to the output's precision), dSigma += its
-// tail.  A block takes TAIL_ROWS rows (k1, k2); thread k3 walks them.
+// output, the constants rounded to the output's precision; the self-energy
+// rhs has taken its own tail).  A block takes TAIL_ROWS rows (k1, k2); thread
+// k3 walks them.
 constexpr int TAIL_ROWS = 16;
 __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__restrict__ pts,
                                                          const RhsIO *__restrict__ io) {
@@ -418,12 +447,10 @@ __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__rest
   __shared__ double2 tab[2 * (2 * FRG_MAX_N - 1)];
   __shared__ float2 tabf[2 * (2 * FRG_MAX_N - 1)];
   for (int j = threadIdx.x; j < 2 * nrow; j += blockDim.x) {
-    tab[j] = P.tail[j];
+    tab[j] = P.tail[o.par * tail_set(N) + j];
     tabf[j] = make_float2((float)tab[j].x, (float)tab[j].y);
   }
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < N && o.dsig)
-    o.dsig[threadIdx.x] = cadd(o.dsig[threadIdx.x], P.tail[2 * nrow]);
   const int i3 = threadIdx.x;
   // half storage: the rows (i1, i2) with i1 < N/2 only
   const int nrows = o.canon ? N * N / 2 : N * N;
@@ -458,14 +485,19 @@ __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__rest
   }
 }
 
-int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st) {
-  const int W = FRG_TAIL_FACTOR * maxN;
-  k_tail_gs<<<dim3((W + 127) / 128, n_points), 128, 0, st>>>(d_pts, d_io);
-  FRG_COUNT(1);
-  k_tail_sums<<<dim3(2 * (2 * maxN - 1) + 1, n_points), 128, 0, st>>>(d_pts, d_io, maxN, mask);
-  FRG_COUNT(1);
-  k_tail_finish<<<n_points, 256, 0, st>>>(d_pts, d_io, mask);
-  FRG_COUNT(1);
+int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
+                     int parts) {
+  if (parts & TAIL_WINDOW) {
+    const int W = FRG_TAIL_FACTOR * maxN;
+    k_tail_gs<<<dim3((W + TAIL_GS_THREADS - 1) / TAIL_GS_THREADS, n_points), TAIL_GS_THREADS, 0, st>>>(d_pts, d_io);
+    FRG_COUNT(1);
+    k_tail_sums<<<dim3(2 * (2 * maxN - 1), n_points), 128, 0, st>>>(d_pts, d_io, maxN, mask);
+    FRG_COUNT(1);
+  }
+  if (parts & TAIL_FINISH) {
+    k_tail_finish<<<n_points, 256, 0, st>>>(d_pts, d_io, mask);
+    FRG_COUNT(1);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

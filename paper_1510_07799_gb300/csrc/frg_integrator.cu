@@ -137,6 +137,7 @@ __device__ __forceinline__ void write_stage_io(const PointDesc &P, Ctl &c, RhsIO
   o.canon = split ? P.rev_half : 0;
   // the scatter-add of k7 completes the split paths' error estimate
   o.ctl = (split && stage == 6) ? &c : nullptr;
+  o.par = split ? (stage & 1) : 0;
   *io = o;
 }
 
@@ -382,7 +383,7 @@ __device__ __forceinline__ void stage_block(const PointDesc &P, const Ctl &c, in
     lblock_write<true>(P, sm, k, want, S == 0 || c.lay_both != 0);
   else
     lblock_write<false>(P, sm, k, want);
-  if (VMAX) block_max_to(vm, P.vmax);
+  if (VMAX) block_max_to(vm, P.vmax + (S & 1));
 }
 
 template <int S>
@@ -394,14 +395,15 @@ __global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_
   stage_block<S, true>(pts[blockIdx.y], c, want, reinterpret_cast<float2 *>(lsm4));
 }
 
-// A 3xTF32 flow's scatter-add of the rhs of stage S - 1 (it forms k_S) fused
+// A split flow's scatter-add of the rhs of stage S - 1 (it forms k_S) fused
 // with the stage sum S that reads it, block by block: both run over the same
 // layout blocks (the canonical half under the reversal reduction) with the
-// same thread per pair, so a thread's stage sum reads k_S from its own writes
-// (no frequency-box tails; the BF16 vertex bound is not kept, 3xTF32 does not
-// read it).  The scatter-add's IO record is formed from the controller state:
-// output k_S = kG[kslot[S-1]].
-template <int S, bool REV>
+// same thread per pair, so a thread's stage sum reads k_S from its own writes.
+// The scatter-add's IO record is formed from the controller state (output
+// k_S = kG[kslot[S-1]], the per-rhs buffers of parity S - 1); the stage sum
+// keeps the vertex bound of parity S (VMAX: BF16x3 flows, whose contraction
+// reads it).
+template <int S, bool REV, bool VMAX>
 __global__ void __launch_bounds__(LB_THREADS_WIDE, S == 6 ? 3 : LB_MINBLOCKS_WIDE)
     k_combine_stage(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int mask, int want) {
   extern __shared__ float4 lsm4[];
@@ -414,9 +416,10 @@ __global__ void __launch_bounds__(LB_THREADS_WIDE, S == 6 ? 3 : LB_MINBLOCKS_WID
   o.dgam = P.kG[c.kslot[S - 1]];
   o.out_f32 = 1;
   o.canon = P.rev_half;
-  combine_block<REV, false, LB_THREADS_WIDE, false>(P, o, mask, ErrWeights{}, sm);
+  o.par = (S - 1) & 1;
+  combine_block<REV, false, LB_THREADS_WIDE, VMAX>(P, o, mask, ErrWeights{}, sm);
   __syncthreads();  // the scatter-add's reads of the shared block are done
-  stage_block<S, false>(P, c, want, sm);
+  stage_block<S, VMAX>(P, c, want, sm);
 }
 
 // Self-energy part of split stage s (one block per point), and the stage's rhs
@@ -600,15 +603,17 @@ static bool stage_attrs(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LB_SMEM) == cudaSuccess;
 }
 
+template <int S>
+static bool combine_stage_attrs() {
+  return stage_attrs(k_combine_stage<S, true, false>) && stage_attrs(k_combine_stage<S, false, false>) &&
+         stage_attrs(k_combine_stage<S, true, true>) && stage_attrs(k_combine_stage<S, false, true>);
+}
+
 int stage_split_init() {
   const bool ok = stage_attrs(k_stage_split<0>) && stage_attrs(k_stage_split<1>) && stage_attrs(k_stage_split<2>) &&
                   stage_attrs(k_stage_split<3>) && stage_attrs(k_stage_split<4>) && stage_attrs(k_stage_split<5>) &&
-                  stage_attrs(k_stage_split<6>) && stage_attrs(k_combine_stage<2, true>) &&
-                  stage_attrs(k_combine_stage<3, true>) && stage_attrs(k_combine_stage<4, true>) &&
-                  stage_attrs(k_combine_stage<5, true>) && stage_attrs(k_combine_stage<6, true>) &&
-                  stage_attrs(k_combine_stage<2, false>) && stage_attrs(k_combine_stage<3, false>) &&
-                  stage_attrs(k_combine_stage<4, false>) && stage_attrs(k_combine_stage<5, false>) &&
-                  stage_attrs(k_combine_stage<6, false>);
+                  stage_attrs(k_stage_split<6>) && combine_stage_attrs<2>() && combine_stage_attrs<3>() &&
+                  combine_stage_attrs<4>() && combine_stage_attrs<5>() && combine_stage_attrs<6>();
   return ok ? 0 : -3;
 }
 
@@ -636,25 +641,28 @@ int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, int mask, cudaStream_t st,
+template <int S>
+static cudaError_t combine_stage_at(bool rev, bool vmax, dim3 g, cudaStream_t st, int cv, const PointDesc *d_pts,
+                                    const Ctl *c, int m, int want) {
+  auto k = rev ? (vmax ? k_combine_stage<S, true, true> : k_combine_stage<S, true, false>)
+               : (vmax ? k_combine_stage<S, false, true> : k_combine_stage<S, false, false>);
+  return launch_with_carveout(k, g, LB_THREADS_WIDE, LB_SMEM, st, cv, d_pts, c, m, want);
+}
+
+int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, bool vmax, int mask, cudaStream_t st,
                          int lb_grid, int n_points, int want) {
   const dim3 g(lb_grid, n_points);
   const int cv = step_carveout(n_points);
-  const Ctl *c = d_ctl;
   const int m = mask | (rev ? FRG_REVERSAL : 0);
-  cudaError_t e = cudaErrorInvalidValue;
-#define FRG_CS(S)                                                                                              \
-  e = rev ? launch_with_carveout(k_combine_stage<S, true>, g, LB_THREADS_WIDE, LB_SMEM, st, cv, d_pts, c, m, want) \
-          : launch_with_carveout(k_combine_stage<S, false>, g, LB_THREADS_WIDE, LB_SMEM, st, cv, d_pts, c, m, want)
+  cudaError_t e;
   switch (s) {
-    case 2: FRG_CS(2); break;
-    case 3: FRG_CS(3); break;
-    case 4: FRG_CS(4); break;
-    case 5: FRG_CS(5); break;
-    case 6: FRG_CS(6); break;
+    case 2: e = combine_stage_at<2>(rev, vmax, g, st, cv, d_pts, d_ctl, m, want); break;
+    case 3: e = combine_stage_at<3>(rev, vmax, g, st, cv, d_pts, d_ctl, m, want); break;
+    case 4: e = combine_stage_at<4>(rev, vmax, g, st, cv, d_pts, d_ctl, m, want); break;
+    case 5: e = combine_stage_at<5>(rev, vmax, g, st, cv, d_pts, d_ctl, m, want); break;
+    case 6: e = combine_stage_at<6>(rev, vmax, g, st, cv, d_pts, d_ctl, m, want); break;
     default: return -1;
   }
-#undef FRG_CS
   FRG_COUNT(1);
   return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -36,10 +36,11 @@ int launch_prepare(const PointDesc *d_pts, Ctl *d_ctl, int n, cudaStream_t st);
 // launch_sigma_stage does the self-energy part and the IO record.
 int launch_stage(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int s, int split, RhsIO *d_io,
                  cudaStream_t st, int lb_grid = 0, int n_points = 0, int want = 0);
-// 3xTF32 flows without tails: the scatter-add of the rhs of stage s - 1 fused
-// with the vertex part of stage sum s (s = 2..6; rev: the reversal reduction's
-// canonical half and mirrored reads), on the stage kernels' grid.
-int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, int mask, cudaStream_t st,
+// Split flows: the scatter-add of the rhs of stage s - 1 (channel bits and
+// FRG_TAILS of mask) fused with the vertex part of stage sum s (s = 2..6; rev:
+// the reversal reduction's canonical half and mirrored reads; vmax: keep the
+// stage input's bound for the BF16x3 slicing), on the stage kernels' grid.
+int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, bool vmax, int mask, cudaStream_t st,
                          int lb_grid, int n_points, int want);
 // Split paths: the self-energy part of stage s and the stage's rhs IO record
 // (one block per point).  Independent of the vertex part, so it may run on

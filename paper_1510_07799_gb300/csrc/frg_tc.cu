@@ -747,7 +747,7 @@ __device__ __forceinline__ bool xf_tile(const Pipe &S, const PointDesc *__restri
   const uint4 ord = korder_row<CH>(P, ti.N, w.m);
   typename XfV<PREC>::Scale scA{}, scB{};
   if constexpr (PREC == FRG_BF16X3) {
-    const float vb = fmaxf(__uint_as_float(*P.vmax), fabsf((float)P.U));
+    const float vb = fmaxf(__uint_as_float(P.vmax[io[ti.point].par]), fabsf((float)P.U));
     const int row = CH == CH_PP ? w.m : (2 * ti.N - 1) + (CH == CH_XPH ? w.m : 2 * ti.N - 2 - w.m);
     scB = slice_grid(bound_exp(vb));
     scA = slice_grid(bound_exp(P.Lmax[row] * vb * (CH == CH_DPH ? 6.f : 2.f)));
