@@ -250,7 +250,10 @@ inline cudaError_t launch_with_carveout(void (*kernel)(KArgs...), dim3 grid, dim
 // memory share spares the SM a reconfiguration between them (measured: a single
 // N = 128 point's flow step -1.3 %), but leaves an L1 too small for the
 // per-point descriptors that the blocks of a large batch read (64 points: +4.5
-// %), so contexts of more than a few points keep the default.
+// %), so contexts of more than a few points keep the default.  The kernels on
+// the side streams (self-energy, bubble weights, tails) take the same: a
+// contraction CTA cannot start on an SM whose resident blocks hold another
+// configuration until they drain, and these run beside the contraction.
 inline int step_carveout(int n_points) { return n_points <= 4 ? (int)cudaSharedmemCarveoutMaxShared : -1; }
 
 // Stage bookkeeping of the Dormand-Prince pair (coefficients in frg_integrator.cu).

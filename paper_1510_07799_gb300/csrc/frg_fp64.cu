@@ -174,13 +174,16 @@ int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int ma
 }
 
 // ------------------------------------ bubble weights + self-energy, fused ----
-// Everything that needs only the propagators, in one launch after k_bubble_gs:
-// every block stages G and S of its point in shared memory (FP64 divisions are
-// slow on this part, so they are done once per frequency), then computes either
-// one row of a bubble-weight table (blocks [0, 2(2 maxN - 1))) or one
-// self-energy entry dSigma(w)/dl (blocks beyond), with 128 threads over the
-// loop index p and a fixed-order block reduction.  (With the frequency-box
-// tails, k_tail_finish adds the self-energy's tail constant afterwards.)
+// Everything that needs only the propagators, in one launch after k_bubble_gs
+// (which forms G and S once per frequency: FP64 divisions are slow on this
+// part): every block computes either one row of a bubble-weight table (blocks
+// [0, 2(2 maxN - 1))) or one self-energy entry dSigma(w)/dl (blocks beyond),
+// with 128 threads over the loop index p and a fixed-order block reduction.
+// (With the frequency-box tails, k_tail_finish adds the self-energy's tail
+// constant afterwards.)  G and S are read from global memory, not staged: a
+// thread reads each value it needs about once, and the small static shared
+// memory lets the self-energy blocks of a split flow share an SM with the
+// contraction, which runs beside them and leaves about 8 KB of it.
 template <bool SPLIT>
 __global__ void __launch_bounds__(128)
     k_bubble_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int maxN, int sigma_on, int b0) {
@@ -196,13 +199,9 @@ __global__ void __launch_bounds__(128)
   const int row = table ? b % nrow_max : 0;
   const int w = table ? 0 : b - 2 * nrow_max;
   if (table ? row >= 2 * N - 1 : w >= N) return;
-  __shared__ double2 sG[FRG_MAX_N], sS[FRG_MAX_N];
+  const double2 *__restrict__ sG = P.G;
+  const double2 *__restrict__ sS = P.S;
   const double L = *o.lam;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    sG[i] = P.G[i];
-    sS[i] = P.S[i];
-  }
-  __syncthreads();
   if (!table) {
     // dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]
     double2 acc = make_double2(0.0, 0.0);
@@ -292,8 +291,12 @@ __global__ void __launch_bounds__(128)
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
                         cudaStream_t st, int parts) {
   const int nrow_max = 2 * maxN - 1;
+  // split paths run these beside the stage kernel and the contraction
+  const int cv = split ? step_carveout(n_points) : -1;
+  cudaError_t e = cudaSuccess;
   if (parts & BUBBLE_TABLES) {
-    k_bubble_gs<<<dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0, st>>>(d_pts, d_io);
+    e = launch_with_carveout(k_bubble_gs, dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0,
+                             st, cv, d_pts, d_io);
     FRG_COUNT(1);
   }
   // blocks [0, 2 nrow_max): table rows; [2 nrow_max, 2 nrow_max + maxN): self-energy entries
@@ -301,13 +304,13 @@ int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points,
   const int b1 = (parts & BUBBLE_SIGMA) ? 2 * nrow_max + maxN : 2 * nrow_max;
   if (b1 > b0) {
     const dim3 g(b1 - b0, n_points);
-    if (split)
-      k_bubble_sigma<true><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0, b0);
-    else
-      k_bubble_sigma<false><<<g, 128, 0, st>>>(d_pts, d_io, maxN, (mask & 8) != 0, b0);
+    const int sig = (mask & 8) != 0;
+    const cudaError_t e2 = split ? launch_with_carveout(k_bubble_sigma<true>, g, 128, 0, st, cv, d_pts, d_io, maxN, sig, b0)
+                                 : launch_with_carveout(k_bubble_sigma<false>, g, 128, 0, st, cv, d_pts, d_io, maxN, sig, b0);
+    if (e == cudaSuccess) e = e2;
     FRG_COUNT(1);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 // ------------------------------------------------ frequency-box tails ----
@@ -487,18 +490,22 @@ __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__rest
 
 int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
                      int parts) {
+  // a split flow runs these beside the stage kernel and the contraction
+  const int cv = step_carveout(n_points);
+  cudaError_t e = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
   if (parts & TAIL_WINDOW) {
     const int W = FRG_TAIL_FACTOR * maxN;
-    k_tail_gs<<<dim3((W + TAIL_GS_THREADS - 1) / TAIL_GS_THREADS, n_points), TAIL_GS_THREADS, 0, st>>>(d_pts, d_io);
+    e = launch_with_carveout(k_tail_gs, dim3((W + TAIL_GS_THREADS - 1) / TAIL_GS_THREADS, n_points), TAIL_GS_THREADS,
+                             0, st, cv, d_pts, d_io);
     FRG_COUNT(1);
-    k_tail_sums<<<dim3(2 * (2 * maxN - 1), n_points), 128, 0, st>>>(d_pts, d_io, maxN, mask);
+    e2 = launch_with_carveout(k_tail_sums, dim3(2 * (2 * maxN - 1), n_points), 128, 0, st, cv, d_pts, d_io, maxN, mask);
     FRG_COUNT(1);
   }
   if (parts & TAIL_FINISH) {
-    k_tail_finish<<<n_points, 256, 0, st>>>(d_pts, d_io, mask);
+    e3 = launch_with_carveout(k_tail_finish, dim3(n_points), 256, 0, st, cv, d_pts, d_io, mask);
     FRG_COUNT(1);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  return e == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int launch_add_tails(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, cudaStream_t st) {

@@ -668,17 +668,20 @@ int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, bo
 }
 
 int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st) {
+  // beside the stage kernel and the contraction: their carveout
+  const int cv = step_carveout(n_points);
+  cudaError_t e;
   switch (s) {
-    case 0: k_sigma_stage<0><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
-    case 1: k_sigma_stage<1><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
-    case 2: k_sigma_stage<2><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
-    case 3: k_sigma_stage<3><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
-    case 4: k_sigma_stage<4><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
-    case 5: k_sigma_stage<5><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
-    default: k_sigma_stage<6><<<n_points, SIG_THREADS, 0, st>>>(d_pts, d_ctl, d_io); break;
+    case 0: e = launch_with_carveout(k_sigma_stage<0>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
+    case 1: e = launch_with_carveout(k_sigma_stage<1>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
+    case 2: e = launch_with_carveout(k_sigma_stage<2>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
+    case 3: e = launch_with_carveout(k_sigma_stage<3>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
+    case 4: e = launch_with_carveout(k_sigma_stage<4>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
+    case 5: e = launch_with_carveout(k_sigma_stage<5>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
+    default: e = launch_with_carveout(k_sigma_stage<6>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;
   }
   FRG_COUNT(1);
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int split, cudaStream_t st) {
