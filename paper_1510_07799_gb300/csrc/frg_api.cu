@@ -341,8 +341,9 @@ static int stage_grid(const frg_ctx *ctx) { return ctx->rev_on ? ctx->lb_grid_ha
 // the stage input is formed by this function's stage kernel).  Side stream:
 // the self-energy part of the stage input, the propagators and the
 // bubble-weight tables, beside the stage kernel's vertex part on the main
-// stream; then the self-energy rhs, which reads the vertex stage input,
-// beside the contraction.  The frequency-box tail constants (a window of
+// stream; then the self-energy rhs, which reads the vertex stage input: the
+// contraction's epilogue warps form it before their first tile (flows with
+// channel products and without tails), else a kernel beside the contraction.  The frequency-box tail constants (a window of
 // propagators of their own) run on a third stream from the self-energy stage
 // input on; their last kernel, after the self-energy rhs, adds the
 // self-energy's constant to it.  The scatter-add waits for all of them (it
@@ -382,7 +383,11 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool defer
        "stage sum");
   CK(cudaEventRecord(ctx->ev_stage, st), "stage");
   CK(cudaStreamWaitEvent(ss, ctx->ev_stage, 0), "stage");
-  LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_SIGMA), "self-energy rhs");
+  // with the channel products and no tails, the contraction's epilogue warps
+  // form the self-energy rhs; else a kernel beside it
+  const bool sig_in_tc = chmask && !tails;
+  if (!sig_in_tc)
+    LK(launch_bubble_sigma(ctx->d_pts, io, ctx->n, ctx->maxN, 1, ctx->mask, ss, BUBBLE_SIGMA), "self-energy rhs");
   if (tails) {
     // the tail constants, the self-energy's added to the self-energy rhs
     CK(cudaEventRecord(ctx->ev_srhs, ss), "self-energy rhs");
@@ -394,7 +399,8 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool defer
   CK(cudaEventRecord(ctx->ev_sig, ss), "self-energy");
   if (chmask) {
     LK(tc_run(ctx->tc, ctx->d_pts, io, -1, chmask, st, nullptr, nullptr, ctx->n, ctx->maxN, ctx->ev_join, tails,
-              ctx->ev_sig, true, ctx->rev_on, err, ctx->cross, !deferred),
+              ctx->ev_sig, true, ctx->rev_on, err, ctx->cross, !deferred,
+              sig_in_tc ? 1 | ((ctx->mask & 8) ? 2 : 0) : 0),
        "split contraction");
   } else if (!deferred) {
     // no vertex channel: the scatter-add writes the zero (or tail-only)

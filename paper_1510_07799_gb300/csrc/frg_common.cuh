@@ -245,6 +245,65 @@ inline cudaError_t launch_with_carveout(void (*kernel)(KArgs...), dim3 grid, dim
   cfg.numAttrs = carveout < 0 ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
+// Vertex entry V(i1, i2, i3) of an input (FP64, or FP32 on the split paths)
+// under the box rule: the bare U wherever an index leaves the box.
+template <bool SPLIT>
+__device__ __forceinline__ double2 vload(const void *gam, int N, double U, int i1, int i2, int i3) {
+  const int i4 = i1 + i2 - i3;
+  if (inbox(N, i1) && inbox(N, i2) && inbox(N, i3) && inbox(N, i4)) {
+    const size_t at = ((size_t)i1 * N + i2) * N + i3;
+    if (SPLIT) {
+      const float2 v = static_cast<const float2 *>(gam)[at];
+      return make_double2((double)v.x, (double)v.y);
+    }
+    return static_cast<const double2 *>(gam)[at];
+  }
+  return make_double2(U, 0.0);
+}
+
+// Barriers for sigma_entry: the whole (128-thread) block, or a named barrier
+// of 128 threads.
+struct SyncBlock {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int ID>
+struct SyncNamed {
+  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, 128;" ::"n"(ID) : "memory"); }
+};
+
+// One self-energy rhs entry, dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) -
+// V(w,p,p)], by 128 threads (t in [0, 128)): thread t sums p = t, t + 128, ...
+// in FP64, each warp folds its sums by xor shuffles, thread 0 adds the four
+// warp sums in order (part: 4 double2 of shared memory; sync(): a barrier of
+// the 128 threads, after which part may be reused).  The same order wherever
+// it runs, so every path gives the same bits.
+template <bool SPLIT, typename Sync>
+__device__ __forceinline__ void sigma_entry(const PointDesc &P, const RhsIO &o, int w, int t, bool sigma_on,
+                                            double2 *part, Sync sync) {
+  const int N = P.N;
+  double2 acc = make_double2(0.0, 0.0);
+  if (sigma_on) {
+    for (int p = t; p < N; p += 128) {
+      const double2 a = vload<SPLIT>(o.gam, N, P.U, w, p, w);
+      const double2 c = vload<SPLIT>(o.gam, N, P.U, w, p, p);
+      cfma(acc, P.S[p], make_double2(2.0 * a.x - c.x, 2.0 * a.y - c.y));
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if ((t & 31) == 0) part[t >> 5] = acc;
+  sync();
+  if (t == 0) {
+    double2 s = part[0];
+    for (int j = 1; j < 4; ++j) s = cadd(s, part[j]);
+    const double f = (*o.lam) * P.T;
+    o.dsig[w] = make_double2(s.x * f, s.y * f);
+  }
+  sync();
+}
+
 // Carveout of the split paths' stage and combine kernels, which alternate with
 // the contraction (nearly all of an SM's shared memory): the largest shared
 // memory share spares the SM a reconfiguration between them (measured: a single

@@ -119,21 +119,6 @@ int launch_bubble(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int m
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// -------------------------------------------------------- vertex access ----
-template <bool SPLIT>
-__device__ __forceinline__ double2 vload(const void *gam, int N, double U, int i1, int i2, int i3) {
-  const int i4 = i1 + i2 - i3;
-  if (inbox(N, i1) && inbox(N, i2) && inbox(N, i3) && inbox(N, i4)) {
-    const size_t at = ((size_t)i1 * N + i2) * N + i3;
-    if (SPLIT) {
-      const float2 v = static_cast<const float2 *>(gam)[at];
-      return make_double2((double)v.x, (double)v.y);
-    }
-    return static_cast<const double2 *>(gam)[at];
-  }
-  return make_double2(U, 0.0);
-}
-
 // ------------------------------------------------------------ self-energy ----
 // dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]; one warp per w, FP64
 // input (the allocation-free entry point; the context paths use the fused
@@ -203,28 +188,8 @@ __global__ void __launch_bounds__(128)
   const double2 *__restrict__ sS = P.S;
   const double L = *o.lam;
   if (!table) {
-    // dSigma(w)/dl = L T sum_p S(p) [2 V(w,p,w) - V(w,p,p)]
-    double2 acc = make_double2(0.0, 0.0);
-    if (sigma_on) {
-      for (int p = threadIdx.x; p < N; p += blockDim.x) {
-        const double2 a = vload<SPLIT>(o.gam, N, P.U, w, p, w);
-        const double2 c = vload<SPLIT>(o.gam, N, P.U, w, p, p);
-        cfma(acc, sS[p], make_double2(2.0 * a.x - c.x, 2.0 * a.y - c.y));
-      }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
     __shared__ double2 part[4];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double2 t = part[0];
-      for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = cadd(t, part[j]);
-      const double f = L * P.T;
-      o.dsig[w] = make_double2(t.x * f, t.y * f);
-    }
+    sigma_entry<SPLIT>(P, o, w, threadIdx.x, sigma_on != 0, part, SyncBlock{});
     return;
   }
   // Lpp[s][p] = Lb(p, s-p), Lph[Q+N-1][p] = Lb(p, p+Q); split paths also get

@@ -1017,11 +1017,38 @@ __device__ __forceinline__ bool epi_tile(const Pipe &S, const PointDesc *__restr
   return true;
 }
 
+// The self-energy rhs of every point of a split flow (sig_points of them), by
+// the epilogue warps before their first tile, while the first products are
+// under way: warps 0-3 and 4-7 form two groups of 128 threads, and entry g of
+// the points' concatenated entries goes to CTA g % grid, group (g / grid) % 2.
+// Run here rather than as a kernel beside the contraction: blocks of another
+// kernel on an SM keep a contraction CTA from starting there until they end.
+template <int GRP>
+__device__ __forceinline__ void sigma_rhs_group(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                                int npts, bool on, int t, double2 *part) {
+  const int G = gridDim.x;
+  int pi = 0, base = 0;
+  for (int g = blockIdx.x + G * GRP;; g += 2 * G) {
+    while (pi < npts && g >= base + pts[pi].N) base += pts[pi++].N;
+    if (pi >= npts) break;
+    if (io[pi].active) sigma_entry<true>(pts[pi], io[pi], g - base, t, on, part, SyncNamed<1 + GRP>{});
+  }
+}
+__device__ __forceinline__ void sigma_rhs(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
+                                          int npts, bool on, int warp, int lane, float *stg) {
+  const int grp = warp >> 2, t = ((warp & 3) << 5) | lane;
+  double2 *part = reinterpret_cast<double2 *>(stg + grp * 4 * (EPI_STG / 4));
+  if (grp == 0)
+    sigma_rhs_group<0>(pts, io, npts, on, t, part);
+  else
+    sigma_rhs_group<1>(pts, io, npts, on, t, part);
+}
+
 template <int PREC, bool X>
 __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                                          const StWork *__restrict__ work, const int *__restrict__ cta_start,
                                          const int *__restrict__ nt_of, unsigned *__restrict__ err,
-                                         const CUtensorMap *__restrict__ maps, int half) {
+                                         const CUtensorMap *__restrict__ maps, int half, int sig_points, int sig_on) {
   extern __shared__ uint8_t smem_raw[];
   // offset the shared array itself (keeps the shared state space for ld/st.shared)
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -1094,6 +1121,7 @@ __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, cons
       if (!FRG_BY_CH_P(mma_tile, S, pts, io, w, nt_of, it, tb, lane, X)) break;
     }
   } else {
+    if (sig_points) sigma_rhs(pts, io, sig_points, sig_on != 0, warp, lane, S.epi_stg);
     TBuf tb;
     for (int wi = w0; wi < w1; ++wi) {
       const StWork w = work[wi];
@@ -1111,30 +1139,30 @@ __device__ __forceinline__ void contract(const PointDesc *__restrict__ pts, cons
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_tf32(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, const StWork *__restrict__ work,
                     const int *__restrict__ cta_start, const int *__restrict__ nt_of, unsigned *__restrict__ err,
-                    const CUtensorMap *__restrict__ maps, int half) {
-  contract<FRG_3XTF32, false>(pts, io, work, cta_start, nt_of, err, maps, half);
+                    const CUtensorMap *__restrict__ maps, int half, int sig_points, int sig_on) {
+  contract<FRG_3XTF32, false>(pts, io, work, cta_start, nt_of, err, maps, half, sig_points, sig_on);
 }
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_bf16x3(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                       const StWork *__restrict__ work, const int *__restrict__ cta_start,
                       const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps,
-                      int half) {
-  contract<FRG_BF16X3, false>(pts, io, work, cta_start, nt_of, err, maps, half);
+                      int half, int sig_points, int sig_on) {
+  contract<FRG_BF16X3, false>(pts, io, work, cta_start, nt_of, err, maps, half, sig_points, sig_on);
 }
 // The same for crossing-reduced schedules (cross_tile).
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_tf32_x(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                       const StWork *__restrict__ work, const int *__restrict__ cta_start,
                       const int *__restrict__ nt_of, unsigned *__restrict__ err, const CUtensorMap *__restrict__ maps,
-                      int half) {
-  contract<FRG_3XTF32, true>(pts, io, work, cta_start, nt_of, err, maps, half);
+                      int half, int sig_points, int sig_on) {
+  contract<FRG_3XTF32, true>(pts, io, work, cta_start, nt_of, err, maps, half, sig_points, sig_on);
 }
 __global__ void __launch_bounds__(THREADS, 1)
     k_contract_bf16x3_x(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io,
                         const StWork *__restrict__ work, const int *__restrict__ cta_start,
                         const int *__restrict__ nt_of, unsigned *__restrict__ err,
-                        const CUtensorMap *__restrict__ maps, int half) {
-  contract<FRG_BF16X3, true>(pts, io, work, cta_start, nt_of, err, maps, half);
+                        const CUtensorMap *__restrict__ maps, int half, int sig_points, int sig_on) {
+  contract<FRG_BF16X3, true>(pts, io, work, cta_start, nt_of, err, maps, half, sig_points, sig_on);
 }
 }  // namespace st
 
@@ -1415,7 +1443,7 @@ namespace frg {
 int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN, cudaEvent_t wait_before,
            int tails, cudaEvent_t wait_combine, bool layouts_ready, bool half, bool err, bool cross,
-           bool combine) {
+           bool combine, int sigma) {
   // layouts of the stage input: W for the crossed channel, X and Z for the
   // direct one
   if ((chmask & 6) && !layouts_ready) {
@@ -1427,13 +1455,14 @@ int tc_run(TcPlan *p, const PointDesc *d_pts, const RhsIO *d_io, int point, int 
   const std::vector<TcPlan::Sched> &scv = half ? (cross ? p->sched_cross : p->sched_half) : p->sched;
   if ((chmask & 7) != p->mask || point >= p->n || scv.empty()) return -1;
   const TcPlan::Sched &sc = scv[point < 0 ? 0 : 1 + point];
+  if (sigma && (!sc.grid || point >= 0)) return -1;  // the whole flow's points only
   if (sc.grid) {
     const bool x = half && cross;
     auto kern = p->precision == FRG_3XTF32 ? (x ? tc::st::k_contract_tf32_x : tc::st::k_contract_tf32)
                                            : (x ? tc::st::k_contract_bf16x3_x : tc::st::k_contract_bf16x3);
     const int smem = p->precision == FRG_3XTF32 ? tc::st::OpL<FRG_3XTF32>::SMEM : tc::st::OpL<FRG_BF16X3>::SMEM;
     kern<<<sc.grid, tc::st::THREADS, smem, st>>>(d_pts, d_io, sc.d_work, sc.d_start, p->d_nt, p->d_err, p->d_maps,
-                                                 half ? 1 : 0);
+                                                 half ? 1 : 0, sigma ? n_points : 0, (sigma & 2) ? 1 : 0);
     FRG_COUNT(1);
     if (cudaGetLastError() != cudaSuccess) return -3;
   }

@@ -42,10 +42,13 @@ int tc_wait_selftest(unsigned *d_err, double limit_ms, cudaStream_t st);
 // (optional) are recorded after the relayout and after the products; the
 // products wait for wait_before (optional: the bubble weights computed on
 // another stream), the combine for wait_combine (optional: the tail constants
-// and the self-energy rhs computed on another stream).
+// and the self-energy rhs computed on another stream).  sigma (flows of all
+// points, point = -1): the contraction also forms the self-energy rhs of every
+// active point (bit 0: on; bit 1: the self-energy channel is enabled, else
+// the rhs is zero).
 int tc_run(TcPlan *plan, const PointDesc *d_pts, const RhsIO *d_io, int point, int chmask, cudaStream_t st,
            cudaEvent_t ev_gather, cudaEvent_t ev_contract, int n_points, int maxN,
            cudaEvent_t wait_before = nullptr, int tails = 0, cudaEvent_t wait_combine = nullptr,
            bool layouts_ready = false, bool half = false, bool err = false, bool cross = false,
-           bool combine = true);
+           bool combine = true, int sigma = 0);
 }  // namespace frg
