@@ -365,7 +365,7 @@ static int run_split_stage(frg_ctx *ctx, int s, bool err, bool fused, bool defer
   if (fused) CK(cudaStreamWaitEvent(st, ctx->ev_sig, 0), "self-energy");
   CK(cudaEventRecord(ctx->ev_fork, st), "fork");
   CK(cudaStreamWaitEvent(ss, ctx->ev_fork, 0), "fork");
-  LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, io, s, ctx->n, ss), "self-energy stage");
+  LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, io, s, ctx->n, ss, ctx->mask), "self-energy stage");
   if (tails) {
     CK(cudaEventRecord(ctx->ev_sst, ss), "self-energy stage");
     CK(cudaStreamWaitEvent(ts, ctx->ev_sst, 0), "self-energy stage");
@@ -994,7 +994,7 @@ int frg_autotune(frg_ctx *ctx, frg_tune *out) {
     LK(launch_stage(ctx->d_pts, ctx->d_ctl, seg(ctx), ctx->nseg, 0, 1, ctx->d_io_stage, st, stage_grid(ctx), ctx->n,
                     ctx->lb_want),
        "stage 0");
-    LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->n, st), "self-energy stage 0");
+    LK(launch_sigma_stage(ctx->d_pts, ctx->d_ctl, ctx->d_io_stage, 0, ctx->n, st, ctx->mask), "self-energy stage 0");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "events");
     CK(cudaEventCreate(&e1), "events");

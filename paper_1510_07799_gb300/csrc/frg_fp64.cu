@@ -256,8 +256,8 @@ __global__ void __launch_bounds__(128)
 int launch_bubble_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int split, int mask,
                         cudaStream_t st, int parts) {
   const int nrow_max = 2 * maxN - 1;
-  // split paths run these beside the stage kernel and the contraction
-  const int cv = split ? step_carveout(n_points) : -1;
+  // split flows run these beside the stage kernel
+  const int cv = split ? side_carveout(n_points, mask) : -1;
   cudaError_t e = cudaSuccess;
   if (parts & BUBBLE_TABLES) {
     e = launch_with_carveout(k_bubble_gs, dim3((maxN + GS_PER_BLOCK - 1) / GS_PER_BLOCK, n_points), GS_PER_BLOCK, 0,
@@ -455,8 +455,7 @@ __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__rest
 
 int launch_tail_sums(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int maxN, int mask, cudaStream_t st,
                      int parts) {
-  // a split flow runs these beside the stage kernel and the contraction
-  const int cv = step_carveout(n_points);
+  const int cv = -1;  // the default carveout (side_carveout)
   cudaError_t e = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
   if (parts & TAIL_WINDOW) {
     const int W = FRG_TAIL_FACTOR * maxN;

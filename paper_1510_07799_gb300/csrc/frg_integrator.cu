@@ -667,9 +667,9 @@ int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, bo
   return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st) {
-  // beside the stage kernel and the contraction: their carveout
-  const int cv = step_carveout(n_points);
+int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st,
+                       int mask) {
+  const int cv = side_carveout(n_points, mask);
   cudaError_t e;
   switch (s) {
     case 0: e = launch_with_carveout(k_sigma_stage<0>, n_points, SIG_THREADS, 0, st, cv, d_pts, d_ctl, d_io); break;

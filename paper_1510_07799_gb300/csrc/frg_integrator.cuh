@@ -45,7 +45,8 @@ int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, bo
 // Split paths: the self-energy part of stage s and the stage's rhs IO record
 // (one block per point).  Independent of the vertex part, so it may run on
 // another stream beside launch_stage's kernel.
-int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st);
+int launch_sigma_stage(const PointDesc *d_pts, Ctl *d_ctl, RhsIO *d_io, int s, int n_points, cudaStream_t st,
+                       int mask);
 // Dynamic shared-memory limits of the split stage kernels (once per set-up).
 int stage_split_init();
 int launch_error(const PointDesc *d_pts, Ctl *d_ctl, SegTable seg, int nblk, int split, cudaStream_t st);
