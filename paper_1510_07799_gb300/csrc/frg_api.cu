@@ -343,13 +343,13 @@ static int stage_grid(const frg_ctx *ctx) { return ctx->rev_on ? ctx->lb_grid_ha
 // bubble-weight tables, beside the stage kernel's vertex part on the main
 // stream; then the self-energy rhs, which reads the vertex stage input: the
 // contraction's epilogue warps form it before their first tile (flows with
-// channel products and without tails), else a kernel beside the contraction.  The frequency-box tail constants (a window of
-// propagators of their own) run on a third stream from the self-energy stage
-// input on; their last kernel, after the self-energy rhs, adds the
-// self-energy's constant to it.  The scatter-add waits for all of them (it
-// adds the vertex tails and, for k7, takes the self-energy error), and so does
-// everything after it: the next stage kernel overwrites the vertex input that
-// the self-energy rhs reads.
+// channel products and without tails), else a kernel beside the contraction.
+// The frequency-box tail constants (a window of propagators of their own) run
+// on a third stream from the self-energy stage input on; their last kernel,
+// after the self-energy rhs, adds the self-energy's constant to it.  The
+// scatter-add waits for all of them (it adds the vertex tails and, for k7,
+// takes the self-energy error), and so does everything after it: the next
+// stage kernel overwrites the vertex input that the self-energy rhs reads.
 // The tail constants and the BF16x3 vertex bound are kept per stage parity
 // (RhsIO.par): the next rhs's side-stream work may run while this rhs's
 // scatter-add still reads them.
@@ -1079,6 +1079,7 @@ int frg_get_state(frg_ctx *ctx, int point, void *d_gamma, void *d_sigma, double 
   const Ctl &c = ctx->h_ctl[point];
   const PointDesc &P = ctx->hpts[point];
   const double2 *y = P.ybuf[c.yslot];
+  if (ctx->split && ctx->rev_on) LK(launch_mirror_state(ctx->d_pts, ctx->n, ctx->stream), "copy state");
   if (d_gamma) CK(cudaMemcpyAsync(d_gamma, y, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "copy state");
   if (d_sigma) CK(cudaMemcpyAsync(d_sigma, y + P.n3, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "copy state");
   if (Lambda) *Lambda = std::exp(c.t);
@@ -1095,6 +1096,9 @@ int frg_set_state(frg_ctx *ctx, int point, const void *d_gamma, const void *d_si
   if (h > 0.0) return fail(ctx, FRG_EINVAL, "h must be <= 0");
   DevGuard g(ctx->dev);
   const PointDesc &P = ctx->hpts[point];
+  // the other points' states whole before the flows may switch to every
+  // transfer (their stage kernels then read whole states)
+  if (ctx->split && ctx->rev_on) LK(launch_mirror_state(ctx->d_pts, ctx->n, ctx->stream), "set state");
   CK(cudaMemcpyAsync(P.ybuf[0], d_gamma, (size_t)P.n3 * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "set state");
   if (d_sigma)
     CK(cudaMemcpyAsync(P.ybuf[0] + P.n3, d_sigma, (size_t)P.N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream), "set state");
@@ -1131,6 +1135,7 @@ int frg_observables(frg_ctx *ctx, int point, frg_obs *out) {
   std::vector<double2> sig(N);
   double2 ueff;
   const double2 *y = P.ybuf[c.yslot];
+  if (ctx->split && ctx->rev_on) LK(launch_mirror_state(ctx->d_pts, ctx->n, ctx->stream), "observables");
   CK(cudaMemcpyAsync(sig.data(), y + P.n3, N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream), "observables");
   CK(cudaMemcpyAsync(&ueff, y + ((size_t)hN * N + hN) * N + hN, sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream),
      "observables");

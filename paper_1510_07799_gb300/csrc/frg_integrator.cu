@@ -355,12 +355,10 @@ __device__ __forceinline__ void stage_block(const PointDesc &P, const Ctl &c, in
         const double2 y0 = P.ybuf[ys][i], y1 = P.ybuf[ys][i + 1];
         const double2 yn0 = make_double2(fma(h, f2d(sh[0]) + f2d(sl[0]), y0.x), fma(h, f2d(sh[1]) + f2d(sl[1]), y0.y));
         const double2 yn1 = make_double2(fma(h, f2d(sh[2]) + f2d(sl[2]), y1.x), fma(h, f2d(sh[3]) + f2d(sl[3]), y1.y));
+        // the canonical half only under the reversal reduction: the readers
+        // of a whole state mirror it first (launch_mirror_state)
         P.ybuf[ys ^ 1][i] = yn0;
         P.ybuf[ys ^ 1][i + 1] = yn1;
-        if (half) {
-          P.ybuf[ys ^ 1][n3 - 1 - i] = make_double2(yn0.x, -yn0.y);
-          P.ybuf[ys ^ 1][n3 - 2 - i] = make_double2(yn1.x, -yn1.y);
-        }
         float4 lo;
         split_pair(yn0, yn1, out, lo);
         *reinterpret_cast<float4 *>(P.yhi[ys ^ 1] + i) = out;

@@ -103,6 +103,30 @@ __global__ void k_check_reversal(const double2 *__restrict__ y, int N, int *asym
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *asym = 1;
 }
 
+// Under the reversal reduction the seventh stage kernel writes the FP64
+// candidate state's vertex for the canonical half only; the readers of a
+// whole state (frg_get_state, frg_observables, a switch to full flows) first
+// fill in the other half as conjugates: y[n3 - 1 - i] = conj(y[i]), i < n3/2,
+// in both state slots of every point whose flow keeps the canonical half.
+__global__ void k_mirror_state(const PointDesc *__restrict__ pts) {
+  const PointDesc &P = pts[blockIdx.y];
+  if (!P.rev_half) return;
+  const int n3 = P.n3, h = n3 / 2;
+  for (int s = 0; s < 2; ++s) {
+    double2 *y = P.ybuf[s];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < h; i += gridDim.x * blockDim.x) {
+      const double2 a = y[i];
+      y[n3 - 1 - i] = make_double2(a.x, -a.y);
+    }
+  }
+}
+
+int launch_mirror_state(const PointDesc *d_pts, int n_points, cudaStream_t st) {
+  k_mirror_state<<<dim3(296, n_points), 256, 0, st>>>(d_pts);
+  FRG_COUNT(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 int launch_check_reversal(const double2 *y, int N, int *d_asym, cudaStream_t st) {
   k_check_reversal<<<256, 256, 0, st>>>(y, N, d_asym);
   FRG_COUNT(1);
