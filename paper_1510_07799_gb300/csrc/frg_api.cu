@@ -956,17 +956,27 @@ int frg_advance(frg_ctx *ctx, long max_attempts, frg_flow_stats *stats) {
     ctx->need_k1 = false;
   }
   if (max_attempts > 0 && !ctx->step_exec && (rc = build_step_graph(ctx))) return rc;
-  const long period = ctx->split ? 8 : 2;
-  long a = 0;
+  // attempts per burst between reads of the controller state: up to 16, but
+  // no more than the flows seem to need (the slowest point's remaining
+  // interval at its current step, which the step sizes usually outgrow), so
+  // that few attempts run after every point is done
+  const long period = ctx->split ? 16 : 2;
+  long a = 0, est = period;
   while (a < max_attempts) {
-    const long burst = std::min(period, max_attempts - a);
+    const long burst = std::min(std::max(1L, std::min(period, est)), max_attempts - a);
     for (long i = 0; i < burst; ++i)
       if ((rc = launch_step(ctx))) return rc;
     a += burst;
     if ((rc = sync_ctl(ctx))) return rc;
     bool all = true;
-    for (int i = 0; i < ctx->n; ++i) all = all && ctx->h_ctl[i].done;
+    double rem = 0.0;
+    for (int i = 0; i < ctx->n; ++i) {
+      const Ctl &c = ctx->h_ctl[i];
+      all = all && c.done;
+      if (!c.done && c.h != 0.0) rem = std::max(rem, (c.t - ctx->hpts[i].l_end) / std::fabs(c.h));
+    }
     if (all) break;
+    est = (long)(0.6 * std::min(rem, 1e6));
   }
   if (max_attempts == 0 && (rc = sync_ctl(ctx))) return rc;
   fill_stats(ctx, stats);
