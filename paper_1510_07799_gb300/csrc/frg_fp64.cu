@@ -165,10 +165,8 @@ int launch_sigma(const PointDesc *d_pts, const RhsIO *d_io, int n_points, int ma
 // [0, 2(2 maxN - 1))) or one self-energy entry dSigma(w)/dl (blocks beyond),
 // with 128 threads over the loop index p and a fixed-order block reduction.
 // (With the frequency-box tails, k_tail_finish adds the self-energy's tail
-// constant afterwards.)  G and S are read from global memory, not staged: a
-// thread reads each value it needs about once, and the small static shared
-// memory lets the self-energy blocks of a split flow share an SM with the
-// contraction, which runs beside them and leaves about 8 KB of it.
+// constant afterwards.)  G and S are read from global memory, not staged in
+// shared memory: a thread reads each value it needs about once.
 template <bool SPLIT>
 __global__ void __launch_bounds__(128)
     k_bubble_sigma(const PointDesc *__restrict__ pts, const RhsIO *__restrict__ io, int maxN, int sigma_on, int b0) {
@@ -184,8 +182,8 @@ __global__ void __launch_bounds__(128)
   const int row = table ? b % nrow_max : 0;
   const int w = table ? 0 : b - 2 * nrow_max;
   if (table ? row >= 2 * N - 1 : w >= N) return;
-  const double2 *__restrict__ sG = P.G;
-  const double2 *__restrict__ sS = P.S;
+  const double2 *__restrict__ Gp = P.G;
+  const double2 *__restrict__ Sp = P.S;
   const double L = *o.lam;
   if (!table) {
     __shared__ double2 part[4];
@@ -198,7 +196,7 @@ __global__ void __launch_bounds__(128)
   for (int p = threadIdx.x; p < N; p += blockDim.x) {
     const int q = which == 0 ? row - p : p + (row - (N - 1));
     double2 v = make_double2(0.0, 0.0);
-    if (inbox(N, q)) v = cadd(cmul(sS[p], sG[q]), cmul(sG[p], sS[q]));
+    if (inbox(N, q)) v = cadd(cmul(Sp[p], Gp[q]), cmul(Gp[p], Sp[q]));
     (which == 0 ? P.Lpp : P.Lph)[(size_t)row * N + p] = v;
     if (P.Lpp32) {
       const float2 f = make_float2((float)v.x, (float)v.y);
@@ -398,9 +396,9 @@ __global__ void k_tail_finish(const PointDesc *__restrict__ pts, const RhsIO *__
 }
 
 // dGamma(k1,k2,k3) += tail_pp[k1 + k2] + tail_xph[k2 - k3] (FP32 or FP64
-// output, the constants rounded to the output's precision; the self-energy
-// rhs has taken its own tail).  A block takes TAIL_ROWS rows (k1, k2); thread
-// k3 walks them.
+// output, the constants rounded to the output's precision; k_tail_finish has
+// added the self-energy's).  A block takes TAIL_ROWS rows (k1, k2); thread k3
+// walks them.
 constexpr int TAIL_ROWS = 16;
 __global__ void __launch_bounds__(FRG_MAX_N) k_add_tails(const PointDesc *__restrict__ pts,
                                                          const RhsIO *__restrict__ io) {
