@@ -293,10 +293,12 @@ __device__ __forceinline__ void split_pair(const double2 y0, const double2 y1, f
 // bubble weights that depend on it alone).
 // Threads of a stage block: wide blocks (the canonical half of the reversal
 // reduction has half as many blocks with work); the seventh stage, with the
-// FP64 state update and the partial error sum, at three blocks per SM for its
-// registers.
+// FP64 state update and the partial error sum, narrow blocks at six per SM for
+// its registers (the canonical half's blocks then fit in one wave).
 template <int S>
-__host__ __device__ constexpr int stage_threads() { return LB_THREADS_WIDE; }
+__host__ __device__ constexpr int stage_threads() { return S == 6 ? LB_THREADS : LB_THREADS_WIDE; }
+template <int S>
+__host__ __device__ constexpr int stage_minblocks() { return S == 6 ? 6 : LB_MINBLOCKS_WIDE; }
 
 // One layout block of split stage S for a point whose flow is not done; sm:
 // the block in shared memory (LB x LAP float2).  VMAX: fold the block's bound of
@@ -385,7 +387,7 @@ __device__ __forceinline__ void stage_block(const PointDesc &P, const Ctl &c, in
 }
 
 template <int S>
-__global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_WIDE)
+__global__ void __launch_bounds__(stage_threads<S>(), stage_minblocks<S>())
     k_stage_split(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int want) {
   extern __shared__ float4 lsm4[];
   const Ctl &c = ctl[blockIdx.y];
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(stage_threads<S>(), S == 6 ? 3 : LB_MINBLOCKS_
 // keeps the vertex bound of parity S (VMAX: BF16x3 flows, whose contraction
 // reads it).
 template <int S, bool REV, bool VMAX>
-__global__ void __launch_bounds__(LB_THREADS_WIDE, S == 6 ? 3 : LB_MINBLOCKS_WIDE)
+__global__ void __launch_bounds__(stage_threads<S>(), stage_minblocks<S>())
     k_combine_stage(const PointDesc *__restrict__ pts, const Ctl *__restrict__ ctl, int mask, int want) {
   extern __shared__ float4 lsm4[];
   float2 *sm = reinterpret_cast<float2 *>(lsm4);
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(LB_THREADS_WIDE, S == 6 ? 3 : LB_MINBLOCKS_WID
   o.out_f32 = 1;
   o.canon = P.rev_half;
   o.par = (S - 1) & 1;
-  combine_block<REV, false, LB_THREADS_WIDE, VMAX>(P, o, mask, ErrWeights{}, sm);
+  combine_block<REV, false, stage_threads<S>(), VMAX>(P, o, mask, ErrWeights{}, sm);
   __syncthreads();  // the scatter-add's reads of the shared block are done
   stage_block<S, VMAX>(P, c, want, sm);
 }
@@ -644,7 +646,7 @@ static cudaError_t combine_stage_at(bool rev, bool vmax, dim3 g, cudaStream_t st
                                     const Ctl *c, int m, int want) {
   auto k = rev ? (vmax ? k_combine_stage<S, true, true> : k_combine_stage<S, true, false>)
                : (vmax ? k_combine_stage<S, false, true> : k_combine_stage<S, false, false>);
-  return launch_with_carveout(k, g, LB_THREADS_WIDE, LB_SMEM, st, cv, d_pts, c, m, want);
+  return launch_with_carveout(k, g, stage_threads<S>(), LB_SMEM, st, cv, d_pts, c, m, want);
 }
 
 int launch_combine_stage(const PointDesc *d_pts, Ctl *d_ctl, int s, bool rev, bool vmax, int mask, cudaStream_t st,
