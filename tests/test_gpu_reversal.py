@@ -240,3 +240,51 @@ def test_a_state_without_the_symmetry_switches_the_flows_to_every_transfer():
             dg, ds = gpu_rhs(ctx, 0.3, Va, sa)
             fg, fs = gpu_rhs(full, 0.3, Va, sa)
         assert np.array_equal(dg, fg) and np.array_equal(ds, fs)
+
+
+def test_observables_and_state_of_a_reduced_flow_agree():
+    """Under the reduction the seventh stage kernel writes the FP64 state's
+    canonical half only; frg_observables and frg_get_state fill in the other
+    half first: U_eff (the vertex at i1 = i2 = i3 = N/2, in the mirrored half)
+    equals the returned state's entry, with and without a get_state before."""
+    w = inputs.Workload("t", N=24, U=1.6, T=0.03, eps_d=-0.8 + 0.2)
+    with frg.Context([w], precision=frg.TF32X3) as ctx:
+        ctx.advance(5)
+        obs = ctx.observables(0)
+        g, _, _, _ = ctx.get_state(0)
+        obs2 = ctx.observables(0)
+    g = g.cpu().numpy()
+    h = w.N // 2
+    assert obs["U_eff"] == g[h, h, h] and obs2["U_eff"] == g[h, h, h]
+    assert np.array_equal(g, np.conj(g[::-1, ::-1, ::-1]))
+
+
+def test_a_batch_switching_to_every_transfer_keeps_the_other_points_whole():
+    """Two points flow under the reduction; an asymmetric state set on the
+    second switches the context to every transfer.  The first point continues
+    from its whole state (frg_set_state fills in the mirrored half of every
+    point first): close to the flow that takes its state at the switch into a
+    context computing every transfer (that context starts without the split
+    paths' tolerance floors of the error norm, so its steps differ slightly;
+    a stale half would be off by the vertex's whole change since the
+    start)."""
+    w0 = inputs.Workload("a", N=24, U=1.4, T=0.03, eps_d=-0.7 + 0.2)
+    w1 = inputs.Workload("b", N=24, U=1.2, T=0.04, eps_d=-0.6 + 0.1)
+    Va = inputs.random_vertex(w1.N, w1.U, seed=15, amp=0.1, crossing=False)
+    sa = inputs.random_sigma(w1.N, seed=16, amp=0.01)
+    with frg.Context([w0, w1], precision=frg.TF32X3) as ctx:
+        ctx.advance(6)
+        g0, s0, lam0, h0 = ctx.get_state(0)
+    with frg.Context([w0, w1], precision=frg.TF32X3) as ctx:
+        ctx.advance(6)  # no whole-state read before the switch
+        ctx.set_state(1, torch.from_numpy(Va).cuda(), torch.from_numpy(sa).cuda(), w1.Lambda0)
+        ctx.advance(5)
+        gb, sb, lamb, _ = ctx.get_state(0)
+    with frg.Context([w0], precision=frg.TF32X3, channel_mask=frg.CH_ALL | frg.NO_REVERSAL) as ref:
+        ref.set_state(0, g0, s0, lam0, h0)
+        ref.advance(5)
+        gr, sr, lamr, _ = ref.get_state(0)
+    eg = nrel(gb.cpu().numpy(), gr.cpu().numpy())
+    es = nrel(sb.cpu().numpy(), sr.cpu().numpy())
+    print("switch: vertex %.2e, self-energy %.2e, Lambda %.17g vs %.17g" % (eg, es, lamb, lamr))
+    assert abs(lamb - lamr) <= 1e-4 * lamr and eg < 1e-7 and es < 1e-4
